@@ -1,0 +1,328 @@
+"""Seeded synthetic NACA 0012 point clouds for q-LSKUM.
+
+This module builds inputs only: point coordinates, normals, point flags and
+connectivity. It holds none of the method's arithmetic (no stencil split, no
+least squares, no fluxes), so both the CPU oracle and the CUDA path can take
+their inputs from it.
+
+The paper's own clouds (an O-type distribution of 614,400 points with 1280
+points on the airfoil, and levels of 1M to 64M points; Sec. 4 and Sec. 5) are
+not published. These clouds take their shape instead:
+
+* W wall points on the analytic NACA 0012 contour (closed trailing edge,
+  half-thickness 0.6 (0.2969 sqrt(x) - 0.1260 x - 0.3516 x^2 + 0.2843 x^3
+  - 0.1036 x^4)), cosine chord spacing, counter-clockwise from the trailing
+  edge;
+* L layers offset with geometric growth along rays that start at each wall
+  point in the direction of its outward normal, smoothed around the contour
+  so that the trailing-edge corner does not fan out in a single column, the last layer on a far-field circle of radius 15 chords centred at
+  mid-chord (each normal ray is cut at that circle);
+* seeded uniform jitter of +-`jitter` of the local tangential/normal spacing on
+  interior points (wall points stay on the contour, far-field points on the
+  circle);
+* flags 0 interior, 1 wall, 2 far-field; wall points carry the contour's
+  outward normal, interior points the direction of their generating ray
+  (wall-aligned frames), far-field points the radial normal;
+* connectivity: the (at most) 25 nearest points within 1.8 x the local
+  spacing h = max(h_tangential, h_normal), always including the 3x3 block of
+  structured-grid neighbours, ordered by distance (ties by index).
+
+Point index of grid node (i, j) is j*W + i (layer-major) unless `shuffle`.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+FLAG_INTERIOR = 0
+FLAG_WALL = 1
+FLAG_FARFIELD = 2
+
+_CENTRE = (0.5, 0.0)
+_MAX_DEGREE = 25
+
+
+def _naca0012_half_thickness(x):
+    return 0.6 * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x**2
+                  + 0.2843 * x**3 - 0.1036 * x**4)
+
+
+def naca0012_wall(W: int):
+    """Wall points and outward unit normals, counter-clockwise from the TE.
+
+    The contour parameter is phi_k = 2 pi k / W, x = (1 + cos phi)/2 (cosine
+    spacing); the upper surface is phi in (0, pi), the lower one is its mirror
+    image, built by reflection so that the contour is exactly symmetric.
+    Returns (xw, yw, nxw, nyw) as float64 arrays of length W.
+    """
+    if W < 8 or W % 2:
+        raise ValueError("W must be even and >= 8")
+    half = W // 2
+    phi = 2.0 * np.pi * np.arange(half + 1) / W          # 0 .. pi (TE .. LE)
+    x = 0.5 * (1.0 + np.cos(phi))
+    x[0], x[half] = 1.0, 0.0
+    y = _naca0012_half_thickness(x)
+    y[0], y[half] = 0.0, 0.0
+    # Tangent d(x, y)/dphi on the upper surface. sqrt(x) = cos(phi/2) there,
+    # so d sqrt(x)/dphi = -sin(phi/2)/2 has no 0/0 at the leading edge.
+    dx = -0.5 * np.sin(phi)
+    dsqrt = -0.5 * np.sin(0.5 * phi)
+    dpoly = (-0.1260 - 2 * 0.3516 * x + 3 * 0.2843 * x**2 - 4 * 0.1036 * x**3) * dx
+    dy = 0.6 * (0.2969 * dsqrt + dpoly)
+    # Counter-clockwise traversal: outward normal = (dy, -dx)/|.|
+    nrm = np.hypot(dx, dy)
+    nrm[0] = 1.0                     # TE corner: replaced below
+    nx = dy / nrm
+    ny = -dx / nrm
+    nx[0], ny[0] = 1.0, 0.0          # trailing-edge corner: bisector
+    nx[half], ny[half] = -1.0, 0.0   # leading edge
+    xw = np.empty(W); yw = np.empty(W); nxw = np.empty(W); nyw = np.empty(W)
+    xw[:half + 1], yw[:half + 1], nxw[:half + 1], nyw[:half + 1] = x, y, nx, ny
+    lower = np.arange(half + 1, W)
+    mirror = W - lower
+    xw[lower], yw[lower] = x[mirror], -y[mirror]
+    nxw[lower], nyw[lower] = nx[mirror], -ny[mirror]
+    return xw, yw, nxw, nyw
+
+
+def _ray_lengths(xw, yw, nxw, nyw, radius):
+    """Distance t along each outward normal ray to the far-field circle."""
+    cx, cy = _CENTRE
+    ox, oy = xw - cx, yw - cy
+    b = nxw * ox + nyw * oy
+    c = ox * ox + oy * oy - radius * radius
+    return -b + np.sqrt(b * b - c)
+
+
+def _ray_directions(nxw, nyw, sweeps):
+    """Outward ray directions: the wall normals' angle, smoothed around the
+    closed contour by `sweeps` Jacobi sweeps of a (1/4, 1/2, 1/4) filter, so
+    that the 160-degree jump of the normal at the trailing-edge corner is
+    spread over a few dozen columns instead of one. The filter is symmetric,
+    so a mirror-symmetric contour keeps mirror-symmetric rays."""
+    th = np.unwrap(np.arctan2(nyw, nxw))
+    W = th.shape[0]
+    ext = th.copy()
+    for _ in range(sweeps):
+        left = np.roll(ext, 1)
+        right = np.roll(ext, -1)
+        left[0] -= 2.0 * np.pi      # periodic unwrap across the seam
+        right[W - 1] += 2.0 * np.pi
+        ext = 0.25 * left + 0.5 * ext + 0.25 * right
+    return np.cos(ext), np.sin(ext)
+
+
+def _growth_fractions(L, first_fraction):
+    """g_j, j = 0..L, geometric with g_0 = 0, g_L = 1 and g_1 ~ first_fraction."""
+    if first_fraction * L >= 1.0:
+        return np.arange(L + 1) / L
+    lo, hi = 1.0 + 1e-12, min(4.0, float(np.exp(600.0 / L)))
+    for _ in range(200):
+        r = 0.5 * (lo + hi)
+        g1 = (r - 1.0) / (r**L - 1.0)
+        if g1 > first_fraction:
+            lo = r
+        else:
+            hi = r
+    r = 0.5 * (lo + hi)
+    return (r ** np.arange(L + 1) - 1.0) / (r**L - 1.0)
+
+
+def _structured_block(W, L):
+    """(N, 8) int64 indices of the 3x3 grid block around each node, -1 if absent."""
+    i = np.tile(np.arange(W), L + 1)
+    j = np.repeat(np.arange(L + 1), W)
+    cols = []
+    for dj in (-1, 0, 1):
+        for di in (-1, 0, 1):
+            if di == 0 and dj == 0:
+                continue
+            jj = j + dj
+            ii = (i + di) % W
+            ok = (jj >= 0) & (jj <= L)
+            cols.append(np.where(ok, jj * W + ii, -1))
+    return np.stack(cols, axis=1)
+
+
+def _connectivity(x, y, h, block, radius_factor, max_degree, chunk=1 << 19):
+    from scipy.spatial import cKDTree
+
+    n = x.shape[0]
+    pts = np.stack([x, y], axis=1)
+    tree = cKDTree(pts)
+    deg = np.zeros(n, dtype=np.int64)
+    rows = np.empty((n, max_degree), dtype=np.int32)
+    kq = max_degree + 8
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        m = e - s
+        _, knn = tree.query(pts[s:e], k=min(kq, n), workers=-1)
+        knn = np.asarray(knn, dtype=np.int64).reshape(m, -1)
+        blk = block[s:e]
+        cand = np.concatenate([blk, knn], axis=1)
+        is_blk = np.zeros(cand.shape, dtype=bool)
+        is_blk[:, :blk.shape[1]] = True
+        me = np.arange(s, e)[:, None]
+        valid = (cand >= 0) & (cand < n) & (cand != me)
+        cs = np.where(valid, cand, 0)
+        d2 = (x[cs] - x[s:e, None]) ** 2 + (y[cs] - y[s:e, None]) ** 2
+        r2 = (radius_factor * h[s:e, None]) ** 2
+        valid &= is_blk | (d2 <= r2)
+        # de-duplicate: sort by index, keep the first of equal runs (block first)
+        key_idx = np.where(valid, cand, np.iinfo(np.int64).max)
+        order = np.lexsort((~is_blk, key_idx), axis=1)
+        cand = np.take_along_axis(cand, order, 1)
+        valid = np.take_along_axis(valid, order, 1)
+        is_blk = np.take_along_axis(is_blk, order, 1)
+        d2 = np.take_along_axis(d2, order, 1)
+        dup = np.zeros_like(valid)
+        dup[:, 1:] = (cand[:, 1:] == cand[:, :-1]) & valid[:, 1:] & valid[:, :-1]
+        valid &= ~dup
+        # rank non-block candidates by (distance, index); keep block + nearest
+        nblk = (valid & is_blk).sum(axis=1, keepdims=True)
+        big = np.inf
+        dnb = np.where(valid & ~is_blk, d2, big)
+        o2 = np.lexsort((np.where(valid & ~is_blk, cand, np.iinfo(np.int64).max), dnb), axis=1)
+        rank = np.empty_like(o2)
+        np.put_along_axis(rank, o2, np.arange(o2.shape[1])[None, :].repeat(m, 0), 1)
+        limit = max_degree - nblk
+        keep = valid & (is_blk | (rank < limit))
+        # if the cap cuts through a group of equal distances (mirror images of
+        # a point on the symmetry axis), drop the whole group
+        d_sorted = np.take_along_axis(dnb, o2, 1)
+        d_cut = np.take_along_axis(d_sorted, np.minimum(limit, d_sorted.shape[1] - 1), 1)
+        keep &= is_blk | (dnb != d_cut) | ~np.isfinite(d_cut)
+        # final order: by (distance, index)
+        dk = np.where(keep, d2, big)
+        ik = np.where(keep, cand, np.iinfo(np.int64).max)
+        o3 = np.lexsort((ik, dk), axis=1)
+        ck = np.take_along_axis(np.where(keep, cand, -1), o3, 1)[:, :max_degree]
+        dg = keep.sum(axis=1)
+        deg[s:e] = dg
+        rows[s:e] = ck[:, :max_degree].astype(np.int32)
+    offsets = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(deg, out=offsets[1:])
+    mask = np.arange(max_degree)[None, :] < deg[:, None]
+    idx = rows[mask]
+    return offsets.astype(np.int32), idx.astype(np.int32)
+
+
+def naca0012_cloud(W: int = 320, L: int = 30, seed: int = 2403_13287,
+                   jitter: float = 0.10, radius: float = 15.0,
+                   mirror: bool = False, shuffle: bool = False,
+                   radius_factor: float = 1.8, max_degree: int = _MAX_DEGREE,
+                   ray_smoothing: int | None = None):
+    """Build a synthetic NACA 0012 cloud of W*(L+1) points.
+
+    Returns a dict with float64 arrays x, y, nx, ny; int32 flags; int32 CSR
+    connectivity nbr_offsets (n+1) and nbr_idx (nnz); int32 wall_order (the
+    wall points counter-clockwise from the trailing edge); and the grid sizes.
+    `mirror` draws the jitter on the upper half and reflects it, so the cloud
+    is mirror-symmetric about y = 0 (points on the axis move along it only).
+    `shuffle` applies a seeded random permutation of the point order.
+    """
+    if L < 2:
+        raise ValueError("need L >= 2 layers")
+    if ray_smoothing is None:
+        ray_smoothing = max(8, W // 4)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xw, yw, nxw, nyw = naca0012_wall(W)
+    rxw, ryw = _ray_directions(nxw, nyw, ray_smoothing)
+    half = W // 2
+    lower = np.arange(half + 1, W)
+    rxw[lower], ryw[lower] = rxw[W - lower], -ryw[W - lower]   # exact symmetry
+    rxw[0], ryw[0], rxw[half], ryw[half] = 1.0, 0.0, -1.0, 0.0
+    t = _ray_lengths(xw, yw, rxw, ryw, radius)
+    seg = np.hypot(np.roll(xw, -1) - xw, np.roll(yw, -1) - yw)
+    mean_wall_spacing = seg.mean()
+    g = _growth_fractions(L, mean_wall_spacing / t.mean())
+    # nominal grid, layer-major (j, i)
+    X = xw[None, :] + (t[None, :] * g[:, None]) * rxw[None, :]
+    Y = yw[None, :] + (t[None, :] * g[:, None]) * ryw[None, :]
+    # the far-field layer sits exactly on the circle
+    fx, fy = xw + t * rxw - _CENTRE[0], yw + t * ryw - _CENTRE[1]
+    X[L] = _CENTRE[0] + radius * fx / np.hypot(fx, fy)
+    Y[L] = _CENTRE[1] + radius * fy / np.hypot(fx, fy)
+    if mirror:
+        half = W // 2
+        lower = np.arange(half + 1, W)
+        X[:, lower] = X[:, W - lower]
+        Y[:, lower] = -Y[:, W - lower]
+        Y[:, 0] = 0.0
+        Y[:, half] = 0.0
+    ht = 0.5 * (np.hypot(np.roll(X, -1, 1) - X, np.roll(Y, -1, 1) - Y)
+                + np.hypot(X - np.roll(X, 1, 1), Y - np.roll(Y, 1, 1)))
+    dn = np.hypot(np.diff(X, axis=0), np.diff(Y, axis=0))
+    hn = np.empty_like(X)
+    hn[0] = dn[0]
+    hn[L] = dn[L - 1]
+    hn[1:L] = 0.5 * (dn[:-1] + dn[1:])
+    # jitter (interior layers only)
+    txw, tyw = ryw, -rxw
+    a = rng.uniform(-1.0, 1.0, size=(L + 1, W))
+    b = rng.uniform(-1.0, 1.0, size=(L + 1, W))
+    if mirror:
+        half = W // 2
+        lower = np.arange(half + 1, W)
+        # reflection maps the tangent to minus the mirrored tangent and the
+        # normal to the mirrored normal
+        a[:, lower] = -a[:, W - lower]
+        b[:, lower] = b[:, W - lower]
+        a[:, 0] = 0.0      # TE axis: tangent is vertical, keep on axis
+        a[:, half] = 0.0   # LE axis
+    dX = jitter * (a * ht * txw[None, :] + b * hn * rxw[None, :])
+    dY = jitter * (a * ht * tyw[None, :] + b * hn * ryw[None, :])
+    dX[0] = dX[L] = 0.0
+    dY[0] = dY[L] = 0.0
+    X = X + dX
+    Y = Y + dY
+    if mirror:
+        half = W // 2
+        Y[:, 0] = 0.0
+        Y[:, half] = 0.0
+    n = W * (L + 1)
+    x = X.reshape(n).copy()
+    y = Y.reshape(n).copy()
+    nx = np.tile(rxw, L + 1)
+    ny = np.tile(ryw, L + 1)
+    nx[:W], ny[:W] = nxw, nyw
+    ffx = X[L] - _CENTRE[0]
+    ffy = Y[L] - _CENTRE[1]
+    ffr = np.hypot(ffx, ffy)
+    nx[L * W:] = ffx / ffr
+    ny[L * W:] = ffy / ffr
+    flags = np.zeros(n, dtype=np.int32)
+    flags[:W] = FLAG_WALL
+    flags[L * W:] = FLAG_FARFIELD
+    h = np.maximum(ht, hn).reshape(n)
+    offsets, idx = _connectivity(x, y, h, _structured_block(W, L), radius_factor, max_degree)
+    wall_order = np.arange(W, dtype=np.int32)
+    if shuffle:
+        perm = np.random.Generator(np.random.PCG64(seed + 1)).permutation(n)  # new -> old
+        inv = np.empty(n, dtype=np.int64)
+        inv[perm] = np.arange(n)                                              # old -> new
+        x, y, nx, ny, flags = x[perm], y[perm], nx[perm], ny[perm], flags[perm]
+        deg = np.diff(offsets.astype(np.int64))[perm]
+        new_off = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(deg, out=new_off[1:])
+        starts = offsets[:-1].astype(np.int64)[perm]
+        pos = np.repeat(starts - new_off[:-1], deg) + np.arange(new_off[-1])
+        idx = inv[idx[pos]].astype(np.int32)
+        offsets = new_off.astype(np.int32)
+        wall_order = inv[wall_order].astype(np.int32)
+    return {
+        "n": n, "W": W, "L": L,
+        "x": np.ascontiguousarray(x), "y": np.ascontiguousarray(y),
+        "nx": np.ascontiguousarray(nx), "ny": np.ascontiguousarray(ny),
+        "flags": flags, "nbr_offsets": offsets, "nbr_idx": idx,
+        "wall_order": wall_order,
+    }
+
+
+# Named workloads: (W, L). Point counts are W*(L+1).
+CLOUDS = {
+    "naca0012_10k": (320, 30),        # 9,920 points
+    "naca0012_160k": (1280, 124),     # 160,000 points
+    "naca0012_640k": (2560, 249),     # 640,000 points
+    "naca0012_2p5m": (2560, 975),     # 2,498,560 points
+    "naca0012_10m": (5120, 1952),     # 9,999,360 points
+}
