@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Throughput of the q-LSKUM hot path on GB300: point-iterations per second.
+
+One step = one pseudo-time iteration of Algorithm 1 over the whole cloud
+(second-order q-LSKUM, 3 inner iterations, RK4 = 4 residual evaluations, each
+q-derivatives + fused flux residual/update) on a seeded synthetic NACA 0012
+cloud of 2,498,560 points at M = 1.2, alpha = 0. Inputs are resident in HBM
+when the timed region starts; the working set (~3 GB) is far larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU, torchrun), weak scaling.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "q-LSKUM point-iterations/s at 2.5M pts (FP64 vs mixed); % of HBM roofline"
+UNIT = "point-iterations/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="naca0012_2p5m")
+    ap.add_argument("--order", type=int, default=2)
+    ap.add_argument("--inner", type=int, default=3)
+    ap.add_argument("--scheme", choices=["euler", "rk4"], default="rk4")
+    ap.add_argument("--mach", type=float, default=1.2)
+    ap.add_argument("--aoa", type=float, default=0.0)
+    ap.add_argument("--cfl", type=float, default=0.2)
+    ap.add_argument("--limiter", type=float, default=1.0, help="Venkatakrishnan K (0: none)")
+    ap.add_argument("--precision", choices=["fp64"], default="fp64")
+    ap.add_argument("--reorder", type=int, default=1)
+    ap.add_argument("--shuffle", type=int, default=1, help="present the cloud in random point order")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        if not self.rows:
+            return None
+        sm = sorted(float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit())
+        smax = max((float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def algorithmic_bytes_per_point(kernel, dbar, order, scheme, stage_avg=True):
+    """Bytes each array contributes once per launch, per point (FP64 layout):
+    q 32, q-derivatives 64, coordinates 16, normals 16, flag 1, dmin 8, CSR
+    offset 4, and per edge: index 4, mask 1, LS weights 16 (fused kernel:
+    flux weights 16). Neighbour gathers are assumed served from cache."""
+    if kernel == "flux":
+        b = 32 + 16 + 16 + 1 + 4 + dbar * (4 + 1 + 16)       # q, xy, nrm, flag, off, edges
+        if order == 2:
+            b += 64                                           # own q-derivatives
+        b += 32 + 32 + 32                                     # U^n read, U_out and q_out written
+        if scheme == "rk4":
+            # dt (+dmin) at stage 0, acc written at 0-2, read at 1-3
+            b += (8 + 8 + 3 * 8 + 3 * 32 + 3 * 32) / 4.0 if stage_avg else 0
+        else:
+            b += 16
+        return b
+    if kernel == "qgrad_first":
+        return 32 + 4 + dbar * (4 + 16) + 64
+    if kernel == "qgrad_inner":
+        return 32 + 64 + 16 + 4 + dbar * (4 + 16) + 64
+    raise ValueError(kernel)
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on the host cores
+# ----------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_2403_13287_gb300.cloudgen import CLOUDS, naca0012_cloud
+
+    W, L = CLOUDS[args.workload]
+    cloud = naca0012_cloud(W, L, shuffle=bool(args.shuffle))
+    n = cloud["n"]
+    mask = oracle.split_stencils(cloud)
+    U = oracle.freestream_state(n, args.mach, args.aoa)
+    evals = 4 if args.scheme == "rk4" else 1
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.residual(cloud, mask, U, order=args.order, inner=args.inner, limiter=args.limiter)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    t_res = sum(times) / len(times)
+    value = n / (evals * t_res)
+    sample = ("one residual evaluation (q_variables, q_derivatives with %d inner iterations, "
+              "flux_residual) over all %d points per step, scaled by 1/%d for one %s iteration"
+              % (args.inner, n, evals, args.scheme.upper()))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_res * evals, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": args.workload, "points": n, "order": args.order,
+                   "inner_iters": args.inner, "limiter_K": args.limiter, "scheme": args.scheme, "mach": args.mach,
+                   "aoa_deg": args.aoa},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(cloud, mask, args):
+    """The oracle as it stands, on one host core: one residual evaluation of
+    the full cloud (about 10-30 s), scaled to an iteration."""
+    import oracle
+    U = oracle.freestream_state(cloud["n"], args.mach, args.aoa)
+    t0 = time.perf_counter()
+    oracle.residual(cloud, mask, U, order=args.order, inner=args.inner, limiter=args.limiter)
+    t = time.perf_counter() - t0
+    evals = 4 if args.scheme == "rk4" else 1
+    return {"value": cloud["n"] / (evals * t), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one residual evaluation of all %d points (%.1f s), scaled by 1/%d for one %s "
+                      "iteration" % (cloud["n"], t, evals, args.scheme.upper())}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2403_13287_gb300 import lskum
+    from paper_2403_13287_gb300.cloudgen import CLOUDS, naca0012_cloud
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    W, L = CLOUDS[args.workload]
+    cloud = naca0012_cloud(W, L, shuffle=bool(args.shuffle))
+    n = cloud["n"]
+    dbar = cloud["nbr_offsets"][-1] / n
+    scheme = 1 if args.scheme == "rk4" else 0
+    stream = torch.cuda.current_stream()
+    solver = lskum.Solver(cloud, order=args.order, inner_iters=args.inner, time_scheme=scheme,
+                          cfl=args.cfl, mach=args.mach, aoa_deg=args.aoa, reorder=args.reorder,
+                          limiter_K=args.limiter, stream=stream.cuda_stream)
+
+    # warm-up (also moves the state away from the uniform free stream)
+    solver.step(args.warmup, history=False)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    solver.profile(True)
+    launches0 = solver.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    solver.step(args.steps, history=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = solver.launch_count() - launches0
+    flux_ms, flux_n = solver.kernel_time(lskum.LSKUM_KERNEL_FLUX)
+    qg_ms, qg_n = solver.kernel_time(lskum.LSKUM_KERNEL_QGRAD)
+    solver.profile(False)
+    clocks = sampler.stop() if sampler else None
+
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * args.steps / (ms / 1e3)
+
+    # end to end through the public API with host buffers: per step the
+    # state goes host -> device, one iteration runs, the state and the
+    # residue come back
+    Uh = torch.empty((4, n), dtype=torch.float64, pin_memory=True).numpy()
+    Uh[...] = solver.get_state()
+    e2e_steps = max(1, args.steps)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_state(Uh)
+        solver.step(1, history=True)
+        solver.get_state(out=Uh)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * n * e2e_steps / e2e_s
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_src = measured_peaks()
+    flux_avg_s = (flux_ms / max(flux_n, 1)) / 1e3
+    fb = algorithmic_bytes_per_point("flux", dbar, args.order, args.scheme) * n
+    achieved_gbs = fb / flux_avg_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "points": n, "mean_degree": round(float(dbar), 3),
+                   "order": args.order, "inner_iters": args.inner, "scheme": args.scheme,
+                   "mach": args.mach, "aoa_deg": args.aoa, "cfl": args.cfl, "limiter_K": args.limiter,
+                   "precision": args.precision, "reorder": "morton" if args.reorder else "none",
+                   "input_order": "shuffled" if args.shuffle else "structured",
+                   "l2": "inputs larger than L2 (working set ~%.1f GB)" % (
+                       (n * 380 + cloud["nbr_offsets"][-1] * 37) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "kernel": "k_flux_update", "achieved": achieved_gbs,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
+                     "traffic": None, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": fb, "avg_launch_ms": flux_avg_s * 1e3},
+        "kernels": {"k_flux_update": {"launches": flux_n, "total_ms": flux_ms},
+                    "k_qgrad": {"launches": qg_n, "total_ms": qg_ms}},
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n * 8,
+                "d2h_bytes_per_step": 4 * n * 8 + 8},
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        m = oracle.split_stencils(cloud)
+        line["cpu_baseline"] = cpu_baseline_sample(cloud, m, args)
+    print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.gpus != world and world > 1:
+        print("warning: --gpus %d but WORLD_SIZE %d" % (args.gpus, world), file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

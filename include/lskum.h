@@ -1,0 +1,192 @@
+/*
+ * lskum.h - C ABI of the GB300 (sm_103a) q-LSKUM hot path.
+ *
+ * q-LSKUM (arXiv 2403.13287, Sec. 2 and Algorithm 1): meshfree least-squares
+ * kinetic upwind method for the 2D Euler equations on a point cloud. Per
+ * pseudo-time iteration and per point: q-variables (E13), least-squares
+ * q-derivatives with defect-correction inner iterations (E14, E15), the sum
+ * of kinetic split-flux derivatives over the x+-/y+- sub-stencils (E10-E12),
+ * a local time step and the state update (E16; or RK4).
+ *
+ * Conventions shared by every call
+ * - Points are numbered 0..n-1 in the caller's ("input") order; every array
+ *   the caller sees is in input order. The library may renumber points
+ *   internally (lskum_config.reorder) and keeps the permutation to itself.
+ * - Arrays of the four conserved variables U = [rho, rho u, rho v, rho E]
+ *   (and of residuals, q-derivatives) are component-major: A[k*n + p].
+ * - "device" pointers are CUDA device memory owned by the caller (e.g. a
+ *   contiguous torch tensor's data_ptr()); they are used on the context's
+ *   stream, asynchronously, unless a call says it synchronises. "host"
+ *   pointers are ordinary CPU memory.
+ * - Host input arrays passed to lskum_create are copied; the caller keeps
+ *   ownership. The context owns all of its device workspace.
+ * - Every call returns an lskum_status; the library never aborts or exits.
+ *   After a failure lskum_last_error() describes it (per context).
+ * - Calls on one context are not thread-safe; different contexts are
+ *   independent.
+ */
+#ifndef LSKUM_H
+#define LSKUM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LSKUM_OK = 0,
+    LSKUM_ERR_ARG = 1,                /* bad argument (null pointer, size, config value) */
+    LSKUM_ERR_CONNECTIVITY = 2,       /* CSR malformed: index out of range, self loop, duplicate, degree > 25 */
+    LSKUM_ERR_DEGENERATE_STENCIL = 3, /* a needed (sub-)stencil has a singular 2x2 least-squares matrix */
+    LSKUM_ERR_CUDA = 4,               /* a CUDA runtime call failed */
+    LSKUM_ERR_OOM = 5,                /* device allocation failed */
+    LSKUM_ERR_NONPHYSICAL = 6,        /* a state with rho <= 0, p <= 0 or a non-finite value appeared */
+    LSKUM_ERR_TIMEOUT = 7             /* a bounded device-side wait ran out */
+} lskum_status;
+
+/* point flags */
+#define LSKUM_POINT_INTERIOR 0
+#define LSKUM_POINT_WALL 1     /* on the body; normal points into the fluid */
+#define LSKUM_POINT_FARFIELD 2 /* outer boundary; held at the free stream */
+
+/* sub-stencil bits of lskum_get_stencil_masks (Sec. 2, after E12), measured in
+ * the point's frame: tangent t = (ny, -nx), normal n = (nx, ny) */
+#define LSKUM_MASK_XPOS 1u /* ds < 0 : upwind points of Gx+ */
+#define LSKUM_MASK_XNEG 2u /* ds > 0 : upwind points of Gx- */
+#define LSKUM_MASK_YPOS 4u /* dn < 0 : upwind points of Gy+ */
+#define LSKUM_MASK_YNEG 8u /* dn > 0 : upwind points of Gy- */
+
+#define LSKUM_MAX_DEGREE 25
+
+typedef struct {
+    int order;        /* 1: first-order LSKUM (dG uses q); 2: q-LSKUM (dG uses q~ of E14) */
+    int inner_iters;  /* inner iterations of E15 after the first-order solve (paper: 3) */
+    int time_scheme;  /* 0: forward Euler with local dt (E16); 1: classical RK4 with dt frozen per iteration */
+    double cfl;       /* local time step dt = cfl * min|P_i - P_0| / (|u| + 3 sqrt(p/rho)) */
+    double mach;      /* free stream: rho = 1, p = 1/gamma, |u| = mach */
+    double aoa_deg;   /* angle of attack of the free stream, degrees */
+    double gamma;     /* ratio of specific heats (paper: 1.4) */
+    int precision;    /* 0: FP64 throughout */
+    int reorder;      /* 0: keep the input order; 1: Morton (Z-order) renumbering for gather locality */
+    double limiter_K; /* order 2 only. 0: no limiter (the paper's scheme). > 0: Venkatakrishnan's
+                       * limiter (J. Comput. Phys. 118, 1995; not in the paper) scales each
+                       * component of grad q at P_0 by phi = min(1, f(D+, d+), f(D-, -d+)),
+                       * f(D, d) = (D^2 + e^2 + 2Dd)/(D^2 + 2d^2 + Dd + e^2), d+ the largest
+                       * |(P_i - P_0).grad q|/2, D+- = max/min of q over P_0 and N(P_0) minus
+                       * q_0, e^2 = (K h)^3, h the nearest-neighbour distance */
+} lskum_config;
+
+typedef struct lskum_ctx lskum_ctx;
+
+/*
+ * Build a solver context on the current CUDA device (Sec. 3: preprocessor()).
+ *   n                      number of points (>= 1, < 2^31)
+ *   x, y, nx, ny           host float64[n]: coordinates and unit normals
+ *   flags                  host int32[n]: LSKUM_POINT_*
+ *   nbr_offsets            host int32[n+1]: CSR row starts, nbr_offsets[0] = 0
+ *   nbr_idx                host int32[nbr_offsets[n]]: neighbour lists N(P_0); the
+ *                          order within a row is the summation order of every
+ *                          least-squares sum at that point
+ *   n_wall, wall_order     host int32[n_wall]: wall points in contour order
+ *                          (closed contour; used by lskum_forces). n_wall may be 0.
+ *   cfg                    host; copied
+ *   cuda_stream            cudaStream_t to run on, or NULL for the legacy default stream
+ *   out                    receives the context (NULL on failure)
+ * Validates the CSR (LSKUM_ERR_CONNECTIVITY) and every needed stencil: the full
+ * stencil at every point, N_x+, N_x-, N_y+, N_y- at interior points and N_x+,
+ * N_x-, N_y- at wall points must have det > 1e-10 * Sxx * Syy
+ * (LSKUM_ERR_DEGENERATE_STENCIL; the message names the first bad point).
+ * Initialises the state to the free stream. Synchronises.
+ */
+lskum_status lskum_create(int64_t n, const double *x, const double *y, const double *nx,
+                          const double *ny, const int32_t *flags, const int32_t *nbr_offsets,
+                          const int32_t *nbr_idx, int64_t n_wall, const int32_t *wall_order,
+                          const lskum_config *cfg, void *cuda_stream, lskum_ctx **out);
+
+/* Free everything the context owns. NULL is allowed. */
+void lskum_destroy(lskum_ctx *ctx);
+
+/* Last error message of this context ("" if none); valid until the next call on it. */
+const char *lskum_last_error(const lskum_ctx *ctx);
+
+/*
+ * Run n_iters pseudo-time iterations of Algorithm 1 on the context's state:
+ * per iteration q_variables, q_derivatives (order 2), flux_residual, timestep
+ * and state_update (forward Euler, E16, or RK4), then residue().
+ *   res_history  host float64[n_iters] or NULL: residue of each iteration,
+ *                sqrt(sum_p R_rho(U^n)_p^2) / n
+ * Wall points lose their normal momentum after every update; far-field points
+ * are held at the free stream. Synchronises once at the end. On
+ * LSKUM_ERR_NONPHYSICAL the state is rolled back to its value at entry.
+ */
+lskum_status lskum_step(lskum_ctx *ctx, int n_iters, double *res_history);
+
+/*
+ * Residual R(U) = dGx+/dx + dGx-/dx + dGy+/dy + dGy-/dy of E10 (q~ of E14 for
+ * order 2), momentum in global (x, y) components; far-field points get 0.
+ *   U  device float64[4*n] in input order, or NULL for the context's state
+ *   R  device float64[4*n] in input order (written)
+ * Does not change the context's state (its scratch buffers are reused).
+ */
+lskum_status lskum_residual(lskum_ctx *ctx, const double *U, double *R);
+
+/*
+ * q-derivatives of E15 (global x, y frame) after the configured inner
+ * iterations (order 2) or the first-order solve (order 1), for state U.
+ *   U       device float64[4*n] or NULL (context state)
+ *   qx, qy  device float64[4*n], written
+ */
+lskum_status lskum_q_derivatives(lskum_ctx *ctx, const double *U, double *qx, double *qy);
+
+/* Local time step of every point for state U (device [4*n] or NULL) into dt (device float64[n]). */
+lskum_status lskum_timestep(lskum_ctx *ctx, const double *U, double *dt);
+
+/*
+ * Lift and drag of the current state: Cp_i = (p_i - p_inf) / (rho_inf |u_inf|^2 / 2)
+ * at the wall points in contour order, c = -sum_i Cp_i n_i ds_i with
+ * ds_i = (|P_{i+1} - P_i| + |P_i - P_{i-1}|) / 2, Cl = c_y cos a - c_x sin a,
+ * Cd = c_x cos a + c_y sin a.
+ *   cl, cd  host double*, written
+ *   cp      host float64[n_wall] or NULL, in wall_order order
+ * Synchronises.
+ */
+lskum_status lskum_forces(lskum_ctx *ctx, double *cl, double *cd, double *cp);
+
+/* Copy the state out of / into the context. U is float64[4*n] in input order,
+ * host memory if on_host != 0 else device memory. set_state synchronises for
+ * host input; q-variables are refreshed from the new state. */
+lskum_status lskum_get_state(lskum_ctx *ctx, double *U, int on_host);
+lskum_status lskum_set_state(lskum_ctx *ctx, const double *U, int on_host);
+
+/* Sub-stencil masks computed at create, one byte per CSR entry of the input
+ * connectivity (LSKUM_MASK_* bits), written to host uint8[nnz]. Synchronises. */
+lskum_status lskum_get_stencil_masks(lskum_ctx *ctx, uint8_t *mask);
+
+/* Internal numbering: perm[new] = input index of internal point `new`
+ * (host int32[n]). Identity when reorder = 0. Synchronises. */
+lskum_status lskum_get_permutation(lskum_ctx *ctx, int32_t *perm);
+
+/* Number of kernel launches the library has issued on this context so far. */
+int64_t lskum_launch_count(const lskum_ctx *ctx);
+
+/* Kernel classes for lskum_kernel_time */
+#define LSKUM_KERNEL_FLUX 0  /* fused flux residual + state update */
+#define LSKUM_KERNEL_QGRAD 1 /* one least-squares q-derivative pass */
+#define LSKUM_KERNEL_CLASSES 2
+
+/*
+ * Per-kernel timing for throughput reports: while enabled, every launch of a
+ * timed kernel class is bracketed by CUDA events recorded on the context's
+ * stream. lskum_profile(ctx, 1) enables and clears the record, (ctx, 0)
+ * disables it. lskum_kernel_time synchronises and returns the summed event
+ * time (milliseconds) and launch count of one class since it was enabled.
+ */
+lskum_status lskum_profile(lskum_ctx *ctx, int enable);
+lskum_status lskum_kernel_time(lskum_ctx *ctx, int kernel_class, double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSKUM_H */

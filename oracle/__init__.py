@@ -72,9 +72,10 @@ def lib():
         L.orc_residue.restype = _d
         L.orc_euler_step.argtypes = [_i64, _p, _p, _p, _p, _p, _p, RESIDUAL_FN, _p, _p]
         L.orc_rk4_step.argtypes = [_i64, _p, _p, _p, _p, _p, _p, RESIDUAL_FN, _p, _p]
-        L.orc_residual.argtypes = [_i64, _d] + [_p] * 8 + [_int, _int] + [_p] * 5
+        L.orc_residual.argtypes = [_i64, _d] + [_p] * 8 + [_int, _int, _d] + [_p] * 5
+        L.orc_limit_gradients.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _p, _p]
         L.orc_forces.argtypes = [_i64, _d, _d, _d, _p, _p, _p, _p, _p, _i64, _p, _p, _p, _p]
-        L.orc_solve.argtypes = ([_i64, _d] + [_p] * 8 + [_int, _int, _int, _d, _d, _d, _int, _p, _p])
+        L.orc_solve.argtypes = ([_i64, _d] + [_p] * 8 + [_int, _int, _d, _int, _d, _d, _d, _int, _p, _p])
     return _lib
 
 
@@ -164,6 +165,17 @@ def q_derivatives_pass(cloud, q, qx_old=None, qy_old=None):
     return qx, qy
 
 
+def limit_gradients(cloud, q, qx, qy, K):
+    """Venkatakrishnan-limited copies of the gradients (qx, qy) for q."""
+    q = _f64(q)
+    gx = _f64(qx).copy()
+    gy = _f64(qy).copy()
+    _check(lib().orc_limit_gradients(cloud["n"], _ptr(_f64(cloud["x"])), _ptr(_f64(cloud["y"])),
+                                     _ptr(_i32(cloud["nbr_offsets"])), _ptr(_i32(cloud["nbr_idx"])),
+                                     _ptr(q), float(K), _ptr(gx), _ptr(gy)), "limit_gradients")
+    return gx, gy
+
+
 def flux_residual(cloud, mask, q, qx, qy, order=2, gamma=1.4, want_scale=False):
     n = cloud["n"]
     q = _f64(q)
@@ -181,7 +193,8 @@ def flux_residual(cloud, mask, q, qx, qy, order=2, gamma=1.4, want_scale=False):
     return (R, sc) if want_scale else R
 
 
-def residual(cloud, mask, U, order=2, inner=3, gamma=1.4, want_scale=False, want_grad=False):
+def residual(cloud, mask, U, order=2, inner=3, gamma=1.4, want_scale=False, want_grad=False,
+             limiter=0.0):
     """R(U) of the whole scheme; optional error scale and q-derivatives."""
     n = cloud["n"]
     U = _f64(U)
@@ -194,7 +207,8 @@ def residual(cloud, mask, U, order=2, inner=3, gamma=1.4, want_scale=False, want
                               _ptr(_i32(cloud["flags"])), _ptr(_i32(cloud["nbr_offsets"])),
                               _ptr(_i32(cloud["nbr_idx"])),
                               _ptr(np.ascontiguousarray(mask, dtype=np.uint8)),
-                              order, inner, _ptr(U), _ptr(R), _ptr(sc), _ptr(qx), _ptr(qy)),
+                              order, inner, float(limiter), _ptr(U), _ptr(R), _ptr(sc), _ptr(qx),
+                              _ptr(qy)),
            "residual")
     out = [R]
     if want_scale:
@@ -270,7 +284,7 @@ def forces(cloud, U, mach, aoa_deg, gamma=1.4):
 
 
 def solve(cloud, mask, U0, n_iters, order=2, inner=3, scheme=1, cfl=0.2, mach=0.63,
-          aoa_deg=2.0, gamma=1.4):
+          aoa_deg=2.0, gamma=1.4, limiter=0.0):
     """Algorithm 1 for n_iters iterations; returns (U, residue history)."""
     U = _f64(U0).copy()
     hist = np.zeros(n_iters)
@@ -279,6 +293,7 @@ def solve(cloud, mask, U0, n_iters, order=2, inner=3, scheme=1, cfl=0.2, mach=0.
                            _ptr(_i32(cloud["flags"])), _ptr(_i32(cloud["nbr_offsets"])),
                            _ptr(_i32(cloud["nbr_idx"])),
                            _ptr(np.ascontiguousarray(mask, dtype=np.uint8)),
-                           order, inner, scheme, cfl, mach, aoa_deg, n_iters, _ptr(U), _ptr(hist)),
+                           order, inner, float(limiter), scheme, cfl, mach, aoa_deg, n_iters,
+                           _ptr(U), _ptr(hist)),
            "solve")
     return U, hist

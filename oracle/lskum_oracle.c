@@ -249,6 +249,61 @@ int orc_q_derivatives(int64_t n, const double *x, const double *y,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Limiter (not in the paper; optional reading). The reconstruction of E14  */
+/* moves q from P_0 by d = -1/2 dx_i.grad q_0 (as q~_0) and by +1/2 dx_i.   */
+/* grad q_0 (when P_0 is the neighbour P_i of another point), for every     */
+/* neighbour. Venkatakrishnan's limiter (J. Comput. Phys. 118, 1995)        */
+/* scales each component's gradient at P_0 by                               */
+/*   phi = min(1, min over all such d of f(d)),                             */
+/*   f(d) = (D^2 + eps^2 + 2 D d) / (D^2 + 2 d^2 + D d + eps^2), d != 0,    */
+/* with D = max(q over P_0 and N(P_0)) - q_0 for d > 0, min(...) - q_0 for  */
+/* d < 0, and eps^2 = (K h)^3, h the distance to the nearest neighbour.     */
+/* ------------------------------------------------------------------------ */
+static double venkat(double D, double d, double eps2)
+{
+    return (D * D + eps2 + 2.0 * D * d) / (D * D + 2.0 * d * d + D * d + eps2);
+}
+
+int orc_limit_gradients(int64_t n, const double *x, const double *y, const int32_t *off,
+                        const int32_t *idx, const double *q, double K, double *qx, double *qy)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        double h = INFINITY;
+        for (int64_t e = off[p]; e < off[p + 1]; ++e) {
+            int64_t i = idx[e];
+            double d = sqrt((x[i] - x[p]) * (x[i] - x[p]) + (y[i] - y[p]) * (y[i] - y[p]));
+            if (d < h) h = d;
+        }
+        double eps2 = (K * h) * (K * h) * (K * h);
+        for (int k = 0; k < 4; ++k) {
+            double q0 = q[k * n + p], qmax = q0, qmin = q0;
+            for (int64_t e = off[p]; e < off[p + 1]; ++e) {
+                double qi = q[k * n + idx[e]];
+                if (qi > qmax) qmax = qi;
+                if (qi < qmin) qmin = qi;
+            }
+            double phi = 1.0;
+            for (int64_t e = off[p]; e < off[p + 1]; ++e) {
+                int64_t i = idx[e];
+                double dx = x[i] - x[p];
+                double dy = y[i] - y[p];
+                double half = 0.5 * (dx * qx[k * n + p] + dy * qy[k * n + p]);
+                for (int sgn = -1; sgn <= 1; sgn += 2) {
+                    double d = sgn * half;
+                    double f = 1.0;
+                    if (d > 0.0) f = venkat(qmax - q0, d, eps2);
+                    else if (d < 0.0) f = venkat(qmin - q0, d, eps2);
+                    if (f < phi) phi = f;
+                }
+            }
+            qx[k * n + p] *= phi;
+            qy[k * n + p] *= phi;
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* flux_residual(): E10 with E11/E12 and the q~ of E14.                     */
 /* At point P_0 with frame (t, n), for each neighbour P_i:                  */
 /*   q~_i = q_i - 1/2 (dx_i qx_i + dy_i qy_i),                              */
@@ -530,6 +585,7 @@ typedef struct {
     const int32_t *flags, *off, *idx;
     const uint8_t *mask;
     int order, inner;
+    double limiter_K; /* > 0: Venkatakrishnan limiter with this K */
     double *q, *qx, *qy;
 } orc_scheme;
 
@@ -541,6 +597,8 @@ static int scheme_residual(const double *U, double *R, void *user)
     if (s->order == 2) {
         rc = orc_q_derivatives(s->n, s->x, s->y, s->off, s->idx, s->q, s->inner, s->qx, s->qy);
         if (rc) return rc;
+        if (s->limiter_K > 0.0)
+            orc_limit_gradients(s->n, s->x, s->y, s->off, s->idx, s->q, s->limiter_K, s->qx, s->qy);
     }
     return orc_flux_residual(s->n, s->gamma, s->x, s->y, s->nx, s->ny, s->flags, s->off,
                              s->idx, s->mask, s->q, s->qx, s->qy, s->order, R, NULL);
@@ -550,8 +608,8 @@ static int scheme_residual(const double *U, double *R, void *user)
 int orc_residual(int64_t n, double gamma, const double *x, const double *y,
                  const double *nx, const double *ny, const int32_t *flags,
                  const int32_t *off, const int32_t *idx, const uint8_t *mask,
-                 int order, int inner, const double *U, double *R, double *scale,
-                 double *qx_out, double *qy_out)
+                 int order, int inner, double limiter_K, const double *U, double *R,
+                 double *scale, double *qx_out, double *qy_out)
 {
     size_t bytes = (size_t)4 * n * sizeof(double);
     double *q = (double *)malloc(bytes), *qx = (double *)calloc(4 * (size_t)n, sizeof(double));
@@ -563,6 +621,7 @@ int orc_residual(int64_t n, double gamma, const double *x, const double *y,
     if (order == 2) {
         rc = orc_q_derivatives(n, x, y, off, idx, q, inner, qx, qy);
         if (rc) goto done;
+        if (limiter_K > 0.0) orc_limit_gradients(n, x, y, off, idx, q, limiter_K, qx, qy);
     }
     rc = orc_flux_residual(n, gamma, x, y, nx, ny, flags, off, idx, mask, q, qx, qy, order, R, scale);
     if (qx_out) memcpy(qx_out, qx, bytes);
@@ -617,14 +676,14 @@ int orc_forces(int64_t n, double gamma, double mach, double aoa_deg, const doubl
 int orc_solve(int64_t n, double gamma, const double *x, const double *y,
               const double *nx, const double *ny, const int32_t *flags,
               const int32_t *off, const int32_t *idx, const uint8_t *mask,
-              int order, int inner, int scheme, double cfl, double mach, double aoa_deg,
-              int n_iters, double *U, double *res_history)
+              int order, int inner, double limiter_K, int scheme, double cfl, double mach,
+              double aoa_deg, int n_iters, double *U, double *res_history)
 {
     size_t bytes = (size_t)4 * n * sizeof(double);
     orc_scheme s;
     s.n = n; s.gamma = gamma; s.x = x; s.y = y; s.nx = nx; s.ny = ny;
     s.flags = flags; s.off = off; s.idx = idx; s.mask = mask;
-    s.order = order; s.inner = inner;
+    s.order = order; s.inner = inner; s.limiter_K = limiter_K;
     s.q = (double *)malloc(bytes);
     s.qx = (double *)calloc(4 * (size_t)n, sizeof(double));
     s.qy = (double *)calloc(4 * (size_t)n, sizeof(double));

@@ -23,9 +23,13 @@ not published. These clouds take their shape instead:
 * flags 0 interior, 1 wall, 2 far-field; wall points carry the contour's
   outward normal, interior points the direction of their generating ray
   (wall-aligned frames), far-field points the radial normal;
-* connectivity: the (at most) 25 nearest points within 1.8 x the local
-  spacing h = max(h_tangential, h_normal), always including the 3x3 block of
-  structured-grid neighbours, ordered by distance (ties by index).
+* connectivity: the points within 1.8 x the local spacing, measured per
+  direction in the point's frame ((dt/h_t)^2 + (dn/h_n)^2 <= 1.8^2, with h_t,
+  h_n the local tangential and normal grid spacings), searched among the
+  7x7 block of grid neighbours, always including the 3x3 block; then each
+  half-plane of the point's frame (the body side of wall points excepted)
+  is topped up to two clearly-inside neighbours, nearest first; at most 25,
+  ordered by that distance (ties by index).
 
 Point index of grid node (i, j) is j*W + i (layer-major) unless `shuffle`.
 """
@@ -127,83 +131,85 @@ def _growth_fractions(L, first_fraction):
     return (r ** np.arange(L + 1) - 1.0) / (r**L - 1.0)
 
 
-def _structured_block(W, L):
-    """(N, 8) int64 indices of the 3x3 grid block around each node, -1 if absent."""
-    i = np.tile(np.arange(W), L + 1)
-    j = np.repeat(np.arange(L + 1), W)
-    cols = []
-    for dj in (-1, 0, 1):
-        for di in (-1, 0, 1):
-            if di == 0 and dj == 0:
-                continue
-            jj = j + dj
-            ii = (i + di) % W
-            ok = (jj >= 0) & (jj <= L)
-            cols.append(np.where(ok, jj * W + ii, -1))
-    return np.stack(cols, axis=1)
+def _connectivity(x, y, W, L, flags, fnx, fny, ht, hn, radius_factor, max_degree, reach=3,
+                  chunk=1 << 19):
+    """CSR rows from grid candidates (i + di, j + dj), |di|, |dj| <= reach.
 
-
-def _connectivity(x, y, h, block, radius_factor, max_degree, chunk=1 << 19):
-    from scipy.spatial import cKDTree
-
-    n = x.shape[0]
-    pts = np.stack([x, y], axis=1)
-    tree = cKDTree(pts)
+    Distances are measured in the point's frame (tangent (ny, -nx), normal
+    (nx, ny)) in units of its local tangential and normal spacings:
+    d^2 = (dt/h_t)^2 + (dn/h_n)^2. A candidate is kept if d <= radius_factor
+    or it is in the 3x3 block of grid neighbours. Quadrant balance: each
+    half-plane dt < 0, dt > 0, dn < 0, dn > 0 (dn < 0 not for wall points,
+    which have the body there) then receives the nearest further candidates
+    lying clearly inside it (|component| >= 0.05 |offset|) until it holds
+    two. Rows are ordered by d, ties by index, at most max_degree entries.
+    """
+    n = W * (L + 1)
+    offs = [(di, dj) for dj in range(-reach, reach + 1) for di in range(-reach, reach + 1)
+            if di or dj]
+    D = len(offs)
     deg = np.zeros(n, dtype=np.int64)
-    rows = np.empty((n, max_degree), dtype=np.int32)
-    kq = max_degree + 8
+    rows = np.full((n, max_degree), -1, dtype=np.int32)
+    r2 = radius_factor * radius_factor
+    big = np.iinfo(np.int64).max
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
         m = e - s
-        _, knn = tree.query(pts[s:e], k=min(kq, n), workers=-1)
-        knn = np.asarray(knn, dtype=np.int64).reshape(m, -1)
-        blk = block[s:e]
-        cand = np.concatenate([blk, knn], axis=1)
-        is_blk = np.zeros(cand.shape, dtype=bool)
-        is_blk[:, :blk.shape[1]] = True
-        me = np.arange(s, e)[:, None]
-        valid = (cand >= 0) & (cand < n) & (cand != me)
+        p = np.arange(s, e)
+        i = p % W
+        j = p // W
+        cand = np.empty((m, D), dtype=np.int64)
+        blk = np.empty(D, dtype=bool)
+        for k, (di, dj) in enumerate(offs):
+            jj = j + dj
+            cand[:, k] = np.where((jj >= 0) & (jj <= L), jj * W + (i + di) % W, -1)
+            blk[k] = abs(di) <= 1 and abs(dj) <= 1
+        valid = cand >= 0
         cs = np.where(valid, cand, 0)
-        d2 = (x[cs] - x[s:e, None]) ** 2 + (y[cs] - y[s:e, None]) ** 2
-        r2 = (radius_factor * h[s:e, None]) ** 2
-        valid &= is_blk | (d2 <= r2)
-        # de-duplicate: sort by index, keep the first of equal runs (block first)
-        key_idx = np.where(valid, cand, np.iinfo(np.int64).max)
-        order = np.lexsort((~is_blk, key_idx), axis=1)
-        cand = np.take_along_axis(cand, order, 1)
-        valid = np.take_along_axis(valid, order, 1)
-        is_blk = np.take_along_axis(is_blk, order, 1)
-        d2 = np.take_along_axis(d2, order, 1)
-        dup = np.zeros_like(valid)
-        dup[:, 1:] = (cand[:, 1:] == cand[:, :-1]) & valid[:, 1:] & valid[:, :-1]
-        valid &= ~dup
-        # rank non-block candidates by (distance, index); keep block + nearest
-        nblk = (valid & is_blk).sum(axis=1, keepdims=True)
-        big = np.inf
-        dnb = np.where(valid & ~is_blk, d2, big)
-        o2 = np.lexsort((np.where(valid & ~is_blk, cand, np.iinfo(np.int64).max), dnb), axis=1)
-        rank = np.empty_like(o2)
-        np.put_along_axis(rank, o2, np.arange(o2.shape[1])[None, :].repeat(m, 0), 1)
-        limit = max_degree - nblk
-        keep = valid & (is_blk | (rank < limit))
-        # if the cap cuts through a group of equal distances (mirror images of
-        # a point on the symmetry axis), drop the whole group
-        d_sorted = np.take_along_axis(dnb, o2, 1)
-        d_cut = np.take_along_axis(d_sorted, np.minimum(limit, d_sorted.shape[1] - 1), 1)
-        keep &= is_blk | (dnb != d_cut) | ~np.isfinite(d_cut)
-        # final order: by (distance, index)
-        dk = np.where(keep, d2, big)
-        ik = np.where(keep, cand, np.iinfo(np.int64).max)
-        o3 = np.lexsort((ik, dk), axis=1)
-        ck = np.take_along_axis(np.where(keep, cand, -1), o3, 1)[:, :max_degree]
-        dg = keep.sum(axis=1)
-        deg[s:e] = dg
-        rows[s:e] = ck[:, :max_degree].astype(np.int32)
+        dx = x[cs] - x[p, None]
+        dy = y[cs] - y[p, None]
+        dt = dx * fny[p, None] - dy * fnx[p, None]
+        dn = dx * fnx[p, None] + dy * fny[p, None]
+        d2 = (dt / ht[p, None]) ** 2 + (dn / hn[p, None]) ** 2
+        keep = valid & (blk[None, :] | (d2 <= r2))
+        dist = np.sqrt(dx * dx + dy * dy)
+        halves = [dt < -0.05 * dist, dt > 0.05 * dist, dn < -0.05 * dist, dn > 0.05 * dist]
+        for h, inside in enumerate(halves):
+            inside = inside & valid
+            if h == 2:
+                inside = inside & (flags[p, None] != 1)
+            have = (keep & inside).sum(axis=1, keepdims=True)
+            need = np.maximum(0, 2 - have)
+            pool = inside & ~keep
+            dp = np.where(pool, d2, np.inf)
+            # admit the `need` nearest, and any candidate tied with the last
+            # one admitted (mirror images of a point on the symmetry axis)
+            ds = np.sort(dp, axis=1)
+            cut = np.take_along_axis(ds, np.maximum(need - 1, 0), 1)
+            keep |= pool & (need > 0) & (dp <= cut)
+        # cap: block members first, then by distance; a tie group that the
+        # cap would split (mirror images) is dropped whole
+        dk = np.where(keep, d2, np.inf)
+        nb = ~blk[None, :].repeat(m, 0)
+        o = np.lexsort((np.where(keep, cand, big), dk, nb), axis=1)
+        if D > max_degree:
+            dso = np.take_along_axis(dk, o, 1)
+            nbo = np.take_along_axis(nb, o, 1)
+            last_d, last_b = dso[:, max_degree - 1:max_degree], nbo[:, max_degree - 1:max_degree]
+            next_d, next_b = dso[:, max_degree:max_degree + 1], nbo[:, max_degree:max_degree + 1]
+            split = np.isfinite(next_d) & (next_d == last_d) & (next_b == last_b)
+            in_cap = np.zeros_like(keep)
+            np.put_along_axis(in_cap, o[:, :max_degree], True, 1)
+            keep &= in_cap & ~(split & (dk == last_d) & (nb == last_b))
+        dk = np.where(keep, d2, np.inf)
+        o = np.lexsort((np.where(keep, cand, big), dk), axis=1)[:, :max_degree]
+        ck = np.take_along_axis(np.where(keep, cand, -1), o, 1)
+        deg[s:e] = keep.sum(axis=1)
+        rows[s:e] = ck.astype(np.int32)
     offsets = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(deg, out=offsets[1:])
     mask = np.arange(max_degree)[None, :] < deg[:, None]
-    idx = rows[mask]
-    return offsets.astype(np.int32), idx.astype(np.int32)
+    return offsets.astype(np.int32), rows[mask].astype(np.int32)
 
 
 def naca0012_cloud(W: int = 320, L: int = 30, seed: int = 2403_13287,
@@ -293,8 +299,8 @@ def naca0012_cloud(W: int = 320, L: int = 30, seed: int = 2403_13287,
     flags = np.zeros(n, dtype=np.int32)
     flags[:W] = FLAG_WALL
     flags[L * W:] = FLAG_FARFIELD
-    h = np.maximum(ht, hn).reshape(n)
-    offsets, idx = _connectivity(x, y, h, _structured_block(W, L), radius_factor, max_degree)
+    offsets, idx = _connectivity(x, y, W, L, flags, nx, ny, ht.reshape(n), hn.reshape(n),
+                                 radius_factor, max_degree)
     wall_order = np.arange(W, dtype=np.int32)
     if shuffle:
         perm = np.random.Generator(np.random.PCG64(seed + 1)).permutation(n)  # new -> old

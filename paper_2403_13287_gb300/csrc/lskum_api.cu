@@ -1,0 +1,674 @@
+// C ABI of the q-LSKUM hot path (include/lskum.h): context creation with CSR
+// validation, renumbering and geometry; the pseudo-time loop of Algorithm 1
+// (arXiv 2403.13287, Sec. 3); residual, derivative, time-step and force
+// queries; state transfer.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lskum.h"
+#include "lskum_kernels.h"
+
+using namespace lskum;
+
+struct lskum_ctx {
+    int64_t n = 0, nnz = 0, n_wall = 0;
+    lskum_config cfg{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int64_t launches = 0;
+    Gas gas{};
+    std::vector<int32_t> perm_h;
+    std::vector<void *> allocs;
+
+    double2 *xy = nullptr, *nrm = nullptr;
+    uint8_t *flag = nullptr, *mask = nullptr;
+    double *dmin = nullptr;
+    int32_t *off = nullptr, *idx = nullptr, *off_in = nullptr;
+    double2 *lsw = nullptr, *fxw = nullptr;
+    int32_t *perm = nullptr, *inv = nullptr;
+    int32_t *wall = nullptr;
+    double *wall_ds = nullptr;
+
+    double *U = nullptr, *Us = nullptr, *acc = nullptr, *Ubak = nullptr;
+    double *q_cur = nullptr, *q_nxt = nullptr;
+    double *qgA = nullptr, *qgB = nullptr;
+    double *dt = nullptr, *Rt = nullptr, *Ut = nullptr, *Ucm = nullptr;
+    double *norm_part = nullptr;
+    int nparts = 0;
+    double *res_dev = nullptr;
+    int res_cap = 0;
+    int *status = nullptr;
+    double *fbuf = nullptr;
+
+    // kernel timing (lskum_profile): event pairs per kernel class, reused
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed[LSKUM_KERNEL_CLASSES];
+
+    DevGeom geom() const
+    {
+        DevGeom g;
+        g.n = n; g.xy = xy; g.nrm = nrm; g.flag = flag; g.dmin = dmin;
+        g.off = off; g.idx = idx; g.mask = mask; g.lsw = lsw; g.fxw = fxw;
+        return g;
+    }
+};
+
+static thread_local std::string g_create_error;
+
+static lskum_status fail(lskum_ctx *c, lskum_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+#define CK(c, call)                                                                             \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail((c), e_ == cudaErrorMemoryAllocation ? LSKUM_ERR_OOM : LSKUM_ERR_CUDA,  \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                         \
+    } while (0)
+
+#define LAUNCH(c, call)                                                                         \
+    do {                                                                                        \
+        (c)->launches++;                                                                        \
+        CK(c, call);                                                                            \
+    } while (0)
+
+static cudaError_t next_event(lskum_ctx *c, cudaEvent_t *ev)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        c->ev_pool.push_back(e);
+    }
+    *ev = c->ev_pool[c->ev_used++];
+    return cudaSuccess;
+}
+
+// launch of a timed kernel class: bracketed by events while profiling
+#define TIMED_LAUNCH(c, cls, call)                                                              \
+    do {                                                                                        \
+        cudaEvent_t e0_ = nullptr, e1_ = nullptr;                                               \
+        if ((c)->profiling) {                                                                   \
+            CK(c, next_event(c, &e0_));                                                         \
+            CK(c, next_event(c, &e1_));                                                         \
+            CK(c, cudaEventRecord(e0_, (c)->stream));                                           \
+        }                                                                                       \
+        LAUNCH(c, call);                                                                        \
+        if ((c)->profiling) {                                                                   \
+            CK(c, cudaEventRecord(e1_, (c)->stream));                                           \
+            (c)->timed[cls].push_back({e0_, e1_});                                              \
+        }                                                                                       \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(lskum_ctx *c, T **p, size_t count)
+{
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+        c->allocs.push_back(v);
+        *p = static_cast<T *>(v);
+    }
+    return e;
+}
+
+static void free_all(lskum_ctx *c)
+{
+    for (void *p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+}
+
+static void freestream(double gamma, double mach, double aoa_deg, double U[4])
+{
+    const double a = aoa_deg * 3.14159265358979323846 / 180.0;
+    const double rho = 1.0, u = mach * cos(a), v = mach * sin(a), p = 1.0 / gamma;
+    U[0] = rho;
+    U[1] = rho * u;
+    U[2] = rho * v;
+    U[3] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v);
+}
+
+static lskum_status validate_csr(int64_t n, const int32_t *off, const int32_t *idx, std::string &msg)
+{
+    char buf[256];
+    if (off[0] != 0) { msg = "nbr_offsets[0] != 0"; return LSKUM_ERR_CONNECTIVITY; }
+    std::vector<int32_t> row;
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t a = off[p], b = off[p + 1];
+        if (b < a) {
+            snprintf(buf, sizeof buf, "nbr_offsets decreases at point %lld", (long long)p);
+            msg = buf; return LSKUM_ERR_CONNECTIVITY;
+        }
+        if (b - a > LSKUM_MAX_DEGREE) {
+            snprintf(buf, sizeof buf, "point %lld has %lld neighbours (max %d)", (long long)p,
+                     (long long)(b - a), LSKUM_MAX_DEGREE);
+            msg = buf; return LSKUM_ERR_CONNECTIVITY;
+        }
+        row.assign(idx + a, idx + b);
+        for (int32_t i : row) {
+            if (i < 0 || i >= n) {
+                snprintf(buf, sizeof buf, "point %lld has neighbour index %d out of range", (long long)p, i);
+                msg = buf; return LSKUM_ERR_CONNECTIVITY;
+            }
+            if (i == p) {
+                snprintf(buf, sizeof buf, "point %lld lists itself as a neighbour", (long long)p);
+                msg = buf; return LSKUM_ERR_CONNECTIVITY;
+            }
+        }
+        std::sort(row.begin(), row.end());
+        for (size_t k = 1; k < row.size(); ++k)
+            if (row[k] == row[k - 1]) {
+                snprintf(buf, sizeof buf, "point %lld lists neighbour %d twice", (long long)p, row[k]);
+                msg = buf; return LSKUM_ERR_CONNECTIVITY;
+            }
+    }
+    return LSKUM_OK;
+}
+
+extern "C" const char *lskum_last_error(const lskum_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" int64_t lskum_launch_count(const lskum_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" void lskum_destroy(lskum_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    free_all(ctx);
+    delete ctx;
+}
+
+static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, const double *nx,
+                                const double *ny, const int32_t *flags, const int32_t *nbr_offsets,
+                                const int32_t *nbr_idx, const int32_t *wall_order)
+{
+    const int64_t n = c->n, nnz = c->nnz;
+    cudaStream_t s = c->stream;
+    // input-order copies
+    double *dx = nullptr, *dy = nullptr, *dnx = nullptr, *dny = nullptr;
+    int32_t *dflags = nullptr, *didx_in = nullptr;
+    CK(c, dalloc(c, &dx, n));
+    CK(c, dalloc(c, &dy, n));
+    CK(c, dalloc(c, &dnx, n));
+    CK(c, dalloc(c, &dny, n));
+    CK(c, dalloc(c, &dflags, n));
+    CK(c, dalloc(c, &didx_in, nnz));
+    CK(c, dalloc(c, &c->off_in, n + 1));
+    CK(c, cudaMemcpyAsync(dx, x, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(dy, y, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(dnx, nx, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(dny, ny, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(dflags, flags, n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(didx_in, nbr_idx, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(c->off_in, nbr_offsets, (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+
+    CK(c, dalloc(c, &c->xy, n));
+    CK(c, dalloc(c, &c->nrm, n));
+    CK(c, dalloc(c, &c->flag, n));
+    CK(c, dalloc(c, &c->dmin, n));
+    CK(c, dalloc(c, &c->perm, n));
+    CK(c, dalloc(c, &c->inv, n));
+    CK(c, dalloc(c, &c->off, n + 1));
+    CK(c, dalloc(c, &c->idx, nnz));
+    CK(c, dalloc(c, &c->mask, nnz));
+    CK(c, dalloc(c, &c->lsw, nnz));
+    CK(c, dalloc(c, &c->fxw, nnz));
+
+    // numbering
+    if (c->cfg.reorder == 1) {
+        double xmin = x[0], xmax = x[0], ymin = y[0], ymax = y[0];
+        for (int64_t p = 1; p < n; ++p) {
+            xmin = std::min(xmin, x[p]); xmax = std::max(xmax, x[p]);
+            ymin = std::min(ymin, y[p]); ymax = std::max(ymax, y[p]);
+        }
+        const double ext = std::max(std::max(xmax - xmin, ymax - ymin), 1e-300);
+        const double scale = 4294967295.0 / ext;
+        // the Morton kernel reads coordinates in input order
+        double2 *xy_in = nullptr;
+        CK(c, cudaMallocAsync(&xy_in, n * sizeof(double2), s));
+        std::vector<double2> tmp(n);
+        for (int64_t p = 0; p < n; ++p) tmp[p] = make_double2(x[p], y[p]);
+        CK(c, cudaMemcpyAsync(xy_in, tmp.data(), n * sizeof(double2), cudaMemcpyHostToDevice, s));
+        c->launches += 2;
+        CK(c, morton_permutation(n, xy_in, xmin, ymin, scale, c->perm, s));
+        CK(c, cudaFreeAsync(xy_in, s));
+        CK(c, cudaStreamSynchronize(s));
+    } else {
+        std::vector<int32_t> iota(n);
+        for (int64_t p = 0; p < n; ++p) iota[p] = (int32_t)p;
+        CK(c, cudaMemcpyAsync(c->perm, iota.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CK(c, cudaStreamSynchronize(s));
+    }
+    LAUNCH(c, launch_permute_points(n, c->perm, dx, dy, dnx, dny, dflags, c->xy, c->nrm, c->flag, c->inv, s));
+    c->launches += 2;
+    CK(c, permute_csr(n, c->perm, c->inv, c->off_in, didx_in, c->off, c->idx, s));
+
+    int *bad = nullptr;
+    CK(c, dalloc(c, &bad, 2));
+    const int bad_init[2] = {0, 0x7fffffff};
+    CK(c, cudaMemcpyAsync(bad, bad_init, sizeof bad_init, cudaMemcpyHostToDevice, s));
+    LAUNCH(c, launch_geometry(n, c->xy, c->nrm, c->flag, c->off, c->idx, c->mask, c->lsw, c->fxw, c->dmin, bad, s));
+    int bad_h[2];
+    CK(c, cudaMemcpyAsync(bad_h, bad, sizeof bad_h, cudaMemcpyDeviceToHost, s));
+    c->perm_h.resize(n);
+    CK(c, cudaMemcpyAsync(c->perm_h.data(), c->perm, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    if (bad_h[0] > 0) {
+        const int32_t p_in = c->perm_h[bad_h[1]];
+        return fail(c, LSKUM_ERR_DEGENERATE_STENCIL,
+                    "%d point(s) have a singular least-squares stencil; first: point %d (flag %d)",
+                    bad_h[0], p_in, flags[p_in]);
+    }
+
+    // wall contour (internal numbering) and its arc-length weights
+    std::vector<int32_t> inv_h(n);
+    for (int64_t p = 0; p < n; ++p) inv_h[c->perm_h[p]] = (int32_t)p;
+    const int64_t nw = c->n_wall;
+    std::vector<int32_t> wall_h(std::max<int64_t>(nw, 1));
+    std::vector<double> ds_h(std::max<int64_t>(nw, 1));
+    for (int64_t w = 0; w < nw; ++w) {
+        const int32_t p = wall_order[w], pn = wall_order[(w + 1) % nw], pp = wall_order[(w + nw - 1) % nw];
+        const double dn = sqrt((x[pn] - x[p]) * (x[pn] - x[p]) + (y[pn] - y[p]) * (y[pn] - y[p]));
+        const double dp = sqrt((x[p] - x[pp]) * (x[p] - x[pp]) + (y[p] - y[pp]) * (y[p] - y[pp]));
+        ds_h[w] = 0.5 * (dn + dp);
+        wall_h[w] = inv_h[p];
+    }
+    CK(c, dalloc(c, &c->wall, std::max<int64_t>(nw, 1)));
+    CK(c, dalloc(c, &c->wall_ds, std::max<int64_t>(nw, 1)));
+    CK(c, dalloc(c, &c->fbuf, nw + 2));
+    if (nw > 0) {
+        CK(c, cudaMemcpyAsync(c->wall, wall_h.data(), nw * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CK(c, cudaMemcpyAsync(c->wall_ds, ds_h.data(), nw * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+
+    // state and work buffers
+    c->nparts = (int)flux_blocks(n);
+    CK(c, dalloc(c, &c->U, 4 * n));
+    CK(c, dalloc(c, &c->Us, 4 * n));
+    CK(c, dalloc(c, &c->acc, 4 * n));
+    CK(c, dalloc(c, &c->Ubak, 4 * n));
+    CK(c, dalloc(c, &c->q_cur, 4 * n));
+    CK(c, dalloc(c, &c->q_nxt, 4 * n));
+    CK(c, dalloc(c, &c->qgA, 8 * n));
+    CK(c, dalloc(c, &c->qgB, 8 * n));
+    CK(c, dalloc(c, &c->dt, n));
+    CK(c, dalloc(c, &c->Rt, 4 * n));
+    CK(c, dalloc(c, &c->Ut, 4 * n));
+    CK(c, dalloc(c, &c->Ucm, 4 * n));
+    CK(c, dalloc(c, &c->norm_part, c->nparts));
+    CK(c, dalloc(c, &c->status, 2));
+    c->res_cap = 1024;
+    CK(c, dalloc(c, &c->res_dev, c->res_cap));
+    CK(c, cudaMemsetAsync(c->qgA, 0, 8 * n * sizeof(double), s));
+    CK(c, cudaMemsetAsync(c->qgB, 0, 8 * n * sizeof(double), s));
+    const int st_init[2] = {0, 0x7fffffff};
+    CK(c, cudaMemcpyAsync(c->status, st_init, sizeof st_init, cudaMemcpyHostToDevice, s));
+    LAUNCH(c, launch_fill_state(n, c->gas.Uinf, c->U, s));
+    LAUNCH(c, launch_q_from_U(n, c->gas, c->U, c->q_cur, c->status, s));
+    CK(c, cudaStreamSynchronize(s));
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_create(int64_t n, const double *x, const double *y, const double *nx,
+                                     const double *ny, const int32_t *flags, const int32_t *nbr_offsets,
+                                     const int32_t *nbr_idx, int64_t n_wall, const int32_t *wall_order,
+                                     const lskum_config *cfg, void *cuda_stream, lskum_ctx **out)
+{
+    if (!out) return fail(nullptr, LSKUM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n >= (int64_t)0x7fffffff) return fail(nullptr, LSKUM_ERR_ARG, "n = %lld out of range", (long long)n);
+    if (!x || !y || !nx || !ny || !flags || !nbr_offsets || !nbr_idx || !cfg)
+        return fail(nullptr, LSKUM_ERR_ARG, "a required input pointer is NULL");
+    if (n_wall < 0 || n_wall > n || (n_wall > 0 && !wall_order))
+        return fail(nullptr, LSKUM_ERR_ARG, "bad wall contour (n_wall = %lld)", (long long)n_wall);
+    if (cfg->order != 1 && cfg->order != 2) return fail(nullptr, LSKUM_ERR_ARG, "order must be 1 or 2");
+    if (cfg->inner_iters < 0 || cfg->inner_iters > 1000) return fail(nullptr, LSKUM_ERR_ARG, "inner_iters out of range");
+    if (cfg->time_scheme != 0 && cfg->time_scheme != 1) return fail(nullptr, LSKUM_ERR_ARG, "time_scheme must be 0 or 1");
+    if (!(cfg->cfl > 0.0) || !(cfg->gamma > 1.0) || !(cfg->mach >= 0.0) || !std::isfinite(cfg->aoa_deg))
+        return fail(nullptr, LSKUM_ERR_ARG, "cfl, gamma, mach or aoa out of range");
+    if (cfg->precision != 0) return fail(nullptr, LSKUM_ERR_ARG, "precision %d not supported", cfg->precision);
+    if (cfg->reorder != 0 && cfg->reorder != 1) return fail(nullptr, LSKUM_ERR_ARG, "reorder must be 0 or 1");
+    if (!(cfg->limiter_K >= 0.0) || !std::isfinite(cfg->limiter_K))
+        return fail(nullptr, LSKUM_ERR_ARG, "limiter_K must be finite and >= 0");
+    for (int64_t p = 0; p < n; ++p) {
+        if (flags[p] < 0 || flags[p] > 2) return fail(nullptr, LSKUM_ERR_ARG, "point %lld has flag %d", (long long)p, flags[p]);
+        if (!std::isfinite(x[p]) || !std::isfinite(y[p]) || !std::isfinite(nx[p]) || !std::isfinite(ny[p]))
+            return fail(nullptr, LSKUM_ERR_ARG, "point %lld has a non-finite coordinate or normal", (long long)p);
+        const double nn = nx[p] * nx[p] + ny[p] * ny[p];
+        if (fabs(nn - 1.0) > 1e-8) return fail(nullptr, LSKUM_ERR_ARG, "point %lld has a normal that is not unit", (long long)p);
+    }
+    std::string msg;
+    lskum_status st = validate_csr(n, nbr_offsets, nbr_idx, msg);
+    if (st != LSKUM_OK) return fail(nullptr, st, "%s", msg.c_str());
+    for (int64_t w = 0; w < n_wall; ++w)
+        if (wall_order[w] < 0 || wall_order[w] >= n)
+            return fail(nullptr, LSKUM_ERR_ARG, "wall_order[%lld] out of range", (long long)w);
+
+    lskum_ctx *c = new lskum_ctx();
+    c->n = n;
+    c->nnz = nbr_offsets[n];
+    c->n_wall = n_wall;
+    c->cfg = *cfg;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->gas.gamma = cfg->gamma;
+    c->gas.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
+    c->gas.g14 = cfg->gamma == 1.4;
+    freestream(cfg->gamma, cfg->mach, cfg->aoa_deg, c->gas.Uinf);
+    st = create_impl(c, x, y, nx, ny, flags, nbr_offsets, nbr_idx, wall_order);
+    if (st != LSKUM_OK) {
+        g_create_error = c->err;
+        lskum_destroy(c);
+        return st;
+    }
+    *out = c;
+    return LSKUM_OK;
+}
+
+// q-derivatives of the state whose q-variables are in q (E15 with the
+// configured inner iterations); returns the buffer holding the result
+static lskum_status gradients(lskum_ctx *c, const double *q, double **qg_out)
+{
+    const DevGeom g = c->geom();
+    double *src = c->qgA, *dst = c->qgB;
+    const int inner = c->cfg.inner_iters;
+    const double limK = c->cfg.order == 2 ? c->cfg.limiter_K : 0.0;
+    TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, q, nullptr, src, inner == 0 ? limK : 0.0, c->stream));
+    for (int k = 0; k < inner; ++k) {
+        TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, q, src, dst, k == inner - 1 ? limK : 0.0, c->stream));
+        std::swap(src, dst);
+    }
+    *qg_out = src;
+    return LSKUM_OK;
+}
+
+static lskum_status iteration(lskum_ctx *c, int it)
+{
+    const DevGeom g = c->geom();
+    const bool rk4 = c->cfg.time_scheme == 1;
+    const int stages = rk4 ? 4 : 1;
+    for (int k = 0; k < stages; ++k) {
+        double *qg = nullptr;
+        if (c->cfg.order == 2) {
+            lskum_status st = gradients(c, c->q_cur, &qg);
+            if (st != LSKUM_OK) return st;
+        }
+        FluxLaunch L{};
+        L.q = c->q_cur;
+        L.qg = qg;
+        L.Un = c->U;
+        L.Uout = (rk4 && k < 3) ? c->Us : c->U;
+        L.acc = c->acc;
+        L.qout = c->q_nxt;
+        L.dt = c->dt;
+        L.R = nullptr;
+        L.norm_part = c->norm_part;
+        L.status = c->status;
+        L.cfl = c->cfg.cfl;
+        L.order = c->cfg.order;
+        L.mode = rk4 ? 2 : 1;
+        L.stage = k;
+        TIMED_LAUNCH(c, LSKUM_KERNEL_FLUX, launch_flux(g, c->gas, L, c->stream));
+        std::swap(c->q_cur, c->q_nxt);
+        if (k == 0) LAUNCH(c, launch_residue_finish(c->norm_part, c->nparts, c->n, c->res_dev + it, c->stream));
+    }
+    return LSKUM_OK;
+}
+
+static lskum_status reset_status(lskum_ctx *c)
+{
+    const int st_init[2] = {0, 0x7fffffff};
+    CK(c, cudaMemcpyAsync(c->status, st_init, sizeof st_init, cudaMemcpyHostToDevice, c->stream));
+    return LSKUM_OK;
+}
+
+static lskum_status read_status(lskum_ctx *c, int st[2])
+{
+    CK(c, cudaMemcpyAsync(st, c->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_step(lskum_ctx *c, int n_iters, double *res_history)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (n_iters < 0) return fail(c, LSKUM_ERR_ARG, "n_iters < 0");
+    if (n_iters == 0) return LSKUM_OK;
+    if (n_iters > c->res_cap) {
+        double *r = nullptr;
+        CK(c, dalloc(c, &r, n_iters));
+        c->res_dev = r;
+        c->res_cap = n_iters;
+    }
+    lskum_status st = reset_status(c);
+    if (st != LSKUM_OK) return st;
+    CK(c, cudaMemcpyAsync(c->Ubak, c->U, 4 * c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    for (int it = 0; it < n_iters; ++it) {
+        st = iteration(c, it);
+        if (st != LSKUM_OK) return st;
+    }
+    if (res_history)
+        CK(c, cudaMemcpyAsync(res_history, c->res_dev, n_iters * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    int sh[2];
+    st = read_status(c, sh);
+    if (st != LSKUM_OK) return st;
+    if (sh[0] & STATUS_NONPHYSICAL) {
+        CK(c, cudaMemcpyAsync(c->U, c->Ubak, 4 * c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        LAUNCH(c, launch_q_from_U(c->n, c->gas, c->U, c->q_cur, c->status, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        return fail(c, LSKUM_ERR_NONPHYSICAL,
+                    "non-physical state (rho <= 0, p <= 0 or non-finite) at point %d; state rolled back",
+                    c->perm_h[sh[1]]);
+    }
+    return LSKUM_OK;
+}
+
+// q-variables of a caller state (device [4][n], input order) into q_nxt, or the
+// context's own q
+static lskum_status q_of(lskum_ctx *c, const double *U, const double **q)
+{
+    if (!U) {
+        *q = c->q_cur;
+        return LSKUM_OK;
+    }
+    LAUNCH(c, launch_state_in(c->n, c->perm, U, c->Ut, c->stream));
+    LAUNCH(c, launch_q_from_U(c->n, c->gas, c->Ut, c->q_nxt, c->status, c->stream));
+    *q = c->q_nxt;
+    return LSKUM_OK;
+}
+
+static lskum_status check_nonphysical(lskum_ctx *c)
+{
+    int sh[2];
+    lskum_status st = read_status(c, sh);
+    if (st != LSKUM_OK) return st;
+    if (sh[0] & STATUS_NONPHYSICAL)
+        return fail(c, LSKUM_ERR_NONPHYSICAL, "non-physical state at point %d", c->perm_h[sh[1]]);
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_residual(lskum_ctx *c, const double *U, double *R)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!R) return fail(c, LSKUM_ERR_ARG, "R is NULL");
+    lskum_status st = reset_status(c);
+    if (st != LSKUM_OK) return st;
+    const double *q = nullptr;
+    if ((st = q_of(c, U, &q)) != LSKUM_OK) return st;
+    double *qg = nullptr;
+    if (c->cfg.order == 2 && (st = gradients(c, q, &qg)) != LSKUM_OK) return st;
+    FluxLaunch L{};
+    L.q = q;
+    L.qg = qg;
+    L.R = c->Rt;
+    L.status = c->status;
+    L.order = c->cfg.order;
+    L.mode = 0;
+    LAUNCH(c, launch_flux(c->geom(), c->gas, L, c->stream));
+    LAUNCH(c, launch_state_out(c->n, c->perm, c->Rt, R, c->stream));
+    return check_nonphysical(c);
+}
+
+extern "C" lskum_status lskum_q_derivatives(lskum_ctx *c, const double *U, double *qx, double *qy)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!qx || !qy) return fail(c, LSKUM_ERR_ARG, "qx or qy is NULL");
+    lskum_status st = reset_status(c);
+    if (st != LSKUM_OK) return st;
+    const double *q = nullptr;
+    if ((st = q_of(c, U, &q)) != LSKUM_OK) return st;
+    double *qg = nullptr;
+    const int inner = c->cfg.inner_iters;
+    const double limK = c->cfg.limiter_K;
+    if (c->cfg.order == 1) {
+        c->cfg.inner_iters = 0;
+        c->cfg.limiter_K = 0.0;
+    }
+    st = gradients(c, q, &qg);
+    c->cfg.inner_iters = inner;
+    c->cfg.limiter_K = limK;
+    if (st != LSKUM_OK) return st;
+    LAUNCH(c, launch_grad_out(c->n, c->perm, qg, qx, qy, c->stream));
+    return check_nonphysical(c);
+}
+
+extern "C" lskum_status lskum_timestep(lskum_ctx *c, const double *U, double *dt)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!dt) return fail(c, LSKUM_ERR_ARG, "dt is NULL");
+    const double *Ui = c->U;
+    if (U) {
+        LAUNCH(c, launch_state_in(c->n, c->perm, U, c->Ut, c->stream));
+        Ui = c->Ut;
+    }
+    LAUNCH(c, launch_timestep(c->n, c->gas, c->cfg.cfl, c->dmin, Ui, c->Rt, c->stream));
+    LAUNCH(c, launch_scalar_out(c->n, c->perm, c->Rt, dt, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_forces(lskum_ctx *c, double *cl, double *cd, double *cp)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!cl || !cd) return fail(c, LSKUM_ERR_ARG, "cl or cd is NULL");
+    if (c->n_wall == 0) return fail(c, LSKUM_ERR_ARG, "no wall contour was given at create");
+    const double a = c->cfg.aoa_deg * 3.14159265358979323846 / 180.0;
+    const double qinf = 0.5 * c->cfg.mach * c->cfg.mach;
+    if (!(qinf > 0.0)) return fail(c, LSKUM_ERR_ARG, "forces need mach > 0");
+    LAUNCH(c, launch_forces(c->n_wall, c->gas, qinf, c->wall, c->wall_ds, c->nrm, c->U, cos(a), sin(a),
+                            c->fbuf, c->fbuf + c->n_wall, c->stream));
+    double clcd[2];
+    CK(c, cudaMemcpyAsync(clcd, c->fbuf + c->n_wall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (cp) CK(c, cudaMemcpyAsync(cp, c->fbuf, c->n_wall * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *cl = clcd[0];
+    *cd = clcd[1];
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_get_state(lskum_ctx *c, double *U, int on_host)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!U) return fail(c, LSKUM_ERR_ARG, "U is NULL");
+    double *dst = on_host ? c->Ucm : U;
+    LAUNCH(c, launch_state_out(c->n, c->perm, c->U, dst, c->stream));
+    if (on_host) {
+        CK(c, cudaMemcpyAsync(U, c->Ucm, 4 * c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_set_state(lskum_ctx *c, const double *U, int on_host)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!U) return fail(c, LSKUM_ERR_ARG, "U is NULL");
+    const double *src = U;
+    if (on_host) {
+        CK(c, cudaMemcpyAsync(c->Ucm, U, 4 * c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        src = c->Ucm;
+    }
+    lskum_status st = reset_status(c);
+    if (st != LSKUM_OK) return st;
+    LAUNCH(c, launch_state_in(c->n, c->perm, src, c->U, c->stream));
+    LAUNCH(c, launch_q_from_U(c->n, c->gas, c->U, c->q_cur, c->status, c->stream));
+    if (on_host) return check_nonphysical(c);
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_get_stencil_masks(lskum_ctx *c, uint8_t *mask)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!mask) return fail(c, LSKUM_ERR_ARG, "mask is NULL");
+    uint8_t *tmp = nullptr;
+    CK(c, cudaMallocAsync(&tmp, std::max<int64_t>(c->nnz, 1), c->stream));
+    c->launches++;
+    cudaError_t e = launch_mask_out(c->n, c->inv, c->off_in, c->off, c->mask, tmp, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mask, tmp, c->nnz, cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(tmp, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    CK(c, e);
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_get_permutation(lskum_ctx *c, int32_t *perm)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    if (!perm) return fail(c, LSKUM_ERR_ARG, "perm is NULL");
+    memcpy(perm, c->perm_h.data(), c->n * sizeof(int32_t));
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_profile(lskum_ctx *c, int enable)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    CK(c, c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    c->profiling = enable != 0;
+    c->ev_used = 0;
+    for (auto &v : c->timed) v.clear();
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_kernel_time(lskum_ctx *c, int cls, double *total_ms, int64_t *launches)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    if (cls < 0 || cls >= LSKUM_KERNEL_CLASSES || !total_ms || !launches)
+        return fail(c, LSKUM_ERR_ARG, "bad kernel class or output pointer");
+    CK(c, c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    double t = 0.0;
+    for (auto &pr : c->timed[cls]) {
+        float ms = 0.0f;
+        CK(c, cudaEventElapsedTime(&ms, pr.first, pr.second));
+        t += ms;
+    }
+    *total_ms = t;
+    *launches = (int64_t)c->timed[cls].size();
+    return LSKUM_OK;
+}

@@ -1,0 +1,142 @@
+// Device-side building blocks of the q-LSKUM hot path (arXiv 2403.13287, Sec. 2).
+//
+// Internal layout (points renumbered by the context's permutation):
+//   xy[p], nrm[p]       double2   coordinates and unit normal (nx, ny)
+//   flag[p]             uint8     0 interior, 1 wall, 2 far-field
+//   off[p], idx[e]      int32     CSR connectivity N(P_0), rows in caller order
+//   mask[e]             uint8     sub-stencil bits (x+ 1, x- 2, y+ 4, y- 8)
+//   lsw[e]              double2   full-stencil least-squares weights (a_x, a_y):
+//                                 grad f(P_0) = sum_e (a_x, a_y)_e (f_i - f_0)  (E9)
+//   fxw[e]              double2   sub-stencil weights (w_s, w_n): the edge's
+//                                 coefficient in dG/ds of its x+- sub-stencil and
+//                                 in dG/dn of its y+- sub-stencil (E11)
+//   U, q                double[n][4]   conserved state and q-variables (E13)
+//   qg                  double[n][8]   (qx0..3, qy0..3), global-frame q-derivatives
+// The weights are the closed-form 2x2 least-squares solutions written as a
+// linear combination of the perturbations; they depend on geometry only and
+// are computed once, in FP64, when the context is created.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lskum {
+
+enum : uint8_t { FLAG_INTERIOR = 0, FLAG_WALL = 1, FLAG_FARFIELD = 2 };
+enum : uint8_t { M_XPOS = 1, M_XNEG = 2, M_YPOS = 4, M_YNEG = 8 };
+
+enum : int { STATUS_NONPHYSICAL = 1, STATUS_DEGENERATE = 2 };
+
+struct DevGeom {
+    int64_t n;
+    const double2 *__restrict__ xy;
+    const double2 *__restrict__ nrm;
+    const uint8_t *__restrict__ flag;
+    const double *__restrict__ dmin;
+    const int32_t *__restrict__ off;
+    const int32_t *__restrict__ idx;
+    const uint8_t *__restrict__ mask;
+    const double2 *__restrict__ lsw;
+    const double2 *__restrict__ fxw;
+};
+
+// Free-stream and gas constants handed to every kernel.
+struct Gas {
+    double gamma;
+    double inv_gm1;  // 1/(gamma - 1)
+    int g14;         // gamma == 1.4: beta^(-1/(gamma-1)) = beta^(-2.5) without log
+    double Uinf[4];
+};
+
+// Primitive state of a (modified) q-vector, E13 inverted:
+//   beta = -q4/2, u = q2/(2 beta), v = q3/(2 beta),
+//   rho = exp(q1 + beta (u^2 + v^2)) beta^(-1/(gamma-1)), p = rho/(2 beta)
+struct Prim {
+    double rho, u, v, p, rsb, sqb;  // rsb = 1/sqrt(beta), sqb = sqrt(beta)
+};
+
+__device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, Prim &s)
+{
+    const double beta = -0.5 * qt[3];
+    if (!(beta > 0.0)) return false;
+    const double r = 1.0 / qt[3];          // -1/(2 beta)
+    s.u = -qt[1] * r;
+    s.v = -qt[2] * r;
+    s.rsb = rsqrt(beta);
+    s.sqb = beta * s.rsb;
+    const double ke = beta * (s.u * s.u + s.v * s.v);
+    if (gas.g14) {
+        // beta^-2.5 = beta^-1/2 * (1/beta)^2, 1/beta = -2r
+        s.rho = exp(qt[0] + ke) * s.rsb * (4.0 * r * r);
+    } else {
+        s.rho = exp(qt[0] - log(beta) * gas.inv_gm1 + ke);
+    }
+    s.p = -s.rho * r;
+    return isfinite(s.rho) && s.rho > 0.0;
+}
+
+// Kinetic split flux along a direction: normal velocity un, transverse ut,
+// sign +1 for G+, -1 for G- (half-range moments of the Maxwellian):
+//   S = un sqrt(beta), A = (1 + sgn erf S)/2, B = exp(-S^2)/(2 sqrt(pi beta))
+//   G = [rho(un A + sgn B), (p + rho un^2) A + sgn rho un B,
+//        rho ut (un A + sgn B), (rhoE + p) un A + sgn (rhoE + p/2) B]
+__device__ __forceinline__ void split_flux(double sgn, const Prim &s, double un, double ut,
+                                           double rhoE, double G[4])
+{
+    const double S = un * s.sqb;
+    const double A = 0.5 * (1.0 + sgn * erf(S));
+    const double B = exp(-S * S) * s.rsb * 0.28209479177387814;  // 1/(2 sqrt(pi))
+    const double m = un * A + sgn * B;
+    G[0] = s.rho * m;
+    G[1] = (s.p + s.rho * un * un) * A + sgn * s.rho * un * B;
+    G[2] = s.rho * ut * m;
+    G[3] = (rhoE + s.p) * un * A + sgn * (rhoE + 0.5 * s.p) * B;
+}
+
+__device__ __forceinline__ void load4(const double *a, int64_t p, double v[4])
+{
+    const double2 *a2 = reinterpret_cast<const double2 *>(a);
+    double2 lo = a2[2 * p], hi = a2[2 * p + 1];
+    v[0] = lo.x; v[1] = lo.y; v[2] = hi.x; v[3] = hi.y;
+}
+
+__device__ __forceinline__ void store4(double *a, int64_t p, const double v[4])
+{
+    double2 *a2 = reinterpret_cast<double2 *>(a);
+    a2[2 * p] = make_double2(v[0], v[1]);
+    a2[2 * p + 1] = make_double2(v[2], v[3]);
+}
+
+__device__ __forceinline__ void load8(const double *a, int64_t p, double v[8])
+{
+    const double2 *a2 = reinterpret_cast<const double2 *>(a);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double2 t = a2[4 * p + k];
+        v[2 * k] = t.x; v[2 * k + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ void store8(double *a, int64_t p, const double v[8])
+{
+    double2 *a2 = reinterpret_cast<double2 *>(a);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a2[4 * p + k] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+
+// q-variables of a conserved state (E13), same operation order as the
+// primitive form: rho, u = m/rho, p = (gamma-1)(E - rho|u|^2/2), beta = rho/(2p)
+__device__ __forceinline__ bool q_from_U(const double U[4], const Gas &gas, double q[4])
+{
+    const double rho = U[0];
+    const double u = U[1] / rho, v = U[2] / rho;
+    const double p = (gas.gamma - 1.0) * (U[3] - 0.5 * rho * (u * u + v * v));
+    const double beta = 0.5 * rho / p;
+    q[0] = log(rho) + log(beta) * gas.inv_gm1 - beta * (u * u + v * v);
+    q[1] = 2.0 * beta * u;
+    q[2] = 2.0 * beta * v;
+    q[3] = -2.0 * beta;
+    return rho > 0.0 && p > 0.0 && isfinite(q[0]);
+}
+
+}  // namespace lskum

@@ -1,0 +1,410 @@
+// Hot-path kernels of q-LSKUM (arXiv 2403.13287): q-derivatives (E14, E15),
+// the fused flux residual + state update (E10-E12, E16 / RK4) and the
+// reductions (residue, forces). One thread per point; the neighbour loop
+// gathers q, q-derivatives and coordinates of the stencil.
+#include "lskum_device.cuh"
+#include "lskum_kernels.h"
+
+namespace lskum {
+
+// --------------------------------------------------------------------------
+// q_derivatives(): one least-squares solve of E15 per point.
+//   first order (qg_old == nullptr):  grad q_0 = sum_e a_e (q_i - q_0)
+//   inner iteration (Jacobi):         dq~ = dq - 1/2 [dx (qx_i - qx_0) + dy (qy_i - qy_0)]
+// with the previous iterate qg_old read at every point and the new one
+// written to qg_new (no point reads what this pass writes).
+// --------------------------------------------------------------------------
+// Venkatakrishnan's function f(D, d) = (D^2 + e^2 + 2Dd)/(D^2 + 2d^2 + Dd + e^2)
+__device__ __forceinline__ double venkat(double D, double d, double eps2)
+{
+    return (D * D + eps2 + 2.0 * D * d) / (D * D + 2.0 * d * d + D * d + eps2);
+}
+
+// limK > 0 on the final pass: scale each component of the new gradient by
+// Venkatakrishnan's limiter. f(D, d) is >= 1 for 0 < d <= D/2 and decreasing
+// beyond, so its minimum over every reconstruction shift +-(P_i - P_0).grad/2
+// is its value at the largest shift d+ on each side.
+__global__ void __launch_bounds__(128) k_qgrad(DevGeom g, const double *__restrict__ q,
+                                               const double *__restrict__ qg_old,
+                                               double *__restrict__ qg_new, double limK)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.n) return;
+    double q0[4], g0[8], sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
+    load4(q, p, q0);
+    const bool inner = qg_old != nullptr;
+    const bool limit = limK > 0.0;
+    double2 xy0 = make_double2(0.0, 0.0);
+    if (inner) load8(qg_old, p, g0);
+    if (inner || limit) xy0 = g.xy[p];
+    double qmax[4] = {q0[0], q0[1], q0[2], q0[3]}, qmin[4] = {q0[0], q0[1], q0[2], q0[3]};
+    const int e0 = g.off[p], e1 = g.off[p + 1];
+    for (int e = e0; e < e1; ++e) {
+        const int i = g.idx[e];
+        const double2 a = g.lsw[e];
+        double qi[4];
+        load4(q, i, qi);
+        double dq[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            dq[k] = qi[k] - q0[k];
+            qmax[k] = fmax(qmax[k], qi[k]);
+            qmin[k] = fmin(qmin[k], qi[k]);
+        }
+        if (inner) {
+            double gi[8];
+            load8(qg_old, i, gi);
+            const double2 xyi = g.xy[i];
+            const double dx = xyi.x - xy0.x, dy = xyi.y - xy0.y;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                dq[k] = dq[k] - 0.5 * (dx * (gi[k] - g0[k]) + dy * (gi[4 + k] - g0[4 + k]));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            sx[k] += a.x * dq[k];
+            sy[k] += a.y * dq[k];
+        }
+    }
+    if (limit) {
+        double dmax[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int e = e0; e < e1; ++e) {
+            const double2 xyi = g.xy[g.idx[e]];
+            const double dx = xyi.x - xy0.x, dy = xyi.y - xy0.y;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dmax[k] = fmax(dmax[k], fabs(0.5 * (dx * sx[k] + dy * sy[k])));
+        }
+        const double h = g.dmin[p] * limK;
+        const double eps2 = h * h * h;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double phi = 1.0;
+            if (dmax[k] > 0.0) {
+                phi = fmin(phi, venkat(qmax[k] - q0[k], dmax[k], eps2));
+                phi = fmin(phi, venkat(qmin[k] - q0[k], -dmax[k], eps2));
+            }
+            sx[k] *= phi;
+            sy[k] *= phi;
+        }
+    }
+    double out[8] = {sx[0], sx[1], sx[2], sx[3], sy[0], sy[1], sy[2], sy[3]};
+    store8(qg_new, p, out);
+}
+
+// --------------------------------------------------------------------------
+// flux_residual() + timestep() + state_update() (+ residue partials), fused.
+// For each neighbour P_i of P_0 (frame t = (ny, -nx), n = (nx, ny)):
+//   q~_i = q_i - 1/2 (dx qx_i + dy qy_i),  q~_0 = q_0 - 1/2 (dx qx_0 + dy qy_0)   (E14)
+//   R += w_s [Gs(q~_i) - Gs(q~_0)] + w_n [Gn(q~_i) - Gn(q~_0)]                    (E11)
+// where Gs is Gx+ or Gx- and Gn is Gy+ or Gy- by the edge's sub-stencil.
+// --------------------------------------------------------------------------
+struct FluxParams {
+    DevGeom g;
+    Gas gas;
+    const double *q;    // [n][4] q of the state being evaluated
+    const double *qg;   // [n][8] q-derivatives, or nullptr (first order)
+    const double *Un;   // [n][4] U^n (update modes)
+    double *Uout;       // [n][4] next stage state / U^{n+1}
+    double *acc;        // [n][4] RK4 accumulator
+    double *qout;       // [n][4] q of Uout
+    double *dt;         // [n] local time step (computed at stage 0)
+    double *R;          // [n][4] residual output (residual mode)
+    double *norm_part;  // [gridDim.x] block sums of R_rho^2 (stage 0)
+    int *status;        // [0] status bits, [1] smallest offending internal point
+    double cfl;
+    int order;
+    int mode;   // 0 residual only, 1 forward Euler, 2 RK4
+    int stage;  // RK4 stage 0..3
+};
+
+__device__ __forceinline__ void flag_nonphysical(int *status, int64_t p)
+{
+    atomicOr(status, STATUS_NONPHYSICAL);
+    atomicMin(status + 1, (int)p);
+}
+
+__global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
+{
+    const DevGeom &g = P.g;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double Rg[4] = {0.0, 0.0, 0.0, 0.0};
+    const bool live = p < g.n;
+    uint8_t flag = FLAG_FARFIELD;
+    if (live) flag = g.flag[p];
+    if (live && flag != FLAG_FARFIELD) {
+        const double2 xy0 = g.xy[p];
+        const double2 n0 = g.nrm[p];
+        const double tx = n0.y, ty = -n0.x;
+        double q0[4], g0[8];
+        load4(P.q, p, q0);
+        const bool second = P.order == 2;
+        if (second) load8(P.qg, p, g0);
+        double R[4] = {0.0, 0.0, 0.0, 0.0};
+        bool ok = true;
+        const int e0 = g.off[p], e1 = g.off[p + 1];
+        for (int e = e0; e < e1; ++e) {
+            const double2 w = g.fxw[e];
+            if (w.x == 0.0 && w.y == 0.0) continue;
+            const int i = g.idx[e];
+            const uint8_t m = g.mask[e];
+            double qti[4], qt0[4];
+            load4(P.q, i, qti);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qt0[k] = q0[k];
+            if (second) {
+                const double2 xyi = g.xy[i];
+                const double dx = xyi.x - xy0.x, dy = xyi.y - xy0.y;
+                double gi[8];
+                load8(P.qg, i, gi);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    qti[k] = qti[k] - 0.5 * (dx * gi[k] + dy * gi[4 + k]);
+                    qt0[k] = qt0[k] - 0.5 * (dx * g0[k] + dy * g0[4 + k]);
+                }
+            }
+            Prim si, s0;
+            ok &= prim_from_q(qti, P.gas, si);
+            ok &= prim_from_q(qt0, P.gas, s0);
+            const double us_i = si.u * tx + si.v * ty, un_i = si.u * n0.x + si.v * n0.y;
+            const double us_0 = s0.u * tx + s0.v * ty, un_0 = s0.u * n0.x + s0.v * n0.y;
+            const double rE_i = si.p * P.gas.inv_gm1 + 0.5 * si.rho * (us_i * us_i + un_i * un_i);
+            const double rE_0 = s0.p * P.gas.inv_gm1 + 0.5 * s0.rho * (us_0 * us_0 + un_0 * un_0);
+            if (w.x != 0.0) {
+                const double sg = (m & M_XPOS) ? 1.0 : -1.0;
+                double Gi[4], G0[4];
+                split_flux(sg, si, us_i, un_i, rE_i, Gi);
+                split_flux(sg, s0, us_0, un_0, rE_0, G0);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) R[k] += w.x * (Gi[k] - G0[k]);
+            }
+            if (w.y != 0.0) {
+                const double sg = (m & M_YPOS) ? 1.0 : -1.0;
+                double Gi[4], G0[4];
+                split_flux(sg, si, un_i, us_i, rE_i, Gi);
+                split_flux(sg, s0, un_0, us_0, rE_0, G0);
+                // Gn components are [mass, n-momentum, s-momentum, energy]
+                R[0] += w.y * (Gi[0] - G0[0]);
+                R[1] += w.y * (Gi[2] - G0[2]);
+                R[2] += w.y * (Gi[1] - G0[1]);
+                R[3] += w.y * (Gi[3] - G0[3]);
+            }
+        }
+        if (!ok) flag_nonphysical(P.status, p);
+        Rg[0] = R[0];
+        Rg[1] = R[1] * tx + R[2] * n0.x;
+        Rg[2] = R[1] * ty + R[2] * n0.y;
+        Rg[3] = R[3];
+    }
+
+    if (P.mode == 0) {
+        if (live) store4(P.R, p, Rg);
+        return;
+    }
+
+    // ---- time step and state update ----
+    if (live) {
+        double Un[4], Unew[4];
+        load4(P.Un, p, Un);
+        double dt;
+        if (P.mode == 1 || P.stage == 0) {
+            // timestep(): dt = CFL min|P_i - P_0| / (|u| + 3 sqrt(p/rho))
+            const double rho = Un[0], u = Un[1] / rho, v = Un[2] / rho;
+            const double pr = (P.gas.gamma - 1.0) * (Un[3] - 0.5 * rho * (u * u + v * v));
+            dt = P.cfl * g.dmin[p] / (sqrt(u * u + v * v) + 3.0 * sqrt(pr / rho));
+            P.dt[p] = dt;
+        } else {
+            dt = P.dt[p];
+        }
+        if (P.mode == 1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Unew[k] = Un[k] - dt * Rg[k];
+        } else {
+            double a[4];
+            if (P.stage == 0) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) a[k] = Rg[k];
+            } else {
+                load4(P.acc, p, a);
+                if (P.stage < 3) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) a[k] = a[k] + 2.0 * Rg[k];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) a[k] = a[k] + Rg[k];
+                }
+            }
+            if (P.stage < 3) {
+                store4(P.acc, p, a);
+                const double c = (P.stage == 2) ? dt : 0.5 * dt;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Unew[k] = Un[k] - c * Rg[k];
+            } else {
+                const double c = dt / 6.0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Unew[k] = Un[k] - c * a[k];
+            }
+        }
+        if (flag == FLAG_WALL) {
+            const double2 n0 = g.nrm[p];
+            const double mn = Unew[1] * n0.x + Unew[2] * n0.y;
+            Unew[1] = Unew[1] - mn * n0.x;
+            Unew[2] = Unew[2] - mn * n0.y;
+        } else if (flag == FLAG_FARFIELD) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Unew[k] = P.gas.Uinf[k];
+        }
+        store4(P.Uout, p, Unew);
+        double qn[4];
+        if (!q_from_U(Unew, P.gas, qn)) flag_nonphysical(P.status, p);
+        store4(P.qout, p, qn);
+    }
+
+    // ---- residue partials: block sum of R_rho^2 at stage 0 ----
+    if (P.mode == 1 || P.stage == 0) {
+        double s = Rg[0] * Rg[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        __shared__ double ws[4];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) ws[wid] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) P.norm_part[blockIdx.x] = (ws[0] + ws[1]) + (ws[2] + ws[3]);
+    }
+}
+
+// residue() = sqrt(sum R_rho^2)/n from the block partials, in a fixed order
+__global__ void __launch_bounds__(256) k_residue_finish(const double *__restrict__ part, int nparts,
+                                                        double inv_n, double *__restrict__ out)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+    __shared__ double sm[256];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sqrt(sm[0]) * inv_n;
+}
+
+// q-variables of every point from U (used when a state is loaded)
+__global__ void __launch_bounds__(256) k_q_from_U(int64_t n, Gas gas, const double *__restrict__ U,
+                                                  double *__restrict__ q, int *status)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double u[4], qq[4];
+    load4(U, p, u);
+    if (!q_from_U(u, gas, qq)) flag_nonphysical(status, p);
+    store4(q, p, qq);
+}
+
+// timestep() alone: dt = CFL min|P_i - P_0| / (|u| + 3 sqrt(p/rho)) from U
+__global__ void __launch_bounds__(256) k_timestep(int64_t n, Gas gas, double cfl,
+                                                  const double *__restrict__ dmin,
+                                                  const double *__restrict__ U, double *__restrict__ dt)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double Un[4];
+    load4(U, p, Un);
+    const double rho = Un[0], u = Un[1] / rho, v = Un[2] / rho;
+    const double pr = (gas.gamma - 1.0) * (Un[3] - 0.5 * rho * (u * u + v * v));
+    dt[p] = cfl * dmin[p] / (sqrt(u * u + v * v) + 3.0 * sqrt(pr / rho));
+}
+
+// forces: per wall point (contour order) Cp and -Cp n ds; one block sums them
+__global__ void __launch_bounds__(256) k_forces(int64_t nwall, Gas gas, double qinf,
+                                                const int32_t *__restrict__ wall,
+                                                const double *__restrict__ ds,
+                                                const double2 *__restrict__ nrm,
+                                                const double *__restrict__ U, double cosa, double sina,
+                                                double *__restrict__ cp, double *__restrict__ clcd)
+{
+    __shared__ double sx[256], sy[256];
+    double fx = 0.0, fy = 0.0;
+    const double p_inf = 1.0 / gas.gamma;
+    for (int64_t w = threadIdx.x; w < nwall; w += blockDim.x) {
+        const int p = wall[w];
+        double u[4];
+        load4(U, p, u);
+        const double rho = u[0], a = u[1] / rho, b = u[2] / rho;
+        const double pr = (gas.gamma - 1.0) * (u[3] - 0.5 * rho * (a * a + b * b));
+        const double c = (pr - p_inf) / qinf;
+        cp[w] = c;
+        const double2 n = nrm[p];
+        fx -= c * n.x * ds[w];
+        fy -= c * n.y * ds[w];
+    }
+    sx[threadIdx.x] = fx;
+    sy[threadIdx.x] = fy;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sx[threadIdx.x] += sx[threadIdx.x + w];
+            sy[threadIdx.x] += sy[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        clcd[0] = sy[0] * cosa - sx[0] * sina;
+        clcd[1] = sx[0] * cosa + sy[0] * sina;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_qgrad(const DevGeom &g, const double *q, const double *qg_old, double *qg_new,
+                         double limiter_K, cudaStream_t s)
+{
+    k_qgrad<<<blocks_for(g.n, 128), 128, 0, s>>>(g, q, qg_old, qg_new, limiter_K);
+    return cudaGetLastError();
+}
+
+unsigned flux_blocks(int64_t n) { return blocks_for(n, 128); }
+
+cudaError_t launch_flux(const DevGeom &g, const Gas &gas, const FluxLaunch &L, cudaStream_t s)
+{
+    FluxParams P;
+    P.g = g;
+    P.gas = gas;
+    P.q = L.q; P.qg = L.qg; P.Un = L.Un; P.Uout = L.Uout; P.acc = L.acc; P.qout = L.qout;
+    P.dt = L.dt; P.R = L.R; P.norm_part = L.norm_part; P.status = L.status;
+    P.cfl = L.cfl; P.order = L.order; P.mode = L.mode; P.stage = L.stage;
+    k_flux_update<<<blocks_for(g.n, 128), 128, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residue_finish(const double *part, int nparts, int64_t n, double *out, cudaStream_t s)
+{
+    k_residue_finish<<<1, 256, 0, s>>>(part, nparts, 1.0 / (double)n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_q_from_U(int64_t n, const Gas &gas, const double *U, double *q, int *status,
+                            cudaStream_t s)
+{
+    k_q_from_U<<<blocks_for(n, 256), 256, 0, s>>>(n, gas, U, q, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_timestep(int64_t n, const Gas &gas, double cfl, const double *dmin, const double *U,
+                            double *dt, cudaStream_t s)
+{
+    k_timestep<<<blocks_for(n, 256), 256, 0, s>>>(n, gas, cfl, dmin, U, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces(int64_t nwall, const Gas &gas, double qinf, const int32_t *wall,
+                          const double *ds, const double2 *nrm, const double *U, double cosa,
+                          double sina, double *cp, double *clcd, cudaStream_t s)
+{
+    k_forces<<<1, 256, 0, s>>>(nwall, gas, qinf, wall, ds, nrm, U, cosa, sina, cp, clcd);
+    return cudaGetLastError();
+}
+
+}  // namespace lskum

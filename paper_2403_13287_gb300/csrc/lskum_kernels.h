@@ -1,0 +1,67 @@
+// Host-side launchers of the hot-path kernels (lskum_kernels.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lskum_device.cuh"
+
+namespace lskum {
+
+struct FluxLaunch {
+    const double *q;
+    const double *qg;
+    const double *Un;
+    double *Uout;
+    double *acc;
+    double *qout;
+    double *dt;
+    double *R;
+    double *norm_part;
+    int *status;
+    double cfl;
+    int order;
+    int mode;   // 0 residual only, 1 forward Euler, 2 RK4 stage
+    int stage;
+};
+
+unsigned flux_blocks(int64_t n);
+cudaError_t launch_qgrad(const DevGeom &g, const double *q, const double *qg_old, double *qg_new,
+                         double limiter_K, cudaStream_t s);
+cudaError_t launch_flux(const DevGeom &g, const Gas &gas, const FluxLaunch &L, cudaStream_t s);
+cudaError_t launch_residue_finish(const double *part, int nparts, int64_t n, double *out,
+                                  cudaStream_t s);
+cudaError_t launch_q_from_U(int64_t n, const Gas &gas, const double *U, double *q, int *status,
+                            cudaStream_t s);
+cudaError_t launch_timestep(int64_t n, const Gas &gas, double cfl, const double *dmin, const double *U,
+                            double *dt, cudaStream_t s);
+cudaError_t launch_forces(int64_t nwall, const Gas &gas, double qinf, const int32_t *wall,
+                          const double *ds, const double2 *nrm, const double *U, double cosa,
+                          double sina, double *cp, double *clcd, cudaStream_t s);
+
+// create-time geometry (lskum_setup.cu)
+cudaError_t launch_geometry(int64_t n, const double2 *xy, const double2 *nrm, const uint8_t *flag,
+                            const int32_t *off, const int32_t *idx, uint8_t *mask, double2 *lsw,
+                            double2 *fxw, double *dmin, int *bad, cudaStream_t s);
+cudaError_t morton_permutation(int64_t n, const double2 *xy, double xmin, double ymin, double scale,
+                               int32_t *perm, cudaStream_t s);
+cudaError_t launch_permute_points(int64_t n, const int32_t *perm, const double *x, const double *y,
+                                  const double *nx, const double *ny, const int32_t *flags,
+                                  double2 *xy, double2 *nrm, uint8_t *flag, int32_t *inv,
+                                  cudaStream_t s);
+cudaError_t permute_csr(int64_t n, const int32_t *perm, const int32_t *inv, const int32_t *off_in,
+                        const int32_t *idx_in, int32_t *off_out, int32_t *idx_out, cudaStream_t s);
+cudaError_t launch_state_in(int64_t n, const int32_t *perm, const double *Uin_cm, double *U_pm,
+                            cudaStream_t s);
+cudaError_t launch_state_out(int64_t n, const int32_t *perm, const double *U_pm, double *Uout_cm,
+                             cudaStream_t s);
+cudaError_t launch_grad_out(int64_t n, const int32_t *perm, const double *qg, double *qx_cm,
+                            double *qy_cm, cudaStream_t s);
+cudaError_t launch_scalar_out(int64_t n, const int32_t *perm, const double *v, double *out,
+                              cudaStream_t s);
+cudaError_t launch_mask_out(int64_t n, const int32_t *inv, const int32_t *off_in,
+                            const int32_t *off_int, const uint8_t *mask_int, uint8_t *mask_in,
+                            cudaStream_t s);
+cudaError_t launch_fill_state(int64_t n, const double Uinf[4], double *U, cudaStream_t s);
+
+}  // namespace lskum

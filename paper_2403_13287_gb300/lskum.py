@@ -1,0 +1,238 @@
+"""Thin Python binding of the C ABI in include/lskum.h (liblskum.so).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of the shared library. Device arrays are torch CUDA tensors (float64,
+contiguous, component-major [4, n]); host arrays are numpy arrays. There is
+no CPU fallback: if the library cannot be loaded, importing its functions
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LSKUM_OK = 0
+LSKUM_ERR_ARG = 1
+LSKUM_ERR_CONNECTIVITY = 2
+LSKUM_ERR_DEGENERATE_STENCIL = 3
+LSKUM_ERR_CUDA = 4
+LSKUM_ERR_OOM = 5
+LSKUM_ERR_NONPHYSICAL = 6
+LSKUM_ERR_TIMEOUT = 7
+
+LSKUM_KERNEL_FLUX = 0
+LSKUM_KERNEL_QGRAD = 1
+
+_STATUS_NAMES = {0: "LSKUM_OK", 1: "LSKUM_ERR_ARG", 2: "LSKUM_ERR_CONNECTIVITY",
+                 3: "LSKUM_ERR_DEGENERATE_STENCIL", 4: "LSKUM_ERR_CUDA", 5: "LSKUM_ERR_OOM",
+                 6: "LSKUM_ERR_NONPHYSICAL", 7: "LSKUM_ERR_TIMEOUT"}
+
+
+class lskum_config(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("inner_iters", ctypes.c_int),
+                ("time_scheme", ctypes.c_int), ("cfl", ctypes.c_double),
+                ("mach", ctypes.c_double), ("aoa_deg", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("precision", ctypes.c_int),
+                ("reorder", ctypes.c_int), ("limiter_K", ctypes.c_double)]
+
+
+class LskumError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+_lib = None
+_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblskum.so (building it first if asked and needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("liblskum.so not found at %s: run __graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
+    L.lskum_create.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _p, _i64, _p,
+                               ctypes.POINTER(lskum_config), _p, ctypes.POINTER(_p)]
+    L.lskum_create.restype = _int
+    L.lskum_destroy.argtypes = [_p]
+    L.lskum_destroy.restype = None
+    L.lskum_last_error.argtypes = [_p]
+    L.lskum_last_error.restype = ctypes.c_char_p
+    L.lskum_step.argtypes = [_p, _int, _p]
+    L.lskum_residual.argtypes = [_p, _p, _p]
+    L.lskum_q_derivatives.argtypes = [_p, _p, _p, _p]
+    L.lskum_timestep.argtypes = [_p, _p, _p]
+    L.lskum_forces.argtypes = [_p, _p, _p, _p]
+    L.lskum_get_state.argtypes = [_p, _p, _int]
+    L.lskum_set_state.argtypes = [_p, _p, _int]
+    L.lskum_get_stencil_masks.argtypes = [_p, _p]
+    L.lskum_get_permutation.argtypes = [_p, _p]
+    L.lskum_launch_count.argtypes = [_p]
+    L.lskum_launch_count.restype = _i64
+    L.lskum_profile.argtypes = [_p, _int]
+    L.lskum_kernel_time.argtypes = [_p, _int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]
+    for name in ("lskum_step", "lskum_residual", "lskum_q_derivatives", "lskum_timestep",
+                 "lskum_forces", "lskum_get_state", "lskum_set_state", "lskum_get_stencil_masks",
+                 "lskum_get_permutation", "lskum_profile", "lskum_kernel_time"):
+        getattr(L, name).restype = _int
+    _lib = L
+    return L
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(_p)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return _p(t.data_ptr())
+
+
+class Solver:
+    """A q-LSKUM context (lskum_ctx) on the current CUDA device."""
+
+    def __init__(self, cloud, order=2, inner_iters=3, time_scheme=1, cfl=0.2, mach=0.63,
+                 aoa_deg=2.0, gamma=1.4, precision=0, reorder=0, limiter_K=0.0, stream=None):
+        L = load()
+        self._L = L
+        self.n = int(cloud["n"])
+        self.cfg = lskum_config(order, inner_iters, time_scheme, cfl, mach, aoa_deg, gamma,
+                                precision, reorder, limiter_K)
+        self._keep = {k: np.ascontiguousarray(cloud[k], dtype=np.float64) for k in ("x", "y", "nx", "ny")}
+        for k in ("flags", "nbr_offsets", "nbr_idx"):
+            self._keep[k] = np.ascontiguousarray(cloud[k], dtype=np.int32)
+        wo = cloud.get("wall_order")
+        self._keep["wall_order"] = np.ascontiguousarray(wo if wo is not None else np.zeros(0), dtype=np.int32)
+        self.nnz = int(self._keep["nbr_offsets"][-1])
+        self.n_wall = int(self._keep["wall_order"].shape[0])
+        if stream is None:
+            try:
+                import torch
+                stream_ptr = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except Exception:  # noqa: BLE001
+                stream_ptr = 0
+        else:
+            stream_ptr = int(stream)
+        ctx = _p()
+        k = self._keep
+        st = L.lskum_create(self.n, _np_ptr(k["x"]), _np_ptr(k["y"]), _np_ptr(k["nx"]), _np_ptr(k["ny"]),
+                            _np_ptr(k["flags"]), _np_ptr(k["nbr_offsets"]), _np_ptr(k["nbr_idx"]),
+                            self.n_wall, _np_ptr(k["wall_order"]), ctypes.byref(self.cfg),
+                            _p(stream_ptr) if stream_ptr else None, ctypes.byref(ctx))
+        if st != LSKUM_OK:
+            raise LskumError(st, L.lskum_last_error(None).decode())
+        self._ctx = ctx
+
+    def _check(self, st):
+        if st != LSKUM_OK:
+            raise LskumError(st, self._L.lskum_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._L.lskum_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    # --- hot path ---
+    def step(self, n_iters, history=True):
+        hist = np.zeros(n_iters) if history else None
+        self._check(self._L.lskum_step(self._ctx, int(n_iters), _np_ptr(hist) if history else None))
+        return hist
+
+    def residual(self, U=None, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((4, self.n), dtype=torch.float64, device="cuda")
+        self._check(self._L.lskum_residual(self._ctx, _dev_ptr(U), _dev_ptr(out)))
+        return out
+
+    def q_derivatives(self, U=None):
+        import torch
+        qx = torch.empty((4, self.n), dtype=torch.float64, device="cuda")
+        qy = torch.empty_like(qx)
+        self._check(self._L.lskum_q_derivatives(self._ctx, _dev_ptr(U), _dev_ptr(qx), _dev_ptr(qy)))
+        return qx, qy
+
+    def timestep(self, U=None):
+        import torch
+        dt = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        self._check(self._L.lskum_timestep(self._ctx, _dev_ptr(U), _dev_ptr(dt)))
+        return dt
+
+    def forces(self, want_cp=True):
+        cl = ctypes.c_double()
+        cd = ctypes.c_double()
+        cp = np.zeros(self.n_wall) if want_cp else None
+        self._check(self._L.lskum_forces(self._ctx, ctypes.byref(cl), ctypes.byref(cd),
+                                         _np_ptr(cp) if want_cp else None))
+        return cl.value, cd.value, cp
+
+    # --- state ---
+    def get_state(self, out=None):
+        """State U as a [4, n] array: into `out` (a CUDA tensor or a contiguous
+        float64 numpy array) or a new host numpy array."""
+        if isinstance(out, np.ndarray):
+            if not (out.dtype == np.float64 and out.flags.c_contiguous and out.size == 4 * self.n):
+                raise TypeError("expected a contiguous float64 array of 4*n values")
+            self._check(self._L.lskum_get_state(self._ctx, _np_ptr(out), 1))
+            return out
+        if out is not None:
+            self._check(self._L.lskum_get_state(self._ctx, _dev_ptr(out), 0))
+            return out
+        U = np.empty((4, self.n))
+        self._check(self._L.lskum_get_state(self._ctx, _np_ptr(U), 1))
+        return U
+
+    def set_state(self, U):
+        if isinstance(U, np.ndarray):
+            Uh = np.ascontiguousarray(U, dtype=np.float64)
+            self._check(self._L.lskum_set_state(self._ctx, _np_ptr(Uh), 1))
+        else:
+            self._check(self._L.lskum_set_state(self._ctx, _dev_ptr(U), 0))
+
+    def stencil_masks(self):
+        m = np.empty(self.nnz, dtype=np.uint8)
+        self._check(self._L.lskum_get_stencil_masks(self._ctx, _np_ptr(m)))
+        return m
+
+    def permutation(self):
+        p = np.empty(self.n, dtype=np.int32)
+        self._check(self._L.lskum_get_permutation(self._ctx, _np_ptr(p)))
+        return p
+
+    def launch_count(self):
+        return int(self._L.lskum_launch_count(self._ctx))
+
+    # --- kernel timing ---
+    def profile(self, enable=True):
+        self._check(self._L.lskum_profile(self._ctx, 1 if enable else 0))
+
+    def kernel_time(self, kernel_class):
+        """(summed milliseconds, launches) of one kernel class since profile(True)."""
+        ms = ctypes.c_double()
+        cnt = _i64()
+        self._check(self._L.lskum_kernel_time(self._ctx, int(kernel_class), ctypes.byref(ms), ctypes.byref(cnt)))
+        return ms.value, cnt.value

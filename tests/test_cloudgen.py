@@ -30,10 +30,17 @@ def test_csr_well_formed(cloud):
     assert np.all(idx != rows)
     pairs = rows.astype(np.int64) * n + idx
     assert len(np.unique(pairs)) == len(pairs)
-    # rows ordered by distance
-    d = np.hypot(cloud["x"][idx] - cloud["x"][rows], cloud["y"][idx] - cloud["y"][rows])
-    same_row = rows[1:] == rows[:-1]
-    assert np.all(d[1:][same_row] >= d[:-1][same_row])
+    # quadrant balance: interior points have at least two neighbours clearly
+    # inside each half-plane of their frame
+    dx = cloud["x"][idx] - cloud["x"][rows]
+    dy = cloud["y"][idx] - cloud["y"][rows]
+    nx, ny = cloud["nx"][rows], cloud["ny"][rows]
+    dt, dn = dx * ny - dy * nx, dx * nx + dy * ny
+    dist = np.hypot(dx, dy)
+    interior = cloud["flags"][rows] == 0
+    for half in (dt < -0.05 * dist, dt > 0.05 * dist, dn < -0.05 * dist, dn > 0.05 * dist):
+        cnt = np.bincount(rows[half & interior], minlength=n)
+        assert np.all(cnt[cloud["flags"] == 0] >= 2)
 
 
 def test_geometry(cloud):

@@ -485,10 +485,11 @@ def test_forces_divergence_theorem(a, b, cx, mach, aoa):
 
 
 def test_mirror_symmetric_cloud_gives_zero_lift_at_zero_incidence():
-    c = naca0012_cloud(96, 12, seed=5, mirror=True)
+    c = naca0012_cloud(128, 24, seed=5, mirror=True)
     m = oracle.split_stencils(c)
     U0 = oracle.freestream_state(c["n"], 0.63, 0.0)
-    U, hist = oracle.solve(c, m, U0, 30, order=2, inner=3, scheme=1, cfl=0.2, mach=0.63, aoa_deg=0.0)
+    U, hist = oracle.solve(c, m, U0, 30, order=2, inner=3, scheme=1, cfl=0.2, mach=0.63, aoa_deg=0.0,
+                           limiter=1.0)
     cl, cd, cp = oracle.forces(c, U, 0.63, 0.0)
     assert abs(cl) < 1e-11 and cd != 0.0
     # the state itself is mirror-symmetric: point (i, j) <-> (W - i, j)
@@ -499,3 +500,68 @@ def test_mirror_symmetric_cloud_gives_zero_lift_at_zero_incidence():
     assert np.allclose(U[0], U[0][mi], rtol=0, atol=1e-12)
     assert np.allclose(U[1], U[1][mi], rtol=0, atol=1e-12)
     assert np.allclose(U[2], -U[2][mi], rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Venkatakrishnan limiter (optional; not in the paper)
+# --------------------------------------------------------------------------
+
+def _line_cloud(q_values, h=0.1):
+    """Point 0 at the origin with neighbours at (+-h, 0), (0, +-h)."""
+    xs = [0.0, h, -h, 0.0, 0.0]
+    ys = [0.0, 0.0, 0.0, h, -h]
+    c = _cloud(xs, ys, [0.0] * 5, [1.0] * 5, [0] + [2] * 4, [[1, 2, 3, 4], [0, 3, 4], [0, 3, 4],
+                                                             [0, 1, 2], [0, 1, 2]])
+    q = np.zeros((4, 5))
+    q[0] = q_values
+    return c, q
+
+
+def test_limiter_keeps_linear_fields_on_symmetric_stencils():
+    """For q linear, each half shift is half a neighbour difference, inside
+    [q_min - q_0, q_max - q_0] by a factor 2, where f >= 1: no limiting."""
+    c, q = _line_cloud([0.0, 0.3, -0.3, 0.2, -0.2])
+    gx = np.zeros((4, 5)); gy = np.zeros((4, 5))
+    gx[0, 0], gy[0, 0] = 3.0, 2.0
+    lx, ly = oracle.limit_gradients(c, q, gx, gy, 1e-6)
+    # the largest shift is exactly D/2, where f = 1 up to rounding
+    assert abs(lx[0, 0] - 3.0) < 1e-14 and abs(ly[0, 0] - 2.0) < 1e-14
+
+
+def test_limiter_worked_value():
+    """Hand value of the published function: with D/d = 1 and e = 0,
+    f = (1 + 2)/(1 + 2 + 1) = 3/4. Neighbour values 0.1 and -0.5 around q_0 = 0
+    and grad (2, 0): shifts +-0.1 on the x edges; D+ = 0.1 -> f = 3/4,
+    D- = -0.5 -> f(-0.5, -0.1) = (0.25 + 0.1)/(0.25 + 0.02 + 0.05) = 1.09375 (> 1)."""
+    c, q = _line_cloud([0.0, 0.1, -0.5, 0.0, 0.0])
+    gx = np.zeros((4, 5)); gy = np.zeros((4, 5))
+    gx[0, 0] = 2.0
+    lx, _ = oracle.limit_gradients(c, q, gx, gy, 1e-9)
+    assert abs(lx[0, 0] - 2.0 * 0.75) < 1e-9
+
+
+def test_limiter_flattens_extrema_and_bounds_reconstruction():
+    """At a local maximum (q_0 above every neighbour) the limited gradient is
+    ~0 for e -> 0; in general the limited shifts +-(P_i - P_0).grad/2 stay
+    within the neighbour range (f d <= D for e = 0)."""
+    c, q = _line_cloud([1.0, 0.3, 0.2, 0.5, 0.4])
+    gx = np.full((4, 5), 0.0); gy = np.zeros((4, 5))
+    gx[0, 0] = 4.0
+    lx, _ = oracle.limit_gradients(c, q, gx, gy, 1e-9)
+    assert abs(lx[0, 0]) < 1e-12
+    rng = np.random.default_rng(12)
+    cl = naca0012_cloud(64, 12, seed=2)
+    qq = rng.normal(size=(4, cl["n"]))
+    ox, oy = oracle.q_derivatives(cl, qq, inner=0)
+    lx, ly = oracle.limit_gradients(cl, qq, ox, oy, 1e-9)
+    off, idx = cl["nbr_offsets"], cl["nbr_idx"]
+    for p in range(cl["n"]):
+        nb = idx[off[p]:off[p + 1]]
+        dx = cl["x"][nb] - cl["x"][p]
+        dy = cl["y"][nb] - cl["y"][p]
+        for k in range(4):
+            qs = np.concatenate([[qq[k, p]], qq[k, nb]])
+            shift = 0.5 * (dx * lx[k, p] + dy * ly[k, p])
+            lo, hi = qs.min() - qq[k, p], qs.max() - qq[k, p]
+            assert np.all(shift <= hi + 1e-9) and np.all(-shift <= hi + 1e-9)
+            assert np.all(shift >= lo - 1e-9) and np.all(-shift >= lo - 1e-9)
