@@ -174,8 +174,11 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
                 double Gi[4], G0[4];
                 split_flux(sg, si, us_i, un_i, rE_i, Gi);
                 split_flux(sg, s0, us_0, un_0, rE_0, G0);
+                // dG = G(q~_i) - G(q~_0) from the two rounded fluxes: an unfused
+                // subtraction, so equal states give exactly zero (a contracted
+                // fma(rho_i, m_i, -rho_0 m_0) would leave a product's rounding)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) R[k] += w.x * (Gi[k] - G0[k]);
+                for (int k = 0; k < 4; ++k) R[k] += w.x * __dsub_rn(Gi[k], G0[k]);
             }
             if (w.y != 0.0) {
                 const double sg = (m & M_YPOS) ? 1.0 : -1.0;
@@ -183,10 +186,10 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
                 split_flux(sg, si, un_i, us_i, rE_i, Gi);
                 split_flux(sg, s0, un_0, us_0, rE_0, G0);
                 // Gn components are [mass, n-momentum, s-momentum, energy]
-                R[0] += w.y * (Gi[0] - G0[0]);
-                R[1] += w.y * (Gi[2] - G0[2]);
-                R[2] += w.y * (Gi[1] - G0[1]);
-                R[3] += w.y * (Gi[3] - G0[3]);
+                R[0] += w.y * __dsub_rn(Gi[0], G0[0]);
+                R[1] += w.y * __dsub_rn(Gi[2], G0[2]);
+                R[2] += w.y * __dsub_rn(Gi[1], G0[1]);
+                R[3] += w.y * __dsub_rn(Gi[3], G0[3]);
             }
         }
         if (!ok) flag_nonphysical(P.status, p);
