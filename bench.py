@@ -141,6 +141,29 @@ def algorithmic_bytes_per_point(kernel, dbar, order, scheme, stage_avg=True):
     raise ValueError(kernel)
 
 
+# Per-unit figures of the FP64 fused flux kernel, from one ncu capture of the
+# same kernel (profiles/k_flux_update_fp64_naca0012_640k.md): executed FP64
+# flops per stencil edge (2 DFMA + DMUL + DADD) and DRAM bytes per point.
+FP64_FLOPS_PER_EDGE_FLUX = 778.0
+FLUX_DRAM_BYTES_PER_POINT = 456.4
+# FP64 peak: ncu's DFMA unit count (304 thread-FMA per cycle) x 2 flops x the
+# 2070 MHz maximum SM clock
+FP64_PEAK_GFLOPS = 304 * 2 * 2.070
+
+
+def roofline_fp64(flux_avg_s, n, dbar, fb, achieved_gbs, peaks, peak_src):
+    flops = FP64_FLOPS_PER_EDGE_FLUX * dbar * n
+    achieved = flops / flux_avg_s / 1e9
+    return {"bound": "alu", "kernel": "k_flux_update", "achieved": achieved,
+            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS,
+            "traffic": FLUX_DRAM_BYTES_PER_POINT * n,
+            "flops_per_launch": flops, "avg_launch_ms": flux_avg_s * 1e3,
+            "peak_source": "derived: 304 DFMA/cycle x 2 x 2.07 GHz",
+            "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved_gbs / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": fb,
+                    "peak_source": peak_src}}
+
+
 # ----------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle on the host cores
 # ----------------------------------------------------------------------------
@@ -301,10 +324,7 @@ def run_ours(args, rank, world, local):
                    "l2": "inputs larger than L2 (working set ~%.1f GB)" % (
                        (n * 380 + cloud["nbr_offsets"][-1] * 37) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "hbm", "kernel": "k_flux_update", "achieved": achieved_gbs,
-                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
-                     "traffic": None, "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": fb, "avg_launch_ms": flux_avg_s * 1e3},
+        "roofline": roofline_fp64(flux_avg_s, n, dbar, fb, achieved_gbs, peaks, peak_src),
         "kernels": {"k_flux_update": {"launches": flux_n, "total_ms": flux_ms},
                     "k_qgrad": {"launches": qg_n, "total_ms": qg_ms}},
         "gpu_launches": launches,
