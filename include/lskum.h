@@ -170,6 +170,46 @@ lskum_status lskum_get_permutation(lskum_ctx *ctx, int32_t *perm);
 /* Number of kernel launches the library has issued on this context so far. */
 int64_t lskum_launch_count(const lskum_ctx *ctx);
 
+/*
+ * q-derivatives without any device allocation, for callers that cannot
+ * allocate device memory where they call from: a framework whose caching
+ * allocator owns the GPU's memory, a step loop that must not pay the device
+ * synchronisation that cudaMalloc/cudaFree imply, or a process that was
+ * handed a fixed memory budget. It needs no context either. The paper has no
+ * counterpart: this is a plumbing variant of lskum_q_derivatives.
+ *
+ * Computes q (E13) from U and the least-squares q-derivatives of E15 (the
+ * first-order solve, then inner_iters Jacobi inner iterations), in the global
+ * frame, with the 2x2 sums formed on the fly; no limiter. All pointers are
+ * caller-owned device memory, in the caller's numbering:
+ *   n                     number of points, 1 <= n <= LSKUM_NOALLOC_MAX_POINTS
+ *   x, y                  float64[n]
+ *   nbr_offsets, nbr_idx  int32[n+1], int32[nbr_offsets[n]]: a well-formed CSR
+ *                         (the caller's responsibility; a neighbour index outside
+ *                         [0, n) is skipped and reported as LSKUM_ERR_CONNECTIVITY)
+ *   U                     float64[4*n] conserved state (component-major)
+ *   qx, qy                float64[4*n], written
+ *   cuda_stream           cudaStream_t, or NULL for the legacy default stream
+ * Scratch (q and two gradient buffers, 160 bytes per point) lives in one
+ * statically sized __device__ array of LSKUM_NOALLOC_MAX_POINTS points
+ * (21 MB), which every GPU that loads the library holds until the process
+ * exits. The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls share the one array: calls whose
+ * work overlaps on the GPU (other threads, other streams) race and must be
+ * serialised by the caller. The call synchronises the stream at its end to
+ * read its status word. A point whose stencil has a singular 2x2
+ * least-squares matrix gets non-finite derivatives. Errors: LSKUM_ERR_ARG (n out of range, NULL pointer,
+ * inner_iters outside [0, 1000]), LSKUM_ERR_CONNECTIVITY, LSKUM_ERR_NONPHYSICAL
+ * (a point with rho <= 0 or p <= 0), LSKUM_ERR_CUDA; message via
+ * lskum_last_error(NULL).
+ */
+#define LSKUM_NOALLOC_MAX_POINTS 131072
+lskum_status lskum_q_derivatives_noalloc(int64_t n, const double *x, const double *y,
+                                         const int32_t *nbr_offsets, const int32_t *nbr_idx,
+                                         const double *U, double gamma, int inner_iters,
+                                         double *qx, double *qy, void *cuda_stream);
+
 /* Kernel classes for lskum_kernel_time */
 #define LSKUM_KERNEL_FLUX 0  /* fused flux residual + state update */
 #define LSKUM_KERNEL_QGRAD 1 /* one least-squares q-derivative pass */

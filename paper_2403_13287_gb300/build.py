@@ -1,6 +1,6 @@
 """Build the CUDA library (liblskum.so) for sm_103a with nvcc, in-tree.
 
-The three translation units compile in parallel and link into
+The translation units compile in parallel and link into
 paper_2403_13287_gb300/_build/liblskum.so. CUDA runtime is linked statically.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblskum.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["lskum_api.cu", "lskum_kernels.cu", "lskum_setup.cu"]
+SOURCES = ["lskum_api.cu", "lskum_kernels.cu", "lskum_setup.cu", "lskum_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -62,6 +62,11 @@ struct lskum_ctx {
 
 static thread_local std::string g_create_error;
 
+namespace lskum {
+// error text for calls without a context (lskum_last_error(NULL))
+void set_global_error(const char *msg) { g_create_error = msg; }
+}  // namespace lskum
+
 static lskum_status fail(lskum_ctx *c, lskum_status st, const char *fmt, ...)
 {
     char buf[512];

@@ -39,6 +39,9 @@ cudaError_t launch_forces(int64_t nwall, const Gas &gas, double qinf, const int3
                           const double *ds, const double2 *nrm, const double *U, double cosa,
                           double sina, double *cp, double *clcd, cudaStream_t s);
 
+// error text for calls without a context (lskum_api.cu)
+void set_global_error(const char *msg);
+
 // create-time geometry (lskum_setup.cu)
 cudaError_t launch_geometry(int64_t n, const double2 *xy, const double2 *nrm, const uint8_t *flag,
                             const int32_t *off, const int32_t *idx, uint8_t *mask, double2 *lsw,

@@ -236,3 +236,32 @@ class Solver:
         cnt = _i64()
         self._check(self._L.lskum_kernel_time(self._ctx, int(kernel_class), ctypes.byref(ms), ctypes.byref(cnt)))
         return ms.value, cnt.value
+
+
+LSKUM_NOALLOC_MAX_POINTS = 131072
+
+
+def q_derivatives_noalloc(x, y, nbr_offsets, nbr_idx, U, qx, qy, gamma=1.4, inner_iters=3,
+                          stream=None):
+    """lskum_q_derivatives_noalloc on caller-owned CUDA tensors (no context,
+    no device allocation): x, y float64[n]; nbr_offsets int32[n+1]; nbr_idx
+    int32[nnz]; U float64[4, n]; qx, qy float64[4, n] written."""
+    import torch
+    L = load()
+    if not hasattr(L, "_noalloc_ready"):
+        L.lskum_q_derivatives_noalloc.argtypes = [_i64, _p, _p, _p, _p, _p, ctypes.c_double, _int,
+                                                  _p, _p, _p]
+        L.lskum_q_derivatives_noalloc.restype = _int
+        L._noalloc_ready = True
+    for t, dt in ((nbr_offsets, torch.int32), (nbr_idx, torch.int32)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError("expected a contiguous int32 CUDA tensor")
+    n = int(x.shape[0])
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = L.lskum_q_derivatives_noalloc(n, _dev_ptr(x), _dev_ptr(y), _p(nbr_offsets.data_ptr()),
+                                       _p(nbr_idx.data_ptr()), _dev_ptr(U), float(gamma),
+                                       int(inner_iters), _dev_ptr(qx), _dev_ptr(qy),
+                                       _p(int(stream)) if stream else None)
+    if st != LSKUM_OK:
+        raise LskumError(st, L.lskum_last_error(None).decode())
