@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--aoa", type=float, default=0.0)
     ap.add_argument("--cfl", type=float, default=0.2)
     ap.add_argument("--limiter", type=float, default=1.0, help="Venkatakrishnan K (0: none)")
-    ap.add_argument("--precision", choices=["fp64"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--reorder", type=int, default=1)
     ap.add_argument("--shuffle", type=int, default=1, help="present the cloud in random point order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -139,6 +139,22 @@ def algorithmic_bytes_per_point(kernel, dbar, order, scheme, stage_avg=True):
     if kernel == "qgrad_inner":
         return 32 + 64 + 16 + 4 + dbar * (4 + 16) + 64
     raise ValueError(kernel)
+
+
+def algorithmic_bytes_per_point_mixed(dbar, order, scheme):
+    """Fused flux kernel, mixed layout: q 16 (FP32), own q-derivatives 32,
+    normal 8, flag 1, CSR offset 4, per edge index 4 + mask 1 + FP32 flux
+    weights 8 (+ FP32 offset 8 at order 2); U^n 32, U_out 32 (FP64), q_out 16;
+    RK4 terms averaged over the 4 stages: dt and dmin at stage 0, acc written
+    at stages 0-2 and read at 1-3 (FP64)."""
+    b = 16 + 8 + 1 + 4 + dbar * (4 + 1 + 8) + 32 + 32 + 16
+    if order == 2:
+        b += 32 + dbar * 8
+    if scheme == "rk4":
+        b += (8 + 4 + 3 * 8 + 3 * 32 + 3 * 32) / 4.0
+    else:
+        b += 8 + 4
+    return b
 
 
 # Per-unit figures of the FP64 fused flux kernel, from one ncu capture of the
@@ -245,7 +261,8 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream()
     solver = lskum.Solver(cloud, order=args.order, inner_iters=args.inner, time_scheme=scheme,
                           cfl=args.cfl, mach=args.mach, aoa_deg=args.aoa, reorder=args.reorder,
-                          limiter_K=args.limiter, stream=stream.cuda_stream)
+                          limiter_K=args.limiter, precision=1 if args.precision == "mixed" else 0,
+                          stream=stream.cuda_stream)
 
     # warm-up (also moves the state away from the uniform free stream)
     solver.step(args.warmup, history=False)
@@ -310,12 +327,24 @@ def run_ours(args, rank, world, local):
 
     peaks, peak_src = measured_peaks()
     flux_avg_s = (flux_ms / max(flux_n, 1)) / 1e3
-    fb = algorithmic_bytes_per_point("flux", dbar, args.order, args.scheme) * n
+    mixed = args.precision == "mixed"
+    if mixed:
+        fb = algorithmic_bytes_per_point_mixed(dbar, args.order, args.scheme) * n
+    else:
+        fb = algorithmic_bytes_per_point("flux", dbar, args.order, args.scheme) * n
     achieved_gbs = fb / flux_avg_s / 1e9
+    if mixed:
+        roofline = {"bound": "hbm", "kernel": "k_flux_update_mixed", "achieved": achieved_gbs,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
+                    "traffic": None, "peak_source": peak_src,
+                    "algorithmic_bytes_per_launch": fb, "avg_launch_ms": flux_avg_s * 1e3}
+    else:
+        roofline = roofline_fp64(flux_avg_s, n, dbar, fb, achieved_gbs, peaks, peak_src)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed" if mixed else "f64",
+        "data": "synthetic",
         "config": {"workload": args.workload, "points": n, "mean_degree": round(float(dbar), 3),
                    "order": args.order, "inner_iters": args.inner, "scheme": args.scheme,
                    "mach": args.mach, "aoa_deg": args.aoa, "cfl": args.cfl, "limiter_K": args.limiter,
@@ -324,7 +353,7 @@ def run_ours(args, rank, world, local):
                    "l2": "inputs larger than L2 (working set ~%.1f GB)" % (
                        (n * 380 + cloud["nbr_offsets"][-1] * 37) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": roofline_fp64(flux_avg_s, n, dbar, fb, achieved_gbs, peaks, peak_src),
+        "roofline": roofline,
         "kernels": {"k_flux_update": {"launches": flux_n, "total_ms": flux_ms},
                     "k_qgrad": {"launches": qg_n, "total_ms": qg_ms}},
         "gpu_launches": launches,

@@ -12,6 +12,7 @@
 
 #include "lskum.h"
 #include "lskum_kernels.h"
+#include "lskum_mixed.h"
 
 using namespace lskum;
 
@@ -35,8 +36,14 @@ struct lskum_ctx {
     double *wall_ds = nullptr;
 
     double *U = nullptr, *Us = nullptr, *acc = nullptr, *Ubak = nullptr;
-    double *q_cur = nullptr, *q_nxt = nullptr;
-    double *qgA = nullptr, *qgB = nullptr;
+    // q and q-derivative buffers: double in the FP64 form, float in the mixed one
+    void *q_cur = nullptr, *q_nxt = nullptr;
+    void *qgA = nullptr, *qgB = nullptr;
+    bool mixed = false;
+    int n_fp64_closure = 0;
+    // mixed form: FP32 geometry view
+    float2 *nrm_f = nullptr, *dxy_f = nullptr, *lsw_f = nullptr, *fxw_f = nullptr;
+    float *dmin_f = nullptr;
     double *dt = nullptr, *Rt = nullptr, *Ut = nullptr, *Ucm = nullptr;
     double *norm_part = nullptr;
     int nparts = 0;
@@ -56,6 +63,14 @@ struct lskum_ctx {
         DevGeom g;
         g.n = n; g.xy = xy; g.nrm = nrm; g.flag = flag; g.dmin = dmin;
         g.off = off; g.idx = idx; g.mask = mask; g.lsw = lsw; g.fxw = fxw;
+        return g;
+    }
+
+    MixedGeom mgeom() const
+    {
+        MixedGeom g;
+        g.n = n; g.nrm = nrm_f; g.flag = flag; g.dmin = dmin_f; g.off = off; g.idx = idx;
+        g.mask = mask; g.dxy = dxy_f; g.lsw = lsw_f; g.fxw = fxw_f; g.fxw64 = fxw;
         return g;
     }
 };
@@ -203,6 +218,15 @@ extern "C" void lskum_destroy(lskum_ctx *ctx)
     delete ctx;
 }
 
+// q-variables of an internal-layout state U ([n][4]) into qdst, in the
+// context's precision
+static lskum_status refresh_q(lskum_ctx *c, const double *U, void *qdst)
+{
+    if (c->mixed) LAUNCH(c, launch_q_from_U_mixed(c->n, c->gas, U, (float *)qdst, c->status, c->stream));
+    else LAUNCH(c, launch_q_from_U(c->n, c->gas, U, (double *)qdst, c->status, c->stream));
+    return LSKUM_OK;
+}
+
 static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, const double *nx,
                                 const double *ny, const int32_t *flags, const int32_t *nbr_offsets,
                                 const int32_t *nbr_idx, const int32_t *wall_order)
@@ -312,10 +336,28 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     CK(c, dalloc(c, &c->Us, 4 * n));
     CK(c, dalloc(c, &c->acc, 4 * n));
     CK(c, dalloc(c, &c->Ubak, 4 * n));
-    CK(c, dalloc(c, &c->q_cur, 4 * n));
-    CK(c, dalloc(c, &c->q_nxt, 4 * n));
-    CK(c, dalloc(c, &c->qgA, 8 * n));
-    CK(c, dalloc(c, &c->qgB, 8 * n));
+    const size_t qbytes = c->mixed ? sizeof(float) : sizeof(double);
+    {
+        char *b = nullptr;
+        CK(c, dalloc(c, &b, 2 * 4 * n * qbytes));
+        c->q_cur = b;
+        c->q_nxt = b + 4 * n * qbytes;
+        CK(c, dalloc(c, &b, 2 * 8 * n * qbytes));
+        c->qgA = b;
+        c->qgB = b + 8 * n * qbytes;
+    }
+    if (c->mixed) {
+        CK(c, dalloc(c, &c->nrm_f, n));
+        CK(c, dalloc(c, &c->dmin_f, n));
+        CK(c, dalloc(c, &c->dxy_f, nnz));
+        CK(c, dalloc(c, &c->lsw_f, nnz));
+        CK(c, dalloc(c, &c->fxw_f, nnz));
+        int *cnt = nullptr;
+        CK(c, dalloc(c, &cnt, 1));
+        CK(c, cudaMemsetAsync(cnt, 0, sizeof(int), s));
+        LAUNCH(c, launch_mixed_prep(c->geom(), c->mgeom(), c->flag, cnt, s));
+        CK(c, cudaMemcpyAsync(&c->n_fp64_closure, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
     CK(c, dalloc(c, &c->dt, n));
     CK(c, dalloc(c, &c->Rt, 4 * n));
     CK(c, dalloc(c, &c->Ut, 4 * n));
@@ -324,12 +366,12 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     CK(c, dalloc(c, &c->status, 2));
     c->res_cap = 1024;
     CK(c, dalloc(c, &c->res_dev, c->res_cap));
-    CK(c, cudaMemsetAsync(c->qgA, 0, 8 * n * sizeof(double), s));
-    CK(c, cudaMemsetAsync(c->qgB, 0, 8 * n * sizeof(double), s));
+    CK(c, cudaMemsetAsync(c->qgA, 0, 2 * 8 * n * qbytes, s));
     const int st_init[2] = {0, 0x7fffffff};
     CK(c, cudaMemcpyAsync(c->status, st_init, sizeof st_init, cudaMemcpyHostToDevice, s));
     LAUNCH(c, launch_fill_state(n, c->gas.Uinf, c->U, s));
-    LAUNCH(c, launch_q_from_U(n, c->gas, c->U, c->q_cur, c->status, s));
+    lskum_status st = refresh_q(c, c->U, c->q_cur);
+    if (st != LSKUM_OK) return st;
     CK(c, cudaStreamSynchronize(s));
     return LSKUM_OK;
 }
@@ -351,7 +393,8 @@ extern "C" lskum_status lskum_create(int64_t n, const double *x, const double *y
     if (cfg->time_scheme != 0 && cfg->time_scheme != 1) return fail(nullptr, LSKUM_ERR_ARG, "time_scheme must be 0 or 1");
     if (!(cfg->cfl > 0.0) || !(cfg->gamma > 1.0) || !(cfg->mach >= 0.0) || !std::isfinite(cfg->aoa_deg))
         return fail(nullptr, LSKUM_ERR_ARG, "cfl, gamma, mach or aoa out of range");
-    if (cfg->precision != 0) return fail(nullptr, LSKUM_ERR_ARG, "precision %d not supported", cfg->precision);
+    if (cfg->precision != 0 && cfg->precision != 1)
+        return fail(nullptr, LSKUM_ERR_ARG, "precision must be 0 (FP64) or 1 (mixed)");
     if (cfg->reorder != 0 && cfg->reorder != 1) return fail(nullptr, LSKUM_ERR_ARG, "reorder must be 0 or 1");
     if (!(cfg->limiter_K >= 0.0) || !std::isfinite(cfg->limiter_K))
         return fail(nullptr, LSKUM_ERR_ARG, "limiter_K must be finite and >= 0");
@@ -374,6 +417,7 @@ extern "C" lskum_status lskum_create(int64_t n, const double *x, const double *y
     c->nnz = nbr_offsets[n];
     c->n_wall = n_wall;
     c->cfg = *cfg;
+    c->mixed = cfg->precision == 1;
     c->stream = (cudaStream_t)cuda_stream;
     c->gas.gamma = cfg->gamma;
     c->gas.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
@@ -390,49 +434,98 @@ extern "C" lskum_status lskum_create(int64_t n, const double *x, const double *y
 }
 
 // q-derivatives of the state whose q-variables are in q (E15 with the
-// configured inner iterations); returns the buffer holding the result
-static lskum_status gradients(lskum_ctx *c, const double *q, double **qg_out)
+// configured inner iterations, limiter on the last pass); returns the buffer
+// holding the result
+static lskum_status gradients(lskum_ctx *c, const void *q, void **qg_out, int inner, double limK)
 {
-    const DevGeom g = c->geom();
-    double *src = c->qgA, *dst = c->qgB;
-    const int inner = c->cfg.inner_iters;
-    const double limK = c->cfg.order == 2 ? c->cfg.limiter_K : 0.0;
-    TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, q, nullptr, src, inner == 0 ? limK : 0.0, c->stream));
-    for (int k = 0; k < inner; ++k) {
-        TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, q, src, dst, k == inner - 1 ? limK : 0.0, c->stream));
-        std::swap(src, dst);
+    void *src = c->qgA, *dst = c->qgB;
+    if (c->mixed) {
+        const MixedGeom g = c->mgeom();
+        const float *qf = (const float *)q;
+        TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad_mixed(g, qf, nullptr, (float *)src, inner == 0 ? limK : 0.0, c->stream));
+        for (int k = 0; k < inner; ++k) {
+            TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad_mixed(g, qf, (const float *)src, (float *)dst,
+                                                                   k == inner - 1 ? limK : 0.0, c->stream));
+            std::swap(src, dst);
+        }
+    } else {
+        const DevGeom g = c->geom();
+        const double *qd = (const double *)q;
+        TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, qd, nullptr, (double *)src, inner == 0 ? limK : 0.0, c->stream));
+        for (int k = 0; k < inner; ++k) {
+            TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, qd, (const double *)src, (double *)dst,
+                                                             k == inner - 1 ? limK : 0.0, c->stream));
+            std::swap(src, dst);
+        }
     }
     *qg_out = src;
     return LSKUM_OK;
 }
 
-static lskum_status iteration(lskum_ctx *c, int it)
+static lskum_status gradients(lskum_ctx *c, const void *q, void **qg_out)
 {
-    const DevGeom g = c->geom();
-    const bool rk4 = c->cfg.time_scheme == 1;
-    const int stages = rk4 ? 4 : 1;
-    for (int k = 0; k < stages; ++k) {
-        double *qg = nullptr;
-        if (c->cfg.order == 2) {
-            lskum_status st = gradients(c, c->q_cur, &qg);
-            if (st != LSKUM_OK) return st;
-        }
+    return gradients(c, q, qg_out, c->cfg.inner_iters, c->cfg.order == 2 ? c->cfg.limiter_K : 0.0);
+}
+
+// one launch of the fused flux kernel in the context's precision
+// (mode 0: residual into R; 1: forward Euler; 2: RK4 stage)
+static lskum_status flux(lskum_ctx *c, const void *q, const void *qg, double *Uout, void *qout, int mode,
+                         int stage, double *R)
+{
+    if (c->mixed) {
+        MixedFluxParams P{};
+        P.g = c->mgeom();
+        P.nrm64 = c->nrm;
+        P.q = (const float *)q;
+        P.qg = (const float *)qg;
+        P.Un = c->U;
+        P.Uout = Uout;
+        P.acc = c->acc;
+        P.qout = (float *)qout;
+        P.dt = c->dt;
+        P.R = R;
+        P.norm_part = c->norm_part;
+        P.status = c->status;
+        for (int k = 0; k < 4; ++k) P.Uinf[k] = c->gas.Uinf[k];
+        P.gamma = (float)c->gas.gamma;
+        P.inv_gm1 = (float)c->gas.inv_gm1;
+        P.cfl = (float)c->cfg.cfl;
+        P.g14 = c->gas.g14;
+        P.order = c->cfg.order;
+        P.mode = mode;
+        P.stage = stage;
+        TIMED_LAUNCH(c, LSKUM_KERNEL_FLUX, launch_flux_mixed(P, c->stream));
+    } else {
         FluxLaunch L{};
-        L.q = c->q_cur;
-        L.qg = qg;
+        L.q = (const double *)q;
+        L.qg = (const double *)qg;
         L.Un = c->U;
-        L.Uout = (rk4 && k < 3) ? c->Us : c->U;
+        L.Uout = Uout;
         L.acc = c->acc;
-        L.qout = c->q_nxt;
+        L.qout = (double *)qout;
         L.dt = c->dt;
-        L.R = nullptr;
+        L.R = R;
         L.norm_part = c->norm_part;
         L.status = c->status;
         L.cfl = c->cfg.cfl;
         L.order = c->cfg.order;
-        L.mode = rk4 ? 2 : 1;
-        L.stage = k;
-        TIMED_LAUNCH(c, LSKUM_KERNEL_FLUX, launch_flux(g, c->gas, L, c->stream));
+        L.mode = mode;
+        L.stage = stage;
+        TIMED_LAUNCH(c, LSKUM_KERNEL_FLUX, launch_flux(c->geom(), c->gas, L, c->stream));
+    }
+    return LSKUM_OK;
+}
+
+static lskum_status iteration(lskum_ctx *c, int it)
+{
+    const bool rk4 = c->cfg.time_scheme == 1;
+    const int stages = rk4 ? 4 : 1;
+    for (int k = 0; k < stages; ++k) {
+        void *qg = nullptr;
+        lskum_status st;
+        if (c->cfg.order == 2 && (st = gradients(c, c->q_cur, &qg)) != LSKUM_OK) return st;
+        st = flux(c, c->q_cur, qg, (rk4 && k < 3) ? c->Us : c->U, c->q_nxt, rk4 ? 2 : 1, k, nullptr);
+        if (st != LSKUM_OK) return st;
         std::swap(c->q_cur, c->q_nxt);
         if (k == 0) LAUNCH(c, launch_residue_finish(c->norm_part, c->nparts, c->n, c->res_dev + it, c->stream));
     }
@@ -479,7 +572,7 @@ extern "C" lskum_status lskum_step(lskum_ctx *c, int n_iters, double *res_histor
     if (st != LSKUM_OK) return st;
     if (sh[0] & STATUS_NONPHYSICAL) {
         CK(c, cudaMemcpyAsync(c->U, c->Ubak, 4 * c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-        LAUNCH(c, launch_q_from_U(c->n, c->gas, c->U, c->q_cur, c->status, c->stream));
+        if ((st = refresh_q(c, c->U, c->q_cur)) != LSKUM_OK) return st;
         CK(c, cudaStreamSynchronize(c->stream));
         return fail(c, LSKUM_ERR_NONPHYSICAL,
                     "non-physical state (rho <= 0, p <= 0 or non-finite) at point %d; state rolled back",
@@ -490,14 +583,15 @@ extern "C" lskum_status lskum_step(lskum_ctx *c, int n_iters, double *res_histor
 
 // q-variables of a caller state (device [4][n], input order) into q_nxt, or the
 // context's own q
-static lskum_status q_of(lskum_ctx *c, const double *U, const double **q)
+static lskum_status q_of(lskum_ctx *c, const double *U, const void **q)
 {
     if (!U) {
         *q = c->q_cur;
         return LSKUM_OK;
     }
     LAUNCH(c, launch_state_in(c->n, c->perm, U, c->Ut, c->stream));
-    LAUNCH(c, launch_q_from_U(c->n, c->gas, c->Ut, c->q_nxt, c->status, c->stream));
+    lskum_status st = refresh_q(c, c->Ut, c->q_nxt);
+    if (st != LSKUM_OK) return st;
     *q = c->q_nxt;
     return LSKUM_OK;
 }
@@ -519,18 +613,11 @@ extern "C" lskum_status lskum_residual(lskum_ctx *c, const double *U, double *R)
     if (!R) return fail(c, LSKUM_ERR_ARG, "R is NULL");
     lskum_status st = reset_status(c);
     if (st != LSKUM_OK) return st;
-    const double *q = nullptr;
+    const void *q = nullptr;
     if ((st = q_of(c, U, &q)) != LSKUM_OK) return st;
-    double *qg = nullptr;
+    void *qg = nullptr;
     if (c->cfg.order == 2 && (st = gradients(c, q, &qg)) != LSKUM_OK) return st;
-    FluxLaunch L{};
-    L.q = q;
-    L.qg = qg;
-    L.R = c->Rt;
-    L.status = c->status;
-    L.order = c->cfg.order;
-    L.mode = 0;
-    LAUNCH(c, launch_flux(c->geom(), c->gas, L, c->stream));
+    if ((st = flux(c, q, qg, nullptr, nullptr, 0, 0, c->Rt)) != LSKUM_OK) return st;
     LAUNCH(c, launch_state_out(c->n, c->perm, c->Rt, R, c->stream));
     return check_nonphysical(c);
 }
@@ -542,20 +629,14 @@ extern "C" lskum_status lskum_q_derivatives(lskum_ctx *c, const double *U, doubl
     if (!qx || !qy) return fail(c, LSKUM_ERR_ARG, "qx or qy is NULL");
     lskum_status st = reset_status(c);
     if (st != LSKUM_OK) return st;
-    const double *q = nullptr;
+    const void *q = nullptr;
     if ((st = q_of(c, U, &q)) != LSKUM_OK) return st;
-    double *qg = nullptr;
-    const int inner = c->cfg.inner_iters;
-    const double limK = c->cfg.limiter_K;
-    if (c->cfg.order == 1) {
-        c->cfg.inner_iters = 0;
-        c->cfg.limiter_K = 0.0;
-    }
-    st = gradients(c, q, &qg);
-    c->cfg.inner_iters = inner;
-    c->cfg.limiter_K = limK;
+    void *qg = nullptr;
+    const bool second = c->cfg.order == 2;
+    st = gradients(c, q, &qg, second ? c->cfg.inner_iters : 0, second ? c->cfg.limiter_K : 0.0);
     if (st != LSKUM_OK) return st;
-    LAUNCH(c, launch_grad_out(c->n, c->perm, qg, qx, qy, c->stream));
+    if (c->mixed) LAUNCH(c, launch_grad_out_f(c->n, c->perm, (const float *)qg, qx, qy, c->stream));
+    else LAUNCH(c, launch_grad_out(c->n, c->perm, (const double *)qg, qx, qy, c->stream));
     return check_nonphysical(c);
 }
 
@@ -622,7 +703,7 @@ extern "C" lskum_status lskum_set_state(lskum_ctx *c, const double *U, int on_ho
     lskum_status st = reset_status(c);
     if (st != LSKUM_OK) return st;
     LAUNCH(c, launch_state_in(c->n, c->perm, src, c->U, c->stream));
-    LAUNCH(c, launch_q_from_U(c->n, c->gas, c->U, c->q_cur, c->status, c->stream));
+    if ((st = refresh_q(c, c->U, c->q_cur)) != LSKUM_OK) return st;
     if (on_host) return check_nonphysical(c);
     return LSKUM_OK;
 }

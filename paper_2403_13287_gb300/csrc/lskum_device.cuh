@@ -139,4 +139,81 @@ __device__ __forceinline__ bool q_from_U(const double U[4], const Gas &gas, doub
     return rho > 0.0 && p > 0.0 && isfinite(q[0]);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 forms for the mixed-precision kernels (same formulas as above)
+// ---------------------------------------------------------------------------
+struct PrimF {
+    float rho, u, v, p, rsb, sqb;
+};
+
+__device__ __forceinline__ bool prim_from_q_f(const float qt[4], float inv_gm1, bool g14, PrimF &s)
+{
+    const float beta = -0.5f * qt[3];
+    if (!(beta > 0.0f)) return false;
+    const float r = __fdividef(1.0f, qt[3]);  // -1/(2 beta)
+    s.u = -qt[1] * r;
+    s.v = -qt[2] * r;
+    s.rsb = rsqrtf(beta);
+    s.sqb = beta * s.rsb;
+    const float ke = beta * (s.u * s.u + s.v * s.v);
+    if (g14) s.rho = expf(qt[0] + ke) * s.rsb * (4.0f * r * r);
+    else s.rho = expf(qt[0] - logf(beta) * inv_gm1 + ke);
+    s.p = -s.rho * r;
+    return isfinite(s.rho) && s.rho > 0.0f;
+}
+
+__device__ __forceinline__ void split_flux_f(float sgn, const PrimF &s, float un, float ut, float rhoE,
+                                             float G[4])
+{
+    const float S = un * s.sqb;
+    const float A = 0.5f * (1.0f + sgn * erff(S));
+    const float B = expf(-S * S) * s.rsb * 0.28209479177387814f;
+    const float m = un * A + sgn * B;
+    G[0] = s.rho * m;
+    G[1] = (s.p + s.rho * un * un) * A + sgn * s.rho * un * B;
+    G[2] = s.rho * ut * m;
+    G[3] = (rhoE + s.p) * un * A + sgn * (rhoE + 0.5f * s.p) * B;
+}
+
+__device__ __forceinline__ void load4f(const float *a, int64_t p, float v[4])
+{
+    const float4 t = reinterpret_cast<const float4 *>(a)[p];
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+
+__device__ __forceinline__ void store4f(float *a, int64_t p, const float v[4])
+{
+    reinterpret_cast<float4 *>(a)[p] = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+__device__ __forceinline__ void load8f(const float *a, int64_t p, float v[8])
+{
+    const float4 *a4 = reinterpret_cast<const float4 *>(a);
+    const float4 lo = a4[2 * p], hi = a4[2 * p + 1];
+    v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+    v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+}
+
+__device__ __forceinline__ void store8f(float *a, int64_t p, const float v[8])
+{
+    float4 *a4 = reinterpret_cast<float4 *>(a);
+    a4[2 * p] = make_float4(v[0], v[1], v[2], v[3]);
+    a4[2 * p + 1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// q-variables (E13) of an FP64 state, evaluated in FP32
+__device__ __forceinline__ bool q_from_U_f(const double Ud[4], float gamma, float inv_gm1, float q[4])
+{
+    const float rho = (float)Ud[0], m1 = (float)Ud[1], m2 = (float)Ud[2], E = (float)Ud[3];
+    const float ir = __fdividef(1.0f, rho);
+    const float u = m1 * ir, v = m2 * ir;
+    const float p = (gamma - 1.0f) * (E - 0.5f * (m1 * u + m2 * v));
+    const float beta = 0.5f * rho * __fdividef(1.0f, p);
+    q[0] = logf(rho) + logf(beta) * inv_gm1 - beta * (u * u + v * v);
+    q[1] = 2.0f * beta * u;
+    q[2] = 2.0f * beta * v;
+    q[3] = -2.0f * beta;
+    return rho > 0.0f && p > 0.0f && isfinite(q[0]);
+}
+
 }  // namespace lskum

@@ -120,5 +120,5 @@ def test_shuffle_is_a_relabelling():
 
 def test_named_workload_sizes():
     assert {k: W * (L + 1) for k, (W, L) in CLOUDS.items()} == {
-        "naca0012_10k": 9920, "naca0012_160k": 160000, "naca0012_640k": 640000,
+        "naca0012_10k": 9920, "naca0012_160k": 159744, "naca0012_640k": 640000,
         "naca0012_2p5m": 2498560, "naca0012_10m": 9999360}
