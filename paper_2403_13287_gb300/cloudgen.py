@@ -334,3 +334,28 @@ CLOUDS = {
     "naca0012_2p5m": (2560, 975),     # 2,498,560 points
     "naca0012_10m": (5120, 1952),     # 9,999,360 points
 }
+
+
+def smooth_state(cloud, mach, aoa_deg, amp=0.05, seed=0, gamma=1.4):
+    """A seeded smooth perturbation of the free stream (rho = 1, p = 1/gamma,
+    |u| = mach) as conserved variables U[4, n]: density, velocity and pressure
+    each vary by about `amp` on a scale of a chord. Far-field points carry the
+    free stream, wall points have no normal momentum. An input for tests and
+    timing: every stencil sees a non-uniform state."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x, y = cloud["x"], cloud["y"]
+    k = rng.uniform(1.0, 3.0, 4)
+    ph = rng.uniform(0.0, 2.0 * np.pi, 4)
+    a = np.radians(aoa_deg)
+    rho = 1.0 + amp * np.sin(k[0] * x + ph[0]) * np.cos(k[1] * y + ph[1])
+    u = mach * np.cos(a) + amp * np.cos(k[2] * y + ph[2])
+    v = mach * np.sin(a) + amp * np.sin(k[3] * x + ph[3])
+    p = (1.0 + amp * np.cos(k[1] * x - k[0] * y)) / gamma
+    far = cloud["flags"] == FLAG_FARFIELD
+    rho[far], u[far], v[far], p[far] = 1.0, mach * np.cos(a), mach * np.sin(a), 1.0 / gamma
+    U = np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+    wall = cloud["flags"] == FLAG_WALL
+    mn = U[1, wall] * cloud["nx"][wall] + U[2, wall] * cloud["ny"][wall]
+    U[1, wall] -= mn * cloud["nx"][wall]
+    U[2, wall] -= mn * cloud["ny"][wall]
+    return np.ascontiguousarray(U)

@@ -42,8 +42,11 @@ struct lskum_ctx {
     bool mixed = false;
     int n_fp64_closure = 0;
     // mixed form: FP32 geometry view
-    float2 *nrm_f = nullptr, *dxy_f = nullptr, *lsw_f = nullptr, *fxw_f = nullptr;
+    float2 *nrm_f = nullptr;
     float *dmin_f = nullptr;
+    int32_t *slice_off = nullptr, *s_idx = nullptr;  // SELL-32 edge layout
+    float4 *s_gq = nullptr, *s_gf = nullptr;
+    double2 *s_fxw64 = nullptr;
     double *dt = nullptr, *Rt = nullptr, *Ut = nullptr, *Ucm = nullptr;
     double *norm_part = nullptr;
     int nparts = 0;
@@ -69,8 +72,8 @@ struct lskum_ctx {
     MixedGeom mgeom() const
     {
         MixedGeom g;
-        g.n = n; g.nrm = nrm_f; g.flag = flag; g.dmin = dmin_f; g.off = off; g.idx = idx;
-        g.mask = mask; g.dxy = dxy_f; g.lsw = lsw_f; g.fxw = fxw_f; g.fxw64 = fxw;
+        g.n = n; g.nrm = nrm_f; g.flag = flag; g.dmin = dmin_f; g.off = off;
+        g.slice_off = slice_off; g.sidx = s_idx; g.gq = s_gq; g.gf = s_gf; g.fxw64 = s_fxw64;
         return g;
     }
 };
@@ -331,7 +334,7 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     }
 
     // state and work buffers
-    c->nparts = (int)flux_blocks(n);
+    c->nparts = (int)(c->mixed ? mixed_flux_blocks(n) : flux_blocks(n));
     CK(c, dalloc(c, &c->U, 4 * n));
     CK(c, dalloc(c, &c->Us, 4 * n));
     CK(c, dalloc(c, &c->acc, 4 * n));
@@ -347,16 +350,43 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
         c->qgB = b + 8 * n * qbytes;
     }
     if (c->mixed) {
+        // FP32 geometry in CSR order, then scattered into the SELL-32 layout
         CK(c, dalloc(c, &c->nrm_f, n));
         CK(c, dalloc(c, &c->dmin_f, n));
-        CK(c, dalloc(c, &c->dxy_f, nnz));
-        CK(c, dalloc(c, &c->lsw_f, nnz));
-        CK(c, dalloc(c, &c->fxw_f, nnz));
+        float2 *dxy = nullptr, *lsw = nullptr, *fxw = nullptr;
+        CK(c, cudaMallocAsync(&dxy, std::max<int64_t>(nnz, 1) * sizeof(float2), s));
+        CK(c, cudaMallocAsync(&lsw, std::max<int64_t>(nnz, 1) * sizeof(float2), s));
+        CK(c, cudaMallocAsync(&fxw, std::max<int64_t>(nnz, 1) * sizeof(float2), s));
         int *cnt = nullptr;
         CK(c, dalloc(c, &cnt, 1));
         CK(c, cudaMemsetAsync(cnt, 0, sizeof(int), s));
-        LAUNCH(c, launch_mixed_prep(c->geom(), c->mgeom(), c->flag, cnt, s));
+        LAUNCH(c, launch_mixed_prep(c->geom(), c->flag, c->nrm_f, c->dmin_f, dxy, lsw, fxw, cnt, s));
         CK(c, cudaMemcpyAsync(&c->n_fp64_closure, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        std::vector<int32_t> off_h(n + 1);
+        CK(c, cudaMemcpyAsync(off_h.data(), c->off, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(c, cudaStreamSynchronize(s));
+        const int64_t nslices = (n + 31) / 32;
+        std::vector<int32_t> so(nslices + 1, 0);
+        for (int64_t sl = 0; sl < nslices; ++sl) {
+            int depth = 0;
+            for (int64_t p = 32 * sl; p < std::min<int64_t>(n, 32 * sl + 32); ++p)
+                depth = std::max(depth, off_h[p + 1] - off_h[p]);
+            if ((int64_t)so[sl] + 32 * depth > 0x7fffffff)
+                return fail(c, LSKUM_ERR_ARG, "too many stencil entries for the mixed layout");
+            so[sl + 1] = so[sl] + 32 * depth;
+        }
+        const int64_t nslot = std::max<int32_t>(so[nslices], 1);
+        CK(c, dalloc(c, &c->slice_off, nslices + 1));
+        CK(c, cudaMemcpyAsync(c->slice_off, so.data(), (nslices + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CK(c, dalloc(c, &c->s_idx, nslot));
+        CK(c, dalloc(c, &c->s_gq, nslot));
+        CK(c, dalloc(c, &c->s_gf, nslot));
+        CK(c, dalloc(c, &c->s_fxw64, nslot));
+        LAUNCH(c, launch_sell_fill(n, c->off, c->slice_off, c->idx, c->mask, dxy, lsw, fxw, c->fxw, c->mgeom(), s));
+        CK(c, cudaFreeAsync(dxy, s));
+        CK(c, cudaFreeAsync(lsw, s));
+        CK(c, cudaFreeAsync(fxw, s));
+        CK(c, cudaStreamSynchronize(s));
     }
     CK(c, dalloc(c, &c->dt, n));
     CK(c, dalloc(c, &c->Rt, 4 * n));
@@ -395,6 +425,8 @@ extern "C" lskum_status lskum_create(int64_t n, const double *x, const double *y
         return fail(nullptr, LSKUM_ERR_ARG, "cfl, gamma, mach or aoa out of range");
     if (cfg->precision != 0 && cfg->precision != 1)
         return fail(nullptr, LSKUM_ERR_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+    if (cfg->precision == 1 && n >= (int64_t)1 << 28)
+        return fail(nullptr, LSKUM_ERR_ARG, "the mixed form takes at most 2^28 - 1 points");
     if (cfg->reorder != 0 && cfg->reorder != 1) return fail(nullptr, LSKUM_ERR_ARG, "reorder must be 0 or 1");
     if (!(cfg->limiter_K >= 0.0) || !std::isfinite(cfg->limiter_K))
         return fail(nullptr, LSKUM_ERR_ARG, "limiter_K must be finite and >= 0");

@@ -156,18 +156,36 @@ __device__ __forceinline__ bool prim_from_q_f(const float qt[4], float inv_gm1, 
     s.rsb = rsqrtf(beta);
     s.sqb = beta * s.rsb;
     const float ke = beta * (s.u * s.u + s.v * s.v);
-    if (g14) s.rho = expf(qt[0] + ke) * s.rsb * (4.0f * r * r);
-    else s.rho = expf(qt[0] - logf(beta) * inv_gm1 + ke);
+    // __expf: relative error about |arg| * 6e-8 here (|arg| < ~20), within
+    // the FP32 budget of the form
+    if (g14) s.rho = __expf(qt[0] + ke) * s.rsb * (4.0f * r * r);
+    else s.rho = __expf(qt[0] - __logf(beta) * inv_gm1 + ke);
     s.p = -s.rho * r;
     return isfinite(s.rho) && s.rho > 0.0f;
+}
+
+// A+- = (1 +- erf S)/2 with erfc from Abramowitz & Stegun 7.1.26 (Hastings):
+// erfc(x) = (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2), t = 1/(1 + p x),
+// x >= 0, |error| <= 1.5e-7, about one FP32 ulp of 1. exp(-S^2) is shared with
+// B, and the smaller of A+ and A- is formed directly (no 1 - erf cancellation).
+__device__ __forceinline__ float half_range_A(float sgn, float S, float e)
+{
+    const float x = fabsf(S);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f),
+                                        -0.284496736f), 0.254829592f);
+    const float small = 0.5f * poly * e;  // (1 - erf|S|)/2
+    // A+ is the large one for S > 0, A- for S < 0
+    return (sgn * S >= 0.0f) ? 1.0f - small : small;
 }
 
 __device__ __forceinline__ void split_flux_f(float sgn, const PrimF &s, float un, float ut, float rhoE,
                                              float G[4])
 {
     const float S = un * s.sqb;
-    const float A = 0.5f * (1.0f + sgn * erff(S));
-    const float B = expf(-S * S) * s.rsb * 0.28209479177387814f;
+    const float e = __expf(-S * S);
+    const float A = half_range_A(sgn, S, e);
+    const float B = e * s.rsb * 0.28209479177387814f;
     const float m = un * A + sgn * B;
     G[0] = s.rho * m;
     G[1] = (s.p + s.rho * un * un) * A + sgn * s.rho * un * B;
@@ -199,6 +217,53 @@ __device__ __forceinline__ void store8f(float *a, int64_t p, const float v[8])
     float4 *a4 = reinterpret_cast<float4 *>(a);
     a4[2 * p] = make_float4(v[0], v[1], v[2], v[3]);
     a4[2 * p + 1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// FP64 <-> FP32 conversions on the integer pipe. On this GPU the FP64 pipe
+// runs at 1/64 of the FP32 rate, and a conversion instruction occupies it like
+// an FP64 add, so the mixed kernels move state values across with bit
+// arithmetic, branch-free. double -> float rounds the 29 dropped mantissa
+// bits half away from zero, flushes magnitudes below the FP32 normal range to
+// zero and saturates above it to infinity (NaN stays NaN); float -> double is
+// exact for normal numbers and flushes FP32 subnormals to zero.
+__device__ __forceinline__ float f64_to_f32_ip(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    const unsigned int e = (unsigned int)(mag >> 52);
+    const long long f = (long long)((mag + (1ull << 28)) >> 29) - ((long long)(1023 - 127) << 23);
+    unsigned int out = (unsigned int)f;
+    out = e < 1023u - 126u ? 0u : out;
+    out = f >= 0x7f800000ll ? 0x7f800000u : out;
+    out = e == 2047u ? ((mag & 0xfffffffffffffull) ? 0x7fc00000u : 0x7f800000u) : out;
+    return __uint_as_float(sign | out);
+}
+
+__device__ __forceinline__ double f32_to_f64_ip(float f)
+{
+    const unsigned int b = __float_as_uint(f);
+    const unsigned int mag = b & 0x7fffffffu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    unsigned long long out = ((unsigned long long)mag + ((unsigned long long)(1023 - 127) << 23)) << 29;
+    out = mag < 0x00800000u ? 0ull : out;
+    out = mag >= 0x7f800000u ? ((0x7ffull << 52) | ((unsigned long long)(mag & 0x7fffffu) << 29)) : out;
+    return __longlong_as_double((long long)(sign | out));
+}
+
+// q-variables (E13) of an FP32 copy of the state
+__device__ __forceinline__ bool q_from_Uf(const float U[4], float gamma, float inv_gm1, float q[4])
+{
+    const float rho = U[0], m1 = U[1], m2 = U[2], E = U[3];
+    const float ir = __fdividef(1.0f, rho);
+    const float u = m1 * ir, v = m2 * ir;
+    const float p = (gamma - 1.0f) * (E - 0.5f * (m1 * u + m2 * v));
+    const float beta = 0.5f * rho * __fdividef(1.0f, p);
+    q[0] = logf(rho) + logf(beta) * inv_gm1 - beta * (u * u + v * v);
+    q[1] = 2.0f * beta * u;
+    q[2] = 2.0f * beta * v;
+    q[3] = -2.0f * beta;
+    return rho > 0.0f && p > 0.0f && isfinite(q[0]);
 }
 
 // q-variables (E13) of an FP64 state, evaluated in FP32

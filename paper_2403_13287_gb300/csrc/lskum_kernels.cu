@@ -162,6 +162,8 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
                     qt0[k] = qt0[k] - 0.5 * (dx * g0[k] + dy * g0[4 + k]);
                 }
             }
+            // equal reconstructed states have dG = 0 exactly
+            if (qti[0] == qt0[0] && qti[1] == qt0[1] && qti[2] == qt0[2] && qti[3] == qt0[3]) continue;
             Prim si, s0;
             ok &= prim_from_q(qti, P.gas, si);
             ok &= prim_from_q(qt0, P.gas, s0);

@@ -62,13 +62,12 @@ __global__ void __launch_bounds__(128) k_mixed_prep(int64_t n, const double2 *__
     }
 }
 
-cudaError_t launch_mixed_prep(const DevGeom &g, const MixedGeom &m, uint8_t *flag, int *n_fp64,
-                              cudaStream_t s)
+cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, float *dmin_f,
+                              float2 *dxy_f, float2 *lsw_f, float2 *fxw_f, int *n_fp64, cudaStream_t s)
 {
-    k_mixed_prep<<<(unsigned)((g.n + 127) / 128), 128, 0, s>>>(
-        g.n, g.xy, g.nrm, g.dmin, g.off, g.idx, g.mask, g.lsw, g.fxw, flag,
-        const_cast<float2 *>(m.nrm), const_cast<float *>(m.dmin), const_cast<float2 *>(m.dxy),
-        const_cast<float2 *>(m.lsw), const_cast<float2 *>(m.fxw), n_fp64);
+    k_mixed_prep<<<(unsigned)((g.n + 127) / 128), 128, 0, s>>>(g.n, g.xy, g.nrm, g.dmin, g.off, g.idx, g.mask,
+                                                               g.lsw, g.fxw, flag, nrm_f, dmin_f, dxy_f,
+                                                               lsw_f, fxw_f, n_fp64);
     return cudaGetLastError();
 }
 
@@ -78,24 +77,81 @@ __device__ __forceinline__ float venkat_f(float D, float d, float eps2)
 }
 
 // --------------------------------------------------------------------------
-// q_derivatives() in FP32 (E15; same structure as k_qgrad)
+// Edge layout of the mixed kernels: sliced ELL with slices of 32 points
+// (SELL-32). One thread per point; a warp handles the 32 points of one slice,
+// and slot s of all 32 points is stored contiguously at
+// slice_off[slice] + 32 s + lane, so every per-edge load of a warp is one
+// coalesced run. A slice is as deep as its largest degree; shorter rows stop
+// early (on these clouds almost all points have 8 neighbours).
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_qgrad_mixed(MixedGeom g, const float *__restrict__ q,
-                                                     const float *__restrict__ qg_old,
-                                                     float *__restrict__ qg_new, float limK)
+static constexpr int kMixedThreads = 128;
+
+// create time: scatter the CSR rows of the FP32 (and FP64-closure) edge arrays
+// into the SELL-32 layout; padding slots keep weight 0 and index = the point
+__global__ void __launch_bounds__(256) k_sell_fill(int64_t n, const int32_t *__restrict__ off,
+                                                   const int32_t *__restrict__ slice_off,
+                                                   const int32_t *__restrict__ idx,
+                                                   const uint8_t *__restrict__ mask,
+                                                   const float2 *__restrict__ dxy, const float2 *__restrict__ lsw,
+                                                   const float2 *__restrict__ fxw, const double2 *__restrict__ fxw64,
+                                                   int32_t *__restrict__ s_idx, float4 *__restrict__ s_gq,
+                                                   float4 *__restrict__ s_gf, double2 *__restrict__ s_fxw64)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t slice = p >> 5, lane = p & 31;
+    const int depth = (slice_off[slice + 1] - slice_off[slice]) >> 5;
+    const int e0 = off[p], deg = off[p + 1] - e0;
+    for (int s = 0; s < depth; ++s) {
+        const int64_t d = slice_off[slice] + 32 * s + lane;
+        if (s < deg) {
+            const int e = e0 + s;
+            s_idx[d] = idx[e] | ((int32_t)mask[e] << 28);
+            s_gq[d] = make_float4(dxy[e].x, dxy[e].y, lsw[e].x, lsw[e].y);
+            s_gf[d] = make_float4(dxy[e].x, dxy[e].y, fxw[e].x, fxw[e].y);
+            s_fxw64[d] = fxw64[e];
+        } else {
+            s_idx[d] = (int32_t)p;
+            s_gq[d] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            s_gf[d] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            s_fxw64[d] = make_double2(0.0, 0.0);
+        }
+    }
+}
+
+cudaError_t launch_sell_fill(int64_t n, const int32_t *off, const int32_t *slice_off, const int32_t *idx,
+                             const uint8_t *mask, const float2 *dxy, const float2 *lsw, const float2 *fxw,
+                             const double2 *fxw64, const MixedGeom &m, cudaStream_t s)
+{
+    k_sell_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        n, off, slice_off, idx, mask, dxy, lsw, fxw, fxw64, const_cast<int32_t *>(m.sidx),
+        const_cast<float4 *>(m.gq), const_cast<float4 *>(m.gf), const_cast<double2 *>(m.fxw64));
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// q_derivatives() in FP32 (E15; same arithmetic as k_qgrad)
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kMixedThreads) k_qgrad_mixed(MixedGeom g, const float *__restrict__ q,
+                                                               const float *__restrict__ qg_old,
+                                                               float *__restrict__ qg_new, float limK)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.n) return;
+    const int deg = g.off[p + 1] - g.off[p];
+    const int64_t base = g.slice_off[p >> 5] + (p & 31);
     float q0[4], g0[8], sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
     load4f(q, p, q0);
     const bool inner = qg_old != nullptr;
     const bool limit = limK > 0.0f;
     if (inner) load8f(qg_old, p, g0);
     float qmax[4] = {q0[0], q0[1], q0[2], q0[3]}, qmin[4] = {q0[0], q0[1], q0[2], q0[3]};
-    const int e0 = g.off[p], e1 = g.off[p + 1];
-    for (int e = e0; e < e1; ++e) {
-        const int i = g.idx[e];
-        const float2 a = g.lsw[e];
+#pragma unroll 2
+    for (int s = 0; s < deg; ++s) {
+        const int64_t e = base + 32 * s;
+        const int i = g.sidx[e] & kSlotIndexMask;
+        const float4 rec = g.gq[e];
+        const float2 a = make_float2(rec.z, rec.w);
         float qi[4];
         load4f(q, i, qi);
         float dq[4];
@@ -108,7 +164,7 @@ __global__ void __launch_bounds__(128) k_qgrad_mixed(MixedGeom g, const float *_
         if (inner) {
             float gi[8];
             load8f(qg_old, i, gi);
-            const float2 d = g.dxy[e];
+            const float2 d = make_float2(rec.x, rec.y);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 dq[k] = dq[k] - 0.5f * (d.x * (gi[k] - g0[k]) + d.y * (gi[4 + k] - g0[4 + k]));
@@ -121,8 +177,9 @@ __global__ void __launch_bounds__(128) k_qgrad_mixed(MixedGeom g, const float *_
     }
     if (limit) {
         float dmax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int e = e0; e < e1; ++e) {
-            const float2 d = g.dxy[e];
+        for (int s = 0; s < deg; ++s) {
+            const float4 rec = g.gq[base + 32 * s];
+            const float2 d = make_float2(rec.x, rec.y);
 #pragma unroll
             for (int k = 0; k < 4; ++k) dmax[k] = fmaxf(dmax[k], fabsf(0.5f * (d.x * sx[k] + d.y * sy[k])));
         }
@@ -139,13 +196,16 @@ __global__ void __launch_bounds__(128) k_qgrad_mixed(MixedGeom g, const float *_
             sy[k] *= phi;
         }
     }
-    float out[8] = {sx[0], sx[1], sx[2], sx[3], sy[0], sy[1], sy[2], sy[3]};
+    const float out[8] = {sx[0], sx[1], sx[2], sx[3], sy[0], sy[1], sy[2], sy[3]};
     store8f(qg_new, p, out);
 }
 
 // --------------------------------------------------------------------------
-// flux_residual() + timestep() + state_update(), mixed: the neighbour loop in
-// FP32, the update of U and the residue partials in FP64.
+// flux_residual() + timestep() + state_update(), mixed. The neighbour loop
+// runs in FP32; the state U stays FP64 and is updated by one FP64 add per
+// component from an FP32 increment (U_k <- U_k - inc_k), the RK combination
+// of the stage residuals being formed in FP32. FP64 <-> FP32 conversions go
+// through the integer pipe.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ void flag_nonphysical_m(int *status, int64_t p)
 {
@@ -153,17 +213,20 @@ __device__ __forceinline__ void flag_nonphysical_m(int *status, int64_t p)
     atomicMin(status + 1, (int)p);
 }
 
-__global__ void __launch_bounds__(128) k_flux_update_mixed(MixedFluxParams P)
+__global__ void __launch_bounds__(kMixedThreads, 7) k_flux_update_mixed(MixedFluxParams P)
 {
     const MixedGeom &g = P.g;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double Rg[4] = {0.0, 0.0, 0.0, 0.0};
     const bool live = p < g.n;
     uint8_t fl = FLAG_FARFIELD;
     if (live) fl = g.flag[p];
     const uint8_t flag = fl & 3;
+    const bool fp64 = (fl & FLAG_FP64_CLOSURE) != 0;
+    float Rl[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // residual, global frame
+    double R64g[4] = {0.0, 0.0, 0.0, 0.0};   // FP64-closure points
     if (live && flag != FLAG_FARFIELD) {
-        const bool fp64 = (fl & FLAG_FP64_CLOSURE) != 0;
+        const int deg = g.off[p + 1] - g.off[p];
+        const int64_t base = g.slice_off[p >> 5] + (p & 31);
         const float2 n0 = g.nrm[p];
         const float tx = n0.y, ty = -n0.x;
         float q0[4], g0[8];
@@ -173,18 +236,20 @@ __global__ void __launch_bounds__(128) k_flux_update_mixed(MixedFluxParams P)
         float R[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         double R64[4] = {0.0, 0.0, 0.0, 0.0};
         bool ok = true;
-        const int e0 = g.off[p], e1 = g.off[p + 1];
-        for (int e = e0; e < e1; ++e) {
-            const float2 w = g.fxw[e];
+        for (int s = 0; s < deg; ++s) {
+            const int64_t e = base + 32 * s;
+            const float4 rec = g.gf[e];
+            const float2 w = make_float2(rec.z, rec.w);
             if (w.x == 0.0f && w.y == 0.0f) continue;
-            const int i = g.idx[e];
-            const uint8_t m = g.mask[e];
+            const int32_t im = g.sidx[e];
+            const int i = im & kSlotIndexMask;
+            const uint32_t m = (uint32_t)im >> 28;
             float qti[4], qt0[4];
             load4f(P.q, i, qti);
 #pragma unroll
             for (int k = 0; k < 4; ++k) qt0[k] = q0[k];
             if (second) {
-                const float2 d = g.dxy[e];
+                const float2 d = make_float2(rec.x, rec.y);
                 float gi[8];
                 load8f(P.qg, i, gi);
 #pragma unroll
@@ -193,6 +258,10 @@ __global__ void __launch_bounds__(128) k_flux_update_mixed(MixedFluxParams P)
                     qt0[k] = qt0[k] - 0.5f * (d.x * g0[k] + d.y * g0[4 + k]);
                 }
             }
+            // equal reconstructed states have dG = 0 exactly; the two flux
+            // evaluations may be compiled along different paths (the q~_0 one
+            // partly hoisted), so equality is decided on q~, not on G
+            if (qti[0] == qt0[0] && qti[1] == qt0[1] && qti[2] == qt0[2] && qti[3] == qt0[3]) continue;
             PrimF si, s0;
             ok &= prim_from_q_f(qti, P.inv_gm1, P.g14, si);
             ok &= prim_from_q_f(qt0, P.inv_gm1, P.g14, s0);
@@ -230,63 +299,80 @@ __global__ void __launch_bounds__(128) k_flux_update_mixed(MixedFluxParams P)
             }
         }
         if (!ok) flag_nonphysical_m(P.status, p);
-        if (!fp64) {
+        if (fp64) {
+            const double txd = (double)tx, tyd = (double)ty;
+            R64g[0] = R64[0];
+            R64g[1] = R64[1] * txd + R64[2] * (double)n0.x;
+            R64g[2] = R64[1] * tyd + R64[2] * (double)n0.y;
+            R64g[3] = R64[3];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) R64[k] = (double)R[k];
+            for (int k = 0; k < 4; ++k) Rl[k] = (float)R64g[k];
+        } else {
+            Rl[0] = R[0];
+            Rl[1] = R[1] * tx + R[2] * n0.x;
+            Rl[2] = R[1] * ty + R[2] * n0.y;
+            Rl[3] = R[3];
         }
-        const double txd = (double)tx, tyd = (double)ty;
-        Rg[0] = R64[0];
-        Rg[1] = R64[1] * txd + R64[2] * (double)n0.x;
-        Rg[2] = R64[1] * tyd + R64[2] * (double)n0.y;
-        Rg[3] = R64[3];
     }
 
     if (P.mode == 0) {
-        if (live) store4(P.R, p, Rg);
+        if (live) {
+            double Rd[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Rd[k] = fp64 ? R64g[k] : f32_to_f64_ip(Rl[k]);
+            store4(P.R, p, Rd);
+        }
         return;
     }
 
+    float r0sq = 0.0f;
     if (live) {
-        double Un[4], Unew[4];
+        double Un[4];
+        float Unf[4];
         load4(P.Un, p, Un);
-        double dt;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Unf[k] = f64_to_f32_ip(Un[k]);
+        float dt;
         if (P.mode == 1 || P.stage == 0) {
             // timestep() in FP32: dt = CFL min|P_i - P_0| / (|u| + 3 sqrt(p/rho))
-            const float rho = (float)Un[0], m1 = (float)Un[1], m2 = (float)Un[2], E = (float)Un[3];
-            const float ir = __fdividef(1.0f, rho);
-            const float u = m1 * ir, v = m2 * ir;
-            const float pr = (P.gamma - 1.0f) * (E - 0.5f * (m1 * u + m2 * v));
-            dt = (double)(P.cfl * g.dmin[p] / (sqrtf(u * u + v * v) + 3.0f * sqrtf(pr * ir)));
-            P.dt[p] = dt;
+            const float ir = __fdividef(1.0f, Unf[0]);
+            const float u = Unf[1] * ir, v = Unf[2] * ir;
+            const float pr = (P.gamma - 1.0f) * (Unf[3] - 0.5f * (Unf[1] * u + Unf[2] * v));
+            dt = P.cfl * g.dmin[p] / (sqrtf(u * u + v * v) + 3.0f * sqrtf(pr * ir));
+            P.dt[p] = f32_to_f64_ip(dt);
         } else {
-            dt = P.dt[p];
+            dt = f64_to_f32_ip(P.dt[p]);
         }
+        float *accf = reinterpret_cast<float *>(P.acc);
+        float inc[4];  // U_new = U^n - inc
         if (P.mode == 1) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) Unew[k] = Un[k] - dt * Rg[k];
+            for (int k = 0; k < 4; ++k) inc[k] = dt * Rl[k];
         } else {
-            double a[4];
-            if (P.stage == 0) {
+            float a[4] = {Rl[0], Rl[1], Rl[2], Rl[3]};
+            if (P.stage > 0) {
+                float o[4];
+                load4f(accf, p, o);
+                const float c = P.stage < 3 ? 2.0f : 1.0f;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) a[k] = Rg[k];
-            } else {
-                load4(P.acc, p, a);
-                const double c = P.stage < 3 ? 2.0 : 1.0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) a[k] = a[k] + c * Rg[k];
+                for (int k = 0; k < 4; ++k) a[k] = o[k] + c * Rl[k];
             }
             if (P.stage < 3) {
-                store4(P.acc, p, a);
-                const double c = (P.stage == 2) ? dt : 0.5 * dt;
+                store4f(accf, p, a);
+                const float c = P.stage == 2 ? dt : 0.5f * dt;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) Unew[k] = Un[k] - c * Rg[k];
+                for (int k = 0; k < 4; ++k) inc[k] = c * Rl[k];
             } else {
-                const double c = dt / 6.0;
+                const float c = dt * (1.0f / 6.0f);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) Unew[k] = Un[k] - c * a[k];
+                for (int k = 0; k < 4; ++k) inc[k] = c * a[k];
             }
         }
+        double Unew[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Unew[k] = Un[k] - f32_to_f64_ip(inc[k]);
         if (flag == FLAG_WALL) {
+            // remove the normal momentum (FP64, wall points only)
             const double2 n0 = P.nrm64[p];
             const double mn = Unew[1] * n0.x + Unew[2] * n0.y;
             Unew[1] = Unew[1] - mn * n0.x;
@@ -296,20 +382,29 @@ __global__ void __launch_bounds__(128) k_flux_update_mixed(MixedFluxParams P)
             for (int k = 0; k < 4; ++k) Unew[k] = P.Uinf[k];
         }
         store4(P.Uout, p, Unew);
-        float qn[4];
-        if (!q_from_U_f(Unew, P.gamma, P.inv_gm1, qn)) flag_nonphysical_m(P.status, p);
+        float Uf[4], qn[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Uf[k] = f64_to_f32_ip(Unew[k]);
+        if (!q_from_Uf(Uf, P.gamma, P.inv_gm1, qn)) flag_nonphysical_m(P.status, p);
         store4f(P.qout, p, qn);
+        r0sq = Rl[0] * Rl[0];
     }
 
+    // residue partials: FP32 within a warp, FP64 across warps and blocks
     if (P.mode == 1 || P.stage == 0) {
-        double s = Rg[0] * Rg[0];
+        float s = r0sq;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        __shared__ double ws[4];
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) ws[wid] = s;
+        __shared__ double ws[kMixedThreads / 32];
+        const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (wl == 0) ws[wid] = (double)s;
         __syncthreads();
-        if (threadIdx.x == 0) P.norm_part[blockIdx.x] = (ws[0] + ws[1]) + (ws[2] + ws[3]);
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < kMixedThreads / 32; ++k) t += ws[k];
+            P.norm_part[blockIdx.x] = t;
+        }
     }
 }
 
@@ -342,16 +437,18 @@ __global__ void __launch_bounds__(256) k_grad_out_f(int64_t n, const int32_t *__
     }
 }
 
+unsigned mixed_flux_blocks(int64_t n) { return (unsigned)((n + kMixedThreads - 1) / kMixedThreads); }
+
 cudaError_t launch_qgrad_mixed(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new,
                                double limiter_K, cudaStream_t s)
 {
-    k_qgrad_mixed<<<(unsigned)((g.n + 127) / 128), 128, 0, s>>>(g, q, qg_old, qg_new, (float)limiter_K);
+    k_qgrad_mixed<<<mixed_flux_blocks(g.n), kMixedThreads, 0, s>>>(g, q, qg_old, qg_new, (float)limiter_K);
     return cudaGetLastError();
 }
 
 cudaError_t launch_flux_mixed(const MixedFluxParams &P, cudaStream_t s)
 {
-    k_flux_update_mixed<<<(unsigned)((P.g.n + 127) / 128), 128, 0, s>>>(P);
+    k_flux_update_mixed<<<mixed_flux_blocks(P.g.n), kMixedThreads, 0, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -11,19 +11,22 @@ namespace lskum {
 // flag bit: this point's least-squares closure runs in FP64
 enum : uint8_t { FLAG_FP64_CLOSURE = 0x80 };
 
+// Edge arrays are in the SELL-32 layout: slot s of point p at
+// slice_off[p / 32] + 32 s + p % 32 (see lskum_mixed.cu).
 struct MixedGeom {
     int64_t n;
-    const float2 *__restrict__ nrm;     // frame normal
-    const uint8_t *__restrict__ flag;   // bits 0-1 point flag, bit 7 FP64 closure
-    const float *__restrict__ dmin;     // nearest-neighbour distance
-    const int32_t *__restrict__ off;
-    const int32_t *__restrict__ idx;
-    const uint8_t *__restrict__ mask;
-    const float2 *__restrict__ dxy;     // per edge: P_i - P_0
-    const float2 *__restrict__ lsw;     // per edge: full-stencil weights
-    const float2 *__restrict__ fxw;     // per edge: sub-stencil weights
-    const double2 *__restrict__ fxw64;  // per edge: FP64 sub-stencil weights
+    const float2 *__restrict__ nrm;       // frame normal
+    const uint8_t *__restrict__ flag;     // bits 0-1 point flag, bit 7 FP64 closure
+    const float *__restrict__ dmin;       // nearest-neighbour distance
+    const int32_t *__restrict__ off;      // CSR offsets (degree = off[p+1] - off[p])
+    const int32_t *__restrict__ slice_off;
+    const int32_t *__restrict__ sidx;     // per slot: neighbour index | sub-stencil bits << 28
+    const float4 *__restrict__ gq;        // per slot: (dx, dy, a_x, a_y) full-stencil weights
+    const float4 *__restrict__ gf;        // per slot: (dx, dy, w_s, w_n) sub-stencil weights
+    const double2 *__restrict__ fxw64;    // per slot: FP64 sub-stencil weights
 };
+
+static constexpr int32_t kSlotIndexMask = 0x0fffffff;  // mixed layout: n < 2^28
 
 struct MixedFluxParams {
     MixedGeom g;
@@ -44,11 +47,15 @@ struct MixedFluxParams {
     int order, mode, stage;
 };
 
-cudaError_t launch_mixed_prep(const DevGeom &g, const MixedGeom &m, uint8_t *flag, int *n_fp64,
-                              cudaStream_t s);
+cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, float *dmin_f,
+                              float2 *dxy_f, float2 *lsw_f, float2 *fxw_f, int *n_fp64, cudaStream_t s);
+cudaError_t launch_sell_fill(int64_t n, const int32_t *off, const int32_t *slice_off, const int32_t *idx,
+                             const uint8_t *mask, const float2 *dxy, const float2 *lsw, const float2 *fxw,
+                             const double2 *fxw64, const MixedGeom &m, cudaStream_t s);
 cudaError_t launch_qgrad_mixed(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new,
                                double limiter_K, cudaStream_t s);
 cudaError_t launch_flux_mixed(const MixedFluxParams &P, cudaStream_t s);
+unsigned mixed_flux_blocks(int64_t n);  // grid of the mixed flux kernel (one residue partial per block)
 cudaError_t launch_q_from_U_mixed(int64_t n, const Gas &gas, const double *U, float *q, int *status,
                                   cudaStream_t s);
 cudaError_t launch_grad_out_f(int64_t n, const int32_t *perm, const float *qg, double *qx, double *qy,
