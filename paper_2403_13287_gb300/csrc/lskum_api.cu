@@ -52,7 +52,23 @@ struct lskum_ctx {
     int nparts = 0;
     double *res_dev = nullptr;
     int res_cap = 0;
+    int *res_counter = nullptr;  // next entry of res_dev the residue kernel writes
     int *status = nullptr;
+
+    // lskum_step replays one captured iteration (two for forward Euler, so
+    // the q ping-pong ends where it began) as a CUDA graph; the graph bakes
+    // in q_cur and res_dev, so one exec is kept per starting q buffer and
+    // both are rebuilt when res_dev grows
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        const void *q_start = nullptr;
+        const double *res = nullptr;
+        int iters = 0;
+        int64_t launches = 0;
+    };
+    StepGraph graphs[2];
+    cudaStream_t gstream = nullptr;  // capture stream (never the legacy default stream)
+    bool graphs_off = false;
     double *fbuf = nullptr;
 
     // kernel timing (lskum_profile): event pairs per kernel class, reused
@@ -217,6 +233,9 @@ extern "C" void lskum_destroy(lskum_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (auto &g : ctx->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
     free_all(ctx);
     delete ctx;
 }
@@ -396,6 +415,8 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     CK(c, dalloc(c, &c->status, 2));
     c->res_cap = 1024;
     CK(c, dalloc(c, &c->res_dev, c->res_cap));
+    CK(c, dalloc(c, &c->res_counter, 1));
+    CK(c, cudaMemsetAsync(c->res_counter, 0, sizeof(int), s));
     CK(c, cudaMemsetAsync(c->qgA, 0, 2 * 8 * n * qbytes, s));
     const int st_init[2] = {0, 0x7fffffff};
     CK(c, cudaMemcpyAsync(c->status, st_init, sizeof st_init, cudaMemcpyHostToDevice, s));
@@ -548,7 +569,7 @@ static lskum_status flux(lskum_ctx *c, const void *q, const void *qg, double *Uo
     return LSKUM_OK;
 }
 
-static lskum_status iteration(lskum_ctx *c, int it)
+static lskum_status iteration(lskum_ctx *c)
 {
     const bool rk4 = c->cfg.time_scheme == 1;
     const int stages = rk4 ? 4 : 1;
@@ -559,7 +580,9 @@ static lskum_status iteration(lskum_ctx *c, int it)
         st = flux(c, c->q_cur, qg, (rk4 && k < 3) ? c->Us : c->U, c->q_nxt, rk4 ? 2 : 1, k, nullptr);
         if (st != LSKUM_OK) return st;
         std::swap(c->q_cur, c->q_nxt);
-        if (k == 0) LAUNCH(c, launch_residue_finish(c->norm_part, c->nparts, c->n, c->res_dev + it, c->stream));
+        if (k == 0)
+            LAUNCH(c, launch_residue_finish(c->norm_part, c->nparts, c->n, c->res_dev, c->res_counter, c->res_cap,
+                                            c->stream));
     }
     return LSKUM_OK;
 }
@@ -578,6 +601,68 @@ static lskum_status read_status(lskum_ctx *c, int st[2])
     return LSKUM_OK;
 }
 
+// captures `iters` iterations from the current q buffer into g (the kernels
+// only: status, counter and backup are set up outside the graph)
+static lskum_status capture_step_graph(lskum_ctx *c, lskum_ctx::StepGraph &g, int iters)
+{
+    if (!c->gstream) CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    if (g.exec) {
+        CK(c, cudaGraphExecDestroy(g.exec));
+        g.exec = nullptr;
+    }
+    void *const q_start = c->q_cur, *const q_other = c->q_nxt;
+    cudaStream_t user = c->stream;
+    const int64_t launches0 = c->launches;
+    CK(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+    c->stream = c->gstream;
+    lskum_status st = LSKUM_OK;
+    for (int i = 0; i < iters && st == LSKUM_OK; ++i) st = iteration(c);
+    c->stream = user;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->gstream, &graph);
+    // the capture only recorded the launches: undo the q ping-pong (a replay
+    // ends on q_start again) and the launch count
+    c->q_cur = q_start;
+    c->q_nxt = q_other;
+    g.launches = c->launches - launches0;
+    c->launches = launches0;
+    if (st != LSKUM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    CK(c, ec);
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(c, ei);
+    g.q_start = q_start;
+    g.res = c->res_dev;
+    g.iters = iters;
+    return LSKUM_OK;
+}
+
+// n_iters iterations by graph replay; returns the iterations left to launch
+// directly (an odd forward-Euler remainder)
+static lskum_status replay_step_graph(lskum_ctx *c, int n_iters, int *left)
+{
+    const int per = c->cfg.time_scheme == 1 ? 1 : 2;
+    *left = n_iters % per;
+    const int reps = n_iters / per;
+    if (reps == 0) return LSKUM_OK;
+    lskum_ctx::StepGraph *g = nullptr;
+    for (auto &cand : c->graphs)
+        if (cand.exec && cand.q_start == c->q_cur && cand.res == c->res_dev) g = &cand;
+    if (!g) {
+        g = &c->graphs[c->q_cur < c->q_nxt ? 0 : 1];  // one slot per q buffer
+        lskum_status st = capture_step_graph(c, *g, per);
+        if (st != LSKUM_OK) return st;
+    }
+    for (int r = 0; r < reps; ++r) {
+        CK(c, cudaGraphLaunch(g->exec, c->stream));
+        c->launches += g->launches;
+    }
+    return LSKUM_OK;
+}
+
 extern "C" lskum_status lskum_step(lskum_ctx *c, int n_iters, double *res_history)
 {
     if (!c) return LSKUM_ERR_ARG;
@@ -593,8 +678,14 @@ extern "C" lskum_status lskum_step(lskum_ctx *c, int n_iters, double *res_histor
     lskum_status st = reset_status(c);
     if (st != LSKUM_OK) return st;
     CK(c, cudaMemcpyAsync(c->Ubak, c->U, 4 * c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    for (int it = 0; it < n_iters; ++it) {
-        st = iteration(c, it);
+    CK(c, cudaMemsetAsync(c->res_counter, 0, sizeof(int), c->stream));
+    int direct = n_iters;
+    if (!c->profiling && !c->graphs_off) {
+        st = replay_step_graph(c, n_iters, &direct);
+        if (st != LSKUM_OK) return st;
+    }
+    for (int it = 0; it < direct; ++it) {
+        st = iteration(c);
         if (st != LSKUM_OK) return st;
     }
     if (res_history)

@@ -277,9 +277,12 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
     }
 }
 
-// residue() = sqrt(sum R_rho^2)/n from the block partials, in a fixed order
+// residue() = sqrt(sum R_rho^2)/n from the block partials, in a fixed order,
+// written to out[*counter]; the counter then advances (so one captured
+// iteration can be replayed), bounded by cap
 __global__ void __launch_bounds__(256) k_residue_finish(const double *__restrict__ part, int nparts,
-                                                        double inv_n, double *__restrict__ out)
+                                                        double inv_n, double *__restrict__ out_base,
+                                                        int *counter, int cap)
 {
     double s = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
@@ -290,7 +293,11 @@ __global__ void __launch_bounds__(256) k_residue_finish(const double *__restrict
         if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = sqrt(sm[0]) * inv_n;
+    if (threadIdx.x == 0) {
+        const int it = *counter;
+        if (it >= 0 && it < cap) out_base[it] = sqrt(sm[0]) * inv_n;
+        *counter = it + 1;
+    }
 }
 
 // q-variables of every point from U (used when a state is loaded)
@@ -384,9 +391,10 @@ cudaError_t launch_flux(const DevGeom &g, const Gas &gas, const FluxLaunch &L, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_residue_finish(const double *part, int nparts, int64_t n, double *out, cudaStream_t s)
+cudaError_t launch_residue_finish(const double *part, int nparts, int64_t n, double *out_base, int *counter,
+                                  int cap, cudaStream_t s)
 {
-    k_residue_finish<<<1, 256, 0, s>>>(part, nparts, 1.0 / (double)n, out);
+    k_residue_finish<<<1, 256, 0, s>>>(part, nparts, 1.0 / (double)n, out_base, counter, cap);
     return cudaGetLastError();
 }
 

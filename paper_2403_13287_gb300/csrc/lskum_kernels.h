@@ -29,8 +29,9 @@ unsigned flux_blocks(int64_t n);
 cudaError_t launch_qgrad(const DevGeom &g, const double *q, const double *qg_old, double *qg_new,
                          double limiter_K, cudaStream_t s);
 cudaError_t launch_flux(const DevGeom &g, const Gas &gas, const FluxLaunch &L, cudaStream_t s);
-cudaError_t launch_residue_finish(const double *part, int nparts, int64_t n, double *out,
-                                  cudaStream_t s);
+// writes the residue to out_base[*counter] (when 0 <= *counter < cap), then ++*counter
+cudaError_t launch_residue_finish(const double *part, int nparts, int64_t n, double *out_base, int *counter,
+                                  int cap, cudaStream_t s);
 cudaError_t launch_q_from_U(int64_t n, const Gas &gas, const double *U, double *q, int *status,
                             cudaStream_t s);
 cudaError_t launch_timestep(int64_t n, const Gas &gas, double cfl, const double *dmin, const double *U,
