@@ -1,0 +1,228 @@
+"""Exact directional derivatives of the q-LSKUM residual, for checking its
+vector-Jacobian product (VJP).
+
+TEST INFRASTRUCTURE ONLY: the tests use this module; the CUDA product path
+never imports it.
+
+The residual R(U; x, y) of the scheme (E13 q-variables; E15 q-derivatives
+with the E14 modified variables and `inner` Jacobi iterations; the kinetic
+split fluxes of each x+/x-/y+/y- sub-stencil closed by the least-squares
+formula E11; the sum E10) is written out again here in plain numpy, in the
+same steps and the same order as the C oracle, but over complex numbers.
+The complex-step method (W. Squire and G. Trapp, SIAM Review 40 (1998)
+110-112; J. Martins, P. Sturdza and J. Alonso, ACM TOMS 29 (2003) 245-262)
+then gives the Jacobian-vector product J v without a difference quotient:
+for an analytic f, Im f(z + i h v) / h = f'(z) v + O(h^2), and with
+h = 1e-30 the O(h^2) term is far below rounding. Discrete choices (the
+sub-stencil masks, the positivity checks) use real parts only, and erf of a
+complex argument is its first-order expansion erf(a) + i b erf'(a),
+which is exact to O(b^2).
+
+The VJP of a seeded R_bar is then checked entry by entry:
+(J^T R_bar)_k = <R_bar, J e_k>, one complex-step residual per entry.
+
+Derivatives with respect to x and y hold the frame normals, the
+connectivity and the sub-stencil membership fixed (they are inputs of the
+scheme, not functions of the coordinates).
+
+The module is pinned against the C oracle: its real part is the C oracle's
+residual, and its J v agrees with central differences of the C oracle.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import erf as _erf_real
+
+XPOS, XNEG, YPOS, YNEG = 1, 2, 4, 8
+INTERIOR, WALL, FARFIELD = 0, 1, 2
+
+_TWO_OVER_SQRT_PI = 2.0 / math.sqrt(math.pi)
+
+
+def _erf(z):
+    """erf on the complex-step lattice: erf(a) + i b (2/sqrt(pi)) exp(-a^2)."""
+    if not np.iscomplexobj(z):
+        return _erf_real(z)
+    a = z.real
+    return _erf_real(a) + 1j * z.imag * (_TWO_OVER_SQRT_PI * np.exp(-a * a))
+
+
+class _Edges:
+    """CSR edge lists: src (owner point), dst (neighbour)."""
+
+    def __init__(self, cloud):
+        off = np.asarray(cloud["nbr_offsets"], dtype=np.int64)
+        self.n = int(cloud["n"])
+        self.off = off
+        self.src = np.repeat(np.arange(self.n), np.diff(off))
+        self.dst = np.asarray(cloud["nbr_idx"], dtype=np.int64)
+
+    def rowsum(self, vals):
+        """Per-point sum over the point's CSR row, in CSR order (as the C loop)."""
+        out = np.zeros(self.n, dtype=vals.dtype)
+        np.add.at(out, self.src, vals)
+        return out
+
+
+def q_from_U(U, gamma=1.4):
+    """E13: q = [ln rho + ln(beta)/(gamma-1) - beta |u|^2, 2 beta u1, 2 beta u2, -2 beta]."""
+    rho = U[0]
+    u1 = U[1] / rho
+    u2 = U[2] / rho
+    p = (gamma - 1.0) * (U[3] - 0.5 * rho * (u1 * u1 + u2 * u2))
+    beta = 0.5 * rho / p
+    return np.stack([np.log(rho) + np.log(beta) / (gamma - 1.0) - beta * (u1 * u1 + u2 * u2),
+                     2.0 * beta * u1, 2.0 * beta * u2, -2.0 * beta])
+
+
+def _prim_from_q(qt, gamma):
+    """Inverse of E13 for q[4, m]: (rho, u1, u2, p)."""
+    beta = -0.5 * qt[3]
+    if np.any(beta.real <= 0.0):
+        raise ValueError("reconstructed state with beta <= 0")
+    u1 = qt[1] / (2.0 * beta)
+    u2 = qt[2] / (2.0 * beta)
+    rho = np.exp(qt[0] - np.log(beta) / (gamma - 1.0) + beta * (u1 * u1 + u2 * u2))
+    p = rho / (2.0 * beta)
+    return rho, u1, u2, p
+
+
+def _split_flux(gamma, rho, un, ut, p, sign):
+    """Half-range-moment split flux along a direction (un normal, ut transverse);
+    components [mass, normal momentum, transverse momentum, energy]."""
+    beta = 0.5 * rho / p
+    S = un * np.sqrt(beta)
+    A = 0.5 * (1.0 + sign * _erf(S))
+    B = np.exp(-S * S) / (2.0 * np.sqrt(math.pi * beta))
+    rhoE = p / (gamma - 1.0) + 0.5 * rho * (un * un + ut * ut)
+    return np.stack([rho * (un * A + sign * B),
+                     (p + rho * un * un) * A + sign * rho * un * B,
+                     rho * ut * (un * A + sign * B),
+                     (rhoE + p) * un * A + sign * (rhoE + 0.5 * p) * B])
+
+
+def _frame_flux(gamma, prim, tx, ty, nx, ny, direction, sign):
+    """Split flux along s (direction 0) or n (1) in frame order [mass, s-mom, n-mom, energy]."""
+    rho, u1, u2, p = prim
+    us = u1 * tx + u2 * ty
+    un = u1 * nx + u2 * ny
+    if direction == 0:
+        return _split_flux(gamma, rho, us, un, p, sign)
+    g = _split_flux(gamma, rho, un, us, p, sign)
+    return np.stack([g[0], g[2], g[1], g[3]])
+
+
+def _gradient_pass(E, dx, dy, q, gx_old=None, gy_old=None):
+    """One least-squares solve of E15 (first order when gx_old is None)."""
+    sxx = E.rowsum(dx * dx)
+    sxy = E.rowsum(dx * dy)
+    syy = E.rowsum(dy * dy)
+    det = sxx * syy - sxy * sxy
+    gx = np.empty_like(q)
+    gy = np.empty_like(q)
+    for k in range(4):
+        dq = q[k][E.dst] - q[k][E.src]
+        if gx_old is not None:
+            dq = dq - 0.5 * (dx * (gx_old[k][E.dst] - gx_old[k][E.src])
+                             + dy * (gy_old[k][E.dst] - gy_old[k][E.src]))
+        sxq = E.rowsum(dx * dq)
+        syq = E.rowsum(dy * dq)
+        gx[k] = (syy * sxq - sxy * syq) / det
+        gy[k] = (sxx * syq - sxy * sxq) / det
+    return gx, gy
+
+
+def _residual(cloud, mask, U, x, y, order, inner, gamma):
+    E = _Edges(cloud)
+    n = E.n
+    nx = np.asarray(cloud["nx"], dtype=np.float64)
+    ny = np.asarray(cloud["ny"], dtype=np.float64)
+    flags = np.asarray(cloud["flags"])
+    mask = np.asarray(mask, dtype=np.uint8)
+    dx = x[E.dst] - x[E.src]
+    dy = y[E.dst] - y[E.src]
+    q = q_from_U(U, gamma)
+    if order == 2:
+        gx, gy = _gradient_pass(E, dx, dy, q)
+        for _ in range(inner):
+            gx, gy = _gradient_pass(E, dx, dy, q, gx, gy)
+        qt_i = np.stack([q[k][E.dst] - 0.5 * (dx * gx[k][E.dst] + dy * gy[k][E.dst]) for k in range(4)])
+        qt_0 = np.stack([q[k][E.src] - 0.5 * (dx * gx[k][E.src] + dy * gy[k][E.src]) for k in range(4)])
+    else:
+        qt_i = q[:, E.dst]
+        qt_0 = q[:, E.src]
+    prim_i = _prim_from_q(qt_i, gamma)
+    prim_0 = _prim_from_q(qt_0, gamma)
+    tx, ty = ny[E.src], -nx[E.src]
+    enx, eny = nx[E.src], ny[E.src]
+    ds = dx * tx + dy * ty
+    dn = dx * enx + dy * eny
+    Rl = np.zeros((4, n), dtype=np.result_type(U, x, y, np.float64))
+    subs = ((XPOS, 0, +1.0), (XNEG, 0, -1.0), (YPOS, 1, +1.0), (YNEG, 1, -1.0))
+    for sub, (bit, direction, sign) in enumerate(subs):
+        inside = (mask & bit) != 0
+        # the sub-stencil's own sums: terms of other edges are left out
+        Gi = _frame_flux(gamma, prim_i, tx, ty, enx, eny, direction, sign)
+        G0 = _frame_flux(gamma, prim_0, tx, ty, enx, eny, direction, sign)
+        sel = inside.astype(np.float64)
+        sss = E.rowsum(sel * ds * ds)
+        ssn = E.rowsum(sel * ds * dn)
+        snn = E.rowsum(sel * dn * dn)
+        det = sss * snn - ssn * ssn
+        used = flags != FARFIELD
+        if sub == 2:
+            used &= flags != WALL                       # no dGn+/dn at the wall
+        safe = np.where(used, det, 1.0)
+        for k in range(4):
+            dG = sel * (Gi[k] - G0[k])
+            ssG = E.rowsum(ds * dG)
+            snG = E.rowsum(dn * dG)
+            if direction == 0:
+                d = (snn * ssG - ssn * snG) / safe
+            else:
+                d = (sss * snG - ssn * ssG) / safe
+            Rl[k] += np.where(used, d, 0.0)
+    tx, ty = ny, -nx
+    return np.stack([Rl[0], Rl[1] * tx + Rl[2] * nx, Rl[1] * ty + Rl[2] * ny, Rl[3]])
+
+
+def residual(cloud, mask, U, order=2, inner=3, gamma=1.4):
+    """R(U) of the unlimited scheme in real arithmetic (equals the C oracle's)."""
+    x = np.asarray(cloud["x"], dtype=np.float64)
+    y = np.asarray(cloud["y"], dtype=np.float64)
+    return _residual(cloud, mask, np.asarray(U, dtype=np.float64), x, y, order, inner, gamma)
+
+
+def jvp(cloud, mask, U, dU=None, dx=None, dy=None, order=2, inner=3, gamma=1.4, h=1e-30):
+    """J v = dR/dU dU + dR/dx dx + dR/dy dy at (U, x, y), by complex step."""
+    U = np.asarray(U, dtype=np.float64).astype(np.complex128)
+    x = np.asarray(cloud["x"], dtype=np.float64).astype(np.complex128)
+    y = np.asarray(cloud["y"], dtype=np.float64).astype(np.complex128)
+    if dU is not None:
+        U = U + 1j * h * np.asarray(dU, dtype=np.float64)
+    if dx is not None:
+        x = x + 1j * h * np.asarray(dx, dtype=np.float64)
+    if dy is not None:
+        y = y + 1j * h * np.asarray(dy, dtype=np.float64)
+    return _residual(cloud, mask, U, x, y, order, inner, gamma).imag / h
+
+
+def vjp_entries(cloud, mask, U, R_bar, entries, order=2, inner=3, gamma=1.4):
+    """Selected entries of the VJP J^T R_bar: entries is a list of
+    ("U", component, point), ("x", point) or ("y", point); each is
+    <R_bar, J e> for the unit direction e of that entry."""
+    n = int(cloud["n"])
+    out = np.empty(len(entries))
+    for j, ent in enumerate(entries):
+        if ent[0] == "U":
+            d = np.zeros((4, n))
+            d[ent[1], ent[2]] = 1.0
+            Jv = jvp(cloud, mask, U, dU=d, order=order, inner=inner, gamma=gamma)
+        else:
+            d = np.zeros(n)
+            d[ent[1]] = 1.0
+            Jv = jvp(cloud, mask, U, **{"d" + ent[0]: d}, order=order, inner=inner, gamma=gamma)
+        out[j] = float(np.sum(R_bar * Jv))
+    return out

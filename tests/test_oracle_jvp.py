@@ -1,0 +1,126 @@
+"""Pins of the complex-step derivative oracle (oracle/lskum_jvp.py), no GPU.
+
+The derivative oracle restates the residual over complex numbers. It is tied
+to the C oracle twice: its real arithmetic reproduces the C oracle's
+residual, and its J v agrees with central differences of the C oracle (a
+dropped term, a wrong sign or a transposed operand in either breaks one of
+the two). The entry-wise VJP is checked against a brute-force transpose of
+the full Jacobian on a tiny cloud.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import lskum_jvp
+from paper_2403_13287_gb300.cloudgen import naca0012_cloud, smooth_state
+
+GAMMA = 1.4
+
+
+@pytest.fixture(scope="module")
+def cloud():
+    c = naca0012_cloud(48, 10, seed=4)
+    return c, oracle.split_stencils(c)
+
+
+def _state(c, amp=0.05, seed=3):
+    return smooth_state(c, 0.63, 2.0, amp=amp, seed=seed)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_real_part_is_the_c_oracle_residual(cloud, order):
+    c, mask = cloud
+    U = _state(c)
+    R_c, S = oracle.residual(c, mask, U, order=order, inner=3, want_scale=True)
+    R_py = lskum_jvp.residual(c, mask, U, order=order, inner=3)
+    # same steps and order; only erf comes from another library (cephes)
+    assert np.all(np.abs(R_py - R_c) <= 1e-13 * S + 1e-300)
+
+
+def _fd(c, mask, U, dU, dx, dy, order, eps):
+    def R(s):
+        cc = dict(c)
+        cc["x"] = c["x"] + s * dx
+        cc["y"] = c["y"] + s * dy
+        return oracle.residual(cc, mask, U + s * dU, order=order, inner=3)
+    return (R(eps) - R(-eps)) / (2 * eps)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("what", ["U", "xy"])
+def test_jvp_matches_central_differences_of_the_c_oracle(cloud, order, what):
+    c, mask = cloud
+    n = c["n"]
+    U = _state(c)
+    rng = np.random.default_rng(17)
+    dU = np.zeros((4, n))
+    dx = np.zeros(n)
+    dy = np.zeros(n)
+    if what == "U":
+        dU = rng.standard_normal((4, n)) * np.abs(U)
+    else:
+        # displacements of the order of the local spacing
+        dx = rng.standard_normal(n) * 0.01
+        dy = rng.standard_normal(n) * 0.01
+    J = lskum_jvp.jvp(c, mask, U, dU, dx, dy, order=order, inner=3)
+    F = _fd(c, mask, U, dU, dx, dy, order, 1e-6)
+    F2 = _fd(c, mask, U, dU, dx, dy, order, 2e-6)
+    # Richardson: the difference error is O(eps^2); scale it from two steps
+    err_fd = np.abs(F2 - F) + 1e-9 * np.max(np.abs(J))
+    assert np.max(np.abs(J)) > 0
+    assert np.all(np.abs(J - F) <= 10 * err_fd)
+    assert np.max(np.abs(J - F)) <= 1e-6 * np.max(np.abs(J))
+
+
+def test_jvp_is_linear_in_the_direction(cloud):
+    c, mask = cloud
+    n = c["n"]
+    U = _state(c)
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((4, n)) * np.abs(U)
+    b = rng.standard_normal((4, n)) * np.abs(U)
+    Ja = lskum_jvp.jvp(c, mask, U, dU=a)
+    Jb = lskum_jvp.jvp(c, mask, U, dU=b)
+    Jab = lskum_jvp.jvp(c, mask, U, dU=2.0 * a - 3.0 * b)
+    assert np.allclose(Jab, 2.0 * Ja - 3.0 * Jb, rtol=1e-12, atol=1e-12 * np.max(np.abs(Jab)))
+
+
+def test_uniform_flow_has_no_derivative_along_the_free_stream(cloud):
+    """R(U_inf + t U_inf) = 0 for every t (uniform states give dG = 0 on
+    every edge), so J U_inf = 0 away from the wall, where the uniform state
+    would carry normal momentum."""
+    c, mask = cloud
+    n = c["n"]
+    Uinf = oracle.freestream(0.63, 2.0)
+    U = np.repeat(Uinf[:, None], n, axis=1)
+    J = lskum_jvp.jvp(c, mask, U, dU=U.copy())
+    assert np.all(J == 0.0)
+
+
+def test_vjp_entries_are_the_transposed_jacobian():
+    """Brute force on a tiny cloud: build J column by column, compare J^T r."""
+    c = naca0012_cloud(20, 5, seed=9)
+    mask = oracle.split_stencils(c)
+    n = c["n"]
+    U = _state(c, amp=0.01, seed=8)
+    rng = np.random.default_rng(2)
+    r = rng.standard_normal((4, n))
+    cols = []
+    for k in range(4):
+        for p in range(n):
+            d = np.zeros((4, n))
+            d[k, p] = 1.0
+            cols.append(lskum_jvp.jvp(c, mask, U, dU=d).ravel())
+    for name in ("dx", "dy"):
+        for p in range(n):
+            d = np.zeros(n)
+            d[p] = 1.0
+            cols.append(lskum_jvp.jvp(c, mask, U, **{name: d}).ravel())
+    J = np.stack(cols, axis=1)                    # (4n) x (6n)
+    full = J.T @ r.ravel()
+    ent = ([("U", k, p) for k in range(4) for p in range(0, n, 7)]
+           + [("x", p) for p in range(0, n, 5)] + [("y", p) for p in range(1, n, 5)])
+    pos = {"x": 4 * n, "y": 5 * n}
+    want = np.array([full[e[1] * n + e[2]] if e[0] == "U" else full[pos[e[0]] + e[1]] for e in ent])
+    got = lskum_jvp.vjp_entries(c, mask, U, r, ent)
+    assert np.allclose(got, want, rtol=1e-13, atol=1e-13 * np.max(np.abs(full)))
