@@ -132,6 +132,26 @@ lskum_status lskum_step(lskum_ctx *ctx, int n_iters, double *res_history);
 lskum_status lskum_residual(lskum_ctx *ctx, const double *U, double *R);
 
 /*
+ * Vector-Jacobian product of the residual above (the E10 residual with E11
+ * closures, the E14 reconstruction and the E15 q-derivatives, differentiated
+ * in reverse): for a cotangent R_bar,
+ *   U_bar = (dR/dU)^T R_bar,  x_bar = (dR/dx)^T R_bar,  y_bar = (dR/dy)^T R_bar.
+ * The derivative in x and y holds the frame normals, the connectivity and the
+ * sub-stencil membership fixed (they are inputs, not functions of x and y).
+ * Computed in FP64 whatever the context's precision, for the FP64 residual.
+ *   U      device float64[4*n] in input order, or NULL for the context's state
+ *   R_bar  device float64[4*n] in input order
+ *   U_bar  device float64[4*n] in input order (written), or NULL
+ *   x_bar, y_bar  device float64[n] in input order (written), or NULL
+ * Requires limiter_K = 0 (the limiter's min/max is not differentiated):
+ * LSKUM_ERR_ARG otherwise. Its workspace (about 0.45 KB per point plus
+ * 100 B per edge for K = 3) is allocated on the first call and kept.
+ * Does not change the context's state.
+ */
+lskum_status lskum_residual_vjp(lskum_ctx *ctx, const double *U, const double *R_bar, double *U_bar,
+                                double *x_bar, double *y_bar);
+
+/*
  * q-derivatives of E15 (global x, y frame) after the configured inner
  * iterations (order 2) or the first-order solve (order 1), for state U.
  *   U       device float64[4*n] or NULL (context state)

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblskum.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["lskum_api.cu", "lskum_kernels.cu", "lskum_setup.cu", "lskum_noalloc.cu", "lskum_mixed.cu"]
+SOURCES = ["lskum_api.cu", "lskum_kernels.cu", "lskum_setup.cu", "lskum_noalloc.cu", "lskum_mixed.cu",
+           "lskum_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -1,0 +1,701 @@
+// Vector-Jacobian product of the q-LSKUM residual (E10 with E11, E13-E15):
+// U_bar = (dR/dU)^T R_bar and (x_bar, y_bar) = (dR/dx, dR/dy)^T R_bar, in
+// FP64, for the unlimited scheme of order 1 or 2.
+//
+// Reverse pass, every sum a gather (no atomics, bitwise reproducible):
+//   flux      per point (owner of its edges): the split-flux Jacobians at
+//             both reconstructed states (forward-mode duals, 4 tangents),
+//             cotangents of the owner's q~_0, of each neighbour's q~_i (kept
+//             per edge) and of the sub-stencil weights;
+//   gather    per point over its incoming edges (transpose CSR): the
+//             neighbour-side cotangents;
+//   gradient  the K+1 least-squares passes of E15 in reverse (saved forward
+//             iterates), each pass one kernel with an outgoing-edge loop
+//             (owner terms, weight and offset cotangents) and an incoming-
+//             edge loop (neighbour terms);
+//   geometry  least-squares weight cotangents back to edge offsets
+//             (a = M^-1 d with M = sum d d^T gives d_bar_k = b_k - B d_k,
+//             b = M^-1 a_bar, B = sum (b a^T + a b^T)), then offsets to
+//             points by one more gather;
+//   state     q_bar to U_bar through the E13 Jacobian.
+#include <cub/cub.cuh>
+
+#include "lskum_adjoint.h"
+
+namespace lskum {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// forward-mode dual number with four tangents
+// ---------------------------------------------------------------------------
+struct D4 {
+    double v, d[4];
+};
+
+__device__ __forceinline__ D4 dconst(double v)
+{
+    D4 r;
+    r.v = v;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.d[k] = 0.0;
+    return r;
+}
+__device__ __forceinline__ D4 operator+(const D4 &a, const D4 &b)
+{
+    D4 r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] + b.d[k];
+    return r;
+}
+__device__ __forceinline__ D4 operator-(const D4 &a, const D4 &b)
+{
+    D4 r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] - b.d[k];
+    return r;
+}
+__device__ __forceinline__ D4 operator*(const D4 &a, const D4 &b)
+{
+    D4 r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+__device__ __forceinline__ D4 operator*(double s, const D4 &a)
+{
+    D4 r;
+    r.v = s * a.v;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.d[k] = s * a.d[k];
+    return r;
+}
+__device__ __forceinline__ D4 operator+(double s, const D4 &a)
+{
+    D4 r = a;
+    r.v = s + a.v;
+    return r;
+}
+// f(a) with f(a.v) = fv and f'(a.v) = df
+__device__ __forceinline__ D4 chain(const D4 &a, double fv, double df)
+{
+    D4 r;
+    r.v = fv;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.d[k] = df * a.d[k];
+    return r;
+}
+__device__ __forceinline__ D4 recip(const D4 &a)
+{
+    const double r = 1.0 / a.v;
+    return chain(a, r, -r * r);
+}
+__device__ __forceinline__ D4 dexp(const D4 &a)
+{
+    const double e = exp(a.v);
+    return chain(a, e, e);
+}
+__device__ __forceinline__ D4 dlog(const D4 &a) { return chain(a, log(a.v), 1.0 / a.v); }
+__device__ __forceinline__ D4 dsqrt(const D4 &a)
+{
+    const double s = sqrt(a.v);
+    return chain(a, s, 0.5 / s);
+}
+
+struct PrimD {
+    D4 rho, u, v, p, sqb, rsb;
+};
+
+// inverse of E13 over duals (general gamma): beta = -q4/2, u = -q2/q4,
+// v = -q3/q4, rho = exp(q1 - ln(beta)/(gamma-1) + beta |u|^2), p = rho/(2 beta)
+__device__ __forceinline__ PrimD prim_d(const D4 qt[4], double inv_gm1)
+{
+    PrimD s;
+    const D4 beta = -0.5 * qt[3];
+    const D4 r = recip(qt[3]);
+    s.u = -1.0 * (qt[1] * r);
+    s.v = -1.0 * (qt[2] * r);
+    s.sqb = dsqrt(beta);
+    s.rsb = recip(s.sqb);
+    const D4 ke = beta * (s.u * s.u + s.v * s.v);
+    s.rho = dexp(qt[0] - inv_gm1 * dlog(beta) + ke);
+    s.p = -1.0 * (s.rho * r);
+    return s;
+}
+
+// split flux along a direction over duals; same formula as the forward kernel
+__device__ __forceinline__ void split_flux_d(double sgn, const PrimD &s, const D4 &un, const D4 &ut,
+                                             double inv_gm1, D4 G[4])
+{
+    const D4 S = un * s.sqb;
+    const double e = exp(-S.v * S.v);
+    const D4 erfS = chain(S, erf(S.v), 1.1283791670955126 * e);   // 2/sqrt(pi)
+    const D4 eS = chain(S, e, -2.0 * S.v * e);
+    const D4 A = 0.5 * (1.0 + sgn * erfS);
+    const D4 B = 0.28209479177387814 * (eS * s.rsb);                 // 1/(2 sqrt(pi))
+    const D4 rhoE = inv_gm1 * s.p + 0.5 * (s.rho * (un * un + ut * ut));
+    const D4 m = un * A + sgn * B;
+    G[0] = s.rho * m;
+    G[1] = (s.p + s.rho * un * un) * A + sgn * (s.rho * un * B);
+    G[2] = s.rho * ut * m;
+    G[3] = (rhoE + s.p) * un * A + sgn * ((rhoE + 0.5 * s.p) * B);
+}
+
+__device__ __forceinline__ void ld4(const double *a, int64_t p, double v[4])
+{
+    const double2 *a2 = reinterpret_cast<const double2 *>(a);
+    const double2 lo = a2[2 * p], hi = a2[2 * p + 1];
+    v[0] = lo.x; v[1] = lo.y; v[2] = hi.x; v[3] = hi.y;
+}
+__device__ __forceinline__ void st4(double *a, int64_t p, const double v[4])
+{
+    double2 *a2 = reinterpret_cast<double2 *>(a);
+    a2[2 * p] = make_double2(v[0], v[1]);
+    a2[2 * p + 1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void ld8(const double *a, int64_t p, double v[8])
+{
+    ld4(a, 2 * p, v);
+    ld4(a, 2 * p + 1, v + 4);
+}
+__device__ __forceinline__ void st8(double *a, int64_t p, const double v[8])
+{
+    st4(a, 2 * p, v);
+    st4(a, 2 * p + 1, v + 4);
+}
+
+// sub-stencil slots of an edge: x-sub (0 x+, 1 x-) and y-sub (2 y+, 3 y-), -1 if none
+__device__ __forceinline__ int xsub(uint8_t m) { return (m & M_XPOS) ? 0 : ((m & M_XNEG) ? 1 : -1); }
+__device__ __forceinline__ int ysub(uint8_t m) { return (m & M_YPOS) ? 2 : ((m & M_YNEG) ? 3 : -1); }
+__device__ __forceinline__ bool sub_needed(uint8_t f, int k)
+{
+    return k >= 0 && (f == FLAG_INTERIOR || (f == FLAG_WALL && k != 2));
+}
+
+// cotangent of one reconstructed state: sum over the split fluxes it feeds,
+// cs (frame order) against Gs and cn (frame order) against Gn, plus the
+// flux values for the weight cotangents
+__device__ __forceinline__ void state_adjoint(const double qt[4], double tx, double ty, double nx, double ny,
+                                              bool use_s, double sg_s, bool use_n, double sg_n,
+                                              const double cs[4], const double cn[4], double inv_gm1,
+                                              double qbar[4], double Gs[4], double Gn[4])
+{
+    D4 q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        q[k] = dconst(qt[k]);
+        q[k].d[k] = 1.0;
+    }
+    const PrimD s = prim_d(q, inv_gm1);
+    const D4 us = tx * s.u + ty * s.v;
+    const D4 un = nx * s.u + ny * s.v;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qbar[k] = 0.0;
+    if (use_s) {
+        D4 G[4];
+        split_flux_d(sg_s, s, us, un, inv_gm1, G);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            Gs[c] = G[c].v;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qbar[k] += cs[c] * G[c].d[k];
+        }
+    }
+    if (use_n) {
+        D4 G[4];
+        split_flux_d(sg_n, s, un, us, inv_gm1, G);
+        // Gn components are [mass, n-momentum, s-momentum, energy]
+        const int fr[4] = {0, 2, 1, 3};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            Gn[fr[c]] = G[c].v;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qbar[k] += cn[fr[c]] * G[c].d[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// flux adjoint, owner side
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_adj_flux(AdjParams P)
+{
+    const DevGeom &g = P.g;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.n) return;
+    const uint8_t f = g.flag[p] & 3;
+    const bool second = P.order == 2;
+    double qb0[4] = {0, 0, 0, 0}, gb0[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int e0 = g.off[p], e1 = g.off[p + 1];
+    if (f == FLAG_FARFIELD) {
+        // R = 0 there: no cotangent flows from this point
+        for (int e = e0; e < e1; ++e) {
+            st4(P.ebar, e, qb0);
+            P.wbar[e] = make_double2(0.0, 0.0);
+            P.dbar[e] = make_double2(0.0, 0.0);
+        }
+        st4(P.qbar, p, qb0);
+        if (second) st8(P.gbar, p, gb0);
+        return;
+    }
+    const double2 xy0 = g.xy[p];
+    const double2 n0 = g.nrm[p];
+    const double tx = n0.y, ty = -n0.x;
+    double Rb[4], q0[4], g0[8];
+    ld4(P.Rbar, p, Rb);
+    // frame-order cotangent of R_local: R_global = (R0, R1 t + R2 n, R3)
+    const double Rl[4] = {Rb[0], Rb[1] * tx + Rb[2] * ty, Rb[1] * n0.x + Rb[2] * n0.y, Rb[3]};
+    ld4(P.q, p, q0);
+    if (second) ld8(P.qg, p, g0);
+    for (int e = e0; e < e1; ++e) {
+        const int i = g.idx[e];
+        const uint8_t m = g.mask[e];
+        const int ks = xsub(m), kn = ysub(m);
+        const bool us_ = sub_needed(f, ks), un_ = sub_needed(f, kn);
+        const double2 w = g.fxw[e];
+        double qti[4], qt0[4];
+        ld4(P.q, i, qti);
+        double dx = 0.0, dy = 0.0, gi[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qt0[k] = q0[k];
+        if (second) {
+            const double2 xyi = g.xy[i];
+            dx = xyi.x - xy0.x;
+            dy = xyi.y - xy0.y;
+            ld8(P.qg, i, gi);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                qti[k] = qti[k] - 0.5 * (dx * gi[k] + dy * gi[4 + k]);
+                qt0[k] = qt0[k] - 0.5 * (dx * g0[k] + dy * g0[4 + k]);
+            }
+        }
+        double cs[4], cn[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            cs[k] = us_ ? w.x * Rl[k] : 0.0;
+            cn[k] = un_ ? w.y * Rl[k] : 0.0;
+        }
+        double qbi[4], qbo[4], Gsi[4] = {0, 0, 0, 0}, Gni[4] = {0, 0, 0, 0}, Gs0[4] = {0, 0, 0, 0},
+                                       Gn0[4] = {0, 0, 0, 0};
+        const double sgs = (m & M_XPOS) ? 1.0 : -1.0, sgn = (m & M_YPOS) ? 1.0 : -1.0;
+        if (us_ || un_) {
+            state_adjoint(qti, tx, ty, n0.x, n0.y, us_, sgs, un_, sgn, cs, cn, P.inv_gm1, qbi, Gsi, Gni);
+            state_adjoint(qt0, tx, ty, n0.x, n0.y, us_, sgs, un_, sgn, cs, cn, P.inv_gm1, qbo, Gs0, Gn0);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qbi[k] = qbo[k] = 0.0;
+        }
+        // R += w (G(q~_i) - G(q~_0)): + for the neighbour, - for the owner
+        double wbx = 0.0, wby = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            wbx += Rl[k] * (Gsi[k] - Gs0[k]);
+            wby += Rl[k] * (Gni[k] - Gn0[k]);
+            qbo[k] = -qbo[k];
+        }
+        P.wbar[e] = make_double2(us_ ? wbx : 0.0, un_ ? wby : 0.0);
+        st4(P.ebar, e, qbi);
+        double dxb = 0.0, dyb = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            qb0[k] += qbo[k];
+            if (second) {
+                // q~_0 = q_0 - (dx qx_0 + dy qy_0)/2
+                gb0[k] -= 0.5 * dx * qbo[k];
+                gb0[4 + k] -= 0.5 * dy * qbo[k];
+                dxb -= 0.5 * qbo[k] * g0[k];
+                dyb -= 0.5 * qbo[k] * g0[4 + k];
+            }
+        }
+        P.dbar[e] = make_double2(dxb, dyb);
+    }
+    st4(P.qbar, p, qb0);
+    if (second) st8(P.gbar, p, gb0);
+}
+
+// ---------------------------------------------------------------------------
+// flux adjoint, neighbour side: point p gathers the cotangents of q~_p over
+// the edges that reach it
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_adj_flux_gather(AdjParams P)
+{
+    const DevGeom &g = P.g;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.n) return;
+    const bool second = P.order == 2;
+    double qb[4], gb[8], gp[8];
+    ld4(P.qbar, p, qb);
+    if (second) {
+        ld8(P.gbar, p, gb);
+        ld8(P.qg, p, gp);
+    }
+    const double2 xyp = g.xy[p];
+    for (int t = P.toff[p]; t < P.toff[p + 1]; ++t) {
+        const int e = P.tedge[t];
+        double eb[4];
+        ld4(P.ebar, e, eb);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qb[k] += eb[k];
+        if (second) {
+            const double2 xys = g.xy[P.tsrc[t]];
+            const double dx = xyp.x - xys.x, dy = xyp.y - xys.y;
+            double dxb = 0.0, dyb = 0.0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                // q~_p = q_p - (dx qx_p + dy qy_p)/2 on this edge
+                gb[k] -= 0.5 * dx * eb[k];
+                gb[4 + k] -= 0.5 * dy * eb[k];
+                dxb -= 0.5 * eb[k] * gp[k];
+                dyb -= 0.5 * eb[k] * gp[4 + k];
+            }
+            double2 d = P.dbar[e];
+            d.x += dxb;
+            d.y += dyb;
+            P.dbar[e] = d;
+        }
+    }
+    st4(P.qbar, p, qb);
+    if (second) st8(P.gbar, p, gb);
+}
+
+// ---------------------------------------------------------------------------
+// one least-squares pass of E15 in reverse. Forward (per component c):
+//   g_p = sum_e a_e s_e,  s_e = (q_i - q_p) - [dx (gx'_i - gx'_p) + dy (gy'_i - gy'_p)]/2
+// with g' the previous iterate (absent in the first-order pass).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_adj_grad(AdjParams P, const double *__restrict__ gprev,
+                                                  const double *__restrict__ gbar_in,
+                                                  double *__restrict__ gbar_out)
+{
+    const DevGeom &g = P.g;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.n) return;
+    const bool inner = gprev != nullptr;
+    double qb[4], gb[8], gpp[8], qp[4], gbo[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    ld4(P.qbar, p, qb);
+    ld8(gbar_in, p, gb);
+    ld4(P.q, p, qp);
+    if (inner) ld8(gprev, p, gpp);
+    const double2 xyp = g.xy[p];
+    // outgoing edges: owner terms, and the cotangents of a_e and of the offsets
+    for (int e = g.off[p]; e < g.off[p + 1]; ++e) {
+        const int i = g.idx[e];
+        const double2 a = g.lsw[e];
+        double qi[4], gi[8];
+        ld4(P.q, i, qi);
+        double dx = 0.0, dy = 0.0;
+        if (inner) {
+            ld8(gprev, i, gi);
+            const double2 xyi = g.xy[i];
+            dx = xyi.x - xyp.x;
+            dy = xyi.y - xyp.y;
+        }
+        double2 ab = P.abar[e];
+        double2 db = P.dbar[e];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double sb = a.x * gb[k] + a.y * gb[4 + k];
+            double s = qi[k] - qp[k];
+            if (inner) {
+                const double ddx = gi[k] - gpp[k], ddy = gi[4 + k] - gpp[4 + k];
+                s = s - 0.5 * (dx * ddx + dy * ddy);
+                gbo[k] += 0.5 * dx * sb;
+                gbo[4 + k] += 0.5 * dy * sb;
+                db.x -= 0.5 * sb * ddx;
+                db.y -= 0.5 * sb * ddy;
+            }
+            qb[k] -= sb;
+            ab.x += s * gb[k];
+            ab.y += s * gb[4 + k];
+        }
+        P.abar[e] = ab;
+        P.dbar[e] = db;
+    }
+    // incoming edges: the terms of this point as a neighbour
+    for (int t = P.toff[p]; t < P.toff[p + 1]; ++t) {
+        const int e = P.tedge[t], src = P.tsrc[t];
+        const double2 a = g.lsw[e];
+        double gs[8];
+        ld8(gbar_in, src, gs);
+        double dx = 0.0, dy = 0.0;
+        if (inner) {
+            const double2 xys = g.xy[src];
+            dx = xyp.x - xys.x;
+            dy = xyp.y - xys.y;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double sb = a.x * gs[k] + a.y * gs[4 + k];
+            qb[k] += sb;
+            if (inner) {
+                gbo[k] -= 0.5 * dx * sb;
+                gbo[4 + k] -= 0.5 * dy * sb;
+            }
+        }
+    }
+    st4(P.qbar, p, qb);
+    if (inner) st8(gbar_out, p, gbo);
+}
+
+// ---------------------------------------------------------------------------
+// least-squares weights back to edge offsets (owner side)
+// ---------------------------------------------------------------------------
+struct Sym2 {
+    double xx, xy, yy;
+};
+
+__global__ void __launch_bounds__(128) k_adj_weights(AdjParams P)
+{
+    const DevGeom &g = P.g;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.n) return;
+    const uint8_t f = g.flag[p] & 3;
+    const bool full = P.order == 2;
+    const double2 xy0 = g.xy[p];
+    const double2 n0 = g.nrm[p];
+    const double tx = n0.y, ty = -n0.x;
+    const int e0 = g.off[p], e1 = g.off[p + 1];
+    // normal-equation sums: full stencil (global frame) and the sub-stencils (s, n)
+    Sym2 M = {0, 0, 0}, Ms[4] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int e = e0; e < e1; ++e) {
+        const double2 xyi = g.xy[g.idx[e]];
+        const double dx = xyi.x - xy0.x, dy = xyi.y - xy0.y;
+        const double ds = dx * tx + dy * ty, dn = dx * n0.x + dy * n0.y;
+        M.xx += dx * dx; M.xy += dx * dy; M.yy += dy * dy;
+        const uint8_t m = g.mask[e];
+        const int ks = xsub(m), kn = ysub(m);
+        if (ks >= 0) { Ms[ks].xx += ds * ds; Ms[ks].xy += ds * dn; Ms[ks].yy += dn * dn; }
+        if (kn >= 0) { Ms[kn].xx += ds * ds; Ms[kn].xy += ds * dn; Ms[kn].yy += dn * dn; }
+    }
+    // inverses (M^-1 = [[yy, -xy], [-xy, xx]] / det)
+    auto inv = [](const Sym2 &A) {
+        const double det = A.xx * A.yy - A.xy * A.xy;
+        Sym2 r = {A.yy / det, -A.xy / det, A.xx / det};
+        return r;
+    };
+    const Sym2 Mi = inv(M);
+    Sym2 Msi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Msi[k] = sub_needed(f, k) ? inv(Ms[k]) : Sym2{0, 0, 0};
+    // B = sum (b a^T + a b^T) per system, with a = M^-1 d and b = M^-1 a_bar
+    Sym2 B = {0, 0, 0}, Bs[4] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int e = e0; e < e1; ++e) {
+            const double2 xyi = g.xy[g.idx[e]];
+            const double dx = xyi.x - xy0.x, dy = xyi.y - xy0.y;
+            const double ds = dx * tx + dy * ty, dn = dx * n0.x + dy * n0.y;
+            const uint8_t m = g.mask[e];
+            const int ks = xsub(m), kn = ysub(m);
+            double gx = 0.0, gy = 0.0;   // offset cotangent, global frame
+            double gs = 0.0, gn = 0.0;   // offset cotangent, (s, n) frame
+            if (full) {
+                const double2 ab = P.abar[e];
+                const double ax = Mi.xx * dx + Mi.xy * dy, ay = Mi.xy * dx + Mi.yy * dy;
+                const double bx = Mi.xx * ab.x + Mi.xy * ab.y, by = Mi.xy * ab.x + Mi.yy * ab.y;
+                if (pass == 0) {
+                    B.xx += 2.0 * bx * ax;
+                    B.xy += bx * ay + ax * by;
+                    B.yy += 2.0 * by * ay;
+                } else {
+                    gx += bx - (B.xx * dx + B.xy * dy);
+                    gy += by - (B.xy * dx + B.yy * dy);
+                }
+            }
+            const double2 wb = P.wbar[e];
+            // x-sub weight = row 0 of M_s^-1 d, y-sub weight = row 1
+            for (int h = 0; h < 2; ++h) {
+                const int k = h == 0 ? ks : kn;
+                if (!sub_needed(f, k)) continue;
+                const Sym2 &Ai = Msi[k];
+                const double as = Ai.xx * ds + Ai.xy * dn, an = Ai.xy * ds + Ai.yy * dn;
+                const double abs_ = h == 0 ? wb.x : 0.0, abn = h == 0 ? 0.0 : wb.y;
+                const double bs = Ai.xx * abs_ + Ai.xy * abn, bn = Ai.xy * abs_ + Ai.yy * abn;
+                if (pass == 0) {
+                    Bs[k].xx += 2.0 * bs * as;
+                    Bs[k].xy += bs * an + as * bn;
+                    Bs[k].yy += 2.0 * bn * an;
+                } else {
+                    gs += bs - (Bs[k].xx * ds + Bs[k].xy * dn);
+                    gn += bn - (Bs[k].xy * ds + Bs[k].yy * dn);
+                }
+            }
+            if (pass == 1) {
+                // ds = dx tx + dy ty, dn = dx nx + dy ny
+                double2 d = P.dbar[e];
+                d.x += gx + gs * tx + gn * n0.x;
+                d.y += gy + gs * ty + gn * n0.y;
+                P.dbar[e] = d;
+            }
+        }
+    }
+}
+
+// offsets d_e = P_dst - P_src back to points: x_bar_p = sum_in d_bar - sum_out d_bar
+__global__ void __launch_bounds__(256) k_adj_points(AdjParams P, double *__restrict__ xb_out,
+                                                    double *__restrict__ yb_out)
+{
+    const DevGeom &g = P.g;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.n) return;
+    double xb = 0.0, yb = 0.0;
+    for (int t = P.toff[p]; t < P.toff[p + 1]; ++t) {
+        const double2 d = P.dbar[P.tedge[t]];
+        xb += d.x;
+        yb += d.y;
+    }
+    for (int e = g.off[p]; e < g.off[p + 1]; ++e) {
+        const double2 d = P.dbar[e];
+        xb -= d.x;
+        yb -= d.y;
+    }
+    const int32_t o = P.perm[p];
+    if (xb_out) xb_out[o] = xb;
+    if (yb_out) yb_out[o] = yb;
+}
+
+// q_bar to U_bar through E13 (duals over the four conserved variables);
+// writes component-major input order
+__global__ void __launch_bounds__(256) k_adj_state(AdjParams P, const double *__restrict__ U,
+                                                   double *__restrict__ Ub_out)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = P.g.n;
+    if (p >= n) return;
+    double u[4], qb[4];
+    ld4(U, p, u);
+    ld4(P.qbar, p, qb);
+    D4 Ud[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        Ud[k] = dconst(u[k]);
+        Ud[k].d[k] = 1.0;
+    }
+    const D4 rinv = recip(Ud[0]);
+    const D4 u1 = Ud[1] * rinv, u2 = Ud[2] * rinv;
+    const D4 pr = (1.0 / P.inv_gm1) * (Ud[3] - 0.5 * (Ud[0] * (u1 * u1 + u2 * u2)));
+    const D4 beta = 0.5 * (Ud[0] * recip(pr));
+    D4 q[4];
+    q[0] = dlog(Ud[0]) + P.inv_gm1 * dlog(beta) - beta * (u1 * u1 + u2 * u2);
+    q[1] = 2.0 * (beta * u1);
+    q[2] = 2.0 * (beta * u2);
+    q[3] = -2.0 * beta;
+    const int32_t o = P.perm[p];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) s += qb[c] * q[c].d[k];
+        Ub_out[(int64_t)k * n + o] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// transpose CSR: incoming edges of every point, in edge order
+// ---------------------------------------------------------------------------
+__global__ void k_edge_src(int64_t n, const int32_t *__restrict__ off, int32_t *__restrict__ esrc)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    for (int e = off[p]; e < off[p + 1]; ++e) esrc[e] = (int32_t)p;
+}
+
+__global__ void k_iota(int64_t m, int32_t *__restrict__ v)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) v[t] = (int32_t)t;
+}
+
+// toff[p] = first position of key p in the sorted keys (lower bound)
+__global__ void k_toff(int64_t n, int64_t nnz, const int32_t *__restrict__ keys, int32_t *__restrict__ toff)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > n) return;
+    int64_t lo = 0, hi = nnz;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < p) lo = mid + 1;
+        else hi = mid;
+    }
+    toff[p] = (int32_t)lo;
+}
+
+__global__ void k_tsrc(int64_t nnz, const int32_t *__restrict__ tedge, const int32_t *__restrict__ esrc,
+                       int32_t *__restrict__ tsrc)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nnz) tsrc[t] = esrc[tedge[t]];
+}
+
+unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t build_transpose_csr(int64_t n, int64_t nnz, const int32_t *off, const int32_t *idx, int32_t *toff,
+                                int32_t *tedge, int32_t *tsrc, cudaStream_t s)
+{
+    int32_t *esrc = nullptr, *iota = nullptr, *keys = nullptr;
+    void *tmp = nullptr;
+    size_t tmp_bytes = 0;
+    cudaError_t err = cudaSuccess;
+    const int64_t m = nnz > 0 ? nnz : 1;
+    do {
+        if ((err = cudaMallocAsync(&esrc, m * sizeof(int32_t), s)) != cudaSuccess) break;
+        if ((err = cudaMallocAsync(&iota, m * sizeof(int32_t), s)) != cudaSuccess) break;
+        if ((err = cudaMallocAsync(&keys, m * sizeof(int32_t), s)) != cudaSuccess) break;
+        k_edge_src<<<blocks(n, 256), 256, 0, s>>>(n, off, esrc);
+        k_iota<<<blocks(m, 256), 256, 0, s>>>(nnz, iota);
+        if ((err = cudaGetLastError()) != cudaSuccess) break;
+        if (nnz > 0) {
+            // stable: equal destinations keep edge order
+            err = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, idx, keys, iota, tedge, (int)nnz, 0, 32, s);
+            if (err != cudaSuccess) break;
+            if ((err = cudaMallocAsync(&tmp, tmp_bytes, s)) != cudaSuccess) break;
+            err = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, idx, keys, iota, tedge, (int)nnz, 0, 32, s);
+            if (err != cudaSuccess) break;
+        }
+        k_toff<<<blocks(n + 1, 256), 256, 0, s>>>(n, nnz, keys, toff);
+        if (nnz > 0) k_tsrc<<<blocks(nnz, 256), 256, 0, s>>>(nnz, tedge, esrc, tsrc);
+        err = cudaGetLastError();
+    } while (0);
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (keys) cudaFreeAsync(keys, s);
+    if (iota) cudaFreeAsync(iota, s);
+    if (esrc) cudaFreeAsync(esrc, s);
+    return err;
+}
+
+cudaError_t launch_adj_flux(const AdjParams &P, cudaStream_t s)
+{
+    k_adj_flux<<<blocks(P.g.n, 128), 128, 0, s>>>(P);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    k_adj_flux_gather<<<blocks(P.g.n, 128), 128, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_grad(const AdjParams &P, const double *gprev, const double *gbar_in, double *gbar_out,
+                            cudaStream_t s)
+{
+    k_adj_grad<<<blocks(P.g.n, 128), 128, 0, s>>>(P, gprev, gbar_in, gbar_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_geometry(const AdjParams &P, double *x_bar, double *y_bar, cudaStream_t s)
+{
+    k_adj_weights<<<blocks(P.g.n, 128), 128, 0, s>>>(P);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    k_adj_points<<<blocks(P.g.n, 256), 256, 0, s>>>(P, x_bar, y_bar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_state(const AdjParams &P, const double *U, double *U_bar, cudaStream_t s)
+{
+    k_adj_state<<<blocks(P.g.n, 256), 256, 0, s>>>(P, U, U_bar);
+    return cudaGetLastError();
+}
+
+}  // namespace lskum

@@ -13,6 +13,7 @@
 #include "lskum.h"
 #include "lskum_kernels.h"
 #include "lskum_mixed.h"
+#include "lskum_adjoint.h"
 
 using namespace lskum;
 
@@ -69,6 +70,13 @@ struct lskum_ctx {
     StepGraph graphs[2];
     cudaStream_t gstream = nullptr;  // capture stream (never the legacy default stream)
     bool graphs_off = false;
+
+    // residual VJP workspace (FP64, allocated on the first lskum_residual_vjp)
+    bool vjp_ready = false;
+    double *vq = nullptr, *vG = nullptr, *vRb = nullptr, *vqb = nullptr, *vgb = nullptr, *vgb2 = nullptr;
+    double *vebar = nullptr;
+    double2 *vwbar = nullptr, *vabar = nullptr, *vdbar = nullptr;
+    int32_t *toff = nullptr, *tedge = nullptr, *tsrc = nullptr;
     double *fbuf = nullptr;
 
     // kernel timing (lskum_profile): event pairs per kernel class, reused
@@ -742,6 +750,98 @@ extern "C" lskum_status lskum_residual(lskum_ctx *c, const double *U, double *R)
     if (c->cfg.order == 2 && (st = gradients(c, q, &qg)) != LSKUM_OK) return st;
     if ((st = flux(c, q, qg, nullptr, nullptr, 0, 0, c->Rt)) != LSKUM_OK) return st;
     LAUNCH(c, launch_state_out(c->n, c->perm, c->Rt, R, c->stream));
+    return check_nonphysical(c);
+}
+
+static lskum_status vjp_workspace(lskum_ctx *c)
+{
+    if (c->vjp_ready) return LSKUM_OK;
+    const int64_t n = c->n, m = std::max<int64_t>(c->nnz, 1);
+    const int K = c->cfg.order == 2 ? c->cfg.inner_iters : 0;
+    CK(c, dalloc(c, &c->vq, 4 * n));
+    if (c->cfg.order == 2) {
+        CK(c, dalloc(c, &c->vG, (int64_t)(K + 1) * 8 * n));
+        CK(c, dalloc(c, &c->vgb, 8 * n));
+        CK(c, dalloc(c, &c->vgb2, 8 * n));
+    }
+    CK(c, dalloc(c, &c->vRb, 4 * n));
+    CK(c, dalloc(c, &c->vqb, 4 * n));
+    CK(c, dalloc(c, &c->vebar, 4 * m));
+    CK(c, dalloc(c, &c->vwbar, m));
+    CK(c, dalloc(c, &c->vabar, m));
+    CK(c, dalloc(c, &c->vdbar, m));
+    CK(c, dalloc(c, &c->toff, n + 1));
+    CK(c, dalloc(c, &c->tedge, m));
+    CK(c, dalloc(c, &c->tsrc, m));
+    c->launches += 4;
+    LAUNCH(c, build_transpose_csr(n, c->nnz, c->off, c->idx, c->toff, c->tedge, c->tsrc, c->stream));
+    c->vjp_ready = true;
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_residual_vjp(lskum_ctx *c, const double *U, const double *R_bar, double *U_bar,
+                                           double *x_bar, double *y_bar)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!R_bar) return fail(c, LSKUM_ERR_ARG, "R_bar is NULL");
+    if (c->cfg.order == 2 && c->cfg.limiter_K != 0.0)
+        return fail(c, LSKUM_ERR_ARG, "the residual VJP needs limiter_K = 0 (the limiter is not differentiated)");
+    if (!U_bar && !x_bar && !y_bar) return LSKUM_OK;
+    lskum_status st = vjp_workspace(c);
+    if (st != LSKUM_OK) return st;
+    if ((st = reset_status(c)) != LSKUM_OK) return st;
+    const int64_t n = c->n;
+    const bool second = c->cfg.order == 2;
+    const int K = second ? c->cfg.inner_iters : 0;
+    const DevGeom g = c->geom();
+    // forward recomputation in FP64: q, and every q-derivative iterate
+    const double *Ui = c->U;
+    if (U) {
+        LAUNCH(c, launch_state_in(n, c->perm, U, c->Ut, c->stream));
+        Ui = c->Ut;
+    }
+    LAUNCH(c, launch_q_from_U(n, c->gas, Ui, c->vq, c->status, c->stream));
+    if (second) {
+        LAUNCH(c, launch_qgrad(g, c->vq, nullptr, c->vG, 0.0, c->stream));
+        for (int k = 1; k <= K; ++k)
+            LAUNCH(c, launch_qgrad(g, c->vq, c->vG + (int64_t)(k - 1) * 8 * n, c->vG + (int64_t)k * 8 * n, 0.0,
+                                   c->stream));
+    }
+    LAUNCH(c, launch_state_in(n, c->perm, R_bar, c->vRb, c->stream));
+    AdjParams P{};
+    P.g = g;
+    P.q = c->vq;
+    P.qg = second ? c->vG + (int64_t)K * 8 * n : nullptr;
+    P.Rbar = c->vRb;
+    P.qbar = c->vqb;
+    P.gbar = c->vgb;
+    P.ebar = c->vebar;
+    P.wbar = c->vwbar;
+    P.abar = c->vabar;
+    P.dbar = c->vdbar;
+    P.toff = c->toff;
+    P.tedge = c->tedge;
+    P.tsrc = c->tsrc;
+    P.perm = c->perm;
+    P.inv_gm1 = c->gas.inv_gm1;
+    P.order = c->cfg.order;
+    c->launches++;
+    LAUNCH(c, launch_adj_flux(P, c->stream));
+    if (second) {
+        CK(c, cudaMemsetAsync(c->vabar, 0, std::max<int64_t>(c->nnz, 1) * sizeof(double2), c->stream));
+        double *gin = c->vgb, *gout = c->vgb2;
+        for (int k = K; k >= 1; --k) {
+            LAUNCH(c, launch_adj_grad(P, c->vG + (int64_t)(k - 1) * 8 * n, gin, gout, c->stream));
+            std::swap(gin, gout);
+        }
+        LAUNCH(c, launch_adj_grad(P, nullptr, gin, nullptr, c->stream));
+    }
+    if (x_bar || y_bar) {
+        c->launches++;
+        LAUNCH(c, launch_adj_geometry(P, x_bar, y_bar, c->stream));
+    }
+    if (U_bar) LAUNCH(c, launch_adj_state(P, Ui, U_bar, c->stream));
     return check_nonphysical(c);
 }
 

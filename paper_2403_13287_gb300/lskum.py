@@ -74,6 +74,7 @@ def load(build_if_missing: bool = True):
     L.lskum_last_error.restype = ctypes.c_char_p
     L.lskum_step.argtypes = [_p, _int, _p]
     L.lskum_residual.argtypes = [_p, _p, _p]
+    L.lskum_residual_vjp.argtypes = [_p, _p, _p, _p, _p, _p]
     L.lskum_q_derivatives.argtypes = [_p, _p, _p, _p]
     L.lskum_timestep.argtypes = [_p, _p, _p]
     L.lskum_forces.argtypes = [_p, _p, _p, _p]
@@ -85,7 +86,7 @@ def load(build_if_missing: bool = True):
     L.lskum_launch_count.restype = _i64
     L.lskum_profile.argtypes = [_p, _int]
     L.lskum_kernel_time.argtypes = [_p, _int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]
-    for name in ("lskum_step", "lskum_residual", "lskum_q_derivatives", "lskum_timestep",
+    for name in ("lskum_step", "lskum_residual", "lskum_residual_vjp", "lskum_q_derivatives", "lskum_timestep",
                  "lskum_forces", "lskum_get_state", "lskum_set_state", "lskum_get_stencil_masks",
                  "lskum_get_permutation", "lskum_profile", "lskum_kernel_time"):
         getattr(L, name).restype = _int
@@ -168,6 +169,17 @@ class Solver:
             out = torch.empty((4, self.n), dtype=torch.float64, device="cuda")
         self._check(self._L.lskum_residual(self._ctx, _dev_ptr(U), _dev_ptr(out)))
         return out
+
+    def residual_vjp(self, R_bar, U=None, want_U=True, want_xy=True):
+        """(U_bar, x_bar, y_bar) = (dR/dU, dR/dx, dR/dy)^T R_bar at U (the
+        context's state if None); the unrequested ones are None."""
+        import torch
+        Ub = torch.empty((4, self.n), dtype=torch.float64, device="cuda") if want_U else None
+        xb = torch.empty(self.n, dtype=torch.float64, device="cuda") if want_xy else None
+        yb = torch.empty_like(xb) if want_xy else None
+        self._check(self._L.lskum_residual_vjp(self._ctx, _dev_ptr(U), _dev_ptr(R_bar), _dev_ptr(Ub),
+                                               _dev_ptr(xb), _dev_ptr(yb)))
+        return Ub, xb, yb
 
     def q_derivatives(self, U=None):
         import torch
@@ -265,3 +277,43 @@ def q_derivatives_noalloc(x, y, nbr_offsets, nbr_idx, U, qx, qy, gamma=1.4, inne
                                        _p(int(stream)) if stream else None)
     if st != LSKUM_OK:
         raise LskumError(st, L.lskum_last_error(None).decode())
+
+
+def _residual_fn_class():
+    import torch
+
+    class ResidualFn(torch.autograd.Function):
+        """R = residual(U) with backward by lskum_residual_vjp. `xy` ([2, n],
+        the solver's own coordinates, which the forward does not read) is the
+        handle through which coordinate gradients flow."""
+
+        @staticmethod
+        def forward(ctx, solver, U, xy):
+            U = U.contiguous()
+            ctx.solver = solver
+            ctx.save_for_backward(U)
+            return solver.residual(U)
+
+        @staticmethod
+        def backward(ctx, R_bar):
+            (U,) = ctx.saved_tensors
+            want_U, want_xy = ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+            Ub, xb, yb = ctx.solver.residual_vjp(R_bar.contiguous(), U, want_U=want_U, want_xy=want_xy)
+            return None, Ub, (torch.stack([xb, yb]) if want_xy else None)
+
+    return ResidualFn
+
+
+_ResidualFn = None
+
+
+def residual_fn(solver, U, xy=None):
+    """Differentiable residual: R(U) of `solver`'s scheme as a torch op.
+    U is a [4, n] float64 CUDA tensor; xy, if given, is a [2, n] float64 CUDA
+    tensor holding the solver's coordinates, to receive dR/dxy gradients."""
+    global _ResidualFn
+    if _ResidualFn is None:
+        _ResidualFn = _residual_fn_class()
+    if xy is not None and tuple(xy.shape) != (2, solver.n):
+        raise ValueError("xy must have shape [2, n]")
+    return _ResidualFn.apply(solver, U, xy)
