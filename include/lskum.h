@@ -67,7 +67,10 @@ typedef struct {
     double mach;      /* free stream: rho = 1, p = 1/gamma, |u| = mach */
     double aoa_deg;   /* angle of attack of the free stream, degrees */
     double gamma;     /* ratio of specific heats (paper: 1.4) */
-    int precision;    /* 0: FP64 throughout */
+    int precision;    /* 0: FP64 throughout. 1: mixed (not in the paper): q, grad q, the LS
+                       * weights and the split-flux arithmetic in FP32; U, the RK update, the
+                       * residue, the forces and the LS closure of points whose sub-stencil
+                       * weights amplify rounding (sum |w_i||P_i - P_0| > 16) in FP64 */
     int reorder;      /* 0: keep the input order; 1: Morton (Z-order) renumbering for gather locality */
     double limiter_K; /* order 2 only. 0: no limiter (the paper's scheme). > 0: Venkatakrishnan's
                        * limiter (J. Comput. Phys. 118, 1995; not in the paper) scales each
@@ -103,6 +106,46 @@ lskum_status lskum_create(int64_t n, const double *x, const double *y, const dou
                           const double *ny, const int32_t *flags, const int32_t *nbr_offsets,
                           const int32_t *nbr_idx, int64_t n_wall, const int32_t *wall_order,
                           const lskum_config *cfg, void *cuda_stream, lskum_ctx **out);
+
+/*
+ * One case of a batch: a cloud (as for lskum_create) and its free stream.
+ * Cases may share their arrays (e.g. one cloud under several flow conditions).
+ */
+typedef struct {
+    int64_t n;                      /* points of this case (>= 32) */
+    const double *x, *y, *nx, *ny;  /* host float64[n] */
+    const int32_t *flags;           /* host int32[n] */
+    const int32_t *nbr_offsets;     /* host int32[n+1], this case's own numbering */
+    const int32_t *nbr_idx;         /* host int32[nbr_offsets[n]] */
+    int64_t n_wall;                 /* wall points (closed contour) or 0 */
+    const int32_t *wall_order;      /* host int32[n_wall] */
+    double mach, aoa_deg;           /* this case's free stream (cfg.mach/aoa_deg are not used) */
+} lskum_case;
+
+/*
+ * Build one context that advances n_cases independent solves together (not in
+ * the paper): every kernel runs once over the disjoint union of the cases'
+ * clouds, so small and uneven cases share launches and graph replays. The
+ * context's points are the cases' points concatenated in case order (case k
+ * occupies [first_k, first_k + n_k) of every caller-visible array, see
+ * lskum_case_range); the connectivity stays within each case. Each case has
+ * its own free stream (far-field values, initial state, forces), residue and
+ * wall contour; cfg supplies everything else. lskum_step's res_history then
+ * holds n_iters * n_cases values, iteration-major (res[it * n_cases + k]);
+ * lskum_residual, lskum_residual_vjp, lskum_get_state/set_state and the
+ * timing calls act on all cases at once; forces come from lskum_case_forces.
+ * Validation and errors as lskum_create, per case. Synchronises.
+ *   n_cases   1 .. 65535
+ */
+lskum_status lskum_create_batch(int n_cases, const lskum_case *cases, const lskum_config *cfg, void *cuda_stream,
+                                lskum_ctx **out);
+
+/* Number of cases of a context (1 for lskum_create). */
+int lskum_case_count(const lskum_ctx *ctx);
+
+/* Input-order point range and wall-entry range of case k (any pointer may be NULL). */
+lskum_status lskum_case_range(const lskum_ctx *ctx, int k, int64_t *first, int64_t *count, int64_t *wall_first,
+                              int64_t *wall_count);
 
 /* Free everything the context owns. NULL is allowed. */
 void lskum_destroy(lskum_ctx *ctx);
@@ -231,6 +274,37 @@ lskum_status lskum_q_derivatives_noalloc(int64_t n, const double *x, const doubl
                                          double *qx, double *qy, void *cuda_stream);
 
 /* Kernel classes for lskum_kernel_time */
+/*
+ * Launch-shape autotuner (mixed-precision contexts; not in the paper). The
+ * mixed flux kernel and the mixed q-derivative pass are each compiled in
+ * several shapes (threads per block, minimum resident blocks per SM, which
+ * caps registers). lskum_autotune times every shape on this context's own
+ * cloud and state (reps launches each after one warm-up, CUDA events on the
+ * context's stream; the flux in residual mode, the q-derivatives as one inner
+ * pass), keeps the fastest of each and reports them. The state is not
+ * changed. A shape changes only the register budget the compiler works
+ * with, and through it which FP32 multiply-adds are contracted: results of
+ * different shapes agree to FP32 rounding, not bitwise. Synchronises.
+ * LSKUM_ERR_ARG on an FP64 context.
+ */
+typedef struct {
+    int flux_variant, flux_threads, flux_min_blocks;
+    int qgrad_variant, qgrad_threads, qgrad_min_blocks;
+    double flux_ms, qgrad_ms;                  /* per launch, chosen shape */
+    double flux_ms_default, qgrad_ms_default;  /* per launch, shape 0 */
+} lskum_tuning;
+
+lskum_status lskum_autotune(lskum_ctx *ctx, int reps, lskum_tuning *out);
+
+/* Select shapes directly (0 is the default of each kernel). */
+lskum_status lskum_set_tuning(lskum_ctx *ctx, int flux_variant, int qgrad_variant);
+
+/*
+ * Lift and drag of case k (a batch) or of the only case: as lskum_forces,
+ * with case k's free stream; cp receives its n_wall values in its contour order.
+ */
+lskum_status lskum_case_forces(lskum_ctx *ctx, int k, double *cl, double *cd, double *cp);
+
 #define LSKUM_KERNEL_FLUX 0  /* fused flux residual + state update */
 #define LSKUM_KERNEL_QGRAD 1 /* one least-squares q-derivative pass */
 #define LSKUM_KERNEL_CLASSES 2

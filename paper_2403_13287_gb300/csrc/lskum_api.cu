@@ -49,10 +49,9 @@ struct lskum_ctx {
     float4 *s_gq = nullptr, *s_gf = nullptr;
     double2 *s_fxw64 = nullptr;
     double *dt = nullptr, *Rt = nullptr, *Ut = nullptr, *Ucm = nullptr;
-    double *norm_part = nullptr;
-    int nparts = 0;
-    double *res_dev = nullptr;
-    int res_cap = 0;
+    double *norm_part = nullptr;   // residue_parts(n) values: a pair of sums per warp
+    double *res_dev = nullptr;     // residue history, [iteration][case]
+    int res_cap = 0;               // iterations res_dev holds
     int *res_counter = nullptr;  // next entry of res_dev the residue kernel writes
     int *status = nullptr;
 
@@ -70,6 +69,21 @@ struct lskum_ctx {
     StepGraph graphs[2];
     cudaStream_t gstream = nullptr;  // capture stream (never the legacy default stream)
     bool graphs_off = false;
+
+    // cases: a batch context solves several independent problems over the
+    // disjoint union of their clouds; case c owns input and internal points
+    // [case_start_h[c], case_start_h[c+1]) and wall entries
+    // [case_wall_h[c], case_wall_h[c+1]); a single context is one case
+    int ncases = 1;
+    std::vector<int64_t> case_start_h, case_wall_h;
+    std::vector<double> case_mach, case_aoa;
+    int64_t *case_start = nullptr;   // device copy of case_start_h
+    uint16_t *pcase = nullptr;       // per internal point: its case (batches only)
+    double *case_uinf = nullptr;     // [ncases][4] (batches only)
+    std::vector<uint16_t> case_of_input;  // create-time only
+
+    // launch-shape variants of the mixed flux and q-derivative kernels
+    int var_flux = 0, var_qgrad = 0;
 
     // residual VJP workspace (FP64, allocated on the first lskum_residual_vjp)
     bool vjp_ready = false;
@@ -134,6 +148,16 @@ static lskum_status fail(lskum_ctx *c, lskum_status st, const char *fmt, ...)
         (c)->launches++;                                                                        \
         CK(c, call);                                                                            \
     } while (0)
+
+// evaluates a launch; false (and r set) on failure
+#define LAUNCH_OK(c, call, r)                                                                   \
+    ([&]() -> bool {                                                                            \
+        (c)->launches++;                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ == cudaSuccess) return true;                                                     \
+        (r) = fail((c), LSKUM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+        return false;                                                                           \
+    }())
 
 static cudaError_t next_event(lskum_ctx *c, cudaEvent_t *ev)
 {
@@ -293,8 +317,29 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     CK(c, dalloc(c, &c->lsw, nnz));
     CK(c, dalloc(c, &c->fxw, nnz));
 
-    // numbering
-    if (c->cfg.reorder == 1) {
+    // numbering (a batch keeps each case's points together, in case order)
+    if (c->cfg.reorder == 1 && c->ncases > 1) {
+        std::vector<uint64_t> keys(n);
+        for (int k = 0; k < c->ncases; ++k) {
+            const int64_t a = c->case_start_h[k], b = c->case_start_h[k + 1];
+            double xmin = x[a], xmax = x[a], ymin = y[a], ymax = y[a];
+            for (int64_t p = a + 1; p < b; ++p) {
+                xmin = std::min(xmin, x[p]); xmax = std::max(xmax, x[p]);
+                ymin = std::min(ymin, y[p]); ymax = std::max(ymax, y[p]);
+            }
+            const double ext = std::max(std::max(xmax - xmin, ymax - ymin), 1e-300);
+            const double scale = 16777215.0 / ext;  // 24 bits per coordinate below the case bits
+            for (int64_t p = a; p < b; ++p)
+                keys[p] = ((uint64_t)k << 48) | morton_code_host(x[p], y[p], xmin, ymin, scale, 24);
+        }
+        uint64_t *keys_d = nullptr;
+        CK(c, cudaMallocAsync(&keys_d, n * sizeof(uint64_t), s));
+        CK(c, cudaMemcpyAsync(keys_d, keys.data(), n * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+        c->launches += 3;
+        CK(c, sort_permutation(n, keys_d, c->perm, s));
+        CK(c, cudaFreeAsync(keys_d, s));
+        CK(c, cudaStreamSynchronize(s));
+    } else if (c->cfg.reorder == 1) {
         double xmin = x[0], xmax = x[0], ymin = y[0], ymax = y[0];
         for (int64_t p = 1; p < n; ++p) {
             xmin = std::min(xmin, x[p]); xmax = std::max(xmax, x[p]);
@@ -345,23 +390,44 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     const int64_t nw = c->n_wall;
     std::vector<int32_t> wall_h(std::max<int64_t>(nw, 1));
     std::vector<double> ds_h(std::max<int64_t>(nw, 1));
-    for (int64_t w = 0; w < nw; ++w) {
-        const int32_t p = wall_order[w], pn = wall_order[(w + 1) % nw], pp = wall_order[(w + nw - 1) % nw];
-        const double dn = sqrt((x[pn] - x[p]) * (x[pn] - x[p]) + (y[pn] - y[p]) * (y[pn] - y[p]));
-        const double dp = sqrt((x[p] - x[pp]) * (x[p] - x[pp]) + (y[p] - y[pp]) * (y[p] - y[pp]));
-        ds_h[w] = 0.5 * (dn + dp);
-        wall_h[w] = inv_h[p];
+    for (int k = 0; k < c->ncases; ++k) {
+        // each case's contour is closed on itself
+        const int64_t w0 = c->case_wall_h[k], m = c->case_wall_h[k + 1] - w0;
+        for (int64_t j = 0; j < m; ++j) {
+            const int32_t p = wall_order[w0 + j], pn = wall_order[w0 + (j + 1) % m],
+                          pp = wall_order[w0 + (j + m - 1) % m];
+            const double dn = sqrt((x[pn] - x[p]) * (x[pn] - x[p]) + (y[pn] - y[p]) * (y[pn] - y[p]));
+            const double dp = sqrt((x[p] - x[pp]) * (x[p] - x[pp]) + (y[p] - y[pp]) * (y[p] - y[pp]));
+            ds_h[w0 + j] = 0.5 * (dn + dp);
+            wall_h[w0 + j] = inv_h[p];
+        }
     }
     CK(c, dalloc(c, &c->wall, std::max<int64_t>(nw, 1)));
     CK(c, dalloc(c, &c->wall_ds, std::max<int64_t>(nw, 1)));
-    CK(c, dalloc(c, &c->fbuf, nw + 2));
+    CK(c, dalloc(c, &c->fbuf, nw + 2 * c->ncases));
+    // case tables
+    CK(c, dalloc(c, &c->case_start, c->ncases + 1));
+    CK(c, cudaMemcpyAsync(c->case_start, c->case_start_h.data(), (c->ncases + 1) * sizeof(int64_t),
+                          cudaMemcpyHostToDevice, s));
+    if (c->ncases > 1) {
+        std::vector<uint16_t> pc(n);
+        for (int64_t p = 0; p < n; ++p) pc[p] = c->case_of_input[c->perm_h[p]];
+        std::vector<double> ui(4 * c->ncases);
+        for (int k = 0; k < c->ncases; ++k)
+            freestream(c->cfg.gamma, c->case_mach[k], c->case_aoa[k], ui.data() + 4 * k);
+        CK(c, dalloc(c, &c->pcase, n));
+        CK(c, dalloc(c, &c->case_uinf, 4 * c->ncases));
+        CK(c, cudaMemcpyAsync(c->pcase, pc.data(), n * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+        CK(c, cudaMemcpyAsync(c->case_uinf, ui.data(), 4 * c->ncases * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(c, cudaStreamSynchronize(s));
+        std::vector<uint16_t>().swap(c->case_of_input);
+    }
     if (nw > 0) {
         CK(c, cudaMemcpyAsync(c->wall, wall_h.data(), nw * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         CK(c, cudaMemcpyAsync(c->wall_ds, ds_h.data(), nw * sizeof(double), cudaMemcpyHostToDevice, s));
     }
 
     // state and work buffers
-    c->nparts = (int)(c->mixed ? mixed_flux_blocks(n) : flux_blocks(n));
     CK(c, dalloc(c, &c->U, 4 * n));
     CK(c, dalloc(c, &c->Us, 4 * n));
     CK(c, dalloc(c, &c->acc, 4 * n));
@@ -419,19 +485,50 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     CK(c, dalloc(c, &c->Rt, 4 * n));
     CK(c, dalloc(c, &c->Ut, 4 * n));
     CK(c, dalloc(c, &c->Ucm, 4 * n));
-    CK(c, dalloc(c, &c->norm_part, c->nparts));
+    CK(c, dalloc(c, &c->norm_part, residue_parts(n)));
     CK(c, dalloc(c, &c->status, 2));
     c->res_cap = 1024;
-    CK(c, dalloc(c, &c->res_dev, c->res_cap));
+    CK(c, dalloc(c, &c->res_dev, (int64_t)c->res_cap * c->ncases));
     CK(c, dalloc(c, &c->res_counter, 1));
     CK(c, cudaMemsetAsync(c->res_counter, 0, sizeof(int), s));
     CK(c, cudaMemsetAsync(c->qgA, 0, 2 * 8 * n * qbytes, s));
     const int st_init[2] = {0, 0x7fffffff};
     CK(c, cudaMemcpyAsync(c->status, st_init, sizeof st_init, cudaMemcpyHostToDevice, s));
-    LAUNCH(c, launch_fill_state(n, c->gas.Uinf, c->U, s));
+    if (c->ncases > 1) LAUNCH(c, launch_fill_state_cases(n, c->pcase, c->case_uinf, c->U, s));
+    else LAUNCH(c, launch_fill_state(n, c->gas.Uinf, c->U, s));
     lskum_status st = refresh_q(c, c->U, c->q_cur);
     if (st != LSKUM_OK) return st;
     CK(c, cudaStreamSynchronize(s));
+    return LSKUM_OK;
+}
+
+static lskum_status check_config(const lskum_config *cfg, int64_t n)
+{
+    if (cfg->order != 1 && cfg->order != 2) return fail(nullptr, LSKUM_ERR_ARG, "order must be 1 or 2");
+    if (cfg->inner_iters < 0 || cfg->inner_iters > 1000) return fail(nullptr, LSKUM_ERR_ARG, "inner_iters out of range");
+    if (cfg->time_scheme != 0 && cfg->time_scheme != 1) return fail(nullptr, LSKUM_ERR_ARG, "time_scheme must be 0 or 1");
+    if (!(cfg->cfl > 0.0) || !(cfg->gamma > 1.0) || !(cfg->mach >= 0.0) || !std::isfinite(cfg->aoa_deg))
+        return fail(nullptr, LSKUM_ERR_ARG, "cfl, gamma, mach or aoa out of range");
+    if (cfg->precision != 0 && cfg->precision != 1)
+        return fail(nullptr, LSKUM_ERR_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+    if (cfg->precision == 1 && n >= (int64_t)1 << 28)
+        return fail(nullptr, LSKUM_ERR_ARG, "the mixed form takes at most 2^28 - 1 points");
+    if (cfg->reorder != 0 && cfg->reorder != 1) return fail(nullptr, LSKUM_ERR_ARG, "reorder must be 0 or 1");
+    if (!(cfg->limiter_K >= 0.0) || !std::isfinite(cfg->limiter_K))
+        return fail(nullptr, LSKUM_ERR_ARG, "limiter_K must be finite and >= 0");
+    return LSKUM_OK;
+}
+
+static lskum_status check_points(int64_t n, const double *x, const double *y, const double *nx, const double *ny,
+                                 const int32_t *flags)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        if (flags[p] < 0 || flags[p] > 2) return fail(nullptr, LSKUM_ERR_ARG, "point %lld has flag %d", (long long)p, flags[p]);
+        if (!std::isfinite(x[p]) || !std::isfinite(y[p]) || !std::isfinite(nx[p]) || !std::isfinite(ny[p]))
+            return fail(nullptr, LSKUM_ERR_ARG, "point %lld has a non-finite coordinate or normal", (long long)p);
+        const double nn = nx[p] * nx[p] + ny[p] * ny[p];
+        if (fabs(nn - 1.0) > 1e-8) return fail(nullptr, LSKUM_ERR_ARG, "point %lld has a normal that is not unit", (long long)p);
+    }
     return LSKUM_OK;
 }
 
@@ -447,25 +544,9 @@ extern "C" lskum_status lskum_create(int64_t n, const double *x, const double *y
         return fail(nullptr, LSKUM_ERR_ARG, "a required input pointer is NULL");
     if (n_wall < 0 || n_wall > n || (n_wall > 0 && !wall_order))
         return fail(nullptr, LSKUM_ERR_ARG, "bad wall contour (n_wall = %lld)", (long long)n_wall);
-    if (cfg->order != 1 && cfg->order != 2) return fail(nullptr, LSKUM_ERR_ARG, "order must be 1 or 2");
-    if (cfg->inner_iters < 0 || cfg->inner_iters > 1000) return fail(nullptr, LSKUM_ERR_ARG, "inner_iters out of range");
-    if (cfg->time_scheme != 0 && cfg->time_scheme != 1) return fail(nullptr, LSKUM_ERR_ARG, "time_scheme must be 0 or 1");
-    if (!(cfg->cfl > 0.0) || !(cfg->gamma > 1.0) || !(cfg->mach >= 0.0) || !std::isfinite(cfg->aoa_deg))
-        return fail(nullptr, LSKUM_ERR_ARG, "cfl, gamma, mach or aoa out of range");
-    if (cfg->precision != 0 && cfg->precision != 1)
-        return fail(nullptr, LSKUM_ERR_ARG, "precision must be 0 (FP64) or 1 (mixed)");
-    if (cfg->precision == 1 && n >= (int64_t)1 << 28)
-        return fail(nullptr, LSKUM_ERR_ARG, "the mixed form takes at most 2^28 - 1 points");
-    if (cfg->reorder != 0 && cfg->reorder != 1) return fail(nullptr, LSKUM_ERR_ARG, "reorder must be 0 or 1");
-    if (!(cfg->limiter_K >= 0.0) || !std::isfinite(cfg->limiter_K))
-        return fail(nullptr, LSKUM_ERR_ARG, "limiter_K must be finite and >= 0");
-    for (int64_t p = 0; p < n; ++p) {
-        if (flags[p] < 0 || flags[p] > 2) return fail(nullptr, LSKUM_ERR_ARG, "point %lld has flag %d", (long long)p, flags[p]);
-        if (!std::isfinite(x[p]) || !std::isfinite(y[p]) || !std::isfinite(nx[p]) || !std::isfinite(ny[p]))
-            return fail(nullptr, LSKUM_ERR_ARG, "point %lld has a non-finite coordinate or normal", (long long)p);
-        const double nn = nx[p] * nx[p] + ny[p] * ny[p];
-        if (fabs(nn - 1.0) > 1e-8) return fail(nullptr, LSKUM_ERR_ARG, "point %lld has a normal that is not unit", (long long)p);
-    }
+    lskum_status cst = check_config(cfg, n);
+    if (cst != LSKUM_OK) return cst;
+    if ((cst = check_points(n, x, y, nx, ny, flags)) != LSKUM_OK) return cst;
     std::string msg;
     lskum_status st = validate_csr(n, nbr_offsets, nbr_idx, msg);
     if (st != LSKUM_OK) return fail(nullptr, st, "%s", msg.c_str());
@@ -484,6 +565,10 @@ extern "C" lskum_status lskum_create(int64_t n, const double *x, const double *y
     c->gas.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
     c->gas.g14 = cfg->gamma == 1.4;
     freestream(cfg->gamma, cfg->mach, cfg->aoa_deg, c->gas.Uinf);
+    c->case_start_h = {0, n};
+    c->case_wall_h = {0, n_wall};
+    c->case_mach = {cfg->mach};
+    c->case_aoa = {cfg->aoa_deg};
     st = create_impl(c, x, y, nx, ny, flags, nbr_offsets, nbr_idx, wall_order);
     if (st != LSKUM_OK) {
         g_create_error = c->err;
@@ -491,6 +576,109 @@ extern "C" lskum_status lskum_create(int64_t n, const double *x, const double *y
         return st;
     }
     *out = c;
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_create_batch(int n_cases, const lskum_case *cases, const lskum_config *cfg,
+                                           void *cuda_stream, lskum_ctx **out)
+{
+    if (!out) return fail(nullptr, LSKUM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_cases < 1 || n_cases > 65535 || !cases || !cfg)
+        return fail(nullptr, LSKUM_ERR_ARG, "n_cases = %d out of range [1, 65535], or a NULL argument", n_cases);
+    int64_t N = 0, NNZ = 0, NW = 0;
+    for (int k = 0; k < n_cases; ++k) {
+        const lskum_case &a = cases[k];
+        if (a.n < 32) return fail(nullptr, LSKUM_ERR_ARG, "case %d: n = %lld (a case needs at least 32 points)", k,
+                                  (long long)a.n);
+        if (!a.x || !a.y || !a.nx || !a.ny || !a.flags || !a.nbr_offsets || !a.nbr_idx)
+            return fail(nullptr, LSKUM_ERR_ARG, "case %d: a required input pointer is NULL", k);
+        if (a.n_wall < 0 || a.n_wall > a.n || (a.n_wall > 0 && !a.wall_order))
+            return fail(nullptr, LSKUM_ERR_ARG, "case %d: bad wall contour", k);
+        if (!(a.mach > 0.0) || !std::isfinite(a.mach) || !std::isfinite(a.aoa_deg))
+            return fail(nullptr, LSKUM_ERR_ARG, "case %d: mach must be > 0 and aoa finite", k);
+        std::string msg;
+        lskum_status st = validate_csr(a.n, a.nbr_offsets, a.nbr_idx, msg);
+        if (st != LSKUM_OK) return fail(nullptr, st, "case %d: %s", k, msg.c_str());
+        if ((st = check_points(a.n, a.x, a.y, a.nx, a.ny, a.flags)) != LSKUM_OK) {
+            const std::string m2 = g_create_error;
+            return fail(nullptr, st, "case %d: %s", k, m2.c_str());
+        }
+        for (int64_t w = 0; w < a.n_wall; ++w)
+            if (a.wall_order[w] < 0 || a.wall_order[w] >= a.n)
+                return fail(nullptr, LSKUM_ERR_ARG, "case %d: wall_order[%lld] out of range", k, (long long)w);
+        N += a.n;
+        NNZ += a.nbr_offsets[a.n];
+        NW += a.n_wall;
+    }
+    if (N >= (int64_t)0x7fffffff || NNZ >= (int64_t)0x7fffffff)
+        return fail(nullptr, LSKUM_ERR_ARG, "the batch has too many points or edges for 32-bit indices");
+    // the disjoint union of the cases' clouds, in case order
+    std::vector<double> x(N), y(N), nx(N), ny(N);
+    std::vector<int32_t> flags(N), off(N + 1), idx(NNZ), wall(std::max<int64_t>(NW, 1));
+    lskum_ctx *c = new lskum_ctx();
+    c->ncases = n_cases;
+    c->case_start_h.assign(n_cases + 1, 0);
+    c->case_wall_h.assign(n_cases + 1, 0);
+    c->case_of_input.resize(N);
+    int64_t p0 = 0, e0 = 0, w0 = 0;
+    off[0] = 0;
+    for (int k = 0; k < n_cases; ++k) {
+        const lskum_case &a = cases[k];
+        for (int64_t p = 0; p < a.n; ++p) {
+            x[p0 + p] = a.x[p]; y[p0 + p] = a.y[p]; nx[p0 + p] = a.nx[p]; ny[p0 + p] = a.ny[p];
+            flags[p0 + p] = a.flags[p];
+            off[p0 + p + 1] = (int32_t)(e0 + a.nbr_offsets[p + 1]);
+            c->case_of_input[p0 + p] = (uint16_t)k;
+        }
+        const int64_t m = a.nbr_offsets[a.n];
+        for (int64_t e = 0; e < m; ++e) idx[e0 + e] = (int32_t)(p0 + a.nbr_idx[e]);
+        for (int64_t w = 0; w < a.n_wall; ++w) wall[w0 + w] = (int32_t)(p0 + a.wall_order[w]);
+        p0 += a.n;
+        e0 += m;
+        w0 += a.n_wall;
+        c->case_start_h[k + 1] = p0;
+        c->case_wall_h[k + 1] = w0;
+        c->case_mach.push_back(a.mach);
+        c->case_aoa.push_back(a.aoa_deg);
+    }
+    c->n = N;
+    c->nnz = NNZ;
+    c->n_wall = NW;
+    c->cfg = *cfg;
+    c->cfg.mach = cases[0].mach;
+    c->cfg.aoa_deg = cases[0].aoa_deg;
+    c->mixed = cfg->precision == 1;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->gas.gamma = cfg->gamma;
+    c->gas.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
+    c->gas.g14 = cfg->gamma == 1.4;
+    freestream(cfg->gamma, cases[0].mach, cases[0].aoa_deg, c->gas.Uinf);
+    lskum_status st = check_config(cfg, N);
+    if (st != LSKUM_OK) {
+        delete c;
+        return st;
+    }
+    st = create_impl(c, x.data(), y.data(), nx.data(), ny.data(), flags.data(), off.data(), idx.data(), wall.data());
+    if (st != LSKUM_OK) {
+        g_create_error = c->err;
+        lskum_destroy(c);
+        return st;
+    }
+    *out = c;
+    return LSKUM_OK;
+}
+
+extern "C" int lskum_case_count(const lskum_ctx *c) { return c ? c->ncases : 0; }
+
+extern "C" lskum_status lskum_case_range(const lskum_ctx *c, int k, int64_t *first, int64_t *count,
+                                         int64_t *wall_first, int64_t *wall_count)
+{
+    if (!c || k < 0 || k >= c->ncases) return LSKUM_ERR_ARG;
+    if (first) *first = c->case_start_h[k];
+    if (count) *count = c->case_start_h[k + 1] - c->case_start_h[k];
+    if (wall_first) *wall_first = c->case_wall_h[k];
+    if (wall_count) *wall_count = c->case_wall_h[k + 1] - c->case_wall_h[k];
     return LSKUM_OK;
 }
 
@@ -503,10 +691,12 @@ static lskum_status gradients(lskum_ctx *c, const void *q, void **qg_out, int in
     if (c->mixed) {
         const MixedGeom g = c->mgeom();
         const float *qf = (const float *)q;
-        TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad_mixed(g, qf, nullptr, (float *)src, inner == 0 ? limK : 0.0, c->stream));
+        TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad_mixed(g, qf, nullptr, (float *)src, inner == 0 ? limK : 0.0,
+                                                               c->stream, c->var_qgrad));
         for (int k = 0; k < inner; ++k) {
             TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad_mixed(g, qf, (const float *)src, (float *)dst,
-                                                                   k == inner - 1 ? limK : 0.0, c->stream));
+                                                                   k == inner - 1 ? limK : 0.0, c->stream,
+                                                                   c->var_qgrad));
             std::swap(src, dst);
         }
     } else {
@@ -547,6 +737,8 @@ static lskum_status flux(lskum_ctx *c, const void *q, const void *qg, double *Uo
         P.R = R;
         P.norm_part = c->norm_part;
         P.status = c->status;
+        P.pcase = c->pcase;
+        P.case_uinf = c->case_uinf;
         for (int k = 0; k < 4; ++k) P.Uinf[k] = c->gas.Uinf[k];
         P.gamma = (float)c->gas.gamma;
         P.inv_gm1 = (float)c->gas.inv_gm1;
@@ -555,7 +747,7 @@ static lskum_status flux(lskum_ctx *c, const void *q, const void *qg, double *Uo
         P.order = c->cfg.order;
         P.mode = mode;
         P.stage = stage;
-        TIMED_LAUNCH(c, LSKUM_KERNEL_FLUX, launch_flux_mixed(P, c->stream));
+        TIMED_LAUNCH(c, LSKUM_KERNEL_FLUX, launch_flux_mixed(P, c->stream, c->var_flux));
     } else {
         FluxLaunch L{};
         L.q = (const double *)q;
@@ -568,6 +760,8 @@ static lskum_status flux(lskum_ctx *c, const void *q, const void *qg, double *Uo
         L.R = R;
         L.norm_part = c->norm_part;
         L.status = c->status;
+        L.pcase = c->pcase;
+        L.case_uinf = c->case_uinf;
         L.cfl = c->cfg.cfl;
         L.order = c->cfg.order;
         L.mode = mode;
@@ -589,8 +783,8 @@ static lskum_status iteration(lskum_ctx *c)
         if (st != LSKUM_OK) return st;
         std::swap(c->q_cur, c->q_nxt);
         if (k == 0)
-            LAUNCH(c, launch_residue_finish(c->norm_part, c->nparts, c->n, c->res_dev, c->res_counter, c->res_cap,
-                                            c->stream));
+            LAUNCH(c, launch_residue_finish(c->norm_part, c->case_start, c->ncases, c->res_dev, c->res_counter,
+                                            c->res_cap, c->stream));
     }
     return LSKUM_OK;
 }
@@ -679,7 +873,7 @@ extern "C" lskum_status lskum_step(lskum_ctx *c, int n_iters, double *res_histor
     if (n_iters == 0) return LSKUM_OK;
     if (n_iters > c->res_cap) {
         double *r = nullptr;
-        CK(c, dalloc(c, &r, n_iters));
+        CK(c, dalloc(c, &r, (int64_t)n_iters * c->ncases));
         c->res_dev = r;
         c->res_cap = n_iters;
     }
@@ -697,7 +891,8 @@ extern "C" lskum_status lskum_step(lskum_ctx *c, int n_iters, double *res_histor
         if (st != LSKUM_OK) return st;
     }
     if (res_history)
-        CK(c, cudaMemcpyAsync(res_history, c->res_dev, n_iters * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaMemcpyAsync(res_history, c->res_dev, (size_t)n_iters * c->ncases * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
     int sh[2];
     st = read_status(c, sh);
     if (st != LSKUM_OK) return st;
@@ -879,24 +1074,153 @@ extern "C" lskum_status lskum_timestep(lskum_ctx *c, const double *U, double *dt
     return LSKUM_OK;
 }
 
-extern "C" lskum_status lskum_forces(lskum_ctx *c, double *cl, double *cd, double *cp)
+static void drop_graphs(lskum_ctx *c)
+{
+    for (auto &g : c->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = lskum_ctx::StepGraph{};
+    }
+}
+
+extern "C" lskum_status lskum_set_tuning(lskum_ctx *c, int flux_variant, int qgrad_variant)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!c->mixed) return fail(c, LSKUM_ERR_ARG, "launch-shape variants exist for the mixed-precision kernels only");
+    if (flux_variant < 0 || flux_variant >= mixed_variants(0) || qgrad_variant < 0 ||
+        qgrad_variant >= mixed_variants(1))
+        return fail(c, LSKUM_ERR_ARG, "variant out of range");
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->var_flux = flux_variant;
+    c->var_qgrad = qgrad_variant;
+    drop_graphs(c);
+    return LSKUM_OK;
+}
+
+// times `reps` launches of one variant on the context's stream (milliseconds per launch)
+template <class F>
+static lskum_status time_variant(lskum_ctx *c, int reps, cudaEvent_t e0, cudaEvent_t e1, F launch, double *ms)
+{
+    CK(c, launch());  // warm-up
+    CK(c, cudaEventRecord(e0, c->stream));
+    for (int r = 0; r < reps; ++r) CK(c, launch());
+    CK(c, cudaEventRecord(e1, c->stream));
+    CK(c, cudaEventSynchronize(e1));
+    float t = 0.0f;
+    CK(c, cudaEventElapsedTime(&t, e0, e1));
+    c->launches += reps + 1;
+    *ms = (double)t / reps;
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_autotune(lskum_ctx *c, int reps, lskum_tuning *out)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!c->mixed) return fail(c, LSKUM_ERR_ARG, "the autotuner covers the mixed-precision kernels (precision = 1)");
+    if (reps < 1) reps = 5;
+    lskum_status st = reset_status(c);
+    if (st != LSKUM_OK) return st;
+    CK(c, cudaStreamSynchronize(c->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(c, cudaEventCreate(&e0));
+    cudaError_t ee = cudaEventCreate(&e1);
+    if (ee != cudaSuccess) {
+        cudaEventDestroy(e0);
+        CK(c, ee);
+    }
+    const MixedGeom g = c->mgeom();
+    const float *q = (const float *)c->q_cur;
+    float *gA = (float *)c->qgA, *gB = (float *)c->qgB;
+    const bool second = c->cfg.order == 2;
+    double best_q = 1e300, best_f = 1e300, def_q = 0.0, def_f = 0.0;
+    int vq = 0, vf = 0;
+    // q-derivative variants: one inner pass, reading the first-order gradient in gA
+    lskum_status r = LSKUM_OK;
+    if (LAUNCH_OK(c, launch_qgrad_mixed(g, q, nullptr, gA, 0.0, c->stream, 0), r)) {
+        for (int v = 0; v < mixed_variants(1) && r == LSKUM_OK; ++v) {
+            double ms = 0.0;
+            r = time_variant(c, reps, e0, e1,
+                             [&] { return launch_qgrad_mixed(g, q, gA, gB, 0.0, c->stream, v); }, &ms);
+            if (v == 0) def_q = ms;
+            if (r == LSKUM_OK && ms < best_q) { best_q = ms; vq = v; }
+        }
+    }
+    // flux variants: residual mode into the scratch residual
+    MixedFluxParams P{};
+    P.g = g;
+    P.nrm64 = c->nrm;
+    P.q = q;
+    P.qg = second ? gA : nullptr;
+    P.Un = c->U;
+    P.acc = c->acc;
+    P.dt = c->dt;
+    P.R = c->Rt;
+    P.norm_part = c->norm_part;
+    P.status = c->status;
+    P.pcase = c->pcase;
+    P.case_uinf = c->case_uinf;
+    for (int k = 0; k < 4; ++k) P.Uinf[k] = c->gas.Uinf[k];
+    P.gamma = (float)c->gas.gamma;
+    P.inv_gm1 = (float)c->gas.inv_gm1;
+    P.cfl = (float)c->cfg.cfl;
+    P.g14 = c->gas.g14;
+    P.order = c->cfg.order;
+    P.mode = 0;
+    for (int v = 0; v < mixed_variants(0) && r == LSKUM_OK; ++v) {
+        double ms = 0.0;
+        r = time_variant(c, reps, e0, e1, [&] { return launch_flux_mixed(P, c->stream, v); }, &ms);
+        if (v == 0) def_f = ms;
+        if (r == LSKUM_OK && ms < best_f) { best_f = ms; vf = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != LSKUM_OK) return r;
+    if ((st = check_nonphysical(c)) != LSKUM_OK) return st;
+    c->var_flux = vf;
+    c->var_qgrad = vq;
+    drop_graphs(c);
+    if (out) {
+        out->flux_variant = vf;
+        mixed_variant_shape(0, vf, &out->flux_threads, &out->flux_min_blocks);
+        out->qgrad_variant = vq;
+        mixed_variant_shape(1, vq, &out->qgrad_threads, &out->qgrad_min_blocks);
+        out->flux_ms = best_f;
+        out->qgrad_ms = best_q;
+        out->flux_ms_default = def_f;
+        out->qgrad_ms_default = def_q;
+    }
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_case_forces(lskum_ctx *c, int k, double *cl, double *cd, double *cp)
 {
     if (!c) return LSKUM_ERR_ARG;
     c->err.clear();
     if (!cl || !cd) return fail(c, LSKUM_ERR_ARG, "cl or cd is NULL");
-    if (c->n_wall == 0) return fail(c, LSKUM_ERR_ARG, "no wall contour was given at create");
-    const double a = c->cfg.aoa_deg * 3.14159265358979323846 / 180.0;
-    const double qinf = 0.5 * c->cfg.mach * c->cfg.mach;
+    if (k < 0 || k >= c->ncases) return fail(c, LSKUM_ERR_ARG, "case %d out of range", k);
+    const int64_t w0 = c->case_wall_h[k], nw = c->case_wall_h[k + 1] - w0;
+    if (nw == 0) return fail(c, LSKUM_ERR_ARG, "no wall contour was given at create for case %d", k);
+    const double a = c->case_aoa[k] * 3.14159265358979323846 / 180.0;
+    const double qinf = 0.5 * c->case_mach[k] * c->case_mach[k];
     if (!(qinf > 0.0)) return fail(c, LSKUM_ERR_ARG, "forces need mach > 0");
-    LAUNCH(c, launch_forces(c->n_wall, c->gas, qinf, c->wall, c->wall_ds, c->nrm, c->U, cos(a), sin(a),
-                            c->fbuf, c->fbuf + c->n_wall, c->stream));
+    double *out = c->fbuf + c->n_wall + 2 * k;
+    LAUNCH(c, launch_forces(nw, c->gas, qinf, c->wall + w0, c->wall_ds + w0, c->nrm, c->U, cos(a), sin(a),
+                            c->fbuf + w0, out, c->stream));
     double clcd[2];
-    CK(c, cudaMemcpyAsync(clcd, c->fbuf + c->n_wall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    if (cp) CK(c, cudaMemcpyAsync(cp, c->fbuf, c->n_wall * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(clcd, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (cp) CK(c, cudaMemcpyAsync(cp, c->fbuf + w0, nw * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     *cl = clcd[0];
     *cd = clcd[1];
     return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_forces(lskum_ctx *c, double *cl, double *cd, double *cp)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    if (c->ncases != 1) return fail(c, LSKUM_ERR_ARG, "a batch context reports forces per case (lskum_case_forces)");
+    return lskum_case_forces(c, 0, cl, cd, cp);
 }
 
 extern "C" lskum_status lskum_get_state(lskum_ctx *c, double *U, int on_host)

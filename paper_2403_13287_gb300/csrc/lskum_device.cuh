@@ -93,6 +93,30 @@ __device__ __forceinline__ void split_flux(double sgn, const Prim &s, double un,
     G[3] = (rhoE + s.p) * un * A + sgn * (rhoE + 0.5 * s.p) * B;
 }
 
+// per-warp pair of residue partial sums (lo: lanes in the case of the warp's
+// first point, hi: the others, i.e. a second case that starts inside the
+// warp; every case has at least 32 points), summed in T within the warp and
+// stored in FP64
+template <typename T>
+__device__ __forceinline__ void warp_residue_pair(const uint16_t *pcase, int64_t p, bool live, T r2, double *part)
+{
+    const int lane = threadIdx.x & 31;
+    const int c = (pcase && live) ? (int)pcase[p] : 0;
+    const int c0 = __shfl_sync(0xffffffffu, c, 0);
+    T lo = (c == c0) ? r2 : T(0), hi = (c == c0) ? T(0) : r2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo += __shfl_down_sync(0xffffffffu, lo, o);
+        hi += __shfl_down_sync(0xffffffffu, hi, o);
+    }
+    // warps wholly past the last point write nothing
+    if (lane == 0 && live) {
+        const int64_t w = p >> 5;
+        part[2 * w] = (double)lo;
+        part[2 * w + 1] = (double)hi;
+    }
+}
+
 __device__ __forceinline__ void load4(const double *a, int64_t p, double v[4])
 {
     const double2 *a2 = reinterpret_cast<const double2 *>(a);

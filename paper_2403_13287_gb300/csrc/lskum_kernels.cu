@@ -109,8 +109,10 @@ struct FluxParams {
     double *qout;       // [n][4] q of Uout
     double *dt;         // [n] local time step (computed at stage 0)
     double *R;          // [n][4] residual output (residual mode)
-    double *norm_part;  // [gridDim.x] block sums of R_rho^2 (stage 0)
+    double *norm_part;  // per warp: pair of R_rho^2 sums (stage 0), see warp_residue_pair
     int *status;        // [0] status bits, [1] smallest offending internal point
+    const uint16_t *pcase;    // per point: its case in a batch, or nullptr (one case)
+    const double *case_uinf;  // [cases][4] free stream per case, or nullptr (gas.Uinf)
     double cfl;
     int order;
     int mode;   // 0 residual only, 1 forward Euler, 2 RK4
@@ -255,8 +257,9 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
             Unew[1] = Unew[1] - mn * n0.x;
             Unew[2] = Unew[2] - mn * n0.y;
         } else if (flag == FLAG_FARFIELD) {
+            const double *Ui = P.case_uinf ? P.case_uinf + 4 * (int)P.pcase[p] : P.gas.Uinf;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) Unew[k] = P.gas.Uinf[k];
+            for (int k = 0; k < 4; ++k) Unew[k] = Ui[k];
         }
         store4(P.Uout, p, Unew);
         double qn[4];
@@ -264,40 +267,37 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
         store4(P.qout, p, qn);
     }
 
-    // ---- residue partials: block sum of R_rho^2 at stage 0 ----
-    if (P.mode == 1 || P.stage == 0) {
-        double s = Rg[0] * Rg[0];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        __shared__ double ws[4];
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) ws[wid] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) P.norm_part[blockIdx.x] = (ws[0] + ws[1]) + (ws[2] + ws[3]);
-    }
+    // ---- residue partials: a pair of R_rho^2 sums per warp, at stage 0 ----
+    if (P.mode == 1 || P.stage == 0) warp_residue_pair(P.pcase, p, live, Rg[0] * Rg[0], P.norm_part);
 }
 
-// residue() = sqrt(sum R_rho^2)/n from the block partials, in a fixed order,
-// written to out[*counter]; the counter then advances (so one captured
-// iteration can be replayed), bounded by cap
-__global__ void __launch_bounds__(256) k_residue_finish(const double *__restrict__ part, int nparts,
-                                                        double inv_n, double *__restrict__ out_base,
-                                                        int *counter, int cap)
+// residue() of every case = sqrt(sum R_rho^2)/n_case from the per-warp
+// pairs, in a fixed order: case c owns points [start[c], start[c+1]); a warp
+// whose first point lies in c contributes its first sum, a warp that starts
+// in the case before contributes its second. Written to
+// out[(*counter) * ncases + c]; the counter then advances (so one captured
+// iteration can be replayed), bounded by cap iterations.
+__global__ void __launch_bounds__(256) k_residue_finish(const double *__restrict__ part,
+                                                        const int64_t *__restrict__ start, int ncases,
+                                                        double *__restrict__ out_base, int *counter, int cap)
 {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
     __shared__ double sm[256];
-    sm[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    const int it = *counter;
+    for (int c = 0; c < ncases; ++c) {
+        const int64_t p0 = start[c], p1 = start[c + 1];
+        const int64_t w0 = p0 >> 5, w1 = (p1 - 1) >> 5;
+        double s = 0.0;
+        for (int64_t w = w0 + threadIdx.x; w <= w1; w += blockDim.x) s += part[2 * w + ((w << 5) >= p0 ? 0 : 1)];
+        sm[threadIdx.x] = s;
+        __syncthreads();
+        for (int h = 128; h > 0; h >>= 1) {
+            if (threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && it >= 0 && it < cap) out_base[(int64_t)it * ncases + c] = sqrt(sm[0]) / (double)(p1 - p0);
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const int it = *counter;
-        if (it >= 0 && it < cap) out_base[it] = sqrt(sm[0]) * inv_n;
-        *counter = it + 1;
-    }
+    if (threadIdx.x == 0) *counter = it + 1;
 }
 
 // q-variables of every point from U (used when a state is loaded)
@@ -377,7 +377,7 @@ cudaError_t launch_qgrad(const DevGeom &g, const double *q, const double *qg_old
     return cudaGetLastError();
 }
 
-unsigned flux_blocks(int64_t n) { return blocks_for(n, 128); }
+int64_t residue_parts(int64_t n) { return 2 * ((n + 31) / 32); }
 
 cudaError_t launch_flux(const DevGeom &g, const Gas &gas, const FluxLaunch &L, cudaStream_t s)
 {
@@ -386,15 +386,16 @@ cudaError_t launch_flux(const DevGeom &g, const Gas &gas, const FluxLaunch &L, c
     P.gas = gas;
     P.q = L.q; P.qg = L.qg; P.Un = L.Un; P.Uout = L.Uout; P.acc = L.acc; P.qout = L.qout;
     P.dt = L.dt; P.R = L.R; P.norm_part = L.norm_part; P.status = L.status;
+    P.pcase = L.pcase; P.case_uinf = L.case_uinf;
     P.cfl = L.cfl; P.order = L.order; P.mode = L.mode; P.stage = L.stage;
     k_flux_update<<<blocks_for(g.n, 128), 128, 0, s>>>(P);
     return cudaGetLastError();
 }
 
-cudaError_t launch_residue_finish(const double *part, int nparts, int64_t n, double *out_base, int *counter,
-                                  int cap, cudaStream_t s)
+cudaError_t launch_residue_finish(const double *part, const int64_t *case_start, int ncases, double *out_base,
+                                  int *counter, int cap, cudaStream_t s)
 {
-    k_residue_finish<<<1, 256, 0, s>>>(part, nparts, 1.0 / (double)n, out_base, counter, cap);
+    k_residue_finish<<<1, 256, 0, s>>>(part, case_start, ncases, out_base, counter, cap);
     return cudaGetLastError();
 }
 

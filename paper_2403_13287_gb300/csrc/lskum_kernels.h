@@ -19,19 +19,22 @@ struct FluxLaunch {
     double *R;
     double *norm_part;
     int *status;
+    const uint16_t *pcase;
+    const double *case_uinf;
     double cfl;
     int order;
     int mode;   // 0 residual only, 1 forward Euler, 2 RK4 stage
     int stage;
 };
 
-unsigned flux_blocks(int64_t n);
 cudaError_t launch_qgrad(const DevGeom &g, const double *q, const double *qg_old, double *qg_new,
                          double limiter_K, cudaStream_t s);
 cudaError_t launch_flux(const DevGeom &g, const Gas &gas, const FluxLaunch &L, cudaStream_t s);
-// writes the residue to out_base[*counter] (when 0 <= *counter < cap), then ++*counter
-cudaError_t launch_residue_finish(const double *part, int nparts, int64_t n, double *out_base, int *counter,
-                                  int cap, cudaStream_t s);
+// residue of every case into out_base[*counter * ncases + c] (when 0 <= *counter < cap), then ++*counter;
+// part holds a pair of sums per warp of 32 points (residue_parts(n) values)
+cudaError_t launch_residue_finish(const double *part, const int64_t *case_start, int ncases, double *out_base,
+                                  int *counter, int cap, cudaStream_t s);
+int64_t residue_parts(int64_t n);
 cudaError_t launch_q_from_U(int64_t n, const Gas &gas, const double *U, double *q, int *status,
                             cudaStream_t s);
 cudaError_t launch_timestep(int64_t n, const Gas &gas, double cfl, const double *dmin, const double *U,
@@ -67,5 +70,11 @@ cudaError_t launch_mask_out(int64_t n, const int32_t *inv, const int32_t *off_in
                             const int32_t *off_int, const uint8_t *mask_int, uint8_t *mask_in,
                             cudaStream_t s);
 cudaError_t launch_fill_state(int64_t n, const double Uinf[4], double *U, cudaStream_t s);
+cudaError_t launch_fill_state_cases(int64_t n, const uint16_t *pcase, const double *case_uinf, double *U,
+                                    cudaStream_t s);
+// stable sort of 64-bit keys into a permutation (perm[k] = input index of the k-th smallest key)
+cudaError_t sort_permutation(int64_t n, const uint64_t *keys, int32_t *perm, cudaStream_t s);
+// host Morton code of a point in [0, 2^bits)^2 cells of the box (xmin, ymin, scale = cells per unit)
+uint64_t morton_code_host(double x, double y, double xmin, double ymin, double scale, int bits);
 
 }  // namespace lskum

@@ -84,7 +84,6 @@ __device__ __forceinline__ float venkat_f(float D, float d, float eps2)
 // coalesced run. A slice is as deep as its largest degree; shorter rows stop
 // early (on these clouds almost all points have 8 neighbours).
 // --------------------------------------------------------------------------
-static constexpr int kMixedThreads = 128;
 
 // create time: scatter the CSR rows of the FP32 (and FP64-closure) edge arrays
 // into the SELL-32 layout; padding slots keep weight 0 and index = the point
@@ -132,7 +131,8 @@ cudaError_t launch_sell_fill(int64_t n, const int32_t *off, const int32_t *slice
 // --------------------------------------------------------------------------
 // q_derivatives() in FP32 (E15; same arithmetic as k_qgrad)
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(kMixedThreads) k_qgrad_mixed(MixedGeom g, const float *__restrict__ q,
+template <int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, const float *__restrict__ q,
                                                                const float *__restrict__ qg_old,
                                                                float *__restrict__ qg_new, float limK)
 {
@@ -213,7 +213,8 @@ __device__ __forceinline__ void flag_nonphysical_m(int *status, int64_t p)
     atomicMin(status + 1, (int)p);
 }
 
-__global__ void __launch_bounds__(kMixedThreads, 7) k_flux_update_mixed(MixedFluxParams P)
+template <int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxParams P)
 {
     const MixedGeom &g = P.g;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -378,8 +379,9 @@ __global__ void __launch_bounds__(kMixedThreads, 7) k_flux_update_mixed(MixedFlu
             Unew[1] = Unew[1] - mn * n0.x;
             Unew[2] = Unew[2] - mn * n0.y;
         } else if (flag == FLAG_FARFIELD) {
+            const double *Ui = P.case_uinf ? P.case_uinf + 4 * (int)P.pcase[p] : P.Uinf;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) Unew[k] = P.Uinf[k];
+            for (int k = 0; k < 4; ++k) Unew[k] = Ui[k];
         }
         store4(P.Uout, p, Unew);
         float Uf[4], qn[4];
@@ -390,22 +392,10 @@ __global__ void __launch_bounds__(kMixedThreads, 7) k_flux_update_mixed(MixedFlu
         r0sq = Rl[0] * Rl[0];
     }
 
-    // residue partials: FP32 within a warp, FP64 across warps and blocks
-    if (P.mode == 1 || P.stage == 0) {
-        float s = r0sq;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        __shared__ double ws[kMixedThreads / 32];
-        const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (wl == 0) ws[wid] = (double)s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-#pragma unroll
-            for (int k = 0; k < kMixedThreads / 32; ++k) t += ws[k];
-            P.norm_part[blockIdx.x] = t;
-        }
-    }
+    // residue partials, one pair per warp (FP32 within the warp): the points
+    // of the warp's first case, and the rest (a second case that starts
+    // inside the warp; every case has at least 32 points)
+    if (P.mode == 1 || P.stage == 0) warp_residue_pair(P.pcase, p, live, r0sq, P.norm_part);
 }
 
 __global__ void __launch_bounds__(256) k_q_from_U_mixed(int64_t n, float gamma, float inv_gm1,
@@ -437,19 +427,55 @@ __global__ void __launch_bounds__(256) k_grad_out_f(int64_t n, const int32_t *__
     }
 }
 
-unsigned mixed_flux_blocks(int64_t n) { return (unsigned)((n + kMixedThreads - 1) / kMixedThreads); }
-
-cudaError_t launch_qgrad_mixed(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new,
-                               double limiter_K, cudaStream_t s)
+// launch-shape variants of the two hot kernels, chosen by the autotuner:
+// (threads per block, minimum resident blocks per SM for the register cap)
+template <int T, int M>
+static cudaError_t qgrad_v(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new, float limK,
+                           cudaStream_t s)
 {
-    k_qgrad_mixed<<<mixed_flux_blocks(g.n), kMixedThreads, 0, s>>>(g, q, qg_old, qg_new, (float)limiter_K);
+    k_qgrad_mixed<T, M><<<(unsigned)((g.n + T - 1) / T), T, 0, s>>>(g, q, qg_old, qg_new, limK);
     return cudaGetLastError();
 }
 
-cudaError_t launch_flux_mixed(const MixedFluxParams &P, cudaStream_t s)
+template <int T, int M>
+static cudaError_t flux_v(const MixedFluxParams &P, cudaStream_t s)
 {
-    k_flux_update_mixed<<<mixed_flux_blocks(P.g.n), kMixedThreads, 0, s>>>(P);
+    k_flux_update_mixed<T, M><<<(unsigned)((P.g.n + T - 1) / T), T, 0, s>>>(P);
     return cudaGetLastError();
+}
+
+using QgradFn = cudaError_t (*)(const MixedGeom &, const float *, const float *, float *, float, cudaStream_t);
+using FluxFn = cudaError_t (*)(const MixedFluxParams &, cudaStream_t);
+
+static const QgradFn kQgradVariants[] = {qgrad_v<128, 8>, qgrad_v<64, 16>, qgrad_v<256, 4>, qgrad_v<128, 6>,
+                                         qgrad_v<256, 3>, qgrad_v<96, 10>};
+static const FluxFn kFluxVariants[] = {flux_v<128, 7>, flux_v<64, 14>, flux_v<256, 3>, flux_v<128, 6>,
+                                       flux_v<128, 8>, flux_v<256, 4>};
+static const int kQgradShape[][2] = {{128, 8}, {64, 16}, {256, 4}, {128, 6}, {256, 3}, {96, 10}};
+static const int kFluxShape[][2] = {{128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4}};
+
+int mixed_variants(int kernel_class) { return kernel_class == 0 ? 6 : 6; }
+
+void mixed_variant_shape(int kernel_class, int v, int *threads, int *min_blocks)
+{
+    const int(*t)[2] = kernel_class == 0 ? kFluxShape : kQgradShape;
+    *threads = t[v][0];
+    *min_blocks = t[v][1];
+}
+
+cudaError_t launch_qgrad_mixed(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new,
+                               double limiter_K, cudaStream_t s, int variant)
+{
+    if (variant < 0 || variant >= (int)(sizeof kQgradVariants / sizeof kQgradVariants[0]))
+        return cudaErrorInvalidValue;
+    return kQgradVariants[variant](g, q, qg_old, qg_new, (float)limiter_K, s);
+}
+
+cudaError_t launch_flux_mixed(const MixedFluxParams &P, cudaStream_t s, int variant)
+{
+    if (variant < 0 || variant >= (int)(sizeof kFluxVariants / sizeof kFluxVariants[0]))
+        return cudaErrorInvalidValue;
+    return kFluxVariants[variant](P, s);
 }
 
 cudaError_t launch_q_from_U_mixed(int64_t n, const Gas &gas, const double *U, float *q, int *status,

@@ -39,8 +39,10 @@ struct MixedFluxParams {
     float *qout;
     double *dt;
     double *R;
-    double *norm_part;
+    double *norm_part;        // per warp: pair of R_rho^2 sums (see warp_residue_pair)
     int *status;
+    const uint16_t *pcase;    // per point: its case in a batch, or nullptr (one case)
+    const double *case_uinf;  // [cases][4] free stream per case, or nullptr (Uinf)
     double Uinf[4];
     float gamma, inv_gm1, cfl;
     int g14;
@@ -52,10 +54,13 @@ cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, fl
 cudaError_t launch_sell_fill(int64_t n, const int32_t *off, const int32_t *slice_off, const int32_t *idx,
                              const uint8_t *mask, const float2 *dxy, const float2 *lsw, const float2 *fxw,
                              const double2 *fxw64, const MixedGeom &m, cudaStream_t s);
+// launch-shape variants (threads per block, minimum resident blocks per SM);
+// kernel_class 0 = flux, 1 = q-derivatives; variant 0 is the default
+int mixed_variants(int kernel_class);
+void mixed_variant_shape(int kernel_class, int variant, int *threads, int *min_blocks);
 cudaError_t launch_qgrad_mixed(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new,
-                               double limiter_K, cudaStream_t s);
-cudaError_t launch_flux_mixed(const MixedFluxParams &P, cudaStream_t s);
-unsigned mixed_flux_blocks(int64_t n);  // grid of the mixed flux kernel (one residue partial per block)
+                               double limiter_K, cudaStream_t s, int variant);
+cudaError_t launch_flux_mixed(const MixedFluxParams &P, cudaStream_t s, int variant);
 cudaError_t launch_q_from_U_mixed(int64_t n, const Gas &gas, const double *U, float *q, int *status,
                                   cudaStream_t s);
 cudaError_t launch_grad_out_f(int64_t n, const int32_t *perm, const float *qg, double *qx, double *qy,

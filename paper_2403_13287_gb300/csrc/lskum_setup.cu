@@ -114,6 +114,33 @@ __device__ __forceinline__ uint64_t spread32(uint64_t v)
     return v;
 }
 
+// host form of the same interleave, for keys built on the host (batches)
+static uint64_t spread32_host(uint64_t v)
+{
+    v &= 0xffffffffull;
+    v = (v | (v << 16)) & 0x0000ffff0000ffffull;
+    v = (v | (v << 8)) & 0x00ff00ff00ff00ffull;
+    v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
+}
+
+uint64_t morton_code_host(double x, double y, double xmin, double ymin, double scale, int bits)
+{
+    const double top = (double)((1ull << bits) - 1);
+    double fx = (x - xmin) * scale, fy = (y - ymin) * scale;
+    fx = fx < 0.0 ? 0.0 : (fx > top ? top : fx);
+    fy = fy < 0.0 ? 0.0 : (fy > top ? top : fy);
+    return spread32_host((uint64_t)fx) | (spread32_host((uint64_t)fy) << 1);
+}
+
+__global__ void k_iota32(int64_t n, int32_t *__restrict__ v)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) v[p] = (int32_t)p;
+}
+
 __global__ void k_morton(int64_t n, const double2 *__restrict__ xy, double xmin, double ymin,
                          double scale, uint64_t *__restrict__ code, int32_t *__restrict__ iota)
 {
@@ -325,6 +352,48 @@ cudaError_t launch_mask_out(int64_t n, const int32_t *inv, const int32_t *off_in
 {
     k_mask_out<<<nblk(n, 256), 256, 0, s>>>(n, inv, off_in, off_int, mask_int, mask_in);
     return cudaGetLastError();
+}
+
+// free stream of each point's case
+__global__ void k_fill_state_cases(int64_t n, const uint16_t *__restrict__ pcase,
+                                   const double *__restrict__ case_uinf, double *__restrict__ U)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double *u = case_uinf + 4 * (int)pcase[p];
+    double v[4] = {u[0], u[1], u[2], u[3]};
+    store4(U, p, v);
+}
+
+cudaError_t launch_fill_state_cases(int64_t n, const uint16_t *pcase, const double *case_uinf, double *U,
+                                    cudaStream_t s)
+{
+    k_fill_state_cases<<<nblk(n, 256), 256, 0, s>>>(n, pcase, case_uinf, U);
+    return cudaGetLastError();
+}
+
+// sorting keys -> permutation (stable: equal keys keep input order)
+cudaError_t sort_permutation(int64_t n, const uint64_t *keys, int32_t *perm, cudaStream_t s)
+{
+    uint64_t *sorted = nullptr;
+    int32_t *iota = nullptr;
+    void *tmp = nullptr;
+    size_t tmp_bytes = 0;
+    cudaError_t err = cudaSuccess;
+    do {
+        if ((err = cudaMallocAsync(&sorted, n * sizeof(uint64_t), s)) != cudaSuccess) break;
+        if ((err = cudaMallocAsync(&iota, n * sizeof(int32_t), s)) != cudaSuccess) break;
+        k_iota32<<<nblk(n, 256), 256, 0, s>>>(n, iota);
+        if ((err = cudaGetLastError()) != cudaSuccess) break;
+        err = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, sorted, iota, perm, (int)n, 0, 64, s);
+        if (err != cudaSuccess) break;
+        if ((err = cudaMallocAsync(&tmp, tmp_bytes, s)) != cudaSuccess) break;
+        err = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, sorted, iota, perm, (int)n, 0, 64, s);
+    } while (0);
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (iota) cudaFreeAsync(iota, s);
+    if (sorted) cudaFreeAsync(sorted, s);
+    return err;
 }
 
 cudaError_t launch_fill_state(int64_t n, const double Uinf[4], double *U, cudaStream_t s)

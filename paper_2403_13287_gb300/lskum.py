@@ -56,6 +56,20 @@ def library_path() -> str:
     return _build.LIB
 
 
+class lskum_case(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("nx", ctypes.c_void_p), ("ny", ctypes.c_void_p), ("flags", ctypes.c_void_p),
+                ("nbr_offsets", ctypes.c_void_p), ("nbr_idx", ctypes.c_void_p), ("n_wall", ctypes.c_int64),
+                ("wall_order", ctypes.c_void_p), ("mach", ctypes.c_double), ("aoa_deg", ctypes.c_double)]
+
+
+class lskum_tuning(ctypes.Structure):
+    _fields_ = [("flux_variant", ctypes.c_int), ("flux_threads", ctypes.c_int), ("flux_min_blocks", ctypes.c_int),
+                ("qgrad_variant", ctypes.c_int), ("qgrad_threads", ctypes.c_int),
+                ("qgrad_min_blocks", ctypes.c_int), ("flux_ms", ctypes.c_double), ("qgrad_ms", ctypes.c_double),
+                ("flux_ms_default", ctypes.c_double), ("qgrad_ms_default", ctypes.c_double)]
+
+
 def load(build_if_missing: bool = True):
     """Load liblskum.so (building it first if asked and needed)."""
     global _lib
@@ -74,6 +88,16 @@ def load(build_if_missing: bool = True):
     L.lskum_last_error.restype = ctypes.c_char_p
     L.lskum_step.argtypes = [_p, _int, _p]
     L.lskum_residual.argtypes = [_p, _p, _p]
+    L.lskum_create_batch.argtypes = [_int, ctypes.POINTER(lskum_case), ctypes.POINTER(lskum_config), _p,
+                                     ctypes.POINTER(_p)]
+    L.lskum_create_batch.restype = _int
+    L.lskum_case_count.argtypes = [_p]
+    L.lskum_case_count.restype = _int
+    L.lskum_case_range.argtypes = [_p, _int, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                   ctypes.POINTER(_i64)]
+    L.lskum_case_forces.argtypes = [_p, _int, _p, _p, _p]
+    L.lskum_autotune.argtypes = [_p, _int, ctypes.POINTER(lskum_tuning)]
+    L.lskum_set_tuning.argtypes = [_p, _int, _int]
     L.lskum_residual_vjp.argtypes = [_p, _p, _p, _p, _p, _p]
     L.lskum_q_derivatives.argtypes = [_p, _p, _p, _p]
     L.lskum_timestep.argtypes = [_p, _p, _p]
@@ -86,12 +110,24 @@ def load(build_if_missing: bool = True):
     L.lskum_launch_count.restype = _i64
     L.lskum_profile.argtypes = [_p, _int]
     L.lskum_kernel_time.argtypes = [_p, _int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]
+    for name in ("lskum_case_range", "lskum_case_forces", "lskum_autotune", "lskum_set_tuning"):
+        getattr(L, name).restype = _int
     for name in ("lskum_step", "lskum_residual", "lskum_residual_vjp", "lskum_q_derivatives", "lskum_timestep",
                  "lskum_forces", "lskum_get_state", "lskum_set_state", "lskum_get_stencil_masks",
                  "lskum_get_permutation", "lskum_profile", "lskum_kernel_time"):
         getattr(L, name).restype = _int
     _lib = L
     return L
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+    except Exception:  # noqa: BLE001
+        return 0
 
 
 def _np_ptr(a):
@@ -124,14 +160,7 @@ class Solver:
         self._keep["wall_order"] = np.ascontiguousarray(wo if wo is not None else np.zeros(0), dtype=np.int32)
         self.nnz = int(self._keep["nbr_offsets"][-1])
         self.n_wall = int(self._keep["wall_order"].shape[0])
-        if stream is None:
-            try:
-                import torch
-                stream_ptr = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
-            except Exception:  # noqa: BLE001
-                stream_ptr = 0
-        else:
-            stream_ptr = int(stream)
+        stream_ptr = _stream_ptr(stream)
         ctx = _p()
         k = self._keep
         st = L.lskum_create(self.n, _np_ptr(k["x"]), _np_ptr(k["y"]), _np_ptr(k["nx"]), _np_ptr(k["ny"]),
@@ -141,6 +170,73 @@ class Solver:
         if st != LSKUM_OK:
             raise LskumError(st, L.lskum_last_error(None).decode())
         self._ctx = ctx
+        self.ncases = 1
+
+    @classmethod
+    def batch(cls, cases, order=2, inner_iters=3, time_scheme=1, cfl=0.2, gamma=1.4, precision=1, reorder=1,
+              limiter_K=0.0, stream=None):
+        """One context over several independent solves (lskum_create_batch).
+        cases: a list of (cloud, mach, aoa_deg); clouds may repeat."""
+        self = cls.__new__(cls)
+        L = load()
+        self._L = L
+        self.cfg = lskum_config(order, inner_iters, time_scheme, cfl, cases[0][1], cases[0][2], gamma,
+                                precision, reorder, limiter_K)
+        keep, arr = {}, (lskum_case * len(cases))()
+        for k, (cloud, mach, aoa) in enumerate(cases):
+            key = id(cloud)
+            if key not in keep:
+                d = {f: np.ascontiguousarray(cloud[f], dtype=np.float64) for f in ("x", "y", "nx", "ny")}
+                for f in ("flags", "nbr_offsets", "nbr_idx"):
+                    d[f] = np.ascontiguousarray(cloud[f], dtype=np.int32)
+                wo = cloud.get("wall_order")
+                d["wall_order"] = np.ascontiguousarray(wo if wo is not None else np.zeros(0), dtype=np.int32)
+                keep[key] = d
+            d = keep[key]
+            a = arr[k]
+            a.n = int(cloud["n"])
+            for f in ("x", "y", "nx", "ny", "flags", "nbr_offsets", "nbr_idx", "wall_order"):
+                setattr(a, f, d[f].ctypes.data)
+            a.n_wall = int(d["wall_order"].shape[0])
+            a.mach = float(mach)
+            a.aoa_deg = float(aoa)
+        self._keep = keep
+        ctx = _p()
+        stream_ptr = _stream_ptr(stream)
+        st = L.lskum_create_batch(len(cases), arr, ctypes.byref(self.cfg), _p(stream_ptr) if stream_ptr else None,
+                                  ctypes.byref(ctx))
+        if st != LSKUM_OK:
+            raise LskumError(st, L.lskum_last_error(None).decode())
+        self._ctx = ctx
+        self.ncases = int(L.lskum_case_count(ctx))
+        self.n = sum(int(c[0]["n"]) for c in cases)
+        self.nnz = sum(int(np.asarray(c[0]["nbr_offsets"])[-1]) for c in cases)
+        self.n_wall = sum(int(keep[id(c[0])]["wall_order"].shape[0]) for c in cases)
+        return self
+
+    def case_range(self, k):
+        """(first, count, wall_first, wall_count) of case k in caller-visible arrays."""
+        v = [_i64() for _ in range(4)]
+        self._check(self._L.lskum_case_range(self._ctx, int(k), *[ctypes.byref(x) for x in v]))
+        return tuple(int(x.value) for x in v)
+
+    def case_forces(self, k, want_cp=True):
+        nw = self.case_range(k)[3]
+        cl = ctypes.c_double()
+        cd = ctypes.c_double()
+        cp = np.zeros(nw) if want_cp else None
+        self._check(self._L.lskum_case_forces(self._ctx, int(k), ctypes.byref(cl), ctypes.byref(cd),
+                                              _np_ptr(cp) if want_cp else None))
+        return cl.value, cd.value, cp
+
+    def autotune(self, reps=5):
+        """Time every launch shape of the mixed kernels on this context and keep the fastest."""
+        t = lskum_tuning()
+        self._check(self._L.lskum_autotune(self._ctx, int(reps), ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in lskum_tuning._fields_}
+
+    def set_tuning(self, flux_variant, qgrad_variant):
+        self._check(self._L.lskum_set_tuning(self._ctx, int(flux_variant), int(qgrad_variant)))
 
     def _check(self, st):
         if st != LSKUM_OK:
@@ -159,7 +255,8 @@ class Solver:
 
     # --- hot path ---
     def step(self, n_iters, history=True):
-        hist = np.zeros(n_iters) if history else None
+        """n_iters iterations; the residue history ([n_iters], or [n_iters, ncases] for a batch)."""
+        hist = np.zeros((n_iters, self.ncases) if self.ncases > 1 else n_iters) if history else None
         self._check(self._L.lskum_step(self._ctx, int(n_iters), _np_ptr(hist) if history else None))
         return hist
 
