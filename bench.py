@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--shuffle", type=int, default=1, help="present the cloud in random point order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single-form", action="store_true", help="time only --precision's form")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solves form")
+    ap.add_argument("--batch-clouds", type=int, default=16)
+    ap.add_argument("--batch-conditions", type=int, default=3)
     return ap.parse_args()
 
 
@@ -142,20 +145,30 @@ def algorithmic_bytes_per_point(kernel, dbar, order, scheme, stage_avg=True):
     raise ValueError(kernel)
 
 
-def algorithmic_bytes_per_point_mixed(dbar, order, scheme):
-    """Fused flux kernel, mixed layout: q 16 (FP32), own q-derivatives 32,
-    normal 8, flag 1, CSR offset 4, per edge index 4 + mask 1 + FP32 flux
-    weights 8 (+ FP32 offset 8 at order 2); U^n 32, U_out 32 (FP64), q_out 16;
-    RK4 terms averaged over the 4 stages: dt and dmin at stage 0, acc written
-    at stages 0-2 and read at 1-3 (FP64)."""
-    b = 16 + 8 + 1 + 4 + dbar * (4 + 1 + 8) + 32 + 32 + 16
-    if order == 2:
-        b += 32 + dbar * 8
-    if scheme == "rk4":
-        b += (8 + 4 + 3 * 8 + 3 * 32 + 3 * 32) / 4.0
-    else:
-        b += 8 + 4
-    return b
+def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
+    """Mixed layout, bytes each array contributes once per launch, per point.
+    Flux: q 16 (FP32), normal 8, flag 1, CSR offset 4, U^n 32 and U_out 32
+    (FP64), q_out 16, own q-derivatives 32 (order 2), per SELL slot the index
+    word (with the sub-stencil bits) 4 + (dx, dy, w_s, w_n) 16; RK4 terms
+    averaged over the 4 stages: dt written (FP64) and dmin read (FP32) at
+    stage 0, dt read at stages 1-3, the FP32 accumulator written at 0-2 and
+    read at 1-3. q-derivative pass: own q 16, CSR offset 4, per slot 4 +
+    (dx, dy, a_x, a_y) 16, the new derivatives 32; an inner pass also reads
+    its own previous derivatives 32. Neighbour gathers are served from cache."""
+    if kernel == "flux":
+        b = 16 + 8 + 1 + 4 + 32 + 32 + 16 + dbar * 20
+        if order == 2:
+            b += 32
+        if scheme == "rk4":
+            b += (8 + 4 + 3 * 8 + 3 * 16 + 3 * 16) / 4.0
+        else:
+            b += 8 + 4
+        return b
+    if kernel == "qgrad_first":
+        return 16 + 4 + dbar * 20 + 32
+    if kernel == "qgrad_inner":
+        return 16 + 32 + 4 + dbar * 20 + 32
+    raise ValueError(kernel)
 
 
 # Per-unit figures of the FP64 fused flux kernel, from one ncu capture of the
@@ -262,6 +275,8 @@ def measure_form(args, cloud, precision, dist, sampler):
     # dG vanishes identically, and a few iterations would not be representative
     from paper_2403_13287_gb300.cloudgen import smooth_state
     solver.set_state(smooth_state(cloud, args.mach, args.aoa, amp=0.05, seed=7))
+    # the mixed kernels come in several launch shapes: pick them on this cloud
+    tuning = solver.autotune(reps=5) if precision == "mixed" else None
     solver.step(args.warmup, history=False)
     torch.cuda.synchronize()
     if sampler:
@@ -291,7 +306,7 @@ def measure_form(args, cloud, precision, dist, sampler):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     return {"solver": solver, "ms": ms, "launches": launches, "flux_ms": flux_ms, "flux_n": flux_n,
-            "qg_ms": qg_ms, "qg_n": qg_n, "clocks": clocks}
+            "qg_ms": qg_ms, "qg_n": qg_n, "clocks": clocks, "tuning": tuning}
 
 
 def measure_e2e(solver, n, steps, dist):
@@ -318,15 +333,43 @@ def measure_e2e(solver, n, steps, dist):
     return n * steps / e2e_s
 
 
+# DRAM bytes per point of one launch of the mixed kernels on the 2.5M-point
+# workload, from a full-size single-pass ncu capture of the current kernels
+# (profiles/mixed_kernels_naca0012_2p5m.md); None where not captured
+MIXED_TRAFFIC_PER_POINT = {"flux": None, "qgrad": None}
+
+
 def form_summary(args, r, n, dbar, world, precision, peaks, peak_src):
     flux_avg_s = (r["flux_ms"] / max(r["flux_n"], 1)) / 1e3
     if precision == "mixed":
-        fb = algorithmic_bytes_per_point_mixed(dbar, args.order, args.scheme) * n
+        fb = algorithmic_bytes_per_point_mixed("flux", dbar, args.order, args.scheme) * n
         gbs = fb / flux_avg_s / 1e9
-        roofline = {"bound": "hbm", "kernel": "k_flux_update_mixed", "achieved": gbs,
-                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
-                    "traffic": None, "peak_source": peak_src,
-                    "algorithmic_bytes_per_launch": fb, "avg_launch_ms": flux_avg_s * 1e3}
+        tf = MIXED_TRAFFIC_PER_POINT["flux"]
+        flux_roof = {"bound": "hbm", "kernel": "k_flux_update_mixed", "achieved": gbs,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                     "traffic": tf * n if tf else None, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": fb, "avg_launch_ms": flux_avg_s * 1e3,
+                     "share_of_kernel_time": r["flux_ms"] / (r["flux_ms"] + r["qg_ms"])}
+        roofline = flux_roof
+        if r["qg_n"]:
+            # launches per stage: one first-order pass, then the inner passes
+            per_stage = args.inner + 1
+            qb = (algorithmic_bytes_per_point_mixed("qgrad_first", dbar, args.order, args.scheme)
+                  + args.inner * algorithmic_bytes_per_point_mixed("qgrad_inner", dbar, args.order, args.scheme)
+                  ) / per_stage * n
+            qg_avg_s = (r["qg_ms"] / r["qg_n"]) / 1e3
+            qgbs = qb / qg_avg_s / 1e9
+            tq = MIXED_TRAFFIC_PER_POINT["qgrad"]
+            qg_roof = {"bound": "hbm", "kernel": "k_qgrad_mixed", "achieved": qgbs, "peak": peaks["hbm_gbs"],
+                       "unit": "GB/s", "frac": qgbs / peaks["hbm_gbs"], "traffic": tq * n if tq else None,
+                       "peak_source": peak_src, "algorithmic_bytes_per_launch": qb,
+                       "avg_launch_ms": qg_avg_s * 1e3,
+                       "share_of_kernel_time": r["qg_ms"] / (r["flux_ms"] + r["qg_ms"])}
+            # the roofline line names the kernel that takes most of the step
+            if r["qg_ms"] > r["flux_ms"]:
+                roofline = dict(qg_roof, other=flux_roof)
+            else:
+                roofline = dict(flux_roof, other=qg_roof)
     else:
         fb = algorithmic_bytes_per_point("flux", dbar, args.order, args.scheme) * n
         gbs = fb / flux_avg_s / 1e9
@@ -336,6 +379,97 @@ def form_summary(args, r, n, dbar, world, precision, peaks, peak_src):
             "kernels": {"k_flux_update": {"launches": r["flux_n"], "total_ms": r["flux_ms"]},
                         "k_qgrad": {"launches": r["qg_n"], "total_ms": r["qg_ms"]}},
             "gpu_launches": r["launches"]}
+
+
+def batch_workload(n_clouds, n_cond, seed=240313292):
+    """Seeded uneven batch: cloud sizes log-uniform in [20k, 400k] points
+    (W:L about 2.6, as the single-cloud workloads), each under n_cond free
+    streams with M uniform in [0.5, 1.2] and alpha uniform in [-2, 4] deg."""
+    import numpy as np
+
+    from paper_2403_13287_gb300.cloudgen import naca0012_cloud
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(20000.0), np.log(400000.0), n_clouds))
+    cases = []
+    for k, target in enumerate(sizes):
+        W = max(32, int(round(math.sqrt(2.6 * target) / 8.0)) * 8)
+        L = max(8, int(round(target / W)))
+        c = naca0012_cloud(W, L, seed=seed + k)
+        for _ in range(n_cond):
+            cases.append((c, float(rng.uniform(0.5, 1.2)), float(rng.uniform(-2.0, 4.0))))
+    return cases
+
+
+def measure_batched(args, dist, sampler):
+    """The batched form: all cases in one context (mixed precision, one
+    autotuning), against the same cases stepped one context after another
+    with the same launch shapes. Both timed over args.steps iterations with
+    CUDA events on the library stream."""
+    import numpy as np
+    import torch
+
+    from paper_2403_13287_gb300 import lskum
+    from paper_2403_13287_gb300.cloudgen import smooth_state
+
+    cases = batch_workload(args.batch_clouds, args.batch_conditions)
+    stream = torch.cuda.current_stream()
+    scheme = 1 if args.scheme == "rk4" else 0
+    kw = dict(order=args.order, inner_iters=args.inner, time_scheme=scheme, cfl=args.cfl,
+              limiter_K=args.limiter, precision=1, reorder=args.reorder, stream=stream.cuda_stream)
+    U0 = [smooth_state(c, m, a, amp=0.05, seed=100 + k) for k, (c, m, a) in enumerate(cases)]
+    npts = int(sum(c["n"] for c, _, _ in cases))
+
+    def timed(fn):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    B = lskum.Solver.batch(cases, **kw)
+    B.set_state(np.concatenate(U0, axis=1))
+    tuning = B.autotune(reps=5)
+    B.step(args.warmup, history=False)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    l0 = B.launch_count()
+    ms_b = timed(lambda: B.step(args.steps, history=False))
+    launches = B.launch_count() - l0
+    clocks = sampler.stop() if sampler else None
+    B.close()
+
+    singles = []
+    for k, (c, m, a) in enumerate(cases):
+        s = lskum.Solver(c, mach=m, aoa_deg=a, **kw)
+        s.set_tuning(tuning["flux_variant"], tuning["qgrad_variant"])
+        s.set_state(U0[k])
+        s.step(args.warmup, history=False)
+        singles.append(s)
+    ms_s = timed(lambda: [s.step(args.steps, history=False) for s in singles])
+    for s in singles:
+        s.close()
+    value_b = npts * args.steps / (ms_b / 1e3)
+    value_s = npts * args.steps / (ms_s / 1e3)
+    sizes = sorted({int(c["n"]) for c, _, _ in cases})
+    return {"value": value_b, "unit": UNIT, "ms_per_step": ms_b / args.steps, "dtype": "f32/f64 mixed",
+            "cases": len(cases), "points": npts, "cloud_sizes": [sizes[0], sizes[-1]],
+            "clouds": args.batch_clouds, "conditions_per_cloud": args.batch_conditions,
+            "gpu_launches": launches, "tuning": tuning, "clocks": clocks,
+            "sequential": {"value": value_s, "ms_per_step": ms_s / args.steps,
+                           "note": "one context per case, stepped one after another with the same "
+                                   "launch shapes; small cases then run from L2"},
+            "speedup_vs_sequential": value_b / value_s}
 
 
 def run_ours(args, rank, world, local):
@@ -358,6 +492,7 @@ def run_ours(args, rank, world, local):
     peaks, peak_src = measured_peaks()
 
     rp = measure_form(args, cloud, primary, dist, ClockSampler(local) if rank == 0 else None)
+    tuning = rp.get("tuning")
     e2e_value = world * measure_e2e(rp["solver"], n, max(1, args.steps), dist)
     rp["solver"].close()
     forms = {primary: form_summary(args, rp, n, dbar, world, primary, peaks, peak_src)}
@@ -366,7 +501,12 @@ def run_ours(args, rank, world, local):
         ro["solver"].close()
         forms[other] = form_summary(args, ro, n, dbar, world, other, peaks, peak_src)
         forms[other]["clocks"] = ro["clocks"]
+        if ro.get("tuning"):
+            forms[other]["tuning"] = ro["tuning"]
         forms["mixed_speedup_vs_fp64"] = forms["mixed"]["value"] / forms["fp64"]["value"]
+    if not args.no_batch and not args.single_form:
+        forms["batched"] = measure_batched(args, dist, ClockSampler(local) if rank == 0 else None)
+        forms["batched_speedup_vs_fp64"] = forms["batched"]["value"] / forms["fp64"]["value"]
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -392,6 +532,8 @@ def run_ours(args, rank, world, local):
         "clocks": rp["clocks"],
         "forms": {k: v for k, v in forms.items() if k != primary},
     }
+    if tuning:
+        line["tuning"] = tuning
     if not args.no_cpu_baseline and world == 1:
         import oracle
         m = oracle.split_stencils(cloud)
