@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single-form", action="store_true", help="time only --precision's form")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solves form")
+    ap.add_argument("--tuning", default="auto",
+                    help="mixed launch shapes: 'auto' (autotune on the cloud) or 'F,Q' (flux, q-derivative variant)")
     ap.add_argument("--batch-clouds", type=int, default=16)
     ap.add_argument("--batch-conditions", type=int, default=3)
     return ap.parse_args()
@@ -152,9 +154,11 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
     word (with the sub-stencil bits) 4 + (dx, dy, w_s, w_n) 16; RK4 terms
     averaged over the 4 stages: dt written (FP64) and dmin read (FP32) at
     stage 0, dt read at stages 1-3, the FP32 accumulator written at 0-2 and
-    read at 1-3. q-derivative pass: own q 16, CSR offset 4, per slot 4 +
-    (dx, dy, a_x, a_y) 16, the new derivatives 32; an inner pass also reads
-    its own previous derivatives 32. Neighbour gathers are served from cache."""
+    read at 1-3. q-derivative pass: own q 16, CSR offset 4, per slot the
+    index word 4 + (a_x, a_y) 8, the new derivatives 32; an inner pass also
+    reads its own previous derivatives 32 and the normal matrix (Sxx, Sxy,
+    Syy) 16 from which the slot offsets are recovered. Neighbour gathers are
+    served from cache."""
     if kernel == "flux":
         b = 16 + 8 + 1 + 4 + 32 + 32 + 16 + dbar * 20
         if order == 2:
@@ -165,9 +169,9 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
             b += 8 + 4
         return b
     if kernel == "qgrad_first":
-        return 16 + 4 + dbar * 20 + 32
+        return 16 + 4 + dbar * 12 + 32
     if kernel == "qgrad_inner":
-        return 16 + 32 + 4 + dbar * 20 + 32
+        return 16 + 32 + 16 + 4 + dbar * 12 + 32
     raise ValueError(kernel)
 
 
@@ -276,7 +280,14 @@ def measure_form(args, cloud, precision, dist, sampler):
     from paper_2403_13287_gb300.cloudgen import smooth_state
     solver.set_state(smooth_state(cloud, args.mach, args.aoa, amp=0.05, seed=7))
     # the mixed kernels come in several launch shapes: pick them on this cloud
-    tuning = solver.autotune(reps=5) if precision == "mixed" else None
+    tuning = None
+    if precision == "mixed":
+        if args.tuning == "auto":
+            tuning = solver.autotune(reps=5)
+        else:
+            fv, qv = (int(v) for v in args.tuning.split(","))
+            solver.set_tuning(fv, qv)
+            tuning = {"flux_variant": fv, "qgrad_variant": qv, "fixed": True}
     solver.step(args.warmup, history=False)
     torch.cuda.synchronize()
     if sampler:
@@ -438,7 +449,12 @@ def measure_batched(args, dist, sampler):
 
     B = lskum.Solver.batch(cases, **kw)
     B.set_state(np.concatenate(U0, axis=1))
-    tuning = B.autotune(reps=5)
+    if args.tuning == "auto":
+        tuning = B.autotune(reps=5)
+    else:
+        fv, qv = (int(v) for v in args.tuning.split(","))
+        B.set_tuning(fv, qv)
+        tuning = {"flux_variant": fv, "qgrad_variant": qv, "fixed": True}
     B.step(args.warmup, history=False)
     if sampler:
         sampler.start()

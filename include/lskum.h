@@ -288,6 +288,8 @@ lskum_status lskum_q_derivatives_noalloc(int64_t n, const double *x, const doubl
  * LSKUM_ERR_ARG on an FP64 context.
  */
 typedef struct {
+    /* flux variants 6 and up use a software-pipelined neighbour loop (the next
+     * slot's data is loaded while the current slot is evaluated) */
     int flux_variant, flux_threads, flux_min_blocks;
     int qgrad_variant, qgrad_threads, qgrad_min_blocks;
     double flux_ms, qgrad_ms;                  /* per launch, chosen shape */

@@ -46,7 +46,8 @@ struct lskum_ctx {
     float2 *nrm_f = nullptr;
     float *dmin_f = nullptr;
     int32_t *slice_off = nullptr, *s_idx = nullptr;  // SELL-32 edge layout
-    float4 *s_gq = nullptr, *s_gf = nullptr;
+    float2 *s_ga = nullptr;
+    float4 *s_gf = nullptr, *gm = nullptr;
     double2 *s_fxw64 = nullptr;
     double *dt = nullptr, *Rt = nullptr, *Ut = nullptr, *Ucm = nullptr;
     double *norm_part = nullptr;   // residue_parts(n) values: a pair of sums per warp
@@ -111,7 +112,7 @@ struct lskum_ctx {
     {
         MixedGeom g;
         g.n = n; g.nrm = nrm_f; g.flag = flag; g.dmin = dmin_f; g.off = off;
-        g.slice_off = slice_off; g.sidx = s_idx; g.gq = s_gq; g.gf = s_gf; g.fxw64 = s_fxw64;
+        g.slice_off = slice_off; g.sidx = s_idx; g.ga = s_ga; g.gm = gm; g.gf = s_gf; g.fxw64 = s_fxw64;
         return g;
     }
 };
@@ -453,7 +454,8 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
         int *cnt = nullptr;
         CK(c, dalloc(c, &cnt, 1));
         CK(c, cudaMemsetAsync(cnt, 0, sizeof(int), s));
-        LAUNCH(c, launch_mixed_prep(c->geom(), c->flag, c->nrm_f, c->dmin_f, dxy, lsw, fxw, cnt, s));
+        CK(c, dalloc(c, &c->gm, n));
+        LAUNCH(c, launch_mixed_prep(c->geom(), c->flag, c->nrm_f, c->dmin_f, c->gm, dxy, lsw, fxw, cnt, s));
         CK(c, cudaMemcpyAsync(&c->n_fp64_closure, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
         std::vector<int32_t> off_h(n + 1);
         CK(c, cudaMemcpyAsync(off_h.data(), c->off, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -472,7 +474,7 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
         CK(c, dalloc(c, &c->slice_off, nslices + 1));
         CK(c, cudaMemcpyAsync(c->slice_off, so.data(), (nslices + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         CK(c, dalloc(c, &c->s_idx, nslot));
-        CK(c, dalloc(c, &c->s_gq, nslot));
+        CK(c, dalloc(c, &c->s_ga, nslot));
         CK(c, dalloc(c, &c->s_gf, nslot));
         CK(c, dalloc(c, &c->s_fxw64, nslot));
         LAUNCH(c, launch_sell_fill(n, c->off, c->slice_off, c->idx, c->mask, dxy, lsw, fxw, c->fxw, c->mgeom(), s));

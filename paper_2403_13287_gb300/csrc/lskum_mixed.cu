@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(128) k_mixed_prep(int64_t n, const double2 *__
                                                     const double2 *__restrict__ lsw,
                                                     const double2 *__restrict__ fxw,
                                                     uint8_t *__restrict__ flag, float2 *__restrict__ nrm_f,
-                                                    float *__restrict__ dmin_f, float2 *__restrict__ dxy_f,
+                                                    float *__restrict__ dmin_f, float4 *__restrict__ gm,
+                                                    float2 *__restrict__ dxy_f,
                                                     float2 *__restrict__ lsw_f, float2 *__restrict__ fxw_f,
                                                     int *n_fp64)
 {
@@ -38,9 +39,13 @@ __global__ void __launch_bounds__(128) k_mixed_prep(int64_t n, const double2 *__
     if (p >= n) return;
     const double2 P0 = xy[p];
     double amp[4] = {0.0, 0.0, 0.0, 0.0};
+    double Sxx = 0.0, Sxy = 0.0, Syy = 0.0;
     for (int e = off[p]; e < off[p + 1]; ++e) {
         const double2 Pi = xy[idx[e]];
         const double dx = Pi.x - P0.x, dy = Pi.y - P0.y;
+        Sxx += dx * dx;
+        Sxy += dx * dy;
+        Syy += dy * dy;
         const double d = sqrt(dx * dx + dy * dy);
         dxy_f[e] = make_float2((float)dx, (float)dy);
         const double2 a = lsw[e], w = fxw[e];
@@ -54,6 +59,7 @@ __global__ void __launch_bounds__(128) k_mixed_prep(int64_t n, const double2 *__
     }
     const double2 n0 = nrm[p];
     nrm_f[p] = make_float2((float)n0.x, (float)n0.y);
+    gm[p] = make_float4((float)Sxx, (float)Sxy, (float)Syy, 0.0f);
     dmin_f[p] = (float)dmin[p];
     const double a = fmax(fmax(amp[0], amp[1]), fmax(amp[2], amp[3]));
     if (a > kAmpLimit) {
@@ -62,11 +68,11 @@ __global__ void __launch_bounds__(128) k_mixed_prep(int64_t n, const double2 *__
     }
 }
 
-cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, float *dmin_f,
+cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, float *dmin_f, float4 *gm,
                               float2 *dxy_f, float2 *lsw_f, float2 *fxw_f, int *n_fp64, cudaStream_t s)
 {
     k_mixed_prep<<<(unsigned)((g.n + 127) / 128), 128, 0, s>>>(g.n, g.xy, g.nrm, g.dmin, g.off, g.idx, g.mask,
-                                                               g.lsw, g.fxw, flag, nrm_f, dmin_f, dxy_f,
+                                                               g.lsw, g.fxw, flag, nrm_f, dmin_f, gm, dxy_f,
                                                                lsw_f, fxw_f, n_fp64);
     return cudaGetLastError();
 }
@@ -93,7 +99,7 @@ __global__ void __launch_bounds__(256) k_sell_fill(int64_t n, const int32_t *__r
                                                    const uint8_t *__restrict__ mask,
                                                    const float2 *__restrict__ dxy, const float2 *__restrict__ lsw,
                                                    const float2 *__restrict__ fxw, const double2 *__restrict__ fxw64,
-                                                   int32_t *__restrict__ s_idx, float4 *__restrict__ s_gq,
+                                                   int32_t *__restrict__ s_idx, float2 *__restrict__ s_ga,
                                                    float4 *__restrict__ s_gf, double2 *__restrict__ s_fxw64)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -106,12 +112,12 @@ __global__ void __launch_bounds__(256) k_sell_fill(int64_t n, const int32_t *__r
         if (s < deg) {
             const int e = e0 + s;
             s_idx[d] = idx[e] | ((int32_t)mask[e] << 28);
-            s_gq[d] = make_float4(dxy[e].x, dxy[e].y, lsw[e].x, lsw[e].y);
+            s_ga[d] = lsw[e];
             s_gf[d] = make_float4(dxy[e].x, dxy[e].y, fxw[e].x, fxw[e].y);
             s_fxw64[d] = fxw64[e];
         } else {
             s_idx[d] = (int32_t)p;
-            s_gq[d] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            s_ga[d] = make_float2(0.0f, 0.0f);
             s_gf[d] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             s_fxw64[d] = make_double2(0.0, 0.0);
         }
@@ -124,7 +130,7 @@ cudaError_t launch_sell_fill(int64_t n, const int32_t *off, const int32_t *slice
 {
     k_sell_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
         n, off, slice_off, idx, mask, dxy, lsw, fxw, fxw64, const_cast<int32_t *>(m.sidx),
-        const_cast<float4 *>(m.gq), const_cast<float4 *>(m.gf), const_cast<double2 *>(m.fxw64));
+        const_cast<float2 *>(m.ga), const_cast<float4 *>(m.gf), const_cast<double2 *>(m.fxw64));
     return cudaGetLastError();
 }
 
@@ -145,13 +151,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
     const bool inner = qg_old != nullptr;
     const bool limit = limK > 0.0f;
     if (inner) load8f(qg_old, p, g0);
+    // the slot's offset d = M a (a = M^-1 d): recovered from the weights, so
+    // a slot carries 8 bytes of geometry instead of 16
+    float4 M = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (inner || limit) M = g.gm[p];
     float qmax[4] = {q0[0], q0[1], q0[2], q0[3]}, qmin[4] = {q0[0], q0[1], q0[2], q0[3]};
 #pragma unroll 2
     for (int s = 0; s < deg; ++s) {
         const int64_t e = base + 32 * s;
         const int i = g.sidx[e] & kSlotIndexMask;
-        const float4 rec = g.gq[e];
-        const float2 a = make_float2(rec.z, rec.w);
+        const float2 a = g.ga[e];
         float qi[4];
         load4f(q, i, qi);
         float dq[4];
@@ -164,7 +173,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
         if (inner) {
             float gi[8];
             load8f(qg_old, i, gi);
-            const float2 d = make_float2(rec.x, rec.y);
+            const float2 d = make_float2(M.x * a.x + M.y * a.y, M.y * a.x + M.z * a.y);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 dq[k] = dq[k] - 0.5f * (d.x * (gi[k] - g0[k]) + d.y * (gi[4 + k] - g0[4 + k]));
@@ -178,8 +187,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
     if (limit) {
         float dmax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int s = 0; s < deg; ++s) {
-            const float4 rec = g.gq[base + 32 * s];
-            const float2 d = make_float2(rec.x, rec.y);
+            const float2 a = g.ga[base + 32 * s];
+            const float2 d = make_float2(M.x * a.x + M.y * a.y, M.y * a.x + M.z * a.y);
 #pragma unroll
             for (int k = 0; k < 4; ++k) dmax[k] = fmaxf(dmax[k], fabsf(0.5f * (d.x * sx[k] + d.y * sy[k])));
         }
@@ -213,7 +222,9 @@ __device__ __forceinline__ void flag_nonphysical_m(int *status, int64_t p)
     atomicMin(status + 1, (int)p);
 }
 
-template <int THREADS, int MINB>
+// PF: software-pipelined neighbour loop (the next slot's record, index and
+// neighbour values are loaded while the current slot's fluxes are evaluated)
+template <int THREADS, int MINB, bool PF>
 __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxParams P)
 {
     const MixedGeom &g = P.g;
@@ -237,26 +248,70 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
         float R[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         double R64[4] = {0.0, 0.0, 0.0, 0.0};
         bool ok = true;
+        float4 rec_n = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        int32_t im_n = 0;
+        float q_n[4] = {0, 0, 0, 0}, g_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if constexpr (PF) {
+            if (deg > 0) {
+                rec_n = g.gf[base];
+                im_n = g.sidx[base];
+                const int i = im_n & kSlotIndexMask;
+                load4f(P.q, i, q_n);
+                if (second) load8f(P.qg, i, g_n);
+            }
+        }
         for (int s = 0; s < deg; ++s) {
             const int64_t e = base + 32 * s;
-            const float4 rec = g.gf[e];
-            const float2 w = make_float2(rec.z, rec.w);
-            if (w.x == 0.0f && w.y == 0.0f) continue;
-            const int32_t im = g.sidx[e];
-            const int i = im & kSlotIndexMask;
-            const uint32_t m = (uint32_t)im >> 28;
             float qti[4], qt0[4];
-            load4f(P.q, i, qti);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) qt0[k] = q0[k];
-            if (second) {
-                const float2 d = make_float2(rec.x, rec.y);
+            uint32_t m;
+            float2 w, d;
+            if constexpr (PF) {
+                const float4 rec = rec_n;
+                const int32_t im = im_n;
                 float gi[8];
-                load8f(P.qg, i, gi);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    qti[k] = qti[k] - 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
-                    qt0[k] = qt0[k] - 0.5f * (d.x * g0[k] + d.y * g0[4 + k]);
+                for (int k = 0; k < 4; ++k) qti[k] = q_n[k];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) gi[k] = g_n[k];
+                if (s + 1 < deg) {
+                    rec_n = g.gf[e + 32];
+                    im_n = g.sidx[e + 32];
+                    const int in = im_n & kSlotIndexMask;
+                    load4f(P.q, in, q_n);
+                    if (second) load8f(P.qg, in, g_n);
+                }
+                w = make_float2(rec.z, rec.w);
+                if (w.x == 0.0f && w.y == 0.0f) continue;
+                m = (uint32_t)im >> 28;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) qt0[k] = q0[k];
+                if (second) {
+                    d = make_float2(rec.x, rec.y);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        qti[k] = qti[k] - 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
+                        qt0[k] = qt0[k] - 0.5f * (d.x * g0[k] + d.y * g0[4 + k]);
+                    }
+                }
+            } else {
+                const float4 rec = g.gf[e];
+                w = make_float2(rec.z, rec.w);
+                if (w.x == 0.0f && w.y == 0.0f) continue;
+                const int32_t im = g.sidx[e];
+                const int i = im & kSlotIndexMask;
+                m = (uint32_t)im >> 28;
+                load4f(P.q, i, qti);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) qt0[k] = q0[k];
+                if (second) {
+                    d = make_float2(rec.x, rec.y);
+                    float gi[8];
+                    load8f(P.qg, i, gi);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        qti[k] = qti[k] - 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
+                        qt0[k] = qt0[k] - 0.5f * (d.x * g0[k] + d.y * g0[4 + k]);
+                    }
                 }
             }
             // equal reconstructed states have dG = 0 exactly; the two flux
@@ -437,10 +492,10 @@ static cudaError_t qgrad_v(const MixedGeom &g, const float *q, const float *qg_o
     return cudaGetLastError();
 }
 
-template <int T, int M>
+template <int T, int M, bool PF>
 static cudaError_t flux_v(const MixedFluxParams &P, cudaStream_t s)
 {
-    k_flux_update_mixed<T, M><<<(unsigned)((P.g.n + T - 1) / T), T, 0, s>>>(P);
+    k_flux_update_mixed<T, M, PF><<<(unsigned)((P.g.n + T - 1) / T), T, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -449,12 +504,23 @@ using FluxFn = cudaError_t (*)(const MixedFluxParams &, cudaStream_t);
 
 static const QgradFn kQgradVariants[] = {qgrad_v<128, 8>, qgrad_v<64, 16>, qgrad_v<256, 4>, qgrad_v<128, 6>,
                                          qgrad_v<256, 3>, qgrad_v<96, 10>};
-static const FluxFn kFluxVariants[] = {flux_v<128, 7>, flux_v<64, 14>, flux_v<256, 3>, flux_v<128, 6>,
-                                       flux_v<128, 8>, flux_v<256, 4>};
+static const FluxFn kFluxVariants[] = {
+    flux_v<128, 7, false>, flux_v<64, 14, false>, flux_v<256, 3, false>, flux_v<128, 6, false>,
+    flux_v<128, 8, false>, flux_v<256, 4, false>, flux_v<128, 7, true>,  flux_v<64, 14, true>,
+    flux_v<256, 3, true>,  flux_v<128, 6, true>,  flux_v<128, 8, true>,  flux_v<256, 4, true>,
+    flux_v<128, 5, true>,  flux_v<128, 4, true>};
 static const int kQgradShape[][2] = {{128, 8}, {64, 16}, {256, 4}, {128, 6}, {256, 3}, {96, 10}};
-static const int kFluxShape[][2] = {{128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4}};
+// flux shapes 6-11 repeat 0-5 with the software-pipelined neighbour loop,
+// 12-13 give that loop more registers
+static const int kFluxShape[][2] = {{128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4},
+                                    {128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4},
+                                    {128, 5}, {128, 4}};
 
-int mixed_variants(int kernel_class) { return kernel_class == 0 ? 6 : 6; }
+int mixed_variants(int kernel_class)
+{
+    return kernel_class == 0 ? (int)(sizeof kFluxVariants / sizeof kFluxVariants[0])
+                             : (int)(sizeof kQgradVariants / sizeof kQgradVariants[0]);
+}
 
 void mixed_variant_shape(int kernel_class, int v, int *threads, int *min_blocks)
 {

@@ -21,7 +21,9 @@ struct MixedGeom {
     const int32_t *__restrict__ off;      // CSR offsets (degree = off[p+1] - off[p])
     const int32_t *__restrict__ slice_off;
     const int32_t *__restrict__ sidx;     // per slot: neighbour index | sub-stencil bits << 28
-    const float4 *__restrict__ gq;        // per slot: (dx, dy, a_x, a_y) full-stencil weights
+    const float2 *__restrict__ ga;        // per slot: (a_x, a_y) full-stencil weights
+    const float4 *__restrict__ gm;        // per point: (Sxx, Sxy, Syy, 0), the full-stencil normal
+                                          // matrix M; the slot's offset is d = M a
     const float4 *__restrict__ gf;        // per slot: (dx, dy, w_s, w_n) sub-stencil weights
     const double2 *__restrict__ fxw64;    // per slot: FP64 sub-stencil weights
 };
@@ -49,7 +51,7 @@ struct MixedFluxParams {
     int order, mode, stage;
 };
 
-cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, float *dmin_f,
+cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, float *dmin_f, float4 *gm,
                               float2 *dxy_f, float2 *lsw_f, float2 *fxw_f, int *n_fp64, cudaStream_t s);
 cudaError_t launch_sell_fill(int64_t n, const int32_t *off, const int32_t *slice_off, const int32_t *idx,
                              const uint8_t *mask, const float2 *dxy, const float2 *lsw, const float2 *fxw,

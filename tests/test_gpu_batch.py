@@ -97,9 +97,9 @@ def test_every_launch_shape_gives_the_same_solution(clouds):
     c = clouds[0]
     U0 = smooth_state(c, 0.85, 1.0, amp=0.05, seed=70)
     ref = None
-    for v in range(6):
+    for v in range(14):                                 # 14 flux shapes, 6 q-derivative shapes
         s = Solver(c, order=2, inner_iters=3, time_scheme=1, mach=0.85, aoa_deg=1.0, limiter_K=1.0, precision=1)
-        s.set_tuning(v, v)
+        s.set_tuning(v, v % 6)
         s.set_state(U0)
         h = s.step(3)
         out = (h, s.get_state())
@@ -120,6 +120,10 @@ def test_batch_arguments(clouds):
     assert e.value.status == LSKUM_ERR_ARG
     with pytest.raises(LskumError) as e:
         Solver.batch([(a, 0.0, 0.0)])
+    assert e.value.status == LSKUM_ERR_ARG
+    s1 = Solver(a, precision=1)
+    with pytest.raises(LskumError) as e:
+        s1.set_tuning(14, 0)
     assert e.value.status == LSKUM_ERR_ARG
     f64 = Solver(a, precision=0)
     with pytest.raises(LskumError) as e:
