@@ -185,14 +185,53 @@ lskum_status lskum_residual(lskum_ctx *ctx, const double *U, double *R);
  *   U      device float64[4*n] in input order, or NULL for the context's state
  *   R_bar  device float64[4*n] in input order
  *   U_bar  device float64[4*n] in input order (written), or NULL
- *   x_bar, y_bar  device float64[n] in input order (written), or NULL
+ *   x_bar, y_bar  device float64[n] in input order (written, or added into with
+ *                 LSKUM_VJP_ACCUMULATE_XY), or NULL
+ *   flags  0 or LSKUM_VJP_ACCUMULATE_XY
  * Requires limiter_K = 0 (the limiter's min/max is not differentiated):
  * LSKUM_ERR_ARG otherwise. Its workspace (about 0.45 KB per point plus
  * 100 B per edge for K = 3) is allocated on the first call and kept.
  * Does not change the context's state.
  */
+#define LSKUM_VJP_ACCUMULATE_XY 1 /* flags: add into x_bar, y_bar instead of overwriting them */
+
 lskum_status lskum_residual_vjp(lskum_ctx *ctx, const double *U, const double *R_bar, double *U_bar,
-                                double *x_bar, double *y_bar);
+                                double *x_bar, double *y_bar, int flags);
+
+/*
+ * Vector-Jacobian product of one pseudo-time iteration, the map U^n -> U^{n+1}
+ * that lskum_step(ctx, 1, .) applies: residual(s), local time step frozen at
+ * U^n (its nearest-neighbour distance differentiated through the nearest
+ * neighbour, the first of equals in row order), forward Euler (E16) or the
+ * four RK4 stages, the wall projection after every stage and the far-field
+ * reset. For the cotangent U_bar_next of U^{n+1}:
+ *   U_bar = (dU^{n+1}/dU^n)^T U_bar_next,  x_bar, y_bar likewise.
+ * Differentiates the FP64 scheme whatever the context's precision; the stage
+ * states are recomputed in FP64. Frame normals, connectivity and sub-stencil
+ * membership are held fixed, as in lskum_residual_vjp; limiter_K = 0 is
+ * required (LSKUM_ERR_ARG otherwise).
+ *   U           device float64[4*n] in input order, or NULL for the context's state
+ *   U_bar_next  device float64[4*n] in input order
+ *   U_bar       device float64[4*n] in input order (written), or NULL
+ *   x_bar, y_bar  device float64[n] in input order (written, or added into with
+ *                 flags = LSKUM_VJP_ACCUMULATE_XY), or NULL
+ * Workspace: about 0.6 KB per point more than lskum_residual_vjp, allocated on
+ * the first call. Does not change the context's state.
+ */
+lskum_status lskum_step_vjp(lskum_ctx *ctx, const double *U, const double *U_bar_next, double *U_bar,
+                            double *x_bar, double *y_bar, int flags);
+
+/*
+ * Vector-Jacobian product of the lift and drag of case k (lskum_case_forces;
+ * k = 0 for a single context) at the context's state:
+ *   U_bar = cl_bar dCl/dU + cd_bar dCd/dU,  x_bar, y_bar likewise
+ * (only wall points have non-zero entries; the frame normals are held fixed
+ * and the arc-length weights ds are differentiated).
+ *   U_bar, x_bar, y_bar  device float64 in input order ([4*n], [n], [n]; written), or NULL
+ *   flags  0 or LSKUM_VJP_ACCUMULATE_XY (add into x_bar, y_bar)
+ */
+lskum_status lskum_forces_vjp(lskum_ctx *ctx, int k, double cl_bar, double cd_bar, double *U_bar, double *x_bar,
+                              double *y_bar, int flags);
 
 /*
  * q-derivatives of E15 (global x, y frame) after the configured inner

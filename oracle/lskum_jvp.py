@@ -226,3 +226,146 @@ def vjp_entries(cloud, mask, U, R_bar, entries, order=2, inner=3, gamma=1.4):
             Jv = jvp(cloud, mask, U, **{"d" + ent[0]: d}, order=order, inner=inner, gamma=gamma)
         out[j] = float(np.sum(R_bar * Jv))
     return out
+
+
+# ---------------------------------------------------------------------------
+# The pseudo-time iteration and the forces over complex numbers, the same
+# steps as the C oracle's orc_timestep, orc_euler_step / orc_rk4_step and
+# orc_forces, for derivatives of Cl and Cd after unrolled iterations.
+# ---------------------------------------------------------------------------
+def _timestep(E, U, x, y, cfl, gamma):
+    """dt = CFL dmin / (|u| + 3 sqrt(p/rho)), dmin the nearest neighbour's
+    distance. dmin is a minimum: at a tie (the leading and trailing edge of a
+    mirror-symmetric contour have two nearest neighbours at equal distance) it
+    has a kink, and its derivative here is that of the first nearest
+    neighbour in row order, ranked by the real squared distance."""
+    rho = U[0]
+    u1 = U[1] / rho
+    u2 = U[2] / rho
+    p = (gamma - 1.0) * (U[3] - 0.5 * rho * (u1 * u1 + u2 * u2))
+    speed = np.sqrt(u1 * u1 + u2 * u2) + 3.0 * np.sqrt(p / rho)
+    dx = x[E.dst] - x[E.src]
+    dy = y[E.dst] - y[E.src]
+    d2 = dx * dx + dy * dy
+    d = np.sqrt(d2)
+    order = np.lexsort((np.arange(len(d)), d2.real, E.src))
+    first = np.ones(len(order), dtype=bool)
+    first[1:] = E.src[order][1:] != E.src[order][:-1]
+    dmin = np.zeros(E.n, dtype=d.dtype)
+    dmin[E.src[order][first]] = d[order][first]
+    return cfl * dmin / speed
+
+
+def _boundary(U, flags, nx, ny, Uinf):
+    """Wall points lose the normal momentum, far-field points take U_inf."""
+    U = U.copy()
+    wall = flags == WALL
+    mn = U[1, wall] * nx[wall] + U[2, wall] * ny[wall]
+    U[1, wall] = U[1, wall] - mn * nx[wall]
+    U[2, wall] = U[2, wall] - mn * ny[wall]
+    far = flags == FARFIELD
+    U[:, far] = np.asarray(Uinf)[:, None]
+    return U
+
+
+def _freestream(mach, aoa_deg, gamma):
+    a = math.radians(aoa_deg)
+    rho, u1, u2, p = 1.0, mach * math.cos(a), mach * math.sin(a), 1.0 / gamma
+    return np.array([rho, rho * u1, rho * u2, p / (gamma - 1.0) + 0.5 * rho * (u1 * u1 + u2 * u2)])
+
+
+def _iterate(cloud, mask, U, x, y, scheme, cfl, mach, aoa_deg, order, inner, gamma):
+    """One pseudo-time iteration: forward Euler (E16) or RK4 with dt frozen."""
+    E = _Edges(cloud)
+    flags = np.asarray(cloud["flags"])
+    nx = np.asarray(cloud["nx"], dtype=np.float64)
+    ny = np.asarray(cloud["ny"], dtype=np.float64)
+    Uinf = _freestream(mach, aoa_deg, gamma)
+    dt = _timestep(E, U, x, y, cfl, gamma)
+
+    def R(V):
+        return _residual(cloud, mask, V, x, y, order, inner, gamma)
+
+    if scheme == 0:
+        return _boundary(U - dt * R(U), flags, nx, ny, Uinf)
+    R0 = R(U)
+    U1 = _boundary(U - 0.5 * dt * R0, flags, nx, ny, Uinf)
+    R1 = R(U1)
+    U2 = _boundary(U - 0.5 * dt * R1, flags, nx, ny, Uinf)
+    R2 = R(U2)
+    U3 = _boundary(U - dt * R2, flags, nx, ny, Uinf)
+    R3 = R(U3)
+    return _boundary(U - dt / 6.0 * (R0 + 2.0 * R1 + 2.0 * R2 + R3), flags, nx, ny, Uinf)
+
+
+def _forces(cloud, U, x, y, mach, aoa_deg, gamma):
+    """Cl, Cd: Cp = (p - p_inf)/q_inf on the closed wall contour, arc-length
+    weights ds = (|P_{w+1} - P_w| + |P_w - P_{w-1}|)/2, (cx, cy) = -sum Cp n ds."""
+    w = np.asarray(cloud["wall_order"], dtype=np.int64)
+    wn, wp = np.roll(w, -1), np.roll(w, 1)
+    nx = np.asarray(cloud["nx"], dtype=np.float64)[w]
+    ny = np.asarray(cloud["ny"], dtype=np.float64)[w]
+    rho = U[0, w]
+    u1 = U[1, w] / rho
+    u2 = U[2, w] / rho
+    p = (gamma - 1.0) * (U[3, w] - 0.5 * rho * (u1 * u1 + u2 * u2))
+    c = (p - 1.0 / gamma) / (0.5 * mach * mach)
+    dsn = np.sqrt((x[wn] - x[w]) ** 2 + (y[wn] - y[w]) ** 2)
+    dsp = np.sqrt((x[w] - x[wp]) ** 2 + (y[w] - y[wp]) ** 2)
+    ds = 0.5 * (dsn + dsp)
+    cx = -np.sum(c * nx * ds)
+    cy = -np.sum(c * ny * ds)
+    a = math.radians(aoa_deg)
+    return cy * math.cos(a) - cx * math.sin(a), cx * math.cos(a) + cy * math.sin(a)
+
+
+def _unrolled(cloud, mask, U0, x, y, iters, scheme, cfl, mach, aoa_deg, order, inner, gamma):
+    U = U0
+    for _ in range(iters):
+        U = _iterate(cloud, mask, U, x, y, scheme, cfl, mach, aoa_deg, order, inner, gamma)
+    return U
+
+
+def iterate(cloud, mask, U, scheme=1, cfl=0.2, mach=0.63, aoa_deg=2.0, order=2, inner=3, gamma=1.4):
+    """One iteration in real arithmetic (equals the C oracle's)."""
+    x = np.asarray(cloud["x"], dtype=np.float64)
+    y = np.asarray(cloud["y"], dtype=np.float64)
+    return _iterate(cloud, mask, np.asarray(U, dtype=np.float64), x, y, scheme, cfl, mach, aoa_deg, order,
+                    inner, gamma)
+
+
+def iterate_jvp(cloud, mask, U, dU=None, dx=None, dy=None, scheme=1, cfl=0.2, mach=0.63, aoa_deg=2.0,
+                order=2, inner=3, gamma=1.4, h=1e-30):
+    """J v of one iteration U^n -> U^{n+1}, by complex step."""
+    U, x, y = _lift(cloud, U, dU, dx, dy, h)
+    return _iterate(cloud, mask, U, x, y, scheme, cfl, mach, aoa_deg, order, inner, gamma).imag / h
+
+
+def forces_jvp(cloud, U, dU=None, dx=None, dy=None, mach=0.63, aoa_deg=2.0, gamma=1.4, h=1e-30):
+    """(dCl, dCd) along (dU, dx, dy), by complex step."""
+    U, x, y = _lift(cloud, U, dU, dx, dy, h)
+    cl, cd = _forces(cloud, U, x, y, mach, aoa_deg, gamma)
+    return cl.imag / h, cd.imag / h
+
+
+def unrolled_forces(cloud, mask, U0, iters, dx=None, dy=None, scheme=1, cfl=0.2, mach=0.63, aoa_deg=2.0,
+                    order=2, inner=3, gamma=1.4, h=1e-30):
+    """(Cl, Cd) after `iters` iterations from U0, and their derivatives along
+    a displacement (dx, dy) of the points (frame normals and connectivity fixed)."""
+    U, x, y = _lift(cloud, U0, None, dx, dy, h)
+    U = _unrolled(cloud, mask, U, x, y, iters, scheme, cfl, mach, aoa_deg, order, inner, gamma)
+    cl, cd = _forces(cloud, U, x, y, mach, aoa_deg, gamma)
+    return (float(np.real(cl)), float(np.real(cd))), (float(np.imag(cl)) / h, float(np.imag(cd)) / h)
+
+
+def _lift(cloud, U, dU, dx, dy, h):
+    U = np.asarray(U, dtype=np.float64).astype(np.complex128)
+    x = np.asarray(cloud["x"], dtype=np.float64).astype(np.complex128)
+    y = np.asarray(cloud["y"], dtype=np.float64).astype(np.complex128)
+    if dU is not None:
+        U = U + 1j * h * np.asarray(dU, dtype=np.float64)
+    if dx is not None:
+        x = x + 1j * h * np.asarray(dx, dtype=np.float64)
+    if dy is not None:
+        y = y + 1j * h * np.asarray(dy, dtype=np.float64)
+    return U, x, y

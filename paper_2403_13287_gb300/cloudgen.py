@@ -359,3 +359,38 @@ def smooth_state(cloud, mach, aoa_deg, amp=0.05, seed=0, gamma=1.4):
     U[1, wall] -= mn * cloud["nx"][wall]
     U[2, wall] -= mn * cloud["ny"][wall]
     return np.ascontiguousarray(U)
+
+
+def hicks_henne_basis(cloud, peaks=(0.2, 0.4, 0.6, 0.8), width=3.0):
+    """Point displacements of 2*len(peaks) Hicks-Henne bumps (R. Hicks and
+    P. Henne, J. Aircraft 15 (1978) 407-412) on a cloud built in grid order
+    (not shuffled): B[k] is the y-displacement of every point per unit
+    amplitude of bump k, so y(a) = y + a @ B. Bump k (peak position x_k,
+    b(x) = sin(pi x^(ln 0.5 / ln x_k))^width on the chord x in [0, 1]) moves
+    the upper surface outward for k < len(peaks), the lower surface outward
+    after; interior points of the same grid column follow with the smooth
+    decay (1 + cos(pi j / L)) / 2 of their layer j, so the far-field layer
+    stays put. The frame normals are not changed."""
+    W, L = cloud["W"], cloud["L"]
+    n = cloud["n"]
+    if n != W * (L + 1):
+        raise ValueError("hicks_henne_basis needs a cloud in grid order (shuffle=False)")
+    xw, yw = cloud["x"][:W], cloud["y"][:W]
+    half = W // 2
+    col = np.arange(n) % W
+    layer = np.arange(n) // W
+    decay = 0.5 * (1.0 + np.cos(np.pi * layer / L))
+    xc = np.clip(xw, 0.0, 1.0)
+    upper = np.zeros(W, dtype=bool)
+    upper[1:half] = True
+    lower = np.zeros(W, dtype=bool)
+    lower[half + 1:] = True
+    B = np.zeros((2 * len(peaks), n))
+    for k, xp in enumerate(peaks):
+        m = np.log(0.5) / np.log(xp)
+        b = np.sin(np.pi * xc ** m) ** width
+        bu = np.where(upper, b, 0.0)
+        bl = np.where(lower, -b, 0.0)
+        B[k] = bu[col] * decay
+        B[len(peaks) + k] = bl[col] * decay
+    return B

@@ -235,7 +235,6 @@ __global__ void __launch_bounds__(128) k_adj_flux(AdjParams P)
         for (int e = e0; e < e1; ++e) {
             st4(P.ebar, e, qb0);
             P.wbar[e] = make_double2(0.0, 0.0);
-            P.dbar[e] = make_double2(0.0, 0.0);
         }
         st4(P.qbar, p, qb0);
         if (second) st8(P.gbar, p, gb0);
@@ -310,7 +309,10 @@ __global__ void __launch_bounds__(128) k_adj_flux(AdjParams P)
                 dyb -= 0.5 * qbo[k] * g0[4 + k];
             }
         }
-        P.dbar[e] = make_double2(dxb, dyb);
+        double2 db = P.dbar[e];
+        db.x += dxb;
+        db.y += dyb;
+        P.dbar[e] = db;
     }
     st4(P.qbar, p, qb0);
     if (second) st8(P.gbar, p, gb0);
@@ -533,14 +535,20 @@ __global__ void __launch_bounds__(128) k_adj_weights(AdjParams P)
     }
 }
 
-// offsets d_e = P_dst - P_src back to points: x_bar_p = sum_in d_bar - sum_out d_bar
-__global__ void __launch_bounds__(256) k_adj_points(AdjParams P, double *__restrict__ xb_out,
-                                                    double *__restrict__ yb_out)
+// offsets d_e = P_dst - P_src back to points: x_bar_p = sum_in d_bar - sum_out d_bar,
+// plus the per-point cotangents already gathered in pxy (internal order, or nullptr)
+__global__ void __launch_bounds__(256) k_adj_points(AdjParams P, const double2 *__restrict__ pxy,
+                                                    double *__restrict__ xb_out, double *__restrict__ yb_out,
+                                                    int accumulate)
 {
     const DevGeom &g = P.g;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.n) return;
     double xb = 0.0, yb = 0.0;
+    if (pxy) {
+        xb = pxy[p].x;
+        yb = pxy[p].y;
+    }
     for (int t = P.toff[p]; t < P.toff[p + 1]; ++t) {
         const double2 d = P.dbar[P.tedge[t]];
         xb += d.x;
@@ -552,14 +560,14 @@ __global__ void __launch_bounds__(256) k_adj_points(AdjParams P, double *__restr
         yb -= d.y;
     }
     const int32_t o = P.perm[p];
-    if (xb_out) xb_out[o] = xb;
-    if (yb_out) yb_out[o] = yb;
+    if (xb_out) xb_out[o] = accumulate ? xb_out[o] + xb : xb;
+    if (yb_out) yb_out[o] = accumulate ? yb_out[o] + yb : yb;
 }
 
 // q_bar to U_bar through E13 (duals over the four conserved variables);
-// writes component-major input order
+// adds into Ub_acc ([n][4], internal order)
 __global__ void __launch_bounds__(256) k_adj_state(AdjParams P, const double *__restrict__ U,
-                                                   double *__restrict__ Ub_out)
+                                                   double *__restrict__ Ub_acc)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n = P.g.n;
@@ -582,14 +590,16 @@ __global__ void __launch_bounds__(256) k_adj_state(AdjParams P, const double *__
     q[1] = 2.0 * (beta * u1);
     q[2] = 2.0 * (beta * u2);
     q[3] = -2.0 * beta;
-    const int32_t o = P.perm[p];
+    double ub[4];
+    ld4(Ub_acc, p, ub);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         double s = 0.0;
 #pragma unroll
         for (int c = 0; c < 4; ++c) s += qb[c] * q[c].d[k];
-        Ub_out[(int64_t)k * n + o] = s;
+        ub[k] += s;
     }
+    st4(Ub_acc, p, ub);
 }
 
 // ---------------------------------------------------------------------------
@@ -683,18 +693,283 @@ cudaError_t launch_adj_grad(const AdjParams &P, const double *gprev, const doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_geometry(const AdjParams &P, double *x_bar, double *y_bar, cudaStream_t s)
+cudaError_t launch_adj_weights(const AdjParams &P, cudaStream_t s)
 {
     k_adj_weights<<<blocks(P.g.n, 128), 128, 0, s>>>(P);
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
-    k_adj_points<<<blocks(P.g.n, 256), 256, 0, s>>>(P, x_bar, y_bar);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_state(const AdjParams &P, const double *U, double *U_bar, cudaStream_t s)
+cudaError_t launch_adj_points(const AdjParams &P, const double2 *pxy, double *x_bar, double *y_bar, bool accumulate,
+                              cudaStream_t s)
 {
-    k_adj_state<<<blocks(P.g.n, 256), 256, 0, s>>>(P, U, U_bar);
+    k_adj_points<<<blocks(P.g.n, 256), 256, 0, s>>>(P, pxy, x_bar, y_bar, accumulate ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_state(const AdjParams &P, const double *U, double *Ub_acc, cudaStream_t s)
+{
+    k_adj_state<<<blocks(P.g.n, 256), 256, 0, s>>>(P, U, Ub_acc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// pseudo-time update in forward (stage states for the reverse sweep) and in
+// reverse. A stage maps U^n and a residual R to
+//   U' = P(U^n - c dt R),
+// P the boundary treatment: wall points lose the normal momentum (a symmetric
+// projection), far-field points are reset to the free stream (no dependence).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_stage_fwd(StageParams S, const double *__restrict__ Un,
+                                                   const double *__restrict__ R, double c,
+                                                   double *__restrict__ Uout)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.n) return;
+    const uint8_t f = S.flag[p] & 3;
+    double u[4], r[4], o[4];
+    ld4(Un, p, u);
+    ld4(R, p, r);
+    const double cdt = c * S.dt[p];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[k] = u[k] - cdt * r[k];
+    if (f == FLAG_WALL) {
+        const double2 n0 = S.nrm[p];
+        const double mn = o[1] * n0.x + o[2] * n0.y;
+        o[1] = o[1] - mn * n0.x;
+        o[2] = o[2] - mn * n0.y;
+    } else if (f == FLAG_FARFIELD) {
+        const double *Ui = S.case_uinf ? S.case_uinf + 4 * (int)S.pcase[p] : S.Uinf;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] = Ui[k];
+    }
+    st4(Uout, p, o);
+}
+
+// reverse of one stage: v = P^T Ub_out; Uacc += v; dtbar (+)= -c sum_k R_k v_k;
+// Rbar (+)= -c dt v (assigned when init, else added)
+__global__ void __launch_bounds__(256) k_stage_adj(StageParams S, const double *__restrict__ Ub_out,
+                                                   const double *__restrict__ R, double c, int init,
+                                                   double *__restrict__ Uacc, double *__restrict__ dtbar,
+                                                   double *__restrict__ Rbar)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.n) return;
+    const uint8_t f = S.flag[p] & 3;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (f != FLAG_FARFIELD) {
+        ld4(Ub_out, p, v);
+        if (f == FLAG_WALL) {
+            const double2 n0 = S.nrm[p];
+            const double mn = v[1] * n0.x + v[2] * n0.y;
+            v[1] = v[1] - mn * n0.x;
+            v[2] = v[2] - mn * n0.y;
+        }
+    }
+    double a[4], r[4], rb[4] = {0.0, 0.0, 0.0, 0.0};
+    ld4(Uacc, p, a);
+    ld4(R, p, r);
+    if (!init) ld4(Rbar, p, rb);
+    const double dt = S.dt[p];
+    double tb = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[k] += v[k];
+        tb -= c * r[k] * v[k];
+        rb[k] -= c * dt * v[k];
+    }
+    st4(Uacc, p, a);
+    st4(Rbar, p, rb);
+    dtbar[p] = init ? tb : dtbar[p] + tb;
+}
+
+// reverse of the last RK4 stage U^{n+1} = P(U^n - dt/6 (R0 + 2 R1 + 2 R2 + R3))
+__global__ void __launch_bounds__(256) k_stage_adj_rk4_final(StageParams S, const double *__restrict__ Ub_out,
+                                                             const double *__restrict__ R0,
+                                                             const double *__restrict__ R1,
+                                                             const double *__restrict__ R2,
+                                                             const double *__restrict__ R3,
+                                                             double *__restrict__ Uacc, double *__restrict__ dtbar,
+                                                             double *__restrict__ Rb0, double *__restrict__ Rb1,
+                                                             double *__restrict__ Rb2, double *__restrict__ Rb3)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.n) return;
+    const uint8_t f = S.flag[p] & 3;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (f != FLAG_FARFIELD) {
+        ld4(Ub_out, p, v);
+        if (f == FLAG_WALL) {
+            const double2 n0 = S.nrm[p];
+            const double mn = v[1] * n0.x + v[2] * n0.y;
+            v[1] = v[1] - mn * n0.x;
+            v[2] = v[2] - mn * n0.y;
+        }
+    }
+    double a[4], r0[4], r1[4], r2[4], r3[4], b0[4], b1[4];
+    ld4(Uacc, p, a);
+    ld4(R0, p, r0);
+    ld4(R1, p, r1);
+    ld4(R2, p, r2);
+    ld4(R3, p, r3);
+    const double dt = S.dt[p];
+    double tb = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[k] += v[k];
+        tb -= (r0[k] + 2.0 * r1[k] + 2.0 * r2[k] + r3[k]) * v[k] / 6.0;
+        b0[k] = -dt / 6.0 * v[k];
+        b1[k] = -dt / 3.0 * v[k];
+    }
+    st4(Uacc, p, a);
+    st4(Rb0, p, b0);
+    st4(Rb1, p, b1);
+    st4(Rb2, p, b1);
+    st4(Rb3, p, b0);
+    dtbar[p] = tb;
+}
+
+// reverse of timestep(): dt = CFL dmin / (|u| + 3 sqrt(p/rho)), dmin the
+// distance to the nearest neighbour (the first of equals in row order)
+__global__ void __launch_bounds__(256) k_dt_adj(StageParams S, DevGeom g, double cfl, double inv_gm1,
+                                                const double *__restrict__ U, const double *__restrict__ dtbar,
+                                                double *__restrict__ Uacc, double2 *__restrict__ dbar)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.n) return;
+    const double tb = dtbar[p];
+    double u[4];
+    ld4(U, p, u);
+    D4 Ud[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        Ud[k] = dconst(u[k]);
+        Ud[k].d[k] = 1.0;
+    }
+    const D4 rinv = recip(Ud[0]);
+    const D4 uu = Ud[1] * rinv, vv = Ud[2] * rinv;
+    const D4 pr = (1.0 / inv_gm1) * (Ud[3] - 0.5 * (Ud[0] * (uu * uu + vv * vv)));
+    const D4 speed = dsqrt(uu * uu + vv * vv) + 3.0 * dsqrt(pr * rinv);
+    const D4 inv_speed = recip(speed);
+    const double dmin = g.dmin[p];
+    double a[4];
+    ld4(Uacc, p, a);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] += tb * cfl * dmin * inv_speed.d[k];
+    st4(Uacc, p, a);
+    // dmin = |P_i - P_0| of the nearest neighbour
+    const double db = tb * cfl * inv_speed.v;
+    const double2 P0 = g.xy[p];
+    int best = -1;
+    double d2best = 0.0;
+    for (int e = g.off[p]; e < g.off[p + 1]; ++e) {
+        const double2 Pi = g.xy[g.idx[e]];
+        const double dx = Pi.x - P0.x, dy = Pi.y - P0.y;
+        const double d2 = dx * dx + dy * dy;
+        if (best < 0 || d2 < d2best) {
+            best = e;
+            d2best = d2;
+        }
+    }
+    if (best >= 0 && dmin > 0.0) {
+        const double2 Pi = g.xy[g.idx[best]];
+        double2 d = dbar[best];
+        d.x += db * (Pi.x - P0.x) / dmin;
+        d.y += db * (Pi.y - P0.y) / dmin;
+        dbar[best] = d;
+    }
+}
+
+// forces: Cp_w = (p_w - p_inf)/q_inf, (fx, fy) = -sum Cp n ds, Cl = fy cos a - fx sin a,
+// Cd = fx cos a + fy sin a. Per wall entry: U cotangent at the wall point and
+// the cotangent of its arc-length weight ds_w
+__global__ void __launch_bounds__(256) k_forces_adj(int64_t nwall, double gamma, double qinf,
+                                                    const int32_t *__restrict__ wall,
+                                                    const double *__restrict__ ds,
+                                                    const double2 *__restrict__ nrm,
+                                                    const double *__restrict__ U, double fxb, double fyb,
+                                                    double *__restrict__ Uacc, double *__restrict__ dsbar)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwall) return;
+    const int p = wall[w];
+    double u[4];
+    ld4(U, p, u);
+    const double rho = u[0], a = u[1] / rho, b = u[2] / rho;
+    const double pr = (gamma - 1.0) * (u[3] - 0.5 * rho * (a * a + b * b));
+    const double c = (pr - 1.0 / gamma) / qinf;
+    const double2 n = nrm[p];
+    const double fn = fxb * n.x + fyb * n.y;
+    const double cb = -fn * ds[w];
+    dsbar[w] = -c * fn;
+    const double pb = cb / qinf, gm1 = gamma - 1.0;
+    double ub[4];
+    ld4(Uacc, p, ub);
+    ub[0] += pb * gm1 * 0.5 * (a * a + b * b);
+    ub[1] += -pb * gm1 * a;
+    ub[2] += -pb * gm1 * b;
+    ub[3] += pb * gm1;
+    st4(Uacc, p, ub);
+}
+
+// ds_w = (|P_{w+1} - P_w| + |P_w - P_{w-1}|)/2 on the closed contour: point
+// cotangents of the wall coordinates (added into pxy, internal order)
+__global__ void __launch_bounds__(256) k_forces_xy_adj(int64_t nwall, const int32_t *__restrict__ wall,
+                                                       const double2 *__restrict__ xy,
+                                                       const double *__restrict__ dsbar,
+                                                       double2 *__restrict__ pxy)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwall) return;
+    const int64_t wp = (w + nwall - 1) % nwall, wn = (w + 1) % nwall;
+    const double2 P = xy[wall[w]], Pp = xy[wall[wp]], Pn = xy[wall[wn]];
+    const double lp = sqrt((P.x - Pp.x) * (P.x - Pp.x) + (P.y - Pp.y) * (P.y - Pp.y));
+    const double ln = sqrt((Pn.x - P.x) * (Pn.x - P.x) + (Pn.y - P.y) * (Pn.y - P.y));
+    // segment (w-1, w) feeds ds_{w-1} and ds_w; segment (w, w+1) feeds ds_w and ds_{w+1}
+    const double gp = 0.5 * (dsbar[wp] + dsbar[w]) / lp, gn = 0.5 * (dsbar[w] + dsbar[wn]) / ln;
+    double2 o = pxy[wall[w]];
+    o.x += gp * (P.x - Pp.x) - gn * (Pn.x - P.x);
+    o.y += gp * (P.y - Pp.y) - gn * (Pn.y - P.y);
+    pxy[wall[w]] = o;
+}
+
+cudaError_t launch_stage_fwd(const StageParams &S, const double *Un, const double *R, double c, double *Uout,
+                             cudaStream_t s)
+{
+    k_stage_fwd<<<blocks(S.n, 256), 256, 0, s>>>(S, Un, R, c, Uout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_adj(const StageParams &S, const double *Ub_out, const double *R, double c, bool init,
+                             double *Uacc, double *dtbar, double *Rbar, cudaStream_t s)
+{
+    k_stage_adj<<<blocks(S.n, 256), 256, 0, s>>>(S, Ub_out, R, c, init ? 1 : 0, Uacc, dtbar, Rbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_adj_rk4_final(const StageParams &S, const double *Ub_out, const double *const R[4],
+                                       double *Uacc, double *dtbar, double *const Rb[4], cudaStream_t s)
+{
+    k_stage_adj_rk4_final<<<blocks(S.n, 256), 256, 0, s>>>(S, Ub_out, R[0], R[1], R[2], R[3], Uacc, dtbar, Rb[0],
+                                                          Rb[1], Rb[2], Rb[3]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt_adj(const StageParams &S, const DevGeom &g, double cfl, double inv_gm1, const double *U,
+                          const double *dtbar, double *Uacc, double2 *dbar, cudaStream_t s)
+{
+    k_dt_adj<<<blocks(S.n, 256), 256, 0, s>>>(S, g, cfl, inv_gm1, U, dtbar, Uacc, dbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces_adj(int64_t nwall, double gamma, double qinf, const int32_t *wall, const double *ds,
+                              const double2 *nrm, const double2 *xy, const double *U, double fxb, double fyb,
+                              double *Uacc, double *dsbar, double2 *pxy, cudaStream_t s)
+{
+    if (nwall <= 0) return cudaSuccess;
+    k_forces_adj<<<blocks(nwall, 256), 256, 0, s>>>(nwall, gamma, qinf, wall, ds, nrm, U, fxb, fyb, Uacc, dsbar);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    k_forces_xy_adj<<<blocks(nwall, 256), 256, 0, s>>>(nwall, wall, xy, dsbar, pxy);
     return cudaGetLastError();
 }
 

@@ -29,15 +29,46 @@ struct AdjParams {
 
 cudaError_t build_transpose_csr(int64_t n, int64_t nnz, const int32_t *off, const int32_t *idx, int32_t *toff,
                                 int32_t *tedge, int32_t *tsrc, cudaStream_t s);
-// flux adjoint: owner pass, then the neighbour-side gather (initialises qbar, gbar, ebar, wbar, dbar)
+// flux adjoint: owner pass, then the neighbour-side gather (initialises qbar, gbar, ebar, wbar; adds into
+// dbar, which the caller zeroes once per product)
 cudaError_t launch_adj_flux(const AdjParams &P, cudaStream_t s);
 // one E15 pass in reverse: gbar_in is the cotangent of this pass's output,
 // gbar_out receives that of its input iterate gprev (nullptr for the first-order pass)
 cudaError_t launch_adj_grad(const AdjParams &P, const double *gprev, const double *gbar_in, double *gbar_out,
                             cudaStream_t s);
-// weights to offsets to points; x_bar, y_bar in input order (either may be nullptr)
-cudaError_t launch_adj_geometry(const AdjParams &P, double *x_bar, double *y_bar, cudaStream_t s);
-// U_bar ([4][n], input order) from qbar at the internal state U ([n][4])
-cudaError_t launch_adj_state(const AdjParams &P, const double *U, double *U_bar, cudaStream_t s);
+// least-squares weight cotangents (abar, wbar) into the offset cotangents dbar
+cudaError_t launch_adj_weights(const AdjParams &P, cudaStream_t s);
+// offsets (dbar) plus per-point cotangents pxy (internal, or nullptr) to x_bar, y_bar in input
+// order (either may be nullptr), written or added
+cudaError_t launch_adj_points(const AdjParams &P, const double2 *pxy, double *x_bar, double *y_bar, bool accumulate,
+                              cudaStream_t s);
+// Ub_acc ([n][4], internal order) += (dq/dU)^T qbar at the internal state U
+cudaError_t launch_adj_state(const AdjParams &P, const double *U, double *Ub_acc, cudaStream_t s);
+
+// pseudo-time update: boundary treatment and time step of the points
+struct StageParams {
+    int64_t n;
+    const uint8_t *flag;
+    const double2 *nrm;
+    const double *dt;
+    const uint16_t *pcase;    // batch: case of each point, or nullptr
+    const double *case_uinf;  // batch: free stream of each case, or nullptr
+    double Uinf[4];
+};
+// U' = P(U^n - c dt R)
+cudaError_t launch_stage_fwd(const StageParams &S, const double *Un, const double *R, double c, double *Uout,
+                             cudaStream_t s);
+// reverse of one stage (see lskum_adjoint.cu)
+cudaError_t launch_stage_adj(const StageParams &S, const double *Ub_out, const double *R, double c, bool init,
+                             double *Uacc, double *dtbar, double *Rbar, cudaStream_t s);
+cudaError_t launch_stage_adj_rk4_final(const StageParams &S, const double *Ub_out, const double *const R[4],
+                                       double *Uacc, double *dtbar, double *const Rb[4], cudaStream_t s);
+// reverse of the local time step: Uacc += (ddt/dU)^T dtbar, dbar of the nearest-neighbour edge
+cudaError_t launch_dt_adj(const StageParams &S, const DevGeom &g, double cfl, double inv_gm1, const double *U,
+                          const double *dtbar, double *Uacc, double2 *dbar, cudaStream_t s);
+// reverse of the force integrals of one wall contour for the force cotangent (fxb, fyb)
+cudaError_t launch_forces_adj(int64_t nwall, double gamma, double qinf, const int32_t *wall, const double *ds,
+                              const double2 *nrm, const double2 *xy, const double *U, double fxb, double fyb,
+                              double *Uacc, double *dsbar, double2 *pxy, cudaStream_t s);
 
 }  // namespace lskum

@@ -51,6 +51,8 @@ struct lskum_ctx {
     double2 *s_fxw64 = nullptr;
     double *dt = nullptr, *Rt = nullptr, *Ut = nullptr, *Ucm = nullptr;
     double *norm_part = nullptr;   // residue_parts(n) values: a pair of sums per warp
+    double *norm_chunk = nullptr;  // ncases * maxchunks chunk sums of the residue reduction
+    int maxchunks = 1;
     double *res_dev = nullptr;     // residue history, [iteration][case]
     int res_cap = 0;               // iterations res_dev holds
     int *res_counter = nullptr;  // next entry of res_dev the residue kernel writes
@@ -92,6 +94,13 @@ struct lskum_ctx {
     double *vebar = nullptr;
     double2 *vwbar = nullptr, *vabar = nullptr, *vdbar = nullptr;
     int32_t *toff = nullptr, *tedge = nullptr, *tsrc = nullptr;
+    double *vUacc = nullptr;      // [n][4] U cotangent being accumulated (internal order)
+    double2 *vpxy = nullptr;      // [n] point cotangents of x, y gathered directly (forces)
+    // update-step VJP (allocated on the first lskum_step_vjp): stage states,
+    // stage residuals, their cotangents, dt and its cotangent
+    bool svjp_ready = false;
+    double *sR[4] = {}, *sU[3] = {}, *sRb[4] = {}, *sUb = nullptr, *sUin = nullptr, *sdt = nullptr, *sdtb = nullptr;
+    double *fdsb = nullptr;       // forces VJP: cotangents of the arc-length weights
     double *fbuf = nullptr;
 
     // kernel timing (lskum_profile): event pairs per kernel class, reused
@@ -488,6 +497,9 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     CK(c, dalloc(c, &c->Ut, 4 * n));
     CK(c, dalloc(c, &c->Ucm, 4 * n));
     CK(c, dalloc(c, &c->norm_part, residue_parts(n)));
+    for (int k = 0; k < c->ncases; ++k)
+        c->maxchunks = std::max(c->maxchunks, residue_chunks(c->case_start_h[k + 1] - c->case_start_h[k]));
+    CK(c, dalloc(c, &c->norm_chunk, (int64_t)c->ncases * c->maxchunks));
     CK(c, dalloc(c, &c->status, 2));
     c->res_cap = 1024;
     CK(c, dalloc(c, &c->res_dev, (int64_t)c->res_cap * c->ncases));
@@ -784,9 +796,10 @@ static lskum_status iteration(lskum_ctx *c)
         st = flux(c, c->q_cur, qg, (rk4 && k < 3) ? c->Us : c->U, c->q_nxt, rk4 ? 2 : 1, k, nullptr);
         if (st != LSKUM_OK) return st;
         std::swap(c->q_cur, c->q_nxt);
+        if (k == 0) c->launches++;  // the residue reduction is two kernels
         if (k == 0)
-            LAUNCH(c, launch_residue_finish(c->norm_part, c->case_start, c->ncases, c->res_dev, c->res_counter,
-                                            c->res_cap, c->stream));
+            LAUNCH(c, launch_residue_finish(c->norm_part, c->case_start, c->ncases, c->maxchunks, c->norm_chunk,
+                                            c->res_dev, c->res_counter, c->res_cap, c->stream));
     }
     return LSKUM_OK;
 }
@@ -970,46 +983,23 @@ static lskum_status vjp_workspace(lskum_ctx *c)
     CK(c, dalloc(c, &c->toff, n + 1));
     CK(c, dalloc(c, &c->tedge, m));
     CK(c, dalloc(c, &c->tsrc, m));
+    CK(c, dalloc(c, &c->vUacc, 4 * n));
+    CK(c, dalloc(c, &c->vpxy, n));
+    CK(c, dalloc(c, &c->fdsb, std::max<int64_t>(c->n_wall, 1)));
     c->launches += 4;
     LAUNCH(c, build_transpose_csr(n, c->nnz, c->off, c->idx, c->toff, c->tedge, c->tsrc, c->stream));
     c->vjp_ready = true;
     return LSKUM_OK;
 }
 
-extern "C" lskum_status lskum_residual_vjp(lskum_ctx *c, const double *U, const double *R_bar, double *U_bar,
-                                           double *x_bar, double *y_bar)
+static AdjParams adj_params(lskum_ctx *c)
 {
-    if (!c) return LSKUM_ERR_ARG;
-    c->err.clear();
-    if (!R_bar) return fail(c, LSKUM_ERR_ARG, "R_bar is NULL");
-    if (c->cfg.order == 2 && c->cfg.limiter_K != 0.0)
-        return fail(c, LSKUM_ERR_ARG, "the residual VJP needs limiter_K = 0 (the limiter is not differentiated)");
-    if (!U_bar && !x_bar && !y_bar) return LSKUM_OK;
-    lskum_status st = vjp_workspace(c);
-    if (st != LSKUM_OK) return st;
-    if ((st = reset_status(c)) != LSKUM_OK) return st;
     const int64_t n = c->n;
-    const bool second = c->cfg.order == 2;
-    const int K = second ? c->cfg.inner_iters : 0;
-    const DevGeom g = c->geom();
-    // forward recomputation in FP64: q, and every q-derivative iterate
-    const double *Ui = c->U;
-    if (U) {
-        LAUNCH(c, launch_state_in(n, c->perm, U, c->Ut, c->stream));
-        Ui = c->Ut;
-    }
-    LAUNCH(c, launch_q_from_U(n, c->gas, Ui, c->vq, c->status, c->stream));
-    if (second) {
-        LAUNCH(c, launch_qgrad(g, c->vq, nullptr, c->vG, 0.0, c->stream));
-        for (int k = 1; k <= K; ++k)
-            LAUNCH(c, launch_qgrad(g, c->vq, c->vG + (int64_t)(k - 1) * 8 * n, c->vG + (int64_t)k * 8 * n, 0.0,
-                                   c->stream));
-    }
-    LAUNCH(c, launch_state_in(n, c->perm, R_bar, c->vRb, c->stream));
+    const int K = c->cfg.order == 2 ? c->cfg.inner_iters : 0;
     AdjParams P{};
-    P.g = g;
+    P.g = c->geom();
     P.q = c->vq;
-    P.qg = second ? c->vG + (int64_t)K * 8 * n : nullptr;
+    P.qg = c->cfg.order == 2 ? c->vG + (int64_t)K * 8 * n : nullptr;
     P.Rbar = c->vRb;
     P.qbar = c->vqb;
     P.gbar = c->vgb;
@@ -1023,6 +1013,55 @@ extern "C" lskum_status lskum_residual_vjp(lskum_ctx *c, const double *U, const 
     P.perm = c->perm;
     P.inv_gm1 = c->gas.inv_gm1;
     P.order = c->cfg.order;
+    return P;
+}
+
+// FP64 q and q-derivative iterates of an internal state (vq, vG)
+static lskum_status vjp_forward(lskum_ctx *c, const double *Ui)
+{
+    const int64_t n = c->n;
+    const DevGeom g = c->geom();
+    LAUNCH(c, launch_q_from_U(n, c->gas, Ui, c->vq, c->status, c->stream));
+    if (c->cfg.order == 2) {
+        LAUNCH(c, launch_qgrad(g, c->vq, nullptr, c->vG, 0.0, c->stream));
+        for (int k = 1; k <= c->cfg.inner_iters; ++k)
+            LAUNCH(c, launch_qgrad(g, c->vq, c->vG + (int64_t)(k - 1) * 8 * n, c->vG + (int64_t)k * 8 * n, 0.0,
+                                   c->stream));
+    }
+    return LSKUM_OK;
+}
+
+// FP64 residual of an internal state (Rout internal [n][4]); leaves vq, vG at that state
+static lskum_status residual_fp64(lskum_ctx *c, const double *Ui, double *Rout)
+{
+    lskum_status st = vjp_forward(c, Ui);
+    if (st != LSKUM_OK) return st;
+    FluxLaunch L{};
+    L.q = c->vq;
+    L.qg = c->cfg.order == 2 ? c->vG + (int64_t)c->cfg.inner_iters * 8 * c->n : nullptr;
+    L.R = Rout;
+    L.norm_part = c->norm_part;
+    L.status = c->status;
+    L.pcase = c->pcase;
+    L.case_uinf = c->case_uinf;
+    L.cfl = c->cfg.cfl;
+    L.order = c->cfg.order;
+    L.mode = 0;
+    LAUNCH(c, launch_flux(c->geom(), c->gas, L, c->stream));
+    return LSKUM_OK;
+}
+
+// one residual VJP at the internal state Ui for the internal cotangent vRb:
+// Ub_acc ([n][4], internal) += (dR/dU)^T R_bar; vdbar += the offset
+// cotangents (the caller zeroes vdbar once per product)
+static lskum_status vjp_residual(lskum_ctx *c, const double *Ui, double *Ub_acc, bool geom, bool fwd_done)
+{
+    const int64_t n = c->n;
+    const bool second = c->cfg.order == 2;
+    const int K = second ? c->cfg.inner_iters : 0;
+    lskum_status st;
+    if (!fwd_done && (st = vjp_forward(c, Ui)) != LSKUM_OK) return st;
+    const AdjParams P = adj_params(c);
     c->launches++;
     LAUNCH(c, launch_adj_flux(P, c->stream));
     if (second) {
@@ -1034,12 +1073,154 @@ extern "C" lskum_status lskum_residual_vjp(lskum_ctx *c, const double *U, const 
         }
         LAUNCH(c, launch_adj_grad(P, nullptr, gin, nullptr, c->stream));
     }
-    if (x_bar || y_bar) {
-        c->launches++;
-        LAUNCH(c, launch_adj_geometry(P, x_bar, y_bar, c->stream));
-    }
-    if (U_bar) LAUNCH(c, launch_adj_state(P, Ui, U_bar, c->stream));
+    if (geom) LAUNCH(c, launch_adj_weights(P, c->stream));
+    LAUNCH(c, launch_adj_state(P, Ui, Ub_acc, c->stream));
+    return LSKUM_OK;
+}
+
+static lskum_status vjp_begin(lskum_ctx *c)
+{
+    if (c->cfg.order == 2 && c->cfg.limiter_K != 0.0)
+        return fail(c, LSKUM_ERR_ARG, "derivatives need limiter_K = 0 (the limiter is not differentiated)");
+    lskum_status st = vjp_workspace(c);
+    if (st != LSKUM_OK) return st;
+    if ((st = reset_status(c)) != LSKUM_OK) return st;
+    CK(c, cudaMemsetAsync(c->vdbar, 0, std::max<int64_t>(c->nnz, 1) * sizeof(double2), c->stream));
+    CK(c, cudaMemsetAsync(c->vpxy, 0, c->n * sizeof(double2), c->stream));
+    CK(c, cudaMemsetAsync(c->vUacc, 0, 4 * c->n * sizeof(double), c->stream));
+    return LSKUM_OK;
+}
+
+// outputs of a product: U_bar from vUacc, x_bar / y_bar from vdbar and vpxy (input order)
+static lskum_status vjp_end(lskum_ctx *c, double *U_bar, double *x_bar, double *y_bar, int flags)
+{
+    if (flags & ~LSKUM_VJP_ACCUMULATE_XY) return fail(c, LSKUM_ERR_ARG, "unknown flags 0x%x", flags);
+    if (x_bar || y_bar)
+        LAUNCH(c, launch_adj_points(adj_params(c), c->vpxy, x_bar, y_bar, (flags & LSKUM_VJP_ACCUMULATE_XY) != 0,
+                                    c->stream));
+    if (U_bar) LAUNCH(c, launch_state_out(c->n, c->perm, c->vUacc, U_bar, c->stream));
     return check_nonphysical(c);
+}
+
+extern "C" lskum_status lskum_residual_vjp(lskum_ctx *c, const double *U, const double *R_bar, double *U_bar,
+                                           double *x_bar, double *y_bar, int flags)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!R_bar) return fail(c, LSKUM_ERR_ARG, "R_bar is NULL");
+    if (!U_bar && !x_bar && !y_bar) return LSKUM_OK;
+    lskum_status st = vjp_begin(c);
+    if (st != LSKUM_OK) return st;
+    const double *Ui = c->U;
+    if (U) {
+        LAUNCH(c, launch_state_in(c->n, c->perm, U, c->Ut, c->stream));
+        Ui = c->Ut;
+    }
+    LAUNCH(c, launch_state_in(c->n, c->perm, R_bar, c->vRb, c->stream));
+    if ((st = vjp_residual(c, Ui, c->vUacc, x_bar || y_bar, false)) != LSKUM_OK) return st;
+    return vjp_end(c, U_bar, x_bar, y_bar, flags);
+}
+
+static lskum_status step_vjp_workspace(lskum_ctx *c)
+{
+    if (c->svjp_ready) return LSKUM_OK;
+    const int64_t n = c->n;
+    for (auto &b : c->sR) CK(c, dalloc(c, &b, 4 * n));
+    for (auto &b : c->sRb) CK(c, dalloc(c, &b, 4 * n));
+    for (auto &b : c->sU) CK(c, dalloc(c, &b, 4 * n));
+    CK(c, dalloc(c, &c->sUb, 4 * n));
+    CK(c, dalloc(c, &c->sUin, 4 * n));
+    CK(c, dalloc(c, &c->sdt, n));
+    CK(c, dalloc(c, &c->sdtb, n));
+    c->svjp_ready = true;
+    return LSKUM_OK;
+}
+
+extern "C" lskum_status lskum_step_vjp(lskum_ctx *c, const double *U, const double *U_bar_next, double *U_bar,
+                                       double *x_bar, double *y_bar, int flags)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (!U_bar_next) return fail(c, LSKUM_ERR_ARG, "U_bar_next is NULL");
+    if (!U_bar && !x_bar && !y_bar) return LSKUM_OK;
+    lskum_status st = vjp_begin(c);
+    if (st != LSKUM_OK) return st;
+    if ((st = step_vjp_workspace(c)) != LSKUM_OK) return st;
+    const int64_t n = c->n;
+    const bool geom = x_bar || y_bar;
+    const double *Un = c->U;
+    if (U) {
+        LAUNCH(c, launch_state_in(n, c->perm, U, c->sUin, c->stream));
+        Un = c->sUin;
+    }
+    LAUNCH(c, launch_state_in(n, c->perm, U_bar_next, c->sUb, c->stream));
+    StageParams S{};
+    S.n = n;
+    S.flag = c->flag;
+    S.nrm = c->nrm;
+    S.dt = c->sdt;
+    S.pcase = c->pcase;
+    S.case_uinf = c->case_uinf;
+    for (int k = 0; k < 4; ++k) S.Uinf[k] = c->gas.Uinf[k];
+    // forward: dt frozen at U^n, the stage states and residuals (FP64)
+    LAUNCH(c, launch_timestep(n, c->gas, c->cfg.cfl, c->dmin, Un, c->sdt, c->stream));
+    if ((st = residual_fp64(c, Un, c->sR[0])) != LSKUM_OK) return st;
+    if (c->cfg.time_scheme == 0) {
+        // U^{n+1} = P(U^n - dt R(U^n))
+        LAUNCH(c, launch_stage_adj(S, c->sUb, c->sR[0], 1.0, true, c->vUacc, c->sdtb, c->vRb, c->stream));
+        if ((st = vjp_residual(c, Un, c->vUacc, geom, true)) != LSKUM_OK) return st;
+    } else {
+        const double cst[3] = {0.5, 0.5, 1.0};
+        const double *Us = Un;
+        for (int k = 0; k < 3; ++k) {
+            LAUNCH(c, launch_stage_fwd(S, Un, c->sR[k], cst[k], c->sU[k], c->stream));
+            if ((st = residual_fp64(c, c->sU[k], c->sR[k + 1])) != LSKUM_OK) return st;
+            Us = c->sU[k];
+        }
+        (void)Us;
+        // reverse: the last stage, then stages 2, 1, 0 (their residuals R3, R2, R1, R0)
+        const double *Rs[4] = {c->sR[0], c->sR[1], c->sR[2], c->sR[3]};
+        LAUNCH(c, launch_stage_adj_rk4_final(S, c->sUb, Rs, c->vUacc, c->sdtb, c->sRb, c->stream));
+        for (int k = 3; k >= 1; --k) {
+            // the cotangent of the stage state U_k from R_k = R(U_k)
+            CK(c, cudaMemsetAsync(c->sUb, 0, 4 * n * sizeof(double), c->stream));
+            CK(c, cudaMemcpyAsync(c->vRb, c->sRb[k], 4 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+            if ((st = vjp_residual(c, c->sU[k - 1], c->sUb, geom, false)) != LSKUM_OK) return st;
+            // U_k = P(U^n - c_k dt R_{k-1})
+            LAUNCH(c, launch_stage_adj(S, c->sUb, c->sR[k - 1], cst[k - 1], false, c->vUacc, c->sdtb,
+                                       c->sRb[k - 1], c->stream));
+        }
+        CK(c, cudaMemcpyAsync(c->vRb, c->sRb[0], 4 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        if ((st = vjp_residual(c, Un, c->vUacc, geom, false)) != LSKUM_OK) return st;
+    }
+    LAUNCH(c, launch_dt_adj(S, c->geom(), c->cfg.cfl, c->gas.inv_gm1, Un, c->sdtb, c->vUacc, c->vdbar, c->stream));
+    return vjp_end(c, U_bar, x_bar, y_bar, flags);
+}
+
+extern "C" lskum_status lskum_forces_vjp(lskum_ctx *c, int k, double cl_bar, double cd_bar, double *U_bar,
+                                         double *x_bar, double *y_bar, int flags)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    c->err.clear();
+    if (k < 0 || k >= c->ncases) return fail(c, LSKUM_ERR_ARG, "case %d out of range", k);
+    const int64_t w0 = c->case_wall_h[k], nw = c->case_wall_h[k + 1] - w0;
+    if (nw == 0) return fail(c, LSKUM_ERR_ARG, "no wall contour was given at create for case %d", k);
+    const double qinf = 0.5 * c->case_mach[k] * c->case_mach[k];
+    if (!(qinf > 0.0)) return fail(c, LSKUM_ERR_ARG, "forces need mach > 0");
+    if (!U_bar && !x_bar && !y_bar) return LSKUM_OK;
+    lskum_status st = vjp_workspace(c);
+    if (st != LSKUM_OK) return st;
+    if ((st = reset_status(c)) != LSKUM_OK) return st;
+    CK(c, cudaMemsetAsync(c->vdbar, 0, std::max<int64_t>(c->nnz, 1) * sizeof(double2), c->stream));
+    CK(c, cudaMemsetAsync(c->vpxy, 0, c->n * sizeof(double2), c->stream));
+    CK(c, cudaMemsetAsync(c->vUacc, 0, 4 * c->n * sizeof(double), c->stream));
+    const double a = c->case_aoa[k] * 3.14159265358979323846 / 180.0;
+    // Cl = fy cos a - fx sin a, Cd = fx cos a + fy sin a
+    const double fxb = -cl_bar * sin(a) + cd_bar * cos(a), fyb = cl_bar * cos(a) + cd_bar * sin(a);
+    c->launches++;
+    LAUNCH(c, launch_forces_adj(nw, c->gas.gamma, qinf, c->wall + w0, c->wall_ds + w0, c->nrm, c->xy, c->U, fxb,
+                                fyb, c->vUacc, c->fdsb + w0, c->vpxy, c->stream));
+    return vjp_end(c, U_bar, x_bar, y_bar, flags);
 }
 
 extern "C" lskum_status lskum_q_derivatives(lskum_ctx *c, const double *U, double *qx, double *qy)

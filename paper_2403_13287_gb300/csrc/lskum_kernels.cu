@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
     double Rg[4] = {0.0, 0.0, 0.0, 0.0};
     const bool live = p < g.n;
     uint8_t flag = FLAG_FARFIELD;
-    if (live) flag = g.flag[p];
+    if (live) flag = g.flag[p] & 3;  // bit 7 marks FP64 closures in mixed contexts
     if (live && flag != FLAG_FARFIELD) {
         const double2 xy0 = g.xy[p];
         const double2 n0 = g.nrm[p];
@@ -272,22 +272,47 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
 }
 
 // residue() of every case = sqrt(sum R_rho^2)/n_case from the per-warp
-// pairs, in a fixed order: case c owns points [start[c], start[c+1]); a warp
+// pairs, in a fixed order. Case c owns points [start[c], start[c+1]); a warp
 // whose first point lies in c contributes its first sum, a warp that starts
-// in the case before contributes its second. Written to
-// out[(*counter) * ncases + c]; the counter then advances (so one captured
-// iteration can be replayed), bounded by cap iterations.
-__global__ void __launch_bounds__(256) k_residue_finish(const double *__restrict__ part,
-                                                        const int64_t *__restrict__ start, int ncases,
+// in the case before contributes its second. Stage 1: block (j, c) sums
+// chunk j (kResidueChunk warps) of case c; stage 2: one block sums each
+// case's chunks and writes out[(*counter) * ncases + c], then advances the
+// counter (so one captured iteration can be replayed), bounded by cap.
+static constexpr int kResidueChunk = 2048;
+
+__global__ void __launch_bounds__(256) k_residue_chunks(const double *__restrict__ part,
+                                                        const int64_t *__restrict__ start, int maxchunks,
+                                                        double *__restrict__ chunk)
+{
+    const int c = blockIdx.y, j = blockIdx.x;
+    const int64_t p0 = start[c], p1 = start[c + 1];
+    const int64_t w0 = p0 >> 5, w1 = (p1 - 1) >> 5;
+    const int64_t a = w0 + (int64_t)j * kResidueChunk;
+    const int64_t b = min(w1 + 1, a + kResidueChunk);
+    double s = 0.0;
+    for (int64_t w = a + threadIdx.x; w < b; w += blockDim.x) s += part[2 * w + ((w << 5) >= p0 ? 0 : 1)];
+    __shared__ double sm[256];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) chunk[(int64_t)c * maxchunks + j] = sm[0];
+}
+
+__global__ void __launch_bounds__(256) k_residue_finish(const double *__restrict__ chunk,
+                                                        const int64_t *__restrict__ start, int ncases, int maxchunks,
                                                         double *__restrict__ out_base, int *counter, int cap)
 {
     __shared__ double sm[256];
     const int it = *counter;
     for (int c = 0; c < ncases; ++c) {
         const int64_t p0 = start[c], p1 = start[c + 1];
-        const int64_t w0 = p0 >> 5, w1 = (p1 - 1) >> 5;
+        const int64_t nw = ((p1 - 1) >> 5) - (p0 >> 5) + 1;
+        const int nch = (int)((nw + kResidueChunk - 1) / kResidueChunk);
         double s = 0.0;
-        for (int64_t w = w0 + threadIdx.x; w <= w1; w += blockDim.x) s += part[2 * w + ((w << 5) >= p0 ? 0 : 1)];
+        for (int j = threadIdx.x; j < nch; j += blockDim.x) s += chunk[(int64_t)c * maxchunks + j];
         sm[threadIdx.x] = s;
         __syncthreads();
         for (int h = 128; h > 0; h >>= 1) {
@@ -299,6 +324,8 @@ __global__ void __launch_bounds__(256) k_residue_finish(const double *__restrict
     }
     if (threadIdx.x == 0) *counter = it + 1;
 }
+
+int residue_chunks(int64_t case_points) { return (int)((((case_points + 31) >> 5) + 1 + kResidueChunk - 1) / kResidueChunk); }
 
 // q-variables of every point from U (used when a state is loaded)
 __global__ void __launch_bounds__(256) k_q_from_U(int64_t n, Gas gas, const double *__restrict__ U,
@@ -392,10 +419,13 @@ cudaError_t launch_flux(const DevGeom &g, const Gas &gas, const FluxLaunch &L, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_residue_finish(const double *part, const int64_t *case_start, int ncases, double *out_base,
-                                  int *counter, int cap, cudaStream_t s)
+cudaError_t launch_residue_finish(const double *part, const int64_t *case_start, int ncases, int maxchunks,
+                                  double *chunk, double *out_base, int *counter, int cap, cudaStream_t s)
 {
-    k_residue_finish<<<1, 256, 0, s>>>(part, case_start, ncases, out_base, counter, cap);
+    k_residue_chunks<<<dim3(maxchunks, ncases), 256, 0, s>>>(part, case_start, maxchunks, chunk);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    k_residue_finish<<<1, 256, 0, s>>>(chunk, case_start, ncases, maxchunks, out_base, counter, cap);
     return cudaGetLastError();
 }
 

@@ -31,10 +31,12 @@ cudaError_t launch_qgrad(const DevGeom &g, const double *q, const double *qg_old
                          double limiter_K, cudaStream_t s);
 cudaError_t launch_flux(const DevGeom &g, const Gas &gas, const FluxLaunch &L, cudaStream_t s);
 // residue of every case into out_base[*counter * ncases + c] (when 0 <= *counter < cap), then ++*counter;
-// part holds a pair of sums per warp of 32 points (residue_parts(n) values)
-cudaError_t launch_residue_finish(const double *part, const int64_t *case_start, int ncases, double *out_base,
-                                  int *counter, int cap, cudaStream_t s);
+// part holds a pair of sums per warp of 32 points (residue_parts(n) values); chunk is scratch of
+// ncases * maxchunks values, maxchunks = the largest residue_chunks() of a case
+cudaError_t launch_residue_finish(const double *part, const int64_t *case_start, int ncases, int maxchunks,
+                                  double *chunk, double *out_base, int *counter, int cap, cudaStream_t s);
 int64_t residue_parts(int64_t n);
+int residue_chunks(int64_t case_points);
 cudaError_t launch_q_from_U(int64_t n, const Gas &gas, const double *U, double *q, int *status,
                             cudaStream_t s);
 cudaError_t launch_timestep(int64_t n, const Gas &gas, double cfl, const double *dmin, const double *U,

@@ -98,7 +98,9 @@ def load(build_if_missing: bool = True):
     L.lskum_case_forces.argtypes = [_p, _int, _p, _p, _p]
     L.lskum_autotune.argtypes = [_p, _int, ctypes.POINTER(lskum_tuning)]
     L.lskum_set_tuning.argtypes = [_p, _int, _int]
-    L.lskum_residual_vjp.argtypes = [_p, _p, _p, _p, _p, _p]
+    L.lskum_residual_vjp.argtypes = [_p, _p, _p, _p, _p, _p, _int]
+    L.lskum_step_vjp.argtypes = [_p, _p, _p, _p, _p, _p, _int]
+    L.lskum_forces_vjp.argtypes = [_p, _int, ctypes.c_double, ctypes.c_double, _p, _p, _p, _int]
     L.lskum_q_derivatives.argtypes = [_p, _p, _p, _p]
     L.lskum_timestep.argtypes = [_p, _p, _p]
     L.lskum_forces.argtypes = [_p, _p, _p, _p]
@@ -110,7 +112,8 @@ def load(build_if_missing: bool = True):
     L.lskum_launch_count.restype = _i64
     L.lskum_profile.argtypes = [_p, _int]
     L.lskum_kernel_time.argtypes = [_p, _int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]
-    for name in ("lskum_case_range", "lskum_case_forces", "lskum_autotune", "lskum_set_tuning"):
+    for name in ("lskum_case_range", "lskum_case_forces", "lskum_autotune", "lskum_set_tuning",
+                 "lskum_step_vjp", "lskum_forces_vjp"):
         getattr(L, name).restype = _int
     for name in ("lskum_step", "lskum_residual", "lskum_residual_vjp", "lskum_q_derivatives", "lskum_timestep",
                  "lskum_forces", "lskum_get_state", "lskum_set_state", "lskum_get_stencil_masks",
@@ -275,8 +278,39 @@ class Solver:
         xb = torch.empty(self.n, dtype=torch.float64, device="cuda") if want_xy else None
         yb = torch.empty_like(xb) if want_xy else None
         self._check(self._L.lskum_residual_vjp(self._ctx, _dev_ptr(U), _dev_ptr(R_bar), _dev_ptr(Ub),
-                                               _dev_ptr(xb), _dev_ptr(yb)))
+                                               _dev_ptr(xb), _dev_ptr(yb), 0))
         return Ub, xb, yb
+
+    def step_vjp(self, U_bar_next, U=None, want_U=True, want_xy=True, U_bar=None, xy_bar=None):
+        """(U_bar, x_bar, y_bar): one iteration U^n -> U^{n+1} differentiated
+        in reverse at U^n = U (the context's state if None). Pass xy_bar
+        (x_bar, y_bar tensors) to add the coordinate cotangents into them."""
+        import torch
+        Ub = U_bar if U_bar is not None else (
+            torch.empty((4, self.n), dtype=torch.float64, device="cuda") if want_U else None)
+        xb, yb, flags = self._xy_out(want_xy, xy_bar)
+        self._check(self._L.lskum_step_vjp(self._ctx, _dev_ptr(U), _dev_ptr(U_bar_next), _dev_ptr(Ub),
+                                           _dev_ptr(xb), _dev_ptr(yb), flags))
+        return Ub, xb, yb
+
+    def forces_vjp(self, cl_bar=1.0, cd_bar=0.0, case=0, want_U=True, want_xy=True, xy_bar=None):
+        """(U_bar, x_bar, y_bar) of cl_bar Cl + cd_bar Cd at the context's state
+        (coordinate cotangents added into xy_bar if given)."""
+        import torch
+        Ub = torch.empty((4, self.n), dtype=torch.float64, device="cuda") if want_U else None
+        xb, yb, flags = self._xy_out(want_xy, xy_bar)
+        self._check(self._L.lskum_forces_vjp(self._ctx, int(case), float(cl_bar), float(cd_bar), _dev_ptr(Ub),
+                                             _dev_ptr(xb), _dev_ptr(yb), flags))
+        return Ub, xb, yb
+
+    def _xy_out(self, want_xy, xy_bar):
+        import torch
+        if xy_bar is not None:
+            return xy_bar[0], xy_bar[1], LSKUM_VJP_ACCUMULATE_XY
+        if not want_xy:
+            return None, None, 0
+        xb = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        return xb, torch.empty_like(xb), 0
 
     def q_derivatives(self, U=None):
         import torch
@@ -348,6 +382,7 @@ class Solver:
 
 
 LSKUM_NOALLOC_MAX_POINTS = 131072
+LSKUM_VJP_ACCUMULATE_XY = 1
 
 
 def q_derivatives_noalloc(x, y, nbr_offsets, nbr_idx, U, qx, qy, gamma=1.4, inner_iters=3,

@@ -299,8 +299,8 @@ def test_launch_count_is_reported(small):
     before = s.launch_count()
     s.step(2)
     # per RK4 stage: 1 first-order + 3 inner gradient passes + 1 fused flux;
-    # per iteration one residue reduction
-    assert s.launch_count() - before == 2 * (4 * 5 + 1)
+    # per iteration one residue reduction (two kernels)
+    assert s.launch_count() - before == 2 * (4 * 5 + 2)
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -124,3 +124,62 @@ def test_vjp_entries_are_the_transposed_jacobian():
     want = np.array([full[e[1] * n + e[2]] if e[0] == "U" else full[pos[e[0]] + e[1]] for e in ent])
     got = lskum_jvp.vjp_entries(c, mask, U, r, ent)
     assert np.allclose(got, want, rtol=1e-13, atol=1e-13 * np.max(np.abs(full)))
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_iteration_real_part_is_the_c_oracle_step(cloud, scheme):
+    c, mask = cloud
+    U0 = _state(c, amp=0.02)
+    Upy = lskum_jvp.iterate(c, mask, U0, scheme=scheme, mach=0.63, aoa_deg=2.0)
+    Uc, _ = oracle.solve(c, mask, U0.copy(), 1, order=2, inner=3, scheme=scheme, cfl=0.2, mach=0.63,
+                         aoa_deg=2.0)
+    assert np.max(np.abs(Upy - Uc)) <= 1e-13 * np.max(np.abs(Uc))
+
+
+def _symmetric_wall_displacement(c, rng, scale):
+    """Random displacements whose wall part keeps the contour's mirror
+    symmetry: the leading- and trailing-edge points keep their two equally
+    near wall neighbours equally near, so the nearest-neighbour distance of
+    the time step is differentiable along them (a central difference across
+    its kink would average two slopes)."""
+    n, W = c["n"], c["W"]
+    dx = rng.standard_normal(n) * scale
+    dy = rng.standard_normal(n) * scale
+    half = W // 2
+    lower = np.arange(half + 1, W)
+    dx[lower] = dx[W - lower]
+    dy[lower] = -dy[W - lower]
+    dy[0] = dy[half] = 0.0
+    return dx, dy
+
+
+def test_unrolled_force_derivative_matches_central_differences_of_the_c_oracle():
+    """d Cl / d (point displacement) after 3 RK4 iterations: complex step
+    against central differences of orc_solve + orc_forces (an isotropic
+    64 x 35 cloud, on which the unlimited second-order scheme is stable)."""
+    c = naca0012_cloud(64, 35, seed=4)
+    mask = oracle.split_stencils(c)
+    n = c["n"]
+    U0 = _state(c, amp=0.02)
+    rng = np.random.default_rng(23)
+    dx, dy = _symmetric_wall_displacement(c, rng, 0.01)
+    (cl, cd), (dcl, dcd) = lskum_jvp.unrolled_forces(c, mask, U0, 3, dx=dx, dy=dy, scheme=1, mach=0.63,
+                                                     aoa_deg=2.0)
+
+    def forces(eps):
+        cc = dict(c)
+        cc["x"] = c["x"] + eps * dx
+        cc["y"] = c["y"] + eps * dy
+        U, _ = oracle.solve(cc, mask, U0.copy(), 3, order=2, inner=3, scheme=1, cfl=0.2, mach=0.63, aoa_deg=2.0)
+        return oracle.forces(cc, U, 0.63, 2.0)[:2]
+
+    cl_c, cd_c = forces(0.0)
+    assert abs(cl - cl_c) <= 1e-13 * abs(cl_c) and abs(cd - cd_c) <= 1e-13 * abs(cd_c)
+    fp, fm = forces(1e-6), forces(-1e-6)
+    fd = [(a - b) / 2e-6 for a, b in zip(fp, fm)]
+    assert abs(dcl - fd[0]) <= 1e-6 * abs(dcl) + 1e-9
+    assert abs(dcd - fd[1]) <= 1e-6 * abs(dcd) + 1e-9
+    # a rigid translation of every point changes nothing
+    (_, _), (tcl, tcd) = lskum_jvp.unrolled_forces(c, mask, U0, 3, dx=np.ones(n), dy=np.ones(n), scheme=1,
+                                                   mach=0.63, aoa_deg=2.0)
+    assert tcl == 0.0 and tcd == 0.0
