@@ -347,7 +347,7 @@ def measure_e2e(solver, n, steps, dist):
 # DRAM bytes per point of one launch of the mixed kernels on the 2.5M-point
 # workload, from a full-size single-pass ncu capture of the current kernels
 # (profiles/mixed_kernels_naca0012_2p5m.md); None where not captured
-MIXED_TRAFFIC_PER_POINT = {"flux": None, "qgrad": None}
+MIXED_TRAFFIC_PER_POINT = {"flux": 345.0, "qgrad": 181.2}
 
 
 def form_summary(args, r, n, dbar, world, precision, peaks, peak_src):
