@@ -242,6 +242,24 @@ def run_reference(args, rank, world):
     return 0
 
 
+def max_over_ranks(value, dist):
+    """The largest of every rank's value (the slowest replica's time); the
+    value itself without a process group."""
+    if not dist:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(points, steps, ms, world):
+    """Whole-job point-iterations/s of `world` replicas that each advanced
+    `points` points by `steps` iterations, the slowest taking `ms`."""
+    return world * points * steps / (ms / 1e3)
+
+
 def cpu_baseline_sample(cloud, mask, args):
     """The oracle as it stands, on one host core: one residual evaluation of
     the full cloud (about 10-30 s), scaled to an iteration."""
@@ -312,10 +330,7 @@ def measure_form(args, cloud, precision, dist, sampler):
     qg_ms, qg_n = solver.kernel_time(lskum.LSKUM_KERNEL_QGRAD)
     solver.profile(False)
     clocks = sampler.stop() if sampler else None
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     return {"solver": solver, "ms": ms, "launches": launches, "flux_ms": flux_ms, "flux_n": flux_n,
             "qg_ms": qg_ms, "qg_n": qg_n, "clocks": clocks, "tuning": tuning}
 
@@ -337,10 +352,7 @@ def measure_e2e(solver, n, steps, dist):
         solver.get_state(out=Uh)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     return n * steps / e2e_s
 
 
@@ -385,7 +397,7 @@ def form_summary(args, r, n, dbar, world, precision, peaks, peak_src):
         fb = algorithmic_bytes_per_point("flux", dbar, args.order, args.scheme) * n
         gbs = fb / flux_avg_s / 1e9
         roofline = roofline_fp64(flux_avg_s, n, dbar, fb, gbs, peaks, peak_src)
-    return {"value": world * n * args.steps / (r["ms"] / 1e3), "ms_per_step": r["ms"] / args.steps,
+    return {"value": replicas_value(n, args.steps, r["ms"], world), "ms_per_step": r["ms"] / args.steps,
             "dtype": "f32/f64 mixed" if precision == "mixed" else "f64", "roofline": roofline,
             "kernels": {"k_flux_update": {"launches": r["flux_n"], "total_ms": r["flux_ms"]},
                         "k_qgrad": {"launches": r["qg_n"], "total_ms": r["qg_ms"]}},
@@ -440,12 +452,7 @@ def measure_batched(args, dist, sampler):
         fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), dist)
 
     B = lskum.Solver.batch(cases, **kw)
     B.set_state(np.concatenate(U0, axis=1))
@@ -475,8 +482,9 @@ def measure_batched(args, dist, sampler):
     ms_s = timed(lambda: [s.step(args.steps, history=False) for s in singles])
     for s in singles:
         s.close()
-    value_b = npts * args.steps / (ms_b / 1e3)
-    value_s = npts * args.steps / (ms_s / 1e3)
+    world = dist.get_world_size() if dist else 1
+    value_b = replicas_value(npts, args.steps, ms_b, world)
+    value_s = replicas_value(npts, args.steps, ms_s, world)
     sizes = sorted({int(c["n"]) for c, _, _ in cases})
     return {"value": value_b, "unit": UNIT, "ms_per_step": ms_b / args.steps, "dtype": "f32/f64 mixed",
             "cases": len(cases), "points": npts, "cloud_sizes": [sizes[0], sizes[-1]],
