@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single-form", action="store_true", help="time only --precision's form")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solves form")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint form")
     ap.add_argument("--tuning", default="auto",
                     help="mixed launch shapes: 'auto' (autotune on the cloud) or 'F,Q' (flux, q-derivative variant)")
     ap.add_argument("--batch-clouds", type=int, default=16)
@@ -175,11 +176,12 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
     raise ValueError(kernel)
 
 
-# Per-unit figures of the FP64 fused flux kernel, from one ncu capture of the
-# same kernel (profiles/k_flux_update_fp64_naca0012_640k.md): executed FP64
-# flops per stencil edge (2 DFMA + DMUL + DADD) and DRAM bytes per point.
+# Per-unit figures of the FP64 fused flux kernel: executed FP64 flops per
+# stencil edge (2 DFMA + DMUL + DADD; profiles/k_flux_update_fp64_naca0012_640k.md)
+# and DRAM bytes per point of one full-size 2.5M launch (single-pass capture,
+# profiles/launch_list_naca0012_2p5m_fp64.md: 1167.3 MB / 2,498,560 points).
 FP64_FLOPS_PER_EDGE_FLUX = 778.0
-FLUX_DRAM_BYTES_PER_POINT = 456.4
+FLUX_DRAM_BYTES_PER_POINT = 467.2
 # FP64 peak: ncu's DFMA unit count (304 thread-FMA per cycle) x 2 flops x the
 # 2070 MHz maximum SM clock
 FP64_PEAK_GFLOPS = 304 * 2 * 2.070
@@ -496,6 +498,74 @@ def measure_batched(args, dist, sampler):
             "speedup_vs_sequential": value_b / value_s}
 
 
+def measure_adjoint(args, dist, sampler):
+    """The adjoint form on the 640k-point cloud at M 0.63, alpha 2 (second
+    order, RK4, unlimited; FP64): one residual VJP, one iteration VJP and a
+    checkpointed reverse sweep through 16 iterations, each against the
+    forward work it differentiates, with the device memory they add."""
+    import numpy as np
+    import torch
+
+    from paper_2403_13287_gb300 import lskum
+    from paper_2403_13287_gb300.adjoint import unrolled_force_gradient
+    from paper_2403_13287_gb300.cloudgen import CLOUDS, naca0012_cloud, smooth_state
+
+    W, L = CLOUDS["naca0012_640k"]
+    cloud = naca0012_cloud(W, L)
+    n = cloud["n"]
+    mach, aoa = 0.63, 2.0
+    stream = torch.cuda.current_stream()
+    s = lskum.Solver(cloud, order=2, inner_iters=args.inner, time_scheme=1, cfl=args.cfl, mach=mach,
+                     aoa_deg=aoa, reorder=1, limiter_K=0.0, precision=0, stream=stream.cuda_stream)
+    U = torch.from_numpy(smooth_state(cloud, mach, aoa, amp=0.05, seed=9)).cuda()
+    s.set_state(U)
+    Rb = torch.from_numpy(np.random.default_rng(5).standard_normal((4, n))).cuda()
+
+    def timed(fn, reps):
+        fn()                                     # warm-up (allocates the workspace on first use)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / reps, dist)
+
+    free0 = torch.cuda.mem_get_info()[0]
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ms_res = timed(lambda: s.residual(U), 5)
+    ms_res_vjp = timed(lambda: s.residual_vjp(Rb, U), 3)
+    free1 = torch.cuda.mem_get_info()[0]
+    ms_step = timed(lambda: s.step(1, history=False), 3)
+    s.set_state(U)
+    ms_step_vjp = timed(lambda: s.step_vjp(Rb, U), 3)
+    free2 = torch.cuda.mem_get_info()[0]
+    iters = 16
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    (cl, cd), (Ub, xb, yb), info = unrolled_force_gradient(s, U, iters)
+    torch.cuda.synchronize()
+    sweep_s = max_over_ranks(time.perf_counter() - t0, dist)
+    clocks = sampler.stop() if sampler else None
+    s.close()
+    return {"workload": "naca0012_640k", "points": n, "mach": mach, "aoa_deg": aoa, "scheme": "rk4",
+            "dtype": "f64", "residual_ms": ms_res, "residual_vjp_ms": ms_res_vjp,
+            "residual_vjp_over_residual": ms_res_vjp / ms_res, "iteration_ms": ms_step,
+            "iteration_vjp_ms": ms_step_vjp, "iteration_vjp_over_iteration": ms_step_vjp / ms_step,
+            "residual_vjp_workspace_bytes": free0 - free1, "iteration_vjp_workspace_bytes": free1 - free2,
+            "unrolled": {"iterations": iters, "seconds": sweep_s, "cl": cl, "checkpoint_every": info["checkpoint_every"],
+                         "recomputed_iterations": info["recomputed_iterations"],
+                         "state_bytes_peak": info["state_bytes_peak"],
+                         "state_bytes_unrolled": info["state_bytes_unrolled"]},
+            "clocks": clocks}
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -531,6 +601,8 @@ def run_ours(args, rank, world, local):
     if not args.no_batch and not args.single_form:
         forms["batched"] = measure_batched(args, dist, ClockSampler(local) if rank == 0 else None)
         forms["batched_speedup_vs_fp64"] = forms["batched"]["value"] / forms["fp64"]["value"]
+    if not args.no_adjoint and not args.single_form:
+        forms["adjoint"] = measure_adjoint(args, dist, ClockSampler(local) if rank == 0 else None)
     if rank != 0:
         if dist:
             dist.destroy_process_group()

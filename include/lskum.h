@@ -189,8 +189,9 @@ lskum_status lskum_residual(lskum_ctx *ctx, const double *U, double *R);
  *                 LSKUM_VJP_ACCUMULATE_XY), or NULL
  *   flags  0 or LSKUM_VJP_ACCUMULATE_XY
  * Requires limiter_K = 0 (the limiter's min/max is not differentiated):
- * LSKUM_ERR_ARG otherwise. Its workspace (about 0.45 KB per point plus
- * 100 B per edge for K = 3) is allocated on the first call and kept.
+ * LSKUM_ERR_ARG otherwise. Its workspace (about 0.53 KB per point plus
+ * 88 B per edge for K = 3: 0.8 GB at 640k points) is allocated on the first
+ * call and kept.
  * Does not change the context's state.
  */
 #define LSKUM_VJP_ACCUMULATE_XY 1 /* flags: add into x_bar, y_bar instead of overwriting them */
@@ -215,7 +216,7 @@ lskum_status lskum_residual_vjp(lskum_ctx *ctx, const double *U, const double *R
  *   U_bar       device float64[4*n] in input order (written), or NULL
  *   x_bar, y_bar  device float64[n] in input order (written, or added into with
  *                 flags = LSKUM_VJP_ACCUMULATE_XY), or NULL
- * Workspace: about 0.6 KB per point more than lskum_residual_vjp, allocated on
+ * Workspace: about 0.45 KB per point more than lskum_residual_vjp, allocated on
  * the first call. Does not change the context's state.
  */
 lskum_status lskum_step_vjp(lskum_ctx *ctx, const double *U, const double *U_bar_next, double *U_bar,
