@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--single-form", action="store_true", help="time only --precision's form")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solves form")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint form")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the forward-Euler, input-order and 10M-point forms")
     ap.add_argument("--tuning", default="auto",
                     help="mixed launch shapes: 'auto' (autotune on the cloud) or 'F,Q' (flux, q-derivative variant)")
     ap.add_argument("--batch-clouds", type=int, default=16)
@@ -603,6 +605,38 @@ def run_ours(args, rank, world, local):
         forms["batched_speedup_vs_fp64"] = forms["batched"]["value"] / forms["fp64"]["value"]
     if not args.no_adjoint and not args.single_form:
         forms["adjoint"] = measure_adjoint(args, dist, ClockSampler(local) if rank == 0 else None)
+    if not args.no_extra and not args.single_form:
+        import copy
+
+        def variant(precision, cl, **over):
+            a = copy.copy(args)
+            for k, v in over.items():
+                setattr(a, k, v)
+            r = measure_form(a, cl, precision, dist, ClockSampler(local) if rank == 0 else None)
+            r["solver"].close()
+            nn = cl["n"]
+            out = form_summary(a, r, nn, cl["nbr_offsets"][-1] / nn, world, precision, peaks, peak_src)
+            out["clocks"] = r["clocks"]
+            if r.get("tuning"):
+                out["tuning"] = r["tuning"]
+            out["config"] = {k: getattr(a, k) for k in ("scheme", "mach", "aoa", "limiter", "reorder")}
+            out["config"]["points"] = nn
+            return out
+
+        # the paper's own benchmark condition: 2nd order, 3 inner iterations,
+        # forward Euler, M 0.63, alpha 2, no limiter (its A100 figures are FP64)
+        fe = {p_: variant(p_, cloud, scheme="euler", mach=0.63, aoa=2.0, limiter=0.0) for p_ in ("fp64", "mixed")}
+        fe["paper_a100_cuda_c_fp64"] = {"2M": 1.52e8, "4M": 1.81e8, "unit": UNIT,
+                                        "note": "context: A100, FP64, the paper's clouds; not this GPU or cloud"}
+        forms["forward_euler_m063"] = fe
+        # ablation: the shuffled input order kept (no renumbering)
+        forms["mixed_input_order"] = variant("mixed", cloud, reorder=0)
+        forms["mixed_input_order"]["speedup_of_morton"] = forms["mixed"]["value"] / forms["mixed_input_order"]["value"]
+        # throughput at 10M points
+        W10, L10 = CLOUDS["naca0012_10m"]
+        c10 = naca0012_cloud(W10, L10, shuffle=bool(args.shuffle))
+        forms["mixed_10m"] = variant("mixed", c10)
+        del c10
     if rank != 0:
         if dist:
             dist.destroy_process_group()

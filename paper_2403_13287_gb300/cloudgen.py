@@ -35,6 +35,8 @@ Point index of grid node (i, j) is j*W + i (layer-major) unless `shuffle`.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 FLAG_INTERIOR = 0
@@ -132,7 +134,7 @@ def _growth_fractions(L, first_fraction):
 
 
 def _connectivity(x, y, W, L, flags, fnx, fny, ht, hn, radius_factor, max_degree, reach=3,
-                  chunk=1 << 19):
+                  chunk=1 << 16):
     """CSR rows from grid candidates (i + di, j + dj), |di|, |dj| <= reach.
 
     Distances are measured in the point's frame (tangent (ny, -nx), normal
@@ -152,7 +154,9 @@ def _connectivity(x, y, W, L, flags, fnx, fny, ht, hn, radius_factor, max_degree
     rows = np.full((n, max_degree), -1, dtype=np.int32)
     r2 = radius_factor * radius_factor
     big = np.iinfo(np.int64).max
-    for s in range(0, n, chunk):
+
+    def rows_of(s):
+        # the rows of points [s, e): written to disjoint slices, so chunks run concurrently
         e = min(n, s + chunk)
         m = e - s
         p = np.arange(s, e)
@@ -206,6 +210,10 @@ def _connectivity(x, y, W, L, flags, fnx, fny, ht, hn, radius_factor, max_degree
         ck = np.take_along_axis(np.where(keep, cand, -1), o, 1)
         deg[s:e] = keep.sum(axis=1)
         rows[s:e] = ck.astype(np.int32)
+
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        list(ex.map(rows_of, range(0, n, chunk)))
     offsets = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(deg, out=offsets[1:])
     mask = np.arange(max_degree)[None, :] < deg[:, None]
