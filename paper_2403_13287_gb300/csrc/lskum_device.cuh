@@ -20,6 +20,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "erf_table.h"
+
 namespace lskum {
 
 enum : uint8_t { FLAG_INTERIOR = 0, FLAG_WALL = 1, FLAG_FARFIELD = 2 };
@@ -75,6 +77,48 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
     return isfinite(s.rho) && s.rho > 0.0;
 }
 
+// erf(S) and exp(-S^2) together, from one row of a Taylor table: on the grid
+// s_k = k/32 (0 <= s_k <= 6) the row holds the degree-8 Taylor coefficients
+// of both functions in d = |S| - s_k (|d| <= 1/64), so each is one Horner
+// chain with an absolute error of about one unit in the last place of 1
+// (gen_erf_table.py; the first omitted terms are below 1e-18). The nearest
+// grid index comes from the top bits of |S| by integer operations, so the
+// FP64 pipe sees one subtraction and 16 fused multiply-adds. |S| >= 6:
+// erf = +-1 (erfc(6) = 2e-17) and exp(-S^2) directly.
+__device__ __forceinline__ void erf_exp(double S, double &erfS, double &eS)
+{
+    const double a = fabs(S);
+    const int hi = __double2hiint(a);
+    if (hi >= 0x40180000) {  // a >= 6
+        erfS = copysign(1.0, S);
+        eS = exp(-S * S);
+        return;
+    }
+    const unsigned lo = (unsigned)__double2loint(a);
+    // an FP32 copy of a (truncated mantissa) built from the FP64 bits
+    const float af = hi < ((1023 - 30) << 20)
+                         ? 0.0f
+                         : __int_as_float(((hi - ((1023 - 127) << 20)) << 3) | (int)(lo >> 29));
+    const int k = __float2int_rn(af * (float)LSKUM_ERF_STEP);
+    const double2 *r = reinterpret_cast<const double2 *>(kErfExpTable[k]);
+    double v[LSKUM_ERF_ROW];
+#pragma unroll
+    for (int j = 0; j < LSKUM_ERF_ROW / 2; ++j) {
+        const double2 t = __ldg(r + j);
+        v[2 * j] = t.x;
+        v[2 * j + 1] = t.y;
+    }
+    const double d = a - v[0];
+    double c = v[1 + LSKUM_ERF_DEG], e = v[2 + 2 * LSKUM_ERF_DEG];
+#pragma unroll
+    for (int n = LSKUM_ERF_DEG - 1; n >= 0; --n) {
+        c = fma(c, d, v[1 + n]);
+        e = fma(e, d, v[2 + LSKUM_ERF_DEG + n]);
+    }
+    erfS = copysign(c, S);
+    eS = e;
+}
+
 // Kinetic split flux along a direction: normal velocity un, transverse ut,
 // sign +1 for G+, -1 for G- (half-range moments of the Maxwellian):
 //   S = un sqrt(beta), A = (1 + sgn erf S)/2, B = exp(-S^2)/(2 sqrt(pi beta))
@@ -84,8 +128,10 @@ __device__ __forceinline__ void split_flux(double sgn, const Prim &s, double un,
                                            double rhoE, double G[4])
 {
     const double S = un * s.sqb;
-    const double A = 0.5 * (1.0 + sgn * erf(S));
-    const double B = exp(-S * S) * s.rsb * 0.28209479177387814;  // 1/(2 sqrt(pi))
+    double erfS, eS;
+    erf_exp(S, erfS, eS);
+    const double A = 0.5 * (1.0 + sgn * erfS);
+    const double B = eS * s.rsb * 0.28209479177387814;  // 1/(2 sqrt(pi))
     const double m = un * A + sgn * B;
     G[0] = s.rho * m;
     G[1] = (s.p + s.rho * un * un) * A + sgn * s.rho * un * B;
