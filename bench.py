@@ -178,25 +178,35 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
     raise ValueError(kernel)
 
 
-# Per-unit figures of the FP64 fused flux kernel: executed FP64 flops per
-# stencil edge (2 DFMA + DMUL + DADD; profiles/k_flux_update_fp64_naca0012_640k.md)
-# and DRAM bytes per point of one full-size 2.5M launch (single-pass capture,
-# profiles/launch_list_naca0012_2p5m_fp64.md: 1167.3 MB / 2,498,560 points).
-FP64_FLOPS_PER_EDGE_FLUX = 778.0
+# Per-unit figures of the FP64 fused flux kernel (ncu counters, 640k-point
+# capture, profiles/k_flux_update_fp64_naca0012_640k.md): executed FP64
+# instructions per stencil edge (DFMA + DMUL + DADD) and the flops they carry
+# (2 DFMA + DMUL + DADD); DRAM bytes per point of one full-size 2.5M launch
+# (single-pass capture, profiles/launch_list_naca0012_2p5m_fp64.md).
+FP64_INSTR_PER_EDGE_FLUX = 309.16
+FP64_FLOPS_PER_EDGE_FLUX = 482.77
 FLUX_DRAM_BYTES_PER_POINT = 467.2
-# FP64 peak: ncu's DFMA unit count (304 thread-FMA per cycle) x 2 flops x the
-# 2070 MHz maximum SM clock
-FP64_PEAK_GFLOPS = 304 * 2 * 2.070
+# FP64 peak: ncu's DFMA unit count, 304 FP64 thread-instructions per cycle
+# (each DFMA 2 flops), at the 2070 MHz maximum SM clock
+FP64_PEAK_GINSTR = 304 * 2.070
+FP64_PEAK_GFLOPS = 2 * FP64_PEAK_GINSTR
 
 
 def roofline_fp64(flux_avg_s, n, dbar, fb, achieved_gbs, peaks, peak_src):
+    """The FP64 flux kernel is bound by the FP64 pipe: its issue rate of FP64
+    instructions (a DMUL or DADD takes a slot as a DFMA does) against the
+    pipe's 304 per cycle; the flop rate and the HBM view beside it."""
+    instr = FP64_INSTR_PER_EDGE_FLUX * dbar * n
     flops = FP64_FLOPS_PER_EDGE_FLUX * dbar * n
-    achieved = flops / flux_avg_s / 1e9
+    achieved = instr / flux_avg_s / 1e9
+    gflops = flops / flux_avg_s / 1e9
     return {"bound": "alu", "kernel": "k_flux_update", "achieved": achieved,
-            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS,
+            "peak": FP64_PEAK_GINSTR, "unit": "G FP64 instructions/s", "frac": achieved / FP64_PEAK_GINSTR,
             "traffic": FLUX_DRAM_BYTES_PER_POINT * n,
-            "flops_per_launch": flops, "avg_launch_ms": flux_avg_s * 1e3,
-            "peak_source": "derived: 304 DFMA/cycle x 2 x 2.07 GHz",
+            "fp64_instructions_per_launch": instr, "flops_per_launch": flops,
+            "gflops": gflops, "gflops_peak": FP64_PEAK_GFLOPS, "gflops_frac": gflops / FP64_PEAK_GFLOPS,
+            "avg_launch_ms": flux_avg_s * 1e3,
+            "peak_source": "derived: 304 FP64 instructions/cycle x 2.07 GHz (ncu unit count, max SM clock)",
             "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved_gbs / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": fb,
                     "peak_source": peak_src}}
