@@ -52,18 +52,28 @@ __global__ void __launch_bounds__(128) k_qgrad(DevGeom g, const double *__restri
             qmin[k] = fmin(qmin[k], qi[k]);
         }
         if (inner) {
+            // the previous iterate at P_0 is taken out of the sum below
             double gi[8];
             load8(qg_old, i, gi);
             const double2 xyi = g.xy[i];
             const double dx = xyi.x - xy0.x, dy = xyi.y - xy0.y;
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                dq[k] = dq[k] - 0.5 * (dx * (gi[k] - g0[k]) + dy * (gi[4 + k] - g0[4 + k]));
+            for (int k = 0; k < 4; ++k) dq[k] = dq[k] - 0.5 * (dx * gi[k] + dy * gi[4 + k]);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             sx[k] += a.x * dq[k];
             sy[k] += a.y * dq[k];
+        }
+    }
+    if (inner) {
+        // sum_e a_e (d_e . g_0) = g_0, since the weights a_e = M^-1 d_e with
+        // M = sum_e d_e d_e^T give sum_e a_e d_e^T = I: the +1/2 d_e . g_0 of
+        // every corrected difference (E14) adds up to g_0 / 2
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            sx[k] += 0.5 * g0[k];
+            sy[k] += 0.5 * g0[4 + k];
         }
     }
     if (limit) {
