@@ -1,4 +1,6 @@
-"""Write erf_table.h: Taylor coefficients of erf(s) and exp(-s^2) on a grid.
+"""Write fp64_tables.h: the tables of the FP64 flux kernel's elementary functions.
+
+1. erf(S) and exp(-S^2), Taylor coefficients on a grid.
 
 The FP64 split fluxes need erf(S) and exp(-S^2) of the same S. On the grid
 s_k = k/32, k = 0..192 (0 <= s <= 6), each row holds s_k and the degree-8
@@ -15,7 +17,14 @@ and two Horner chains to about one unit in the last place of 1. The values
 are computed with mpmath at 50 significant digits and written as exactly
 rounded hexadecimal doubles.
 
-Run from the repository root:  python paper_2403_13287_gb300/csrc/gen_erf_table.py
+2. exp(x), table-driven (P. T. P. Tang, ACM Trans. Math. Software 15 (1989)
+144-157): x = n ln2/64 + r with |r| <= ln2/128 and n = 64 m + j, so
+exp(x) = 2^m 2^(j/64) p(r), p the degree-5 Taylor polynomial of exp
+(truncation below 4e-17). The table holds 2^(j/64), j = 0..63, exactly
+rounded; ln2/64 is split into a head with 32 significant bits (so that
+n * head is exact for |n| < 2^21) and the rounded remainder.
+
+Run from the repository root:  python paper_2403_13287_gb300/csrc/gen_fp64_tables.py
 """
 import os
 
@@ -49,7 +58,7 @@ def main():
     rows = [row(k) for k in range(KMAX + 1)]
     width = 1 + 2 * (DEG + 1)
     lines = [
-        "// Generated by gen_erf_table.py (mpmath, 50 digits): do not edit.",
+        "// Generated by gen_fp64_tables.py (mpmath, 50 digits): do not edit.",
         "// Row k: s_k = k/%d, then the degree-%d Taylor coefficients in d = s - s_k" % (STEP, DEG),
         "// of erf(s) (c_0..c_%d) and of exp(-s^2) (e_0..e_%d); one padding entry." % (DEG, DEG),
         "#pragma once",
@@ -65,7 +74,24 @@ def main():
         vals = [float(v).hex() for v in r] + ["0x0.0p+0"]
         lines.append("    {" + ", ".join(vals) + "},")
     lines.append("};")
-    with open(os.path.join(here, "erf_table.h"), "w") as f:
+    # exp: 2^(j/64) and the split of ln2/64
+    L = mp.log(2) / 64
+    m_, e_ = mp.frexp(L)                       # L = m_ 2^e_, 1/2 <= m_ < 1
+    head = mp.ldexp(mp.floor(mp.ldexp(m_, 32)), e_ - 32)
+    tail = L - head
+    lines += [
+        "",
+        "// exp(x) = 2^m 2^(j/64) p(r), x = (64 m + j) ln2/64 + r (Tang's table-driven method)",
+        "#define LSKUM_EXP_INV_L %s   // 64/ln2" % float(64 / mp.log(2)).hex(),
+        "#define LSKUM_EXP_L_HI %s    // ln2/64, 32 significant bits" % float(head).hex(),
+        "#define LSKUM_EXP_L_LO %s    // ln2/64 - LSKUM_EXP_L_HI" % float(tail).hex(),
+        "__device__ __align__(16) const double kExp2Table[64] = {",
+    ]
+    vals = [float(mp.mpf(2) ** (mp.mpf(j) / 64)).hex() for j in range(64)]
+    for j in range(0, 64, 4):
+        lines.append("    " + ", ".join(vals[j:j + 4]) + ",")
+    lines.append("};")
+    with open(os.path.join(here, "fp64_tables.h"), "w") as f:
         f.write("\n".join(lines) + "\n")
 
 

@@ -20,7 +20,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "erf_table.h"
+#include "fp64_tables.h"
 
 namespace lskum {
 
@@ -57,23 +57,45 @@ struct Prim {
     double rho, u, v, p, rsb, sqb;  // rsb = 1/sqrt(beta), sqb = sqrt(beta)
 };
 
+// exp(x), table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157):
+// x = n ln2/64 + r, |r| <= ln2/128, n = 64 m + j, exp(x) = 2^m 2^(j/64) p(r)
+// with p the degree-5 Taylor polynomial (gen_fp64_tables.py): 11 FP64
+// instructions. |x| >= 708 (or NaN) goes to the library exp.
+__device__ __forceinline__ double exp_tab(double x)
+{
+    if (!(fabs(x) < 708.0)) return exp(x);
+    const double magic = 0x1.8p52;
+    const double t = fma(x, LSKUM_EXP_INV_L, magic);
+    const int n = __double2loint(t);  // round-to-nearest integer held in the low word
+    const double kd = t - magic;
+    double r = fma(-kd, LSKUM_EXP_L_HI, x);
+    r = fma(-kd, LSKUM_EXP_L_LO, r);
+    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    p = fma(p, r, 1.0 / 6.0);
+    p = fma(p, r, 0.5);
+    p = fma(p, r, 1.0);
+    p = fma(p, r, 1.0);
+    const double two_m = __hiloint2double(((n >> 6) + 1023) << 20, 0);
+    return __ldg(&kExp2Table[n & 63]) * p * two_m;
+}
+
 __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, Prim &s)
 {
     const double beta = -0.5 * qt[3];
     if (!(beta > 0.0)) return false;
-    const double r = 1.0 / qt[3];          // -1/(2 beta)
-    s.u = -qt[1] * r;
-    s.v = -qt[2] * r;
     s.rsb = rsqrt(beta);
+    const double ib = s.rsb * s.rsb;       // 1/beta, so 1/q4 = -ib/2 without a division
+    s.u = 0.5 * qt[1] * ib;
+    s.v = 0.5 * qt[2] * ib;
     s.sqb = beta * s.rsb;
     const double ke = beta * (s.u * s.u + s.v * s.v);
     if (gas.g14) {
-        // beta^-2.5 = beta^-1/2 * (1/beta)^2, 1/beta = -2r
-        s.rho = exp(qt[0] + ke) * s.rsb * (4.0 * r * r);
+        // beta^-2.5 = beta^-1/2 (1/beta)^2
+        s.rho = exp_tab(qt[0] + ke) * s.rsb * (ib * ib);
     } else {
-        s.rho = exp(qt[0] - log(beta) * gas.inv_gm1 + ke);
+        s.rho = exp_tab(qt[0] - log(beta) * gas.inv_gm1 + ke);
     }
-    s.p = -s.rho * r;
+    s.p = 0.5 * s.rho * ib;
     return isfinite(s.rho) && s.rho > 0.0;
 }
 
@@ -81,7 +103,7 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
 // s_k = k/32 (0 <= s_k <= 6) the row holds the degree-8 Taylor coefficients
 // of both functions in d = |S| - s_k (|d| <= 1/64), so each is one Horner
 // chain with an absolute error of about one unit in the last place of 1
-// (gen_erf_table.py; the first omitted terms are below 1e-18). The nearest
+// (gen_fp64_tables.py; the first omitted terms are below 1e-18). The nearest
 // grid index comes from the top bits of |S| by integer operations, so the
 // FP64 pipe sees one subtraction and 16 fused multiply-adds. |S| >= 6:
 // erf = +-1 (erfc(6) = 2e-17) and exp(-S^2) directly.

@@ -1,5 +1,5 @@
 """The FP64 split fluxes take erf(S) and exp(-S^2) from one Taylor table
-(csrc/erf_table.h, written by csrc/gen_erf_table.py). Checked here without a
+(csrc/fp64_tables.h, written by csrc/gen_fp64_tables.py). Checked here without a
 GPU: the committed table is what the generator writes, and the table's two
 Horner chains reproduce erf and exp(-S^2) to about one unit in the last place
 of 1 on a dense grid (the device code runs the same chains with fused
@@ -17,20 +17,20 @@ CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
 
 
 def _table():
-    txt = open(os.path.join(CSRC, "erf_table.h")).read()
-    body = txt.split("= {", 1)[1]
+    txt = open(os.path.join(CSRC, "fp64_tables.h")).read()
+    body = txt.split("kErfExpTable", 1)[1].split("= {", 1)[1].split("};", 1)[0]
     rows = re.findall(r"\{([^{}]*)\}", body)
     return np.array([[float.fromhex(v.strip()) for v in r.split(",")] for r in rows])
 
 
 def test_table_is_the_generator_output(tmp_path):
     pytest.importorskip("mpmath")
-    src = os.path.join(CSRC, "gen_erf_table.py")
+    src = os.path.join(CSRC, "gen_fp64_tables.py")
     work = tmp_path / "csrc"
     work.mkdir()
-    (work / "gen_erf_table.py").write_text(open(src).read())
-    subprocess.run([sys.executable, str(work / "gen_erf_table.py")], check=True)
-    assert (work / "erf_table.h").read_text() == open(os.path.join(CSRC, "erf_table.h")).read()
+    (work / "gen_fp64_tables.py").write_text(open(src).read())
+    subprocess.run([sys.executable, str(work / "gen_fp64_tables.py")], check=True)
+    assert (work / "fp64_tables.h").read_text() == open(os.path.join(CSRC, "fp64_tables.h")).read()
 
 
 def test_table_reproduces_erf_and_exp():
@@ -56,3 +56,32 @@ def test_table_reproduces_erf_and_exp():
     off = (np.arange(192) + 0.5) / 32.0
     assert np.max(np.abs(np.array([math.erf(x) for x in off]) -
                          np.array([np.polyval(T[j, 9:0:-1], 1 / 64) for j in range(192)]))) <= 2.3e-16
+
+
+def _exp_consts():
+    txt = open(os.path.join(CSRC, "fp64_tables.h")).read()
+    def const(name):
+        return float.fromhex(re.search(r"#define %s (\S+)" % name, txt).group(1))
+    body = txt.split("kExp2Table", 1)[1].split("= {", 1)[1].split("};", 1)[0]
+    T = np.array([float.fromhex(v.strip()) for v in body.split(",") if v.strip()])
+    return const("LSKUM_EXP_INV_L"), const("LSKUM_EXP_L_HI"), const("LSKUM_EXP_L_LO"), T
+
+
+def test_exp_table_reproduces_exp():
+    """The table-driven exp of the device, step by step in double precision
+    (numpy rounds each operation; the device fuses multiply-adds)."""
+    inv_l, l_hi, l_lo, T = _exp_consts()
+    assert T.shape == (64,) and T[0] == 1.0 and np.all(np.diff(T) > 0)
+    assert np.all(np.abs(T - np.array([2.0 ** (j / 64) for j in range(64)])) <= np.spacing(T))
+    # the head of ln2/64 has 32 significant bits, so n * head is exact for |n| < 2^21
+    m, e = math.frexp(l_hi)
+    assert m * 2.0 ** 32 == int(m * 2.0 ** 32)
+    assert abs((l_hi + l_lo) - math.log(2) / 64) <= 1e-18
+    x = np.concatenate([np.linspace(-700.0, 700.0, 200001), np.linspace(-5.0, 5.0, 200001)])
+    kd = np.rint(x * inv_l)
+    n = kd.astype(np.int64)
+    r = (x - kd * l_hi) - kd * l_lo
+    p = ((((r / 120 + 1 / 24) * r + 1 / 6) * r + 0.5) * r + 1) * r + 1
+    got = T[n & 63] * p * np.ldexp(1.0, (n >> 6).astype(np.int32))
+    rel = np.abs(got - np.exp(x)) / np.exp(x)
+    assert np.max(rel) <= 4.5e-16
