@@ -55,6 +55,8 @@ struct Gas {
 //   rho = exp(q1 + beta (u^2 + v^2)) beta^(-1/(gamma-1)), p = rho/(2 beta)
 struct Prim {
     double rho, u, v, p, rsb, sqb;  // rsb = 1/sqrt(beta), sqb = sqrt(beta)
+    double h, e2;                   // (rho E + p)/rho and (rho E + p/2)/rho
+    double rsbc;                    // rsb / (2 sqrt(pi))
 };
 
 // exp(x), table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157):
@@ -96,6 +98,11 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
         s.rho = exp_tab(qt[0] - log(beta) * gas.inv_gm1 + ke);
     }
     s.p = 0.5 * s.rho * ib;
+    // per unit mass: p/rho = 1/(2 beta), rho E = p/(gamma-1) + rho |u|^2/2
+    const double hu2 = 0.5 * (s.u * s.u + s.v * s.v);
+    s.h = fma(0.5 * (gas.inv_gm1 + 1.0), ib, hu2);
+    s.e2 = fma(0.5 * (gas.inv_gm1 + 0.5), ib, hu2);
+    s.rsbc = s.rsb * 0.28209479177387814;  // 1/(2 sqrt(pi))
     return isfinite(s.rho) && s.rho > 0.0;
 }
 
@@ -146,19 +153,20 @@ __device__ __forceinline__ void erf_exp(double S, double &erfS, double &eS)
 //   S = un sqrt(beta), A = (1 + sgn erf S)/2, B = exp(-S^2)/(2 sqrt(pi beta))
 //   G = [rho(un A + sgn B), (p + rho un^2) A + sgn rho un B,
 //        rho ut (un A + sgn B), (rhoE + p) un A + sgn (rhoE + p/2) B]
-__device__ __forceinline__ void split_flux(double sgn, const Prim &s, double un, double ut,
-                                           double rhoE, double G[4])
+// evaluated as Q = rho A, W = sgn rho B: G0 = un Q + W, G1 = p A + un G0,
+// G2 = ut G0, G3 = h un Q + e2 W (h, e2 per unit mass, from the primitive state)
+__device__ __forceinline__ void split_flux(double sgn, const Prim &s, double un, double ut, double G[4])
 {
     const double S = un * s.sqb;
     double erfS, eS;
     erf_exp(S, erfS, eS);
-    const double A = 0.5 * (1.0 + sgn * erfS);
-    const double B = eS * s.rsb * 0.28209479177387814;  // 1/(2 sqrt(pi))
-    const double m = un * A + sgn * B;
-    G[0] = s.rho * m;
-    G[1] = (s.p + s.rho * un * un) * A + sgn * s.rho * un * B;
-    G[2] = s.rho * ut * m;
-    G[3] = (rhoE + s.p) * un * A + sgn * (rhoE + 0.5 * s.p) * B;
+    const double A = fma(0.5 * sgn, erfS, 0.5);
+    const double Q = s.rho * A;
+    const double W = s.rho * (eS * (sgn * s.rsbc));
+    G[0] = fma(un, Q, W);
+    G[1] = fma(un, G[0], s.p * A);
+    G[2] = ut * G[0];
+    G[3] = fma(s.h * un, Q, s.e2 * W);
 }
 
 // per-warp pair of residue partial sums (lo: lanes in the case of the warp's

@@ -181,13 +181,11 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
             ok &= prim_from_q(qt0, P.gas, s0);
             const double us_i = si.u * tx + si.v * ty, un_i = si.u * n0.x + si.v * n0.y;
             const double us_0 = s0.u * tx + s0.v * ty, un_0 = s0.u * n0.x + s0.v * n0.y;
-            const double rE_i = si.p * P.gas.inv_gm1 + 0.5 * si.rho * (us_i * us_i + un_i * un_i);
-            const double rE_0 = s0.p * P.gas.inv_gm1 + 0.5 * s0.rho * (us_0 * us_0 + un_0 * un_0);
             if (w.x != 0.0) {
                 const double sg = (m & M_XPOS) ? 1.0 : -1.0;
                 double Gi[4], G0[4];
-                split_flux(sg, si, us_i, un_i, rE_i, Gi);
-                split_flux(sg, s0, us_0, un_0, rE_0, G0);
+                split_flux(sg, si, us_i, un_i, Gi);
+                split_flux(sg, s0, us_0, un_0, G0);
                 // dG = G(q~_i) - G(q~_0) from the two rounded fluxes: an unfused
                 // subtraction, so equal states give exactly zero (a contracted
                 // fma(rho_i, m_i, -rho_0 m_0) would leave a product's rounding)
@@ -197,8 +195,8 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
             if (w.y != 0.0) {
                 const double sg = (m & M_YPOS) ? 1.0 : -1.0;
                 double Gi[4], G0[4];
-                split_flux(sg, si, un_i, us_i, rE_i, Gi);
-                split_flux(sg, s0, un_0, us_0, rE_0, G0);
+                split_flux(sg, si, un_i, us_i, Gi);
+                split_flux(sg, s0, un_0, us_0, G0);
                 // Gn components are [mass, n-momentum, s-momentum, energy]
                 R[0] += w.y * __dsub_rn(Gi[0], G0[0]);
                 R[1] += w.y * __dsub_rn(Gi[2], G0[2]);
