@@ -244,23 +244,28 @@ __device__ __forceinline__ bool q_from_U(const double U[4], const Gas &gas, doub
 // ---------------------------------------------------------------------------
 struct PrimF {
     float rho, u, v, p, rsb, sqb;
+    float h, e2, rsbc;  // (rho E + p)/rho, (rho E + p/2)/rho, rsb / (2 sqrt(pi))
 };
 
 __device__ __forceinline__ bool prim_from_q_f(const float qt[4], float inv_gm1, bool g14, PrimF &s)
 {
     const float beta = -0.5f * qt[3];
     if (!(beta > 0.0f)) return false;
-    const float r = __fdividef(1.0f, qt[3]);  // -1/(2 beta)
-    s.u = -qt[1] * r;
-    s.v = -qt[2] * r;
     s.rsb = rsqrtf(beta);
+    const float ib = s.rsb * s.rsb;  // 1/beta, so 1/q4 = -ib/2 without a division
+    s.u = 0.5f * qt[1] * ib;
+    s.v = 0.5f * qt[2] * ib;
     s.sqb = beta * s.rsb;
-    const float ke = beta * (s.u * s.u + s.v * s.v);
+    const float u2 = s.u * s.u + s.v * s.v;
+    const float ke = beta * u2;
     // __expf: relative error about |arg| * 6e-8 here (|arg| < ~20), within
     // the FP32 budget of the form
-    if (g14) s.rho = __expf(qt[0] + ke) * s.rsb * (4.0f * r * r);
+    if (g14) s.rho = __expf(qt[0] + ke) * s.rsb * (ib * ib);
     else s.rho = __expf(qt[0] - __logf(beta) * inv_gm1 + ke);
-    s.p = -s.rho * r;
+    s.p = 0.5f * s.rho * ib;
+    s.h = fmaf(0.5f * (inv_gm1 + 1.0f), ib, 0.5f * u2);
+    s.e2 = fmaf(0.5f * (inv_gm1 + 0.5f), ib, 0.5f * u2);
+    s.rsbc = s.rsb * 0.28209479177387814f;
     return isfinite(s.rho) && s.rho > 0.0f;
 }
 
@@ -279,18 +284,18 @@ __device__ __forceinline__ float half_range_A(float sgn, float S, float e)
     return (sgn * S >= 0.0f) ? 1.0f - small : small;
 }
 
-__device__ __forceinline__ void split_flux_f(float sgn, const PrimF &s, float un, float ut, float rhoE,
-                                             float G[4])
+// same regrouping as split_flux: Q = rho A, W = sgn rho B
+__device__ __forceinline__ void split_flux_f(float sgn, const PrimF &s, float un, float ut, float G[4])
 {
     const float S = un * s.sqb;
     const float e = __expf(-S * S);
     const float A = half_range_A(sgn, S, e);
-    const float B = e * s.rsb * 0.28209479177387814f;
-    const float m = un * A + sgn * B;
-    G[0] = s.rho * m;
-    G[1] = (s.p + s.rho * un * un) * A + sgn * s.rho * un * B;
-    G[2] = s.rho * ut * m;
-    G[3] = (rhoE + s.p) * un * A + sgn * (rhoE + 0.5f * s.p) * B;
+    const float Q = s.rho * A;
+    const float W = s.rho * (e * (sgn * s.rsbc));
+    G[0] = fmaf(un, Q, W);
+    G[1] = fmaf(un, G[0], s.p * A);
+    G[2] = ut * G[0];
+    G[3] = fmaf(s.h * un, Q, s.e2 * W);
 }
 
 __device__ __forceinline__ void load4f(const float *a, int64_t p, float v[4])

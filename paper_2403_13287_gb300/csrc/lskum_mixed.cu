@@ -323,22 +323,20 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
             ok &= prim_from_q_f(qt0, P.inv_gm1, P.g14, s0);
             const float us_i = si.u * tx + si.v * ty, un_i = si.u * n0.x + si.v * n0.y;
             const float us_0 = s0.u * tx + s0.v * ty, un_0 = s0.u * n0.x + s0.v * n0.y;
-            const float rE_i = si.p * P.inv_gm1 + 0.5f * si.rho * (us_i * us_i + un_i * un_i);
-            const float rE_0 = s0.p * P.inv_gm1 + 0.5f * s0.rho * (us_0 * us_0 + un_0 * un_0);
             float dGs[4] = {0, 0, 0, 0}, dGn[4] = {0, 0, 0, 0};
             if (w.x != 0.0f) {
                 const float sg = (m & M_XPOS) ? 1.0f : -1.0f;
                 float Gi[4], G0[4];
-                split_flux_f(sg, si, us_i, un_i, rE_i, Gi);
-                split_flux_f(sg, s0, us_0, un_0, rE_0, G0);
+                split_flux_f(sg, si, us_i, un_i, Gi);
+                split_flux_f(sg, s0, us_0, un_0, G0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) dGs[k] = __fsub_rn(Gi[k], G0[k]);
             }
             if (w.y != 0.0f) {
                 const float sg = (m & M_YPOS) ? 1.0f : -1.0f;
                 float Gi[4], G0[4];
-                split_flux_f(sg, si, un_i, us_i, rE_i, Gi);
-                split_flux_f(sg, s0, un_0, us_0, rE_0, G0);
+                split_flux_f(sg, si, un_i, us_i, Gi);
+                split_flux_f(sg, s0, un_0, us_0, G0);
                 // Gn components are [mass, n-momentum, s-momentum, energy]
                 dGn[0] = __fsub_rn(Gi[0], G0[0]);
                 dGn[1] = __fsub_rn(Gi[2], G0[2]);
