@@ -1170,14 +1170,12 @@ extern "C" lskum_status lskum_step_vjp(lskum_ctx *c, const double *U, const doub
         LAUNCH(c, launch_stage_adj(S, c->sUb, c->sR[0], 1.0, true, c->vUacc, c->sdtb, c->vRb, c->stream));
         if ((st = vjp_residual(c, Un, c->vUacc, geom, true)) != LSKUM_OK) return st;
     } else {
+        // U_{k+1} = P(U^n - c_k dt R_k), R_{k+1} = R(U_{k+1}); U_{k+1} is kept in sU[k]
         const double cst[3] = {0.5, 0.5, 1.0};
-        const double *Us = Un;
         for (int k = 0; k < 3; ++k) {
             LAUNCH(c, launch_stage_fwd(S, Un, c->sR[k], cst[k], c->sU[k], c->stream));
             if ((st = residual_fp64(c, c->sU[k], c->sR[k + 1])) != LSKUM_OK) return st;
-            Us = c->sU[k];
         }
-        (void)Us;
         // reverse: the last stage, then stages 2, 1, 0 (their residuals R3, R2, R1, R0)
         const double *Rs[4] = {c->sR[0], c->sR[1], c->sR[2], c->sR[3]};
         LAUNCH(c, launch_stage_adj_rk4_final(S, c->sUb, Rs, c->vUacc, c->sdtb, c->sRb, c->stream));
