@@ -71,7 +71,9 @@ typedef struct {
                        * weights and the split-flux arithmetic in FP32; U, the RK update, the
                        * residue, the forces and the LS closure of points whose sub-stencil
                        * weights amplify rounding (sum |w_i||P_i - P_0| > 16) in FP64 */
-    int reorder;      /* 0: keep the input order; 1: Morton (Z-order) renumbering for gather locality */
+    int reorder;      /* internal numbering for gather locality: 0 the input order; 1 Morton (Z-order) of
+                       * the coordinates; 2 reverse Cuthill-McKee of the stencil graph (a batch keeps
+                       * each case's points together in either) */
     double limiter_K; /* order 2 only. 0: no limiter (the paper's scheme). > 0: Venkatakrishnan's
                        * limiter (J. Comput. Phys. 118, 1995; not in the paper) scales each
                        * component of grad q at P_0 by phi = min(1, f(D+, d+), f(D-, -d+)),

@@ -10,12 +10,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lskum.h"
 #include "lskum_kernels.h"
 #include "lskum_mixed.h"
 #include "lskum_adjoint.h"
 
 using namespace lskum;
+
+// NVTX range over one library call (visible to Nsight tools; no cost without them)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct lskum_ctx {
     int64_t n = 0, nnz = 0, n_wall = 0;
@@ -291,10 +299,103 @@ static lskum_status refresh_q(lskum_ctx *c, const double *U, void *qdst)
     return LSKUM_OK;
 }
 
+// Reverse Cuthill-McKee numbering of the stencil graph (E. Cuthill and
+// J. McKee, Proc. 24th ACM National Conference, 1969; reversed as in A.
+// George, 1971): per connected component, breadth-first from a
+// pseudo-peripheral point (George-Liu: repeat from a farthest point of
+// smallest degree while the eccentricity grows), neighbours visited by
+// increasing degree, ties by index; each component's order is then reversed
+// in place, so components keep the order of their smallest point (a batch's
+// cases stay contiguous and in case order). The graph is the CSR relation
+// made symmetric. perm[k] = input index of the k-th point.
+static void rcm_permutation(int64_t n, const int32_t *off, const int32_t *idx, std::vector<int32_t> &perm)
+{
+    // symmetric adjacency
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int64_t p = 0; p < n; ++p)
+        for (int32_t e = off[p]; e < off[p + 1]; ++e) {
+            ++cnt[p + 1];
+            ++cnt[idx[e] + 1];
+        }
+    for (int64_t p = 0; p < n; ++p) cnt[p + 1] += cnt[p];
+    std::vector<int32_t> adj(cnt[n]);
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t p = 0; p < n; ++p)
+        for (int32_t e = off[p]; e < off[p + 1]; ++e) {
+            adj[fill[p]++] = idx[e];
+            adj[fill[idx[e]]++] = (int32_t)p;
+        }
+    std::vector<int32_t> deg(n);
+    for (int64_t p = 0; p < n; ++p) {
+        std::sort(adj.begin() + cnt[p], adj.begin() + cnt[p + 1]);
+        const auto last = std::unique(adj.begin() + cnt[p], adj.begin() + cnt[p + 1]);
+        deg[p] = (int32_t)(last - (adj.begin() + cnt[p]));
+    }
+    std::vector<int32_t> level(n, -1), order;
+    order.reserve(n);
+    std::vector<int32_t> nb;
+    // breadth-first from `root`, neighbours by (degree, index); appends to out,
+    // marks level; returns the last level's size and a smallest-degree point on it
+    auto bfs = [&](int32_t root, std::vector<int32_t> &out, std::vector<int32_t> &lv, int32_t *far) {
+        const size_t start = out.size();
+        lv[root] = 0;
+        out.push_back(root);
+        for (size_t h = start; h < out.size(); ++h) {
+            const int32_t u = out[h];
+            nb.assign(adj.begin() + cnt[u], adj.begin() + cnt[u] + deg[u]);
+            std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
+                return deg[a] != deg[b] ? deg[a] < deg[b] : a < b;
+            });
+            for (int32_t v : nb)
+                if (lv[v] < 0) {
+                    lv[v] = lv[u] + 1;
+                    out.push_back(v);
+                }
+        }
+        const int32_t depth = lv[out.back()];
+        int32_t best = out.back();
+        for (size_t h = start; h < out.size(); ++h) {
+            const int32_t v = out[h];
+            if (lv[v] == depth && (deg[v] < deg[best] || (deg[v] == deg[best] && v < best))) best = v;
+        }
+        *far = best;
+        return depth;
+    };
+    std::vector<int32_t> scratch, lv2(n, -1);
+    for (int64_t s0 = 0; s0 < n; ++s0) {
+        if (level[s0] >= 0) continue;
+        // pseudo-peripheral root of this component
+        int32_t root = (int32_t)s0, far = root;
+        scratch.clear();
+        int32_t ecc = bfs(root, scratch, lv2, &far);
+        for (int it = 0; it < 8; ++it) {
+            for (int32_t v : scratch) lv2[v] = -1;
+            std::vector<int32_t> tmp;
+            int32_t far2 = far;
+            const int32_t e2 = bfs(far, tmp, lv2, &far2);
+            if (e2 <= ecc) {
+                for (int32_t v : tmp) lv2[v] = -1;
+                break;
+            }
+            root = far;
+            ecc = e2;
+            scratch.swap(tmp);
+            far = far2;
+        }
+        for (int32_t v : scratch) lv2[v] = -1;
+        const size_t a = order.size();
+        int32_t dummy;
+        bfs(root, order, level, &dummy);
+        std::reverse(order.begin() + a, order.end());
+    }
+    perm.assign(order.begin(), order.end());
+}
+
 static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, const double *nx,
                                 const double *ny, const int32_t *flags, const int32_t *nbr_offsets,
                                 const int32_t *nbr_idx, const int32_t *wall_order)
 {
+    NvtxRange nvtx_("lskum_create");
     const int64_t n = c->n, nnz = c->nnz;
     cudaStream_t s = c->stream;
     // input-order copies
@@ -348,6 +449,11 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
         c->launches += 3;
         CK(c, sort_permutation(n, keys_d, c->perm, s));
         CK(c, cudaFreeAsync(keys_d, s));
+        CK(c, cudaStreamSynchronize(s));
+    } else if (c->cfg.reorder == 2) {
+        std::vector<int32_t> pr;
+        rcm_permutation(n, nbr_offsets, nbr_idx, pr);
+        CK(c, cudaMemcpyAsync(c->perm, pr.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         CK(c, cudaStreamSynchronize(s));
     } else if (c->cfg.reorder == 1) {
         double xmin = x[0], xmax = x[0], ymin = y[0], ymax = y[0];
@@ -527,7 +633,7 @@ static lskum_status check_config(const lskum_config *cfg, int64_t n)
         return fail(nullptr, LSKUM_ERR_ARG, "precision must be 0 (FP64) or 1 (mixed)");
     if (cfg->precision == 1 && n >= (int64_t)1 << 28)
         return fail(nullptr, LSKUM_ERR_ARG, "the mixed form takes at most 2^28 - 1 points");
-    if (cfg->reorder != 0 && cfg->reorder != 1) return fail(nullptr, LSKUM_ERR_ARG, "reorder must be 0 or 1");
+    if (cfg->reorder < 0 || cfg->reorder > 2) return fail(nullptr, LSKUM_ERR_ARG, "reorder must be 0, 1 or 2");
     if (!(cfg->limiter_K >= 0.0) || !std::isfinite(cfg->limiter_K))
         return fail(nullptr, LSKUM_ERR_ARG, "limiter_K must be finite and >= 0");
     return LSKUM_OK;
@@ -883,6 +989,7 @@ static lskum_status replay_step_graph(lskum_ctx *c, int n_iters, int *left)
 extern "C" lskum_status lskum_step(lskum_ctx *c, int n_iters, double *res_history)
 {
     if (!c) return LSKUM_ERR_ARG;
+    NvtxRange nvtx_("lskum_step");
     c->err.clear();
     if (n_iters < 0) return fail(c, LSKUM_ERR_ARG, "n_iters < 0");
     if (n_iters == 0) return LSKUM_OK;
@@ -950,6 +1057,7 @@ static lskum_status check_nonphysical(lskum_ctx *c)
 extern "C" lskum_status lskum_residual(lskum_ctx *c, const double *U, double *R)
 {
     if (!c) return LSKUM_ERR_ARG;
+    NvtxRange nvtx_("lskum_residual");
     c->err.clear();
     if (!R) return fail(c, LSKUM_ERR_ARG, "R is NULL");
     lskum_status st = reset_status(c);
@@ -1106,6 +1214,7 @@ extern "C" lskum_status lskum_residual_vjp(lskum_ctx *c, const double *U, const 
                                            double *x_bar, double *y_bar, int flags)
 {
     if (!c) return LSKUM_ERR_ARG;
+    NvtxRange nvtx_("lskum_residual_vjp");
     c->err.clear();
     if (!R_bar) return fail(c, LSKUM_ERR_ARG, "R_bar is NULL");
     if (!U_bar && !x_bar && !y_bar) return LSKUM_OK;
@@ -1140,6 +1249,7 @@ extern "C" lskum_status lskum_step_vjp(lskum_ctx *c, const double *U, const doub
                                        double *x_bar, double *y_bar, int flags)
 {
     if (!c) return LSKUM_ERR_ARG;
+    NvtxRange nvtx_("lskum_step_vjp");
     c->err.clear();
     if (!U_bar_next) return fail(c, LSKUM_ERR_ARG, "U_bar_next is NULL");
     if (!U_bar && !x_bar && !y_bar) return LSKUM_OK;
@@ -1199,6 +1309,7 @@ extern "C" lskum_status lskum_forces_vjp(lskum_ctx *c, int k, double cl_bar, dou
                                          double *x_bar, double *y_bar, int flags)
 {
     if (!c) return LSKUM_ERR_ARG;
+    NvtxRange nvtx_("lskum_forces_vjp");
     c->err.clear();
     if (k < 0 || k >= c->ncases) return fail(c, LSKUM_ERR_ARG, "case %d out of range", k);
     const int64_t w0 = c->case_wall_h[k], nw = c->case_wall_h[k + 1] - w0;
@@ -1224,6 +1335,7 @@ extern "C" lskum_status lskum_forces_vjp(lskum_ctx *c, int k, double cl_bar, dou
 extern "C" lskum_status lskum_q_derivatives(lskum_ctx *c, const double *U, double *qx, double *qy)
 {
     if (!c) return LSKUM_ERR_ARG;
+    NvtxRange nvtx_("lskum_q_derivatives");
     c->err.clear();
     if (!qx || !qy) return fail(c, LSKUM_ERR_ARG, "qx or qy is NULL");
     lskum_status st = reset_status(c);
@@ -1297,6 +1409,7 @@ static lskum_status time_variant(lskum_ctx *c, int reps, cudaEvent_t e0, cudaEve
 extern "C" lskum_status lskum_autotune(lskum_ctx *c, int reps, lskum_tuning *out)
 {
     if (!c) return LSKUM_ERR_ARG;
+    NvtxRange nvtx_("lskum_autotune");
     c->err.clear();
     if (!c->mixed) return fail(c, LSKUM_ERR_ARG, "the autotuner covers the mixed-precision kernels (precision = 1)");
     if (reps < 1) reps = 5;

@@ -68,7 +68,7 @@ def ten_k():
     return naca0012_cloud(320, 30)                # the ~10k first-order workload
 
 
-@pytest.mark.parametrize("reorder", [0, 1])
+@pytest.mark.parametrize("reorder", [0, 1, 2])
 def test_stencil_masks_bit_exact(small, reorder):
     s = _solver(small, reorder=reorder)
     assert np.array_equal(s.stencil_masks(), oracle.split_stencils(small))
@@ -118,7 +118,7 @@ def test_q_derivatives_match_oracle(small, inner, limiter):
 
 
 @pytest.mark.parametrize("order,limiter", [(1, 0.0), (2, 0.0), (2, 1.0)])
-@pytest.mark.parametrize("reorder", [0, 1])
+@pytest.mark.parametrize("reorder", [0, 1, 2])
 def test_residual_matches_oracle(small, order, limiter, reorder):
     U = _perturbed_state(small, 0.85, 1.0, seed=2)
     s = _solver(small, order=order, inner_iters=3, reorder=reorder, limiter_K=limiter)
@@ -182,11 +182,47 @@ def test_trajectory_matches_oracle(request, order, scheme, iters, mach, aoa, lim
 
 
 def test_reordering_does_not_change_the_solution(small):
-    a = _solver(small, order=2, time_scheme=1, mach=0.85, aoa_deg=1.0, reorder=0, limiter_K=1.0)
-    b = _solver(small, order=2, time_scheme=1, mach=0.85, aoa_deg=1.0, reorder=1, limiter_K=1.0)
+    states = []
+    for reorder in (0, 1, 2):
+        s = _solver(small, order=2, time_scheme=1, mach=0.85, aoa_deg=1.0, reorder=reorder, limiter_K=1.0)
+        s.step(10)
+        states.append(s.get_state())
+    assert np.array_equal(states[0], states[1]) and np.array_equal(states[0], states[2])
+
+
+def _bandwidth(cloud, perm):
+    """Largest |internal(p) - internal(i)| over the stencil edges."""
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    src = np.repeat(np.arange(cloud["n"]), np.diff(cloud["nbr_offsets"]))
+    return int(np.max(np.abs(inv[src] - inv[cloud["nbr_idx"]])))
+
+
+def test_rcm_numbering_is_a_permutation_that_narrows_the_stencil_band():
+    c = naca0012_cloud(130, 24, seed=11, shuffle=True)
+    s0 = _solver(c, reorder=0)
+    s2 = _solver(c, reorder=2)
+    p0, p2 = s0.permutation(), s2.permutation()
+    assert np.array_equal(p0, np.arange(c["n"]))
+    assert np.array_equal(np.sort(p2), np.arange(c["n"]))
+    # shuffled input: the band of the stencil graph collapses under RCM
+    assert _bandwidth(c, p2) * 10 < _bandwidth(c, p0)
+    assert _bandwidth(c, p2) <= 2 * 130 + 10        # about one grid ring of the O-grid
+
+
+def test_resume_continues_bitwise(small):
+    """Checkpoint/resume: 6 iterations, state out, a new context, state in,
+    4 more iterations equal 10 iterations in one run."""
+    kw = dict(order=2, time_scheme=1, mach=0.85, aoa_deg=1.0, limiter_K=1.0, reorder=1)
+    a = _solver(small, **kw)
     a.step(10)
-    b.step(10)
-    assert np.array_equal(a.get_state(), b.get_state())
+    b = _solver(small, **kw)
+    b.step(6)
+    U6 = b.get_state()
+    c = _solver(small, **kw)
+    c.set_state(U6)
+    c.step(4)
+    assert np.array_equal(a.get_state(), c.get_state())
 
 
 def test_runs_are_bitwise_deterministic(small):
