@@ -554,6 +554,12 @@ def measure_adjoint(args, dist, sampler):
     ms_res = timed(lambda: s.residual(U), 5)
     ms_res_vjp = timed(lambda: s.residual_vjp(Rb, U), 3)
     free1 = torch.cuda.mem_get_info()[0]
+    # the FP32 product, on a mixed context of the same cloud
+    sm = lskum.Solver(cloud, order=2, inner_iters=args.inner, time_scheme=1, cfl=args.cfl, mach=mach,
+                      aoa_deg=aoa, reorder=1, limiter_K=0.0, precision=1, stream=stream.cuda_stream)
+    ms_res_m = timed(lambda: sm.residual(U), 5)
+    ms_res_vjp32 = timed(lambda: sm.residual_vjp(Rb, U, fp32=True), 3)
+    sm.close()
     ms_step = timed(lambda: s.step(1, history=False), 3)
     s.set_state(U)
     ms_step_vjp = timed(lambda: s.step_vjp(Rb, U), 3)
@@ -568,7 +574,9 @@ def measure_adjoint(args, dist, sampler):
     s.close()
     return {"workload": "naca0012_640k", "points": n, "mach": mach, "aoa_deg": aoa, "scheme": "rk4",
             "dtype": "f64", "residual_ms": ms_res, "residual_vjp_ms": ms_res_vjp,
-            "residual_vjp_over_residual": ms_res_vjp / ms_res, "iteration_ms": ms_step,
+            "residual_vjp_over_residual": ms_res_vjp / ms_res,
+            "mixed_residual_ms": ms_res_m, "residual_vjp_fp32_ms": ms_res_vjp32,
+            "fp32_vjp_speedup": ms_res_vjp / ms_res_vjp32, "iteration_ms": ms_step,
             "iteration_vjp_ms": ms_step_vjp, "iteration_vjp_over_iteration": ms_step_vjp / ms_step,
             "residual_vjp_workspace_bytes": free0 - free1, "iteration_vjp_workspace_bytes": free1 - free2,
             "unrolled": {"iterations": iters, "seconds": sweep_s, "cl": cl, "checkpoint_every": info["checkpoint_every"],

@@ -183,13 +183,14 @@ lskum_status lskum_residual(lskum_ctx *ctx, const double *U, double *R);
  *   U_bar = (dR/dU)^T R_bar,  x_bar = (dR/dx)^T R_bar,  y_bar = (dR/dy)^T R_bar.
  * The derivative in x and y holds the frame normals, the connectivity and the
  * sub-stencil membership fixed (they are inputs, not functions of x and y).
- * Computed in FP64 whatever the context's precision, for the FP64 residual.
+ * Computed in FP64 whatever the context's precision, for the FP64 residual,
+ * unless flags has LSKUM_VJP_FP32 (mixed contexts only).
  *   U      device float64[4*n] in input order, or NULL for the context's state
  *   R_bar  device float64[4*n] in input order
  *   U_bar  device float64[4*n] in input order (written), or NULL
  *   x_bar, y_bar  device float64[n] in input order (written, or added into with
  *                 LSKUM_VJP_ACCUMULATE_XY), or NULL
- *   flags  0 or LSKUM_VJP_ACCUMULATE_XY
+ *   flags  0, or LSKUM_VJP_ACCUMULATE_XY and/or LSKUM_VJP_FP32
  * Requires limiter_K = 0 (the limiter's min/max is not differentiated):
  * LSKUM_ERR_ARG otherwise. Its workspace (about 0.53 KB per point plus
  * 88 B per edge for K = 3: 0.8 GB at 640k points) is allocated on the first
@@ -197,6 +198,12 @@ lskum_status lskum_residual(lskum_ctx *ctx, const double *U, double *R);
  * Does not change the context's state.
  */
 #define LSKUM_VJP_ACCUMULATE_XY 1 /* flags: add into x_bar, y_bar instead of overwriting them */
+#define LSKUM_VJP_FP32 2          /* lskum_residual_vjp flags: the product in FP32 (mixed contexts): q, the
+                                   * q-derivative iterates (the mixed form's FP32 passes) and the reverse pass
+                                   * in FP32; geometry cotangents and the E13 Jacobian in FP64. U_bar agrees
+                                   * with the FP64 product to ~1e-4 of its largest entry; x_bar, y_bar only to
+                                   * ~1e-2 (the FP32 flux differences in the weight cotangents cancel), so
+                                   * coordinate gradients should use the FP64 product */
 
 lskum_status lskum_residual_vjp(lskum_ctx *ctx, const double *U, const double *R_bar, double *U_bar,
                                 double *x_bar, double *y_bar, int flags);

@@ -27,121 +27,150 @@ namespace lskum {
 namespace {
 
 // ---------------------------------------------------------------------------
-// forward-mode dual number with four tangents
+// forward-mode dual number with four tangents, over T (double, or float for
+// the FP32 product)
 // ---------------------------------------------------------------------------
-struct D4 {
-    double v, d[4];
+template <class T>
+struct D4T {
+    T v, d[4];
 };
+using D4 = D4T<double>;
 
-__device__ __forceinline__ D4 dconst(double v)
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_erf(double x) { return erf(x); }
+__device__ __forceinline__ float m_erf(float x) { return erff(x); }
+
+template <class T>
+__device__ __forceinline__ D4T<T> dconst(T v)
 {
-    D4 r;
+    D4T<T> r;
     r.v = v;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) r.d[k] = 0.0;
+    for (int k = 0; k < 4; ++k) r.d[k] = T(0);
     return r;
 }
-__device__ __forceinline__ D4 operator+(const D4 &a, const D4 &b)
+template <class T>
+__device__ __forceinline__ D4T<T> operator+(const D4T<T> &a, const D4T<T> &b)
 {
-    D4 r;
+    D4T<T> r;
     r.v = a.v + b.v;
 #pragma unroll
     for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] + b.d[k];
     return r;
 }
-__device__ __forceinline__ D4 operator-(const D4 &a, const D4 &b)
+template <class T>
+__device__ __forceinline__ D4T<T> operator-(const D4T<T> &a, const D4T<T> &b)
 {
-    D4 r;
+    D4T<T> r;
     r.v = a.v - b.v;
 #pragma unroll
     for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] - b.d[k];
     return r;
 }
-__device__ __forceinline__ D4 operator*(const D4 &a, const D4 &b)
+template <class T>
+__device__ __forceinline__ D4T<T> operator*(const D4T<T> &a, const D4T<T> &b)
 {
-    D4 r;
+    D4T<T> r;
     r.v = a.v * b.v;
 #pragma unroll
     for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
     return r;
 }
-__device__ __forceinline__ D4 operator*(double s, const D4 &a)
+template <class T>
+__device__ __forceinline__ D4T<T> operator*(T s, const D4T<T> &a)
 {
-    D4 r;
+    D4T<T> r;
     r.v = s * a.v;
 #pragma unroll
     for (int k = 0; k < 4; ++k) r.d[k] = s * a.d[k];
     return r;
 }
-__device__ __forceinline__ D4 operator+(double s, const D4 &a)
+template <class T>
+__device__ __forceinline__ D4T<T> operator+(T s, const D4T<T> &a)
 {
-    D4 r = a;
+    D4T<T> r = a;
     r.v = s + a.v;
     return r;
 }
 // f(a) with f(a.v) = fv and f'(a.v) = df
-__device__ __forceinline__ D4 chain(const D4 &a, double fv, double df)
+template <class T>
+__device__ __forceinline__ D4T<T> chain(const D4T<T> &a, T fv, T df)
 {
-    D4 r;
+    D4T<T> r;
     r.v = fv;
 #pragma unroll
     for (int k = 0; k < 4; ++k) r.d[k] = df * a.d[k];
     return r;
 }
-__device__ __forceinline__ D4 recip(const D4 &a)
+template <class T>
+__device__ __forceinline__ D4T<T> recip(const D4T<T> &a)
 {
-    const double r = 1.0 / a.v;
+    const T r = T(1) / a.v;
     return chain(a, r, -r * r);
 }
-__device__ __forceinline__ D4 dexp(const D4 &a)
+template <class T>
+__device__ __forceinline__ D4T<T> dexp(const D4T<T> &a)
 {
-    const double e = exp(a.v);
+    const T e = m_exp(a.v);
     return chain(a, e, e);
 }
-__device__ __forceinline__ D4 dlog(const D4 &a) { return chain(a, log(a.v), 1.0 / a.v); }
-__device__ __forceinline__ D4 dsqrt(const D4 &a)
+template <class T>
+__device__ __forceinline__ D4T<T> dlog(const D4T<T> &a)
 {
-    const double s = sqrt(a.v);
-    return chain(a, s, 0.5 / s);
+    return chain(a, m_log(a.v), T(1) / a.v);
+}
+template <class T>
+__device__ __forceinline__ D4T<T> dsqrt(const D4T<T> &a)
+{
+    const T s = m_sqrt(a.v);
+    return chain(a, s, T(0.5) / s);
 }
 
-struct PrimD {
-    D4 rho, u, v, p, sqb, rsb;
+template <class T>
+struct PrimDT {
+    D4T<T> rho, u, v, p, sqb, rsb;
 };
 
 // inverse of E13 over duals (general gamma): beta = -q4/2, u = -q2/q4,
 // v = -q3/q4, rho = exp(q1 - ln(beta)/(gamma-1) + beta |u|^2), p = rho/(2 beta)
-__device__ __forceinline__ PrimD prim_d(const D4 qt[4], double inv_gm1)
+template <class T>
+__device__ __forceinline__ PrimDT<T> prim_d(const D4T<T> qt[4], T inv_gm1)
 {
-    PrimD s;
-    const D4 beta = -0.5 * qt[3];
-    const D4 r = recip(qt[3]);
-    s.u = -1.0 * (qt[1] * r);
-    s.v = -1.0 * (qt[2] * r);
+    PrimDT<T> s;
+    const D4T<T> beta = T(-0.5) * qt[3];
+    const D4T<T> r = recip(qt[3]);
+    s.u = T(-1) * (qt[1] * r);
+    s.v = T(-1) * (qt[2] * r);
     s.sqb = dsqrt(beta);
     s.rsb = recip(s.sqb);
-    const D4 ke = beta * (s.u * s.u + s.v * s.v);
+    const D4T<T> ke = beta * (s.u * s.u + s.v * s.v);
     s.rho = dexp(qt[0] - inv_gm1 * dlog(beta) + ke);
-    s.p = -1.0 * (s.rho * r);
+    s.p = T(-1) * (s.rho * r);
     return s;
 }
 
-// split flux along a direction over duals; same formula as the forward kernel
-__device__ __forceinline__ void split_flux_d(double sgn, const PrimD &s, const D4 &un, const D4 &ut,
-                                             double inv_gm1, D4 G[4])
+// split flux along a direction over duals, in the paper's form
+template <class T>
+__device__ __forceinline__ void split_flux_d(T sgn, const PrimDT<T> &s, const D4T<T> &un, const D4T<T> &ut,
+                                             T inv_gm1, D4T<T> G[4])
 {
-    const D4 S = un * s.sqb;
-    const double e = exp(-S.v * S.v);
-    const D4 erfS = chain(S, erf(S.v), 1.1283791670955126 * e);   // 2/sqrt(pi)
-    const D4 eS = chain(S, e, -2.0 * S.v * e);
-    const D4 A = 0.5 * (1.0 + sgn * erfS);
-    const D4 B = 0.28209479177387814 * (eS * s.rsb);                 // 1/(2 sqrt(pi))
-    const D4 rhoE = inv_gm1 * s.p + 0.5 * (s.rho * (un * un + ut * ut));
-    const D4 m = un * A + sgn * B;
+    const D4T<T> S = un * s.sqb;
+    const T e = m_exp(-S.v * S.v);
+    const D4T<T> erfS = chain(S, m_erf(S.v), T(1.1283791670955126) * e);   // 2/sqrt(pi)
+    const D4T<T> eS = chain(S, e, T(-2) * S.v * e);
+    const D4T<T> A = T(0.5) * (T(1) + sgn * erfS);
+    const D4T<T> B = T(0.28209479177387814) * (eS * s.rsb);                 // 1/(2 sqrt(pi))
+    const D4T<T> rhoE = inv_gm1 * s.p + T(0.5) * (s.rho * (un * un + ut * ut));
+    const D4T<T> m = un * A + sgn * B;
     G[0] = s.rho * m;
     G[1] = (s.p + s.rho * un * un) * A + sgn * (s.rho * un * B);
     G[2] = s.rho * ut * m;
-    G[3] = (rhoE + s.p) * un * A + sgn * ((rhoE + 0.5 * s.p) * B);
+    G[3] = (rhoE + s.p) * un * A + sgn * ((rhoE + T(0.5) * s.p) * B);
 }
 
 __device__ __forceinline__ void ld4(const double *a, int64_t p, double v[4])
@@ -166,6 +195,25 @@ __device__ __forceinline__ void st8(double *a, int64_t p, const double v[8])
     st4(a, 2 * p, v);
     st4(a, 2 * p + 1, v + 4);
 }
+__device__ __forceinline__ void ld4(const float *a, int64_t p, float v[4])
+{
+    const float4 t = reinterpret_cast<const float4 *>(a)[p];
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void st4(float *a, int64_t p, const float v[4])
+{
+    reinterpret_cast<float4 *>(a)[p] = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void ld8(const float *a, int64_t p, float v[8])
+{
+    ld4(a, 2 * p, v);
+    ld4(a, 2 * p + 1, v + 4);
+}
+__device__ __forceinline__ void st8(float *a, int64_t p, const float v[8])
+{
+    st4(a, 2 * p, v);
+    st4(a, 2 * p + 1, v + 4);
+}
 
 // sub-stencil slots of an edge: x-sub (0 x+, 1 x-) and y-sub (2 y+, 3 y-), -1 if none
 __device__ __forceinline__ int xsub(uint8_t m) { return (m & M_XPOS) ? 0 : ((m & M_XNEG) ? 1 : -1); }
@@ -178,24 +226,24 @@ __device__ __forceinline__ bool sub_needed(uint8_t f, int k)
 // cotangent of one reconstructed state: sum over the split fluxes it feeds,
 // cs (frame order) against Gs and cn (frame order) against Gn, plus the
 // flux values for the weight cotangents
-__device__ __forceinline__ void state_adjoint(const double qt[4], double tx, double ty, double nx, double ny,
-                                              bool use_s, double sg_s, bool use_n, double sg_n,
-                                              const double cs[4], const double cn[4], double inv_gm1,
-                                              double qbar[4], double Gs[4], double Gn[4])
+template <class T>
+__device__ __forceinline__ void state_adjoint(const T qt[4], T tx, T ty, T nx, T ny, bool use_s, T sg_s, bool use_n,
+                                              T sg_n, const T cs[4], const T cn[4], T inv_gm1, T qbar[4], T Gs[4],
+                                              T Gn[4])
 {
-    D4 q[4];
+    D4T<T> q[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         q[k] = dconst(qt[k]);
-        q[k].d[k] = 1.0;
+        q[k].d[k] = T(1);
     }
-    const PrimD s = prim_d(q, inv_gm1);
-    const D4 us = tx * s.u + ty * s.v;
-    const D4 un = nx * s.u + ny * s.v;
+    const PrimDT<T> s = prim_d(q, inv_gm1);
+    const D4T<T> us = tx * s.u + ty * s.v;
+    const D4T<T> un = nx * s.u + ny * s.v;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) qbar[k] = 0.0;
+    for (int k = 0; k < 4; ++k) qbar[k] = T(0);
     if (use_s) {
-        D4 G[4];
+        D4T<T> G[4];
         split_flux_d(sg_s, s, us, un, inv_gm1, G);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -205,7 +253,7 @@ __device__ __forceinline__ void state_adjoint(const double qt[4], double tx, dou
         }
     }
     if (use_n) {
-        D4 G[4];
+        D4T<T> G[4];
         split_flux_d(sg_n, s, un, us, inv_gm1, G);
         // Gn components are [mass, n-momentum, s-momentum, energy]
         const int fr[4] = {0, 2, 1, 3};
@@ -221,14 +269,16 @@ __device__ __forceinline__ void state_adjoint(const double qt[4], double tx, dou
 // ---------------------------------------------------------------------------
 // flux adjoint, owner side
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_adj_flux(AdjParams P)
+template <class T>
+__global__ void __launch_bounds__(128) k_adj_flux(AdjParamsT<T> P)
 {
     const DevGeom &g = P.g;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.n) return;
     const uint8_t f = g.flag[p] & 3;
     const bool second = P.order == 2;
-    double qb0[4] = {0, 0, 0, 0}, gb0[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const T h = T(0.5);
+    T qb0[4] = {0, 0, 0, 0}, gb0[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int e0 = g.off[p], e1 = g.off[p + 1];
     if (f == FLAG_FARFIELD) {
         // R = 0 there: no cotangent flows from this point
@@ -241,12 +291,14 @@ __global__ void __launch_bounds__(128) k_adj_flux(AdjParams P)
         return;
     }
     const double2 xy0 = g.xy[p];
-    const double2 n0 = g.nrm[p];
-    const double tx = n0.y, ty = -n0.x;
-    double Rb[4], q0[4], g0[8];
+    const double2 n0d = g.nrm[p];
+    const T nx = T(n0d.x), ny = T(n0d.y);
+    const T tx = ny, ty = -nx;
+    const T inv_gm1 = T(P.inv_gm1);
+    T Rb[4], q0[4], g0[8];
     ld4(P.Rbar, p, Rb);
     // frame-order cotangent of R_local: R_global = (R0, R1 t + R2 n, R3)
-    const double Rl[4] = {Rb[0], Rb[1] * tx + Rb[2] * ty, Rb[1] * n0.x + Rb[2] * n0.y, Rb[3]};
+    const T Rl[4] = {Rb[0], Rb[1] * tx + Rb[2] * ty, Rb[1] * nx + Rb[2] * ny, Rb[3]};
     ld4(P.q, p, q0);
     if (second) ld8(P.qg, p, g0);
     for (int e = e0; e < e1; ++e) {
@@ -254,64 +306,65 @@ __global__ void __launch_bounds__(128) k_adj_flux(AdjParams P)
         const uint8_t m = g.mask[e];
         const int ks = xsub(m), kn = ysub(m);
         const bool us_ = sub_needed(f, ks), un_ = sub_needed(f, kn);
-        const double2 w = g.fxw[e];
-        double qti[4], qt0[4];
+        const double2 wd = g.fxw[e];
+        const T wx = T(wd.x), wy = T(wd.y);
+        T qti[4], qt0[4];
         ld4(P.q, i, qti);
-        double dx = 0.0, dy = 0.0, gi[8];
+        T dx = T(0), dy = T(0), gi[8];
 #pragma unroll
         for (int k = 0; k < 4; ++k) qt0[k] = q0[k];
         if (second) {
             const double2 xyi = g.xy[i];
-            dx = xyi.x - xy0.x;
-            dy = xyi.y - xy0.y;
+            dx = T(xyi.x - xy0.x);
+            dy = T(xyi.y - xy0.y);
             ld8(P.qg, i, gi);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                qti[k] = qti[k] - 0.5 * (dx * gi[k] + dy * gi[4 + k]);
-                qt0[k] = qt0[k] - 0.5 * (dx * g0[k] + dy * g0[4 + k]);
+                qti[k] = qti[k] - h * (dx * gi[k] + dy * gi[4 + k]);
+                qt0[k] = qt0[k] - h * (dx * g0[k] + dy * g0[4 + k]);
             }
         }
-        double cs[4], cn[4];
+        T cs[4], cn[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            cs[k] = us_ ? w.x * Rl[k] : 0.0;
-            cn[k] = un_ ? w.y * Rl[k] : 0.0;
+            cs[k] = us_ ? wx * Rl[k] : T(0);
+            cn[k] = un_ ? wy * Rl[k] : T(0);
         }
-        double qbi[4], qbo[4], Gsi[4] = {0, 0, 0, 0}, Gni[4] = {0, 0, 0, 0}, Gs0[4] = {0, 0, 0, 0},
-                                       Gn0[4] = {0, 0, 0, 0};
-        const double sgs = (m & M_XPOS) ? 1.0 : -1.0, sgn = (m & M_YPOS) ? 1.0 : -1.0;
+        T qbi[4], qbo[4], Gsi[4] = {0, 0, 0, 0}, Gni[4] = {0, 0, 0, 0}, Gs0[4] = {0, 0, 0, 0},
+                              Gn0[4] = {0, 0, 0, 0};
+        const T sgs = (m & M_XPOS) ? T(1) : T(-1), sgn = (m & M_YPOS) ? T(1) : T(-1);
         if (us_ || un_) {
-            state_adjoint(qti, tx, ty, n0.x, n0.y, us_, sgs, un_, sgn, cs, cn, P.inv_gm1, qbi, Gsi, Gni);
-            state_adjoint(qt0, tx, ty, n0.x, n0.y, us_, sgs, un_, sgn, cs, cn, P.inv_gm1, qbo, Gs0, Gn0);
+            state_adjoint(qti, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, qbi, Gsi, Gni);
+            state_adjoint(qt0, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, qbo, Gs0, Gn0);
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) qbi[k] = qbo[k] = 0.0;
+            for (int k = 0; k < 4; ++k) qbi[k] = qbo[k] = T(0);
         }
         // R += w (G(q~_i) - G(q~_0)): + for the neighbour, - for the owner
-        double wbx = 0.0, wby = 0.0;
+        T wbx = T(0), wby = T(0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             wbx += Rl[k] * (Gsi[k] - Gs0[k]);
             wby += Rl[k] * (Gni[k] - Gn0[k]);
             qbo[k] = -qbo[k];
         }
-        P.wbar[e] = make_double2(us_ ? wbx : 0.0, un_ ? wby : 0.0);
+        P.wbar[e] = make_double2(us_ ? (double)wbx : 0.0, un_ ? (double)wby : 0.0);
         st4(P.ebar, e, qbi);
-        double dxb = 0.0, dyb = 0.0;
+        T dxb = T(0), dyb = T(0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             qb0[k] += qbo[k];
             if (second) {
                 // q~_0 = q_0 - (dx qx_0 + dy qy_0)/2
-                gb0[k] -= 0.5 * dx * qbo[k];
-                gb0[4 + k] -= 0.5 * dy * qbo[k];
-                dxb -= 0.5 * qbo[k] * g0[k];
-                dyb -= 0.5 * qbo[k] * g0[4 + k];
+                gb0[k] -= h * dx * qbo[k];
+                gb0[4 + k] -= h * dy * qbo[k];
+                dxb -= h * qbo[k] * g0[k];
+                dyb -= h * qbo[k] * g0[4 + k];
             }
         }
         double2 db = P.dbar[e];
-        db.x += dxb;
-        db.y += dyb;
+        db.x += (double)dxb;
+        db.y += (double)dyb;
         P.dbar[e] = db;
     }
     st4(P.qbar, p, qb0);
@@ -322,13 +375,15 @@ __global__ void __launch_bounds__(128) k_adj_flux(AdjParams P)
 // flux adjoint, neighbour side: point p gathers the cotangents of q~_p over
 // the edges that reach it
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_adj_flux_gather(AdjParams P)
+template <class T>
+__global__ void __launch_bounds__(128) k_adj_flux_gather(AdjParamsT<T> P)
 {
     const DevGeom &g = P.g;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.n) return;
     const bool second = P.order == 2;
-    double qb[4], gb[8], gp[8];
+    const T h = T(0.5);
+    T qb[4], gb[8], gp[8];
     ld4(P.qbar, p, qb);
     if (second) {
         ld8(P.gbar, p, gb);
@@ -337,25 +392,25 @@ __global__ void __launch_bounds__(128) k_adj_flux_gather(AdjParams P)
     const double2 xyp = g.xy[p];
     for (int t = P.toff[p]; t < P.toff[p + 1]; ++t) {
         const int e = P.tedge[t];
-        double eb[4];
+        T eb[4];
         ld4(P.ebar, e, eb);
 #pragma unroll
         for (int k = 0; k < 4; ++k) qb[k] += eb[k];
         if (second) {
             const double2 xys = g.xy[P.tsrc[t]];
-            const double dx = xyp.x - xys.x, dy = xyp.y - xys.y;
-            double dxb = 0.0, dyb = 0.0;
+            const T dx = T(xyp.x - xys.x), dy = T(xyp.y - xys.y);
+            T dxb = T(0), dyb = T(0);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 // q~_p = q_p - (dx qx_p + dy qy_p)/2 on this edge
-                gb[k] -= 0.5 * dx * eb[k];
-                gb[4 + k] -= 0.5 * dy * eb[k];
-                dxb -= 0.5 * eb[k] * gp[k];
-                dyb -= 0.5 * eb[k] * gp[4 + k];
+                gb[k] -= h * dx * eb[k];
+                gb[4 + k] -= h * dy * eb[k];
+                dxb -= h * eb[k] * gp[k];
+                dyb -= h * eb[k] * gp[4 + k];
             }
             double2 d = P.dbar[e];
-            d.x += dxb;
-            d.y += dyb;
+            d.x += (double)dxb;
+            d.y += (double)dyb;
             P.dbar[e] = d;
         }
     }
@@ -368,15 +423,16 @@ __global__ void __launch_bounds__(128) k_adj_flux_gather(AdjParams P)
 //   g_p = sum_e a_e s_e,  s_e = (q_i - q_p) - [dx (gx'_i - gx'_p) + dy (gy'_i - gy'_p)]/2
 // with g' the previous iterate (absent in the first-order pass).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_adj_grad(AdjParams P, const double *__restrict__ gprev,
-                                                  const double *__restrict__ gbar_in,
-                                                  double *__restrict__ gbar_out)
+template <class T>
+__global__ void __launch_bounds__(128) k_adj_grad(AdjParamsT<T> P, const T *__restrict__ gprev,
+                                                  const T *__restrict__ gbar_in, T *__restrict__ gbar_out)
 {
     const DevGeom &g = P.g;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.n) return;
     const bool inner = gprev != nullptr;
-    double qb[4], gb[8], gpp[8], qp[4], gbo[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const T h = T(0.5);
+    T qb[4], gb[8], gpp[8], qp[4], gbo[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     ld4(P.qbar, p, qb);
     ld8(gbar_in, p, gb);
     ld4(P.q, p, qp);
@@ -385,56 +441,65 @@ __global__ void __launch_bounds__(128) k_adj_grad(AdjParams P, const double *__r
     // outgoing edges: owner terms, and the cotangents of a_e and of the offsets
     for (int e = g.off[p]; e < g.off[p + 1]; ++e) {
         const int i = g.idx[e];
-        const double2 a = g.lsw[e];
-        double qi[4], gi[8];
+        const double2 ad = g.lsw[e];
+        const T ax = T(ad.x), ay = T(ad.y);
+        T qi[4], gi[8];
         ld4(P.q, i, qi);
-        double dx = 0.0, dy = 0.0;
+        T dx = T(0), dy = T(0);
         if (inner) {
             ld8(gprev, i, gi);
             const double2 xyi = g.xy[i];
-            dx = xyi.x - xyp.x;
-            dy = xyi.y - xyp.y;
+            dx = T(xyi.x - xyp.x);
+            dy = T(xyi.y - xyp.y);
         }
-        double2 ab = P.abar[e];
-        double2 db = P.dbar[e];
+        T abx = T(0), aby = T(0), dbx = T(0), dby = T(0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const double sb = a.x * gb[k] + a.y * gb[4 + k];
-            double s = qi[k] - qp[k];
+            const T sb = ax * gb[k] + ay * gb[4 + k];
+            T s = qi[k] - qp[k];
             if (inner) {
-                const double ddx = gi[k] - gpp[k], ddy = gi[4 + k] - gpp[4 + k];
-                s = s - 0.5 * (dx * ddx + dy * ddy);
-                gbo[k] += 0.5 * dx * sb;
-                gbo[4 + k] += 0.5 * dy * sb;
-                db.x -= 0.5 * sb * ddx;
-                db.y -= 0.5 * sb * ddy;
+                const T ddx = gi[k] - gpp[k], ddy = gi[4 + k] - gpp[4 + k];
+                s = s - h * (dx * ddx + dy * ddy);
+                gbo[k] += h * dx * sb;
+                gbo[4 + k] += h * dy * sb;
+                dbx -= h * sb * ddx;
+                dby -= h * sb * ddy;
             }
             qb[k] -= sb;
-            ab.x += s * gb[k];
-            ab.y += s * gb[4 + k];
+            abx += s * gb[k];
+            aby += s * gb[4 + k];
         }
+        double2 ab = P.abar[e];
+        ab.x += (double)abx;
+        ab.y += (double)aby;
         P.abar[e] = ab;
-        P.dbar[e] = db;
+        if (inner) {
+            double2 db = P.dbar[e];
+            db.x += (double)dbx;
+            db.y += (double)dby;
+            P.dbar[e] = db;
+        }
     }
     // incoming edges: the terms of this point as a neighbour
     for (int t = P.toff[p]; t < P.toff[p + 1]; ++t) {
         const int e = P.tedge[t], src = P.tsrc[t];
-        const double2 a = g.lsw[e];
-        double gs[8];
+        const double2 ad = g.lsw[e];
+        const T ax = T(ad.x), ay = T(ad.y);
+        T gs[8];
         ld8(gbar_in, src, gs);
-        double dx = 0.0, dy = 0.0;
+        T dx = T(0), dy = T(0);
         if (inner) {
             const double2 xys = g.xy[src];
-            dx = xyp.x - xys.x;
-            dy = xyp.y - xys.y;
+            dx = T(xyp.x - xys.x);
+            dy = T(xyp.y - xys.y);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const double sb = a.x * gs[k] + a.y * gs[4 + k];
+            const T sb = ax * gs[k] + ay * gs[4 + k];
             qb[k] += sb;
             if (inner) {
-                gbo[k] -= 0.5 * dx * sb;
-                gbo[4 + k] -= 0.5 * dy * sb;
+                gbo[k] -= h * dx * sb;
+                gbo[4 + k] -= h * dy * sb;
             }
         }
     }
@@ -566,7 +631,8 @@ __global__ void __launch_bounds__(256) k_adj_points(AdjParams P, const double2 *
 
 // q_bar to U_bar through E13 (duals over the four conserved variables);
 // adds into Ub_acc ([n][4], internal order)
-__global__ void __launch_bounds__(256) k_adj_state(AdjParams P, const double *__restrict__ U,
+template <class T>
+__global__ void __launch_bounds__(256) k_adj_state(AdjParamsT<T> P, const double *__restrict__ U,
                                                    double *__restrict__ Ub_acc)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -574,7 +640,10 @@ __global__ void __launch_bounds__(256) k_adj_state(AdjParams P, const double *__
     if (p >= n) return;
     double u[4], qb[4];
     ld4(U, p, u);
-    ld4(P.qbar, p, qb);
+    T qt[4];
+    ld4(P.qbar, p, qt);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qb[k] = (double)qt[k];
     D4 Ud[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -677,19 +746,20 @@ cudaError_t build_transpose_csr(int64_t n, int64_t nnz, const int32_t *off, cons
     return err;
 }
 
-cudaError_t launch_adj_flux(const AdjParams &P, cudaStream_t s)
+template <class T>
+cudaError_t launch_adj_flux(const AdjParamsT<T> &P, cudaStream_t s)
 {
-    k_adj_flux<<<blocks(P.g.n, 128), 128, 0, s>>>(P);
+    k_adj_flux<T><<<blocks(P.g.n, 128), 128, 0, s>>>(P);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    k_adj_flux_gather<<<blocks(P.g.n, 128), 128, 0, s>>>(P);
+    k_adj_flux_gather<T><<<blocks(P.g.n, 128), 128, 0, s>>>(P);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_grad(const AdjParams &P, const double *gprev, const double *gbar_in, double *gbar_out,
-                            cudaStream_t s)
+template <class T>
+cudaError_t launch_adj_grad(const AdjParamsT<T> &P, const T *gprev, const T *gbar_in, T *gbar_out, cudaStream_t s)
 {
-    k_adj_grad<<<blocks(P.g.n, 128), 128, 0, s>>>(P, gprev, gbar_in, gbar_out);
+    k_adj_grad<T><<<blocks(P.g.n, 128), 128, 0, s>>>(P, gprev, gbar_in, gbar_out);
     return cudaGetLastError();
 }
 
@@ -706,11 +776,34 @@ cudaError_t launch_adj_points(const AdjParams &P, const double2 *pxy, double *x_
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_state(const AdjParams &P, const double *U, double *Ub_acc, cudaStream_t s)
+template <class T>
+cudaError_t launch_adj_state(const AdjParamsT<T> &P, const double *U, double *Ub_acc, cudaStream_t s)
 {
-    k_adj_state<<<blocks(P.g.n, 256), 256, 0, s>>>(P, U, Ub_acc);
+    k_adj_state<T><<<blocks(P.g.n, 256), 256, 0, s>>>(P, U, Ub_acc);
     return cudaGetLastError();
 }
+
+__global__ void k_to_float(int64_t m, const double *__restrict__ a, float *__restrict__ b)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) b[t] = (float)a[t];
+}
+
+cudaError_t launch_to_float(int64_t m, const double *a, float *b, cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_to_float<<<blocks(m, 256), 256, 0, s>>>(m, a, b);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_adj_flux<double>(const AdjParamsT<double> &, cudaStream_t);
+template cudaError_t launch_adj_flux<float>(const AdjParamsT<float> &, cudaStream_t);
+template cudaError_t launch_adj_grad<double>(const AdjParamsT<double> &, const double *, const double *, double *,
+                                             cudaStream_t);
+template cudaError_t launch_adj_grad<float>(const AdjParamsT<float> &, const float *, const float *, float *,
+                                            cudaStream_t);
+template cudaError_t launch_adj_state<double>(const AdjParamsT<double> &, const double *, double *, cudaStream_t);
+template cudaError_t launch_adj_state<float>(const AdjParamsT<float> &, const double *, double *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // pseudo-time update in forward (stage states for the reverse sweep) and in

@@ -8,14 +8,17 @@
 
 namespace lskum {
 
-struct AdjParams {
+// T: double (the FP64 product) or float (the FP32 product of a mixed
+// context); the geometry cotangents (wbar, abar, dbar) are FP64 in both
+template <class T>
+struct AdjParamsT {
     DevGeom g;
-    const double *q;       // [n][4] q-variables of the state
-    const double *qg;      // [n][8] final q-derivative iterate (order 2)
-    const double *Rbar;    // [n][4] residual cotangent
-    double *qbar;          // [n][4] q cotangent (accumulated)
-    double *gbar;          // [n][8] cotangent of the final q-derivative iterate
-    double *ebar;          // [nnz][4] cotangent of the neighbour's reconstructed state, per edge
+    const T *q;            // [n][4] q-variables of the state
+    const T *qg;           // [n][8] final q-derivative iterate (order 2)
+    const T *Rbar;         // [n][4] residual cotangent
+    T *qbar;               // [n][4] q cotangent (accumulated)
+    T *gbar;               // [n][8] cotangent of the final q-derivative iterate
+    T *ebar;               // [nnz][4] cotangent of the neighbour's reconstructed state, per edge
     double2 *wbar;         // [nnz] cotangents of the sub-stencil weights (w_s, w_n)
     double2 *abar;         // [nnz] cotangents of the full-stencil weights (a_x, a_y)
     double2 *dbar;         // [nnz] cotangent of the edge offset P_i - P_0
@@ -26,16 +29,18 @@ struct AdjParams {
     double inv_gm1;
     int order;
 };
+using AdjParams = AdjParamsT<double>;
 
 cudaError_t build_transpose_csr(int64_t n, int64_t nnz, const int32_t *off, const int32_t *idx, int32_t *toff,
                                 int32_t *tedge, int32_t *tsrc, cudaStream_t s);
 // flux adjoint: owner pass, then the neighbour-side gather (initialises qbar, gbar, ebar, wbar; adds into
 // dbar, which the caller zeroes once per product)
-cudaError_t launch_adj_flux(const AdjParams &P, cudaStream_t s);
+template <class T>
+cudaError_t launch_adj_flux(const AdjParamsT<T> &P, cudaStream_t s);
 // one E15 pass in reverse: gbar_in is the cotangent of this pass's output,
 // gbar_out receives that of its input iterate gprev (nullptr for the first-order pass)
-cudaError_t launch_adj_grad(const AdjParams &P, const double *gprev, const double *gbar_in, double *gbar_out,
-                            cudaStream_t s);
+template <class T>
+cudaError_t launch_adj_grad(const AdjParamsT<T> &P, const T *gprev, const T *gbar_in, T *gbar_out, cudaStream_t s);
 // least-squares weight cotangents (abar, wbar) into the offset cotangents dbar
 cudaError_t launch_adj_weights(const AdjParams &P, cudaStream_t s);
 // offsets (dbar) plus per-point cotangents pxy (internal, or nullptr) to x_bar, y_bar in input
@@ -43,7 +48,11 @@ cudaError_t launch_adj_weights(const AdjParams &P, cudaStream_t s);
 cudaError_t launch_adj_points(const AdjParams &P, const double2 *pxy, double *x_bar, double *y_bar, bool accumulate,
                               cudaStream_t s);
 // Ub_acc ([n][4], internal order) += (dq/dU)^T qbar at the internal state U
-cudaError_t launch_adj_state(const AdjParams &P, const double *U, double *Ub_acc, cudaStream_t s);
+template <class T>
+cudaError_t launch_adj_state(const AdjParamsT<T> &P, const double *U, double *Ub_acc, cudaStream_t s);
+
+// b[i] = (float)a[i], i < m
+cudaError_t launch_to_float(int64_t m, const double *a, float *b, cudaStream_t s);
 
 // pseudo-time update: boundary treatment and time step of the points
 struct StageParams {

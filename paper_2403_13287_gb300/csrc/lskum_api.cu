@@ -109,6 +109,9 @@ struct lskum_ctx {
     bool svjp_ready = false;
     double *sR[4] = {}, *sU[3] = {}, *sRb[4] = {}, *sUb = nullptr, *sUin = nullptr, *sdt = nullptr, *sdtb = nullptr;
     double *fdsb = nullptr;       // forces VJP: cotangents of the arc-length weights
+    // FP32 residual VJP (mixed contexts; allocated on the first such call)
+    bool fvjp_ready = false;
+    float *fq = nullptr, *fG = nullptr, *fRb = nullptr, *fqb = nullptr, *fgb = nullptr, *fgb2 = nullptr, *febar = nullptr;
     double *fbuf = nullptr;
 
     // kernel timing (lskum_profile): event pairs per kernel class, reused
@@ -1159,6 +1162,78 @@ static lskum_status residual_fp64(lskum_ctx *c, const double *Ui, double *Rout)
     return LSKUM_OK;
 }
 
+// FP32 workspace of the residual VJP
+static lskum_status fvjp_workspace(lskum_ctx *c)
+{
+    if (c->fvjp_ready) return LSKUM_OK;
+    const int64_t n = c->n, m = std::max<int64_t>(c->nnz, 1);
+    const int K = c->cfg.order == 2 ? c->cfg.inner_iters : 0;
+    CK(c, dalloc(c, &c->fq, 4 * n));
+    if (c->cfg.order == 2) {
+        CK(c, dalloc(c, &c->fG, (int64_t)(K + 1) * 8 * n));
+        CK(c, dalloc(c, &c->fgb, 8 * n));
+        CK(c, dalloc(c, &c->fgb2, 8 * n));
+    }
+    CK(c, dalloc(c, &c->fRb, 4 * n));
+    CK(c, dalloc(c, &c->fqb, 4 * n));
+    CK(c, dalloc(c, &c->febar, 4 * m));
+    c->fvjp_ready = true;
+    return LSKUM_OK;
+}
+
+// the FP32 product: the mixed form's FP32 q and q-derivative passes forward,
+// the reverse pass in FP32, the geometry cotangents and E13 Jacobian in FP64
+static lskum_status vjp_residual_fp32(lskum_ctx *c, const double *Ui, double *Ub_acc, bool geom)
+{
+    const int64_t n = c->n;
+    const bool second = c->cfg.order == 2;
+    const int K = second ? c->cfg.inner_iters : 0;
+    lskum_status st = fvjp_workspace(c);
+    if (st != LSKUM_OK) return st;
+    const MixedGeom mg = c->mgeom();
+    LAUNCH(c, launch_q_from_U_mixed(n, c->gas, Ui, c->fq, c->status, c->stream));
+    if (second) {
+        LAUNCH(c, launch_qgrad_mixed(mg, c->fq, nullptr, c->fG, 0.0, c->stream, c->var_qgrad));
+        for (int k = 1; k <= K; ++k)
+            LAUNCH(c, launch_qgrad_mixed(mg, c->fq, c->fG + (int64_t)(k - 1) * 8 * n, c->fG + (int64_t)k * 8 * n, 0.0,
+                                         c->stream, c->var_qgrad));
+    }
+    LAUNCH(c, launch_to_float(4 * n, c->vRb, c->fRb, c->stream));
+    const AdjParams Pd = adj_params(c);
+    AdjParamsT<float> P{};
+    P.g = Pd.g;
+    P.q = c->fq;
+    P.qg = second ? c->fG + (int64_t)K * 8 * n : nullptr;
+    P.Rbar = c->fRb;
+    P.qbar = c->fqb;
+    P.gbar = c->fgb;
+    P.ebar = c->febar;
+    P.wbar = Pd.wbar;
+    P.abar = Pd.abar;
+    P.dbar = Pd.dbar;
+    P.toff = Pd.toff;
+    P.tedge = Pd.tedge;
+    P.tsrc = Pd.tsrc;
+    P.perm = Pd.perm;
+    P.inv_gm1 = Pd.inv_gm1;
+    P.order = Pd.order;
+    c->launches++;
+    LAUNCH(c, launch_adj_flux(P, c->stream));
+    if (second) {
+        CK(c, cudaMemsetAsync(c->vabar, 0, std::max<int64_t>(c->nnz, 1) * sizeof(double2), c->stream));
+        float *gin = c->fgb, *gout = c->fgb2;
+        for (int k = K; k >= 1; --k) {
+            LAUNCH(c, launch_adj_grad(P, (const float *)(c->fG + (int64_t)(k - 1) * 8 * n), (const float *)gin,
+                                      gout, c->stream));
+            std::swap(gin, gout);
+        }
+        LAUNCH(c, launch_adj_grad(P, (const float *)nullptr, (const float *)gin, (float *)nullptr, c->stream));
+    }
+    if (geom) LAUNCH(c, launch_adj_weights(Pd, c->stream));
+    LAUNCH(c, launch_adj_state(P, Ui, Ub_acc, c->stream));
+    return LSKUM_OK;
+}
+
 // one residual VJP at the internal state Ui for the internal cotangent vRb:
 // Ub_acc ([n][4], internal) += (dR/dU)^T R_bar; vdbar += the offset
 // cotangents (the caller zeroes vdbar once per product)
@@ -1179,7 +1254,7 @@ static lskum_status vjp_residual(lskum_ctx *c, const double *Ui, double *Ub_acc,
             LAUNCH(c, launch_adj_grad(P, c->vG + (int64_t)(k - 1) * 8 * n, gin, gout, c->stream));
             std::swap(gin, gout);
         }
-        LAUNCH(c, launch_adj_grad(P, nullptr, gin, nullptr, c->stream));
+        LAUNCH(c, launch_adj_grad(P, (const double *)nullptr, (const double *)gin, (double *)nullptr, c->stream));
     }
     if (geom) LAUNCH(c, launch_adj_weights(P, c->stream));
     LAUNCH(c, launch_adj_state(P, Ui, Ub_acc, c->stream));
@@ -1226,8 +1301,13 @@ extern "C" lskum_status lskum_residual_vjp(lskum_ctx *c, const double *U, const 
         Ui = c->Ut;
     }
     LAUNCH(c, launch_state_in(c->n, c->perm, R_bar, c->vRb, c->stream));
-    if ((st = vjp_residual(c, Ui, c->vUacc, x_bar || y_bar, false)) != LSKUM_OK) return st;
-    return vjp_end(c, U_bar, x_bar, y_bar, flags);
+    if (flags & LSKUM_VJP_FP32) {
+        if (!c->mixed) return fail(c, LSKUM_ERR_ARG, "the FP32 product needs a mixed-precision context");
+        if ((st = vjp_residual_fp32(c, Ui, c->vUacc, x_bar || y_bar)) != LSKUM_OK) return st;
+    } else if ((st = vjp_residual(c, Ui, c->vUacc, x_bar || y_bar, false)) != LSKUM_OK) {
+        return st;
+    }
+    return vjp_end(c, U_bar, x_bar, y_bar, flags & ~LSKUM_VJP_FP32);
 }
 
 static lskum_status step_vjp_workspace(lskum_ctx *c)

@@ -270,15 +270,16 @@ class Solver:
         self._check(self._L.lskum_residual(self._ctx, _dev_ptr(U), _dev_ptr(out)))
         return out
 
-    def residual_vjp(self, R_bar, U=None, want_U=True, want_xy=True):
+    def residual_vjp(self, R_bar, U=None, want_U=True, want_xy=True, fp32=False):
         """(U_bar, x_bar, y_bar) = (dR/dU, dR/dx, dR/dy)^T R_bar at U (the
-        context's state if None); the unrequested ones are None."""
+        context's state if None); the unrequested ones are None. fp32: the
+        product in FP32 (mixed contexts)."""
         import torch
         Ub = torch.empty((4, self.n), dtype=torch.float64, device="cuda") if want_U else None
         xb = torch.empty(self.n, dtype=torch.float64, device="cuda") if want_xy else None
         yb = torch.empty_like(xb) if want_xy else None
         self._check(self._L.lskum_residual_vjp(self._ctx, _dev_ptr(U), _dev_ptr(R_bar), _dev_ptr(Ub),
-                                               _dev_ptr(xb), _dev_ptr(yb), 0))
+                                               _dev_ptr(xb), _dev_ptr(yb), LSKUM_VJP_FP32 if fp32 else 0))
         return Ub, xb, yb
 
     def step_vjp(self, U_bar_next, U=None, want_U=True, want_xy=True, U_bar=None, xy_bar=None):
@@ -383,6 +384,7 @@ class Solver:
 
 LSKUM_NOALLOC_MAX_POINTS = 131072
 LSKUM_VJP_ACCUMULATE_XY = 1
+LSKUM_VJP_FP32 = 2
 
 
 def q_derivatives_noalloc(x, y, nbr_offsets, nbr_idx, U, qx, qy, gamma=1.4, inner_iters=3,

@@ -164,3 +164,32 @@ def test_autograd_function(small):
     Ub, xb, yb = s.residual_vjp(W, _dev(U0))
     assert torch.equal(U.grad, Ub)
     assert torch.equal(xy.grad, torch.stack([xb, yb]))
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_fp32_vjp_agrees_with_fp64(small, order):
+    """The FP32 product (mixed context) against the FP64 product, entry by
+    entry relative to each output's largest entry, and by the dot-product
+    identity against the oracle. U_bar agrees to FP32 rounding amplified by
+    the stencil closures (2e-4); the coordinate cotangents carry the weight
+    cotangents R_bar . (G(q~_i) - G(q~_0)), where the FP32 flux difference
+    cancels, so they agree only to 2e-2 (use the FP64 product for them)."""
+    from paper_2403_13287_gb300.lskum import LskumError, LSKUM_ERR_ARG
+    c, mask = small
+    n = c["n"]
+    U = smooth_state(c, MACH, AOA, amp=0.05, seed=12)
+    Rb = np.random.default_rng(40 + order).standard_normal((4, n))
+    s64 = _solver(c, order=order, inner_iters=3, reorder=1)
+    s32 = _solver(c, order=order, inner_iters=3, reorder=1, precision=1)
+    a = [t.cpu().numpy() for t in s64.residual_vjp(_dev(Rb), _dev(U))]
+    b = [t.cpu().numpy() for t in s32.residual_vjp(_dev(Rb), _dev(U), fp32=True)]
+    for x, y, tol in zip(a, b, (2e-4, 2e-2, 2e-2)):
+        scale = np.abs(x).max(axis=-1, keepdims=True)
+        assert np.all(np.abs(x - y) <= tol * scale), np.max(np.abs(x - y) / scale)
+    vU = np.random.default_rng(3).standard_normal((4, n)) * np.abs(U)
+    Jv = lskum_jvp.jvp(c, mask, U, dU=vU, order=order, inner=3)
+    ref = np.sum(Rb * Jv)
+    assert abs(np.sum(b[0] * vU) - ref) <= 2e-4 * np.sum(np.abs(Rb * Jv))
+    with pytest.raises(LskumError) as e:
+        s64.residual_vjp(_dev(Rb), _dev(U), fp32=True)
+    assert e.value.status == LSKUM_ERR_ARG
