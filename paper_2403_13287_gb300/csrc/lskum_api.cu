@@ -39,7 +39,7 @@ struct lskum_ctx {
     uint8_t *flag = nullptr, *mask = nullptr;
     double *dmin = nullptr;
     int32_t *off = nullptr, *idx = nullptr, *off_in = nullptr;
-    double2 *lsw = nullptr, *fxw = nullptr;
+    double2 *lsw = nullptr, *fxw = nullptr, *hd = nullptr;
     int32_t *perm = nullptr, *inv = nullptr;
     int32_t *wall = nullptr;
     double *wall_ds = nullptr;
@@ -124,7 +124,7 @@ struct lskum_ctx {
     {
         DevGeom g;
         g.n = n; g.xy = xy; g.nrm = nrm; g.flag = flag; g.dmin = dmin;
-        g.off = off; g.idx = idx; g.mask = mask; g.lsw = lsw; g.fxw = fxw;
+        g.off = off; g.idx = idx; g.mask = mask; g.lsw = lsw; g.fxw = fxw; g.hd = hd;
         return g;
     }
 
@@ -491,6 +491,10 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     const int bad_init[2] = {0, 0x7fffffff};
     CK(c, cudaMemcpyAsync(bad, bad_init, sizeof bad_init, cudaMemcpyHostToDevice, s));
     LAUNCH(c, launch_geometry(n, c->xy, c->nrm, c->flag, c->off, c->idx, c->mask, c->lsw, c->fxw, c->dmin, bad, s));
+    if (!c->mixed) {
+        CK(c, dalloc(c, &c->hd, std::max<int64_t>(nnz, 1)));
+        LAUNCH(c, launch_half_offsets(n, c->xy, c->off, c->idx, c->hd, s));
+    }
     int bad_h[2];
     CK(c, cudaMemcpyAsync(bad_h, bad, sizeof bad_h, cudaMemcpyDeviceToHost, s));
     c->perm_h.resize(n);

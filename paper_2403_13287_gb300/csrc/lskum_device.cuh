@@ -7,6 +7,8 @@
 //   mask[e]             uint8     sub-stencil bits (x+ 1, x- 2, y+ 4, y- 8)
 //   lsw[e]              double2   full-stencil least-squares weights (a_x, a_y):
 //                                 grad f(P_0) = sum_e (a_x, a_y)_e (f_i - f_0)  (E9)
+//   hd[e]               double2   (P_i - P_0)/2 (FP64 contexts): the half offset of
+//                                 the E14 reconstruction and correction terms
 //   fxw[e]              double2   sub-stencil weights (w_s, w_n): the edge's
 //                                 coefficient in dG/ds of its x+- sub-stencil and
 //                                 in dG/dn of its y+- sub-stencil (E11)
@@ -40,6 +42,7 @@ struct DevGeom {
     const uint8_t *__restrict__ mask;
     const double2 *__restrict__ lsw;
     const double2 *__restrict__ fxw;
+    const double2 *__restrict__ hd;  // FP64 contexts: per edge (P_i - P_0)/2, or nullptr
 };
 
 // Free-stream and gas constants handed to every kernel.

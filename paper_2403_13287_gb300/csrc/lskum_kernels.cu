@@ -55,10 +55,15 @@ __global__ void __launch_bounds__(128) k_qgrad(DevGeom g, const double *__restri
             // the previous iterate at P_0 is taken out of the sum below
             double gi[8];
             load8(qg_old, i, gi);
-            const double2 xyi = g.xy[i];
-            const double dx = xyi.x - xy0.x, dy = xyi.y - xy0.y;
+            double2 h;
+            if (g.hd) {
+                h = g.hd[e];
+            } else {
+                const double2 xyi = g.xy[i];
+                h = make_double2(0.5 * (xyi.x - xy0.x), 0.5 * (xyi.y - xy0.y));
+            }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) dq[k] = dq[k] - 0.5 * (dx * gi[k] + dy * gi[4 + k]);
+            for (int k = 0; k < 4; ++k) dq[k] = fma(-h.y, gi[4 + k], fma(-h.x, gi[k], dq[k]));
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -164,14 +169,19 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
 #pragma unroll
             for (int k = 0; k < 4; ++k) qt0[k] = q0[k];
             if (second) {
-                const double2 xyi = g.xy[i];
-                const double dx = xyi.x - xy0.x, dy = xyi.y - xy0.y;
+                double2 h;
+                if (g.hd) {
+                    h = g.hd[e];
+                } else {
+                    const double2 xyi = g.xy[i];
+                    h = make_double2(0.5 * (xyi.x - xy0.x), 0.5 * (xyi.y - xy0.y));
+                }
                 double gi[8];
                 load8(P.qg, i, gi);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    qti[k] = qti[k] - 0.5 * (dx * gi[k] + dy * gi[4 + k]);
-                    qt0[k] = qt0[k] - 0.5 * (dx * g0[k] + dy * g0[4 + k]);
+                    qti[k] = fma(-h.y, gi[4 + k], fma(-h.x, gi[k], qti[k]));
+                    qt0[k] = fma(-h.y, g0[4 + k], fma(-h.x, g0[k], qt0[k]));
                 }
             }
             // equal reconstructed states have dG = 0 exactly
