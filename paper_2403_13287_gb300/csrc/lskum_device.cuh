@@ -84,10 +84,18 @@ __device__ __forceinline__ double exp_tab(double x)
     return __ldg(&kExp2Table[n & 63]) * p * two_m;
 }
 
+// a double strictly between 0 and +inf (not 0, negative, inf or NaN), tested
+// on its bit pattern (integer pipe)
+__device__ __forceinline__ bool finite_positive(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x7ff0000000000000ll;
+}
+
 __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, Prim &s)
 {
     const double beta = -0.5 * qt[3];
-    if (!(beta > 0.0)) return false;
+    if (!finite_positive(beta)) return false;
     s.rsb = rsqrt(beta);
     const double ib = s.rsb * s.rsb;       // 1/beta, so 1/q4 = -ib/2 without a division
     s.u = 0.5 * qt[1] * ib;
@@ -106,7 +114,7 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
     s.h = fma(0.5 * (gas.inv_gm1 + 1.0), ib, hu2);
     s.e2 = fma(0.5 * (gas.inv_gm1 + 0.5), ib, hu2);
     s.rsbc = s.rsb * 0.28209479177387814;  // 1/(2 sqrt(pi))
-    return isfinite(s.rho) && s.rho > 0.0;
+    return finite_positive(s.rho);
 }
 
 // erf(S) and exp(-S^2) together, from one row of a Taylor table: on the grid

@@ -46,10 +46,14 @@ __global__ void __launch_bounds__(128) k_qgrad(DevGeom g, const double *__restri
         load4(q, i, qi);
         double dq[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            dq[k] = qi[k] - q0[k];
-            qmax[k] = fmax(qmax[k], qi[k]);
-            qmin[k] = fmin(qmin[k], qi[k]);
+        for (int k = 0; k < 4; ++k) dq[k] = qi[k] - q0[k];
+        if (limit) {
+            // stencil extrema for the limiter (only its pass needs them)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                qmax[k] = fmax(qmax[k], qi[k]);
+                qmin[k] = fmin(qmin[k], qi[k]);
+            }
         }
         if (inner) {
             // the previous iterate at P_0 is taken out of the sum below
@@ -161,7 +165,8 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
         const int e0 = g.off[p], e1 = g.off[p + 1];
         for (int e = e0; e < e1; ++e) {
             const double2 w = g.fxw[e];
-            if (w.x == 0.0 && w.y == 0.0) continue;
+            // weights outside every needed sub-stencil are +0 exactly: tested on the bits
+            if ((__double_as_longlong(w.x) | __double_as_longlong(w.y)) == 0) continue;
             const int i = g.idx[e];
             const uint8_t m = g.mask[e];
             double qti[4], qt0[4];
@@ -184,8 +189,13 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
                     qt0[k] = fma(-h.y, g0[4 + k], fma(-h.x, g0[k], qt0[k]));
                 }
             }
-            // equal reconstructed states have dG = 0 exactly
-            if (qti[0] == qt0[0] && qti[1] == qt0[1] && qti[2] == qt0[2] && qti[3] == qt0[3]) continue;
+            // equal reconstructed states have dG = 0 exactly (compared as bit patterns,
+            // on the integer pipe; +0 against -0 only costs a flux evaluation giving dG = 0)
+            if (((__double_as_longlong(qti[0]) ^ __double_as_longlong(qt0[0])) |
+                 (__double_as_longlong(qti[1]) ^ __double_as_longlong(qt0[1])) |
+                 (__double_as_longlong(qti[2]) ^ __double_as_longlong(qt0[2])) |
+                 (__double_as_longlong(qti[3]) ^ __double_as_longlong(qt0[3]))) == 0)
+                continue;
             Prim si, s0;
             ok &= prim_from_q(qti, P.gas, si);
             ok &= prim_from_q(qt0, P.gas, s0);

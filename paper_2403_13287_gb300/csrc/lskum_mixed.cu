@@ -165,10 +165,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
         load4f(q, i, qi);
         float dq[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            dq[k] = qi[k] - q0[k];
-            qmax[k] = fmaxf(qmax[k], qi[k]);
-            qmin[k] = fminf(qmin[k], qi[k]);
+        for (int k = 0; k < 4; ++k) dq[k] = qi[k] - q0[k];
+        if (limit) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                qmax[k] = fmaxf(qmax[k], qi[k]);
+                qmin[k] = fminf(qmin[k], qi[k]);
+            }
         }
         if (inner) {
             float gi[8];
