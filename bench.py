@@ -131,11 +131,12 @@ def algorithmic_bytes_per_point(kernel, dbar, order, scheme, stage_avg=True):
     """Bytes each array contributes once per launch, per point (FP64 layout):
     q 32, q-derivatives 64, coordinates 16, normals 16, flag 1, dmin 8, CSR
     offset 4, and per edge: index 4, mask 1, LS weights 16 (fused kernel:
-    flux weights 16). Neighbour gathers are assumed served from cache."""
+    flux weights 16), half offsets (P_i - P_0)/2 16 (second order).
+    Neighbour gathers are assumed served from cache."""
     if kernel == "flux":
         b = 32 + 16 + 16 + 1 + 4 + dbar * (4 + 1 + 16)       # q, xy, nrm, flag, off, edges
         if order == 2:
-            b += 64                                           # own q-derivatives
+            b += 64 + dbar * 16                               # own q-derivatives, half offsets
         b += 32 + 32 + 32                                     # U^n read, U_out and q_out written
         if scheme == "rk4":
             # dt (+dmin) at stage 0, acc written at 0-2, read at 1-3
@@ -146,7 +147,7 @@ def algorithmic_bytes_per_point(kernel, dbar, order, scheme, stage_avg=True):
     if kernel == "qgrad_first":
         return 32 + 4 + dbar * (4 + 16) + 64
     if kernel == "qgrad_inner":
-        return 32 + 64 + 16 + 4 + dbar * (4 + 16) + 64
+        return 32 + 64 + 16 + 4 + dbar * (4 + 16 + 16) + 64
     raise ValueError(kernel)
 
 
@@ -180,12 +181,13 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
 
 # Per-unit figures of the FP64 fused flux kernel (ncu counters, 640k-point
 # capture, profiles/k_flux_update_fp64_naca0012_640k.md): executed FP64
-# instructions per stencil edge (DFMA + DMUL + DADD) and the flops they carry
-# (2 DFMA + DMUL + DADD); DRAM bytes per point of one full-size 2.5M launch
-# (single-pass capture, profiles/launch_list_naca0012_2p5m_fp64.md).
-FP64_INSTR_PER_EDGE_FLUX = 276.19
-FP64_FLOPS_PER_EDGE_FLUX = 424.83
-FLUX_DRAM_BYTES_PER_POINT = 466.5
+# instructions per stencil edge (every FP64 instruction, of which DFMA + DMUL +
+# DADD are 251.7) and the flops they carry (2 DFMA + DMUL + DADD); DRAM bytes
+# per point of one full-size 2.5M launch (single-pass capture,
+# profiles/launch_list_naca0012_2p5m_fp64.md).
+FP64_INSTR_PER_EDGE_FLUX = 256.09
+FP64_FLOPS_PER_EDGE_FLUX = 395.37
+FLUX_DRAM_BYTES_PER_POINT = 598.6
 # FP64 peak: ncu's DFMA unit count, 304 FP64 thread-instructions per cycle
 # (each DFMA 2 flops), at the 2070 MHz maximum SM clock
 FP64_PEAK_GINSTR = 304 * 2.070
