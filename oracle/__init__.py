@@ -76,6 +76,8 @@ def lib():
         L.orc_limit_gradients.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _p, _p]
         L.orc_forces.argtypes = [_i64, _d, _d, _d, _p, _p, _p, _p, _p, _i64, _p, _p, _p, _p]
         L.orc_solve.argtypes = ([_i64, _d] + [_p] * 8 + [_int, _int, _d, _int, _d, _d, _d, _int, _p, _p])
+        L.orc_residual_bc.argtypes = [_i64, _d] + [_p] * 8 + [_int, _int, _d, _int, _d, _d] + [_p] * 5
+        L.orc_solve_bc.argtypes = ([_i64, _d] + [_p] * 8 + [_int, _int, _d, _int, _int, _d, _d, _d, _int, _p, _p])
     return _lib
 
 
@@ -194,21 +196,22 @@ def flux_residual(cloud, mask, q, qx, qy, order=2, gamma=1.4, want_scale=False):
 
 
 def residual(cloud, mask, U, order=2, inner=3, gamma=1.4, want_scale=False, want_grad=False,
-             limiter=0.0):
-    """R(U) of the whole scheme; optional error scale and q-derivatives."""
+             limiter=0.0, boundary=0, mach=0.0, aoa_deg=0.0):
+    """R(U) of the whole scheme; optional error scale and q-derivatives.
+    boundary=1: kinetic boundary mode, mach/aoa_deg give the free stream."""
     n = cloud["n"]
     U = _f64(U)
     R = np.empty_like(U)
     sc = np.empty_like(U) if want_scale else None
     qx = np.empty_like(U) if want_grad else None
     qy = np.empty_like(U) if want_grad else None
-    _check(lib().orc_residual(n, gamma, _ptr(_f64(cloud["x"])), _ptr(_f64(cloud["y"])),
-                              _ptr(_f64(cloud["nx"])), _ptr(_f64(cloud["ny"])),
-                              _ptr(_i32(cloud["flags"])), _ptr(_i32(cloud["nbr_offsets"])),
-                              _ptr(_i32(cloud["nbr_idx"])),
-                              _ptr(np.ascontiguousarray(mask, dtype=np.uint8)),
-                              order, inner, float(limiter), _ptr(U), _ptr(R), _ptr(sc), _ptr(qx),
-                              _ptr(qy)),
+    _check(lib().orc_residual_bc(n, gamma, _ptr(_f64(cloud["x"])), _ptr(_f64(cloud["y"])),
+                                 _ptr(_f64(cloud["nx"])), _ptr(_f64(cloud["ny"])),
+                                 _ptr(_i32(cloud["flags"])), _ptr(_i32(cloud["nbr_offsets"])),
+                                 _ptr(_i32(cloud["nbr_idx"])),
+                                 _ptr(np.ascontiguousarray(mask, dtype=np.uint8)),
+                                 order, inner, float(limiter), int(boundary), float(mach), float(aoa_deg),
+                                 _ptr(U), _ptr(R), _ptr(sc), _ptr(qx), _ptr(qy)),
            "residual")
     out = [R]
     if want_scale:
@@ -284,16 +287,17 @@ def forces(cloud, U, mach, aoa_deg, gamma=1.4):
 
 
 def solve(cloud, mask, U0, n_iters, order=2, inner=3, scheme=1, cfl=0.2, mach=0.63,
-          aoa_deg=2.0, gamma=1.4, limiter=0.0):
-    """Algorithm 1 for n_iters iterations; returns (U, residue history)."""
+          aoa_deg=2.0, gamma=1.4, limiter=0.0, boundary=0):
+    """Algorithm 1 for n_iters iterations; returns (U, residue history).
+    boundary=1: kinetic boundary mode."""
     U = _f64(U0).copy()
     hist = np.zeros(n_iters)
-    _check(lib().orc_solve(cloud["n"], gamma, _ptr(_f64(cloud["x"])), _ptr(_f64(cloud["y"])),
-                           _ptr(_f64(cloud["nx"])), _ptr(_f64(cloud["ny"])),
-                           _ptr(_i32(cloud["flags"])), _ptr(_i32(cloud["nbr_offsets"])),
-                           _ptr(_i32(cloud["nbr_idx"])),
-                           _ptr(np.ascontiguousarray(mask, dtype=np.uint8)),
-                           order, inner, float(limiter), scheme, cfl, mach, aoa_deg, n_iters,
-                           _ptr(U), _ptr(hist)),
+    _check(lib().orc_solve_bc(cloud["n"], gamma, _ptr(_f64(cloud["x"])), _ptr(_f64(cloud["y"])),
+                              _ptr(_f64(cloud["nx"])), _ptr(_f64(cloud["ny"])),
+                              _ptr(_i32(cloud["flags"])), _ptr(_i32(cloud["nbr_offsets"])),
+                              _ptr(_i32(cloud["nbr_idx"])),
+                              _ptr(np.ascontiguousarray(mask, dtype=np.uint8)),
+                              order, inner, float(limiter), int(boundary), scheme, cfl, mach, aoa_deg,
+                              n_iters, _ptr(U), _ptr(hist)),
            "solve")
     return U, hist

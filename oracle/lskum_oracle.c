@@ -10,7 +10,10 @@
  * Routine names follow Algorithm 1 of the paper: q_variables, q_derivatives,
  * flux_residual, timestep, state_update, residue. Where the paper is silent
  * the reading used is stated at the routine (free stream, boundary
- * conditions, local time step, RK4, residue norm, forces).
+ * conditions, local time step, RK4, residue norm, forces). The kinetic
+ * boundary mode (orc_residual_bc / orc_solve_bc with boundary = 1) is a
+ * reading of the kinetic wall and far-field conditions the paper cites
+ * without stating them; see "Stencil members".
  *
  * Arrays of 4 components are stored component-major: A[k*n + p].
  */
@@ -183,6 +186,126 @@ void orc_euler_flux(double gamma, double rho, double un, double ut, double p, do
 }
 
 /* ------------------------------------------------------------------------ */
+/* Stencil members. In the plain boundary reading the stencil of P_0 is its */
+/* list of neighbours. The kinetic boundary mode (not in the paper, which   */
+/* cites kinetic wall and far-field conditions without stating them;       */
+/* reading) also gives a wall or far-field point the mirror image of every  */
+/* neighbour across its tangent line: local offsets (ds, -dn), so the x+-   */
+/* membership is kept and y+ and y- swap. A neighbour on the line (dn = 0)  */
+/* is its own image and adds none. At a wall point the image carries the    */
+/* specularly reflected gas: the velocity part (q1, q2) of q and every      */
+/* gradient reflected across the line, so that the image of a field is     */
+/* q*(P_0 + M d) = Mq(P_0 + d), M = I - 2 n n^T. At a far-field point the   */
+/* image carries the free stream with zero gradient (the gas outside the    */
+/* domain). The point is then treated by the interior formulas (all four    */
+/* sub-stencils, the same least squares, limiter and reconstruction) on the */
+/* augmented stencil.                                                       */
+/* ------------------------------------------------------------------------ */
+#define ORC_IMG_NONE 0
+#define ORC_IMG_WALL 1
+#define ORC_IMG_FAR 2
+
+typedef struct {
+    int64_t n;
+    const double *x, *y;
+    const double *nx, *ny;   /* NULL: no frame (gradients only, plain mode) */
+    const int32_t *flags;    /* NULL: plain mode */
+    const int32_t *off, *idx;
+    const uint8_t *mask;     /* NULL: no sub-stencils (gradients only) */
+    int kinetic;             /* 1: kinetic boundary mode */
+    double qinf[4];          /* q of the free stream (kinetic mode) */
+} orc_geom;
+
+typedef struct {
+    int64_t i;       /* the neighbour, or the neighbour whose image this is */
+    int image;       /* ORC_IMG_* */
+    double dx, dy;   /* offset from P_0, global frame */
+    double ds, dn;   /* offset from P_0, frame of P_0 */
+    uint8_t mask;    /* sub-stencils */
+} orc_member;
+
+static int64_t max_degree(const orc_geom *g)
+{
+    int64_t m = 0;
+    for (int64_t p = 0; p < g->n; ++p)
+        if (g->off[p + 1] - g->off[p] > m) m = g->off[p + 1] - g->off[p];
+    return m;
+}
+
+static int is_kinetic_boundary(const orc_geom *g, int64_t p)
+{
+    return g->kinetic && (g->flags[p] == ORC_WALL || g->flags[p] == ORC_FARFIELD);
+}
+
+/* the members of the stencil of P_0 = p into mem[] (room for 2 x degree);
+ * returns their number: the neighbours in CSR order, then the images */
+static int64_t stencil_members(const orc_geom *g, int64_t p, orc_member *mem)
+{
+    double tx = 0.0, ty = 0.0, nnx = 0.0, nny = 0.0;
+    if (g->nx) { tx = g->ny[p]; ty = -g->nx[p]; nnx = g->nx[p]; nny = g->ny[p]; }
+    int64_t c = 0;
+    for (int64_t e = g->off[p]; e < g->off[p + 1]; ++e) {
+        orc_member *m = &mem[c++];
+        m->i = g->idx[e];
+        m->image = ORC_IMG_NONE;
+        m->dx = g->x[m->i] - g->x[p];
+        m->dy = g->y[m->i] - g->y[p];
+        m->ds = m->dx * tx + m->dy * ty;
+        m->dn = m->dx * nnx + m->dy * nny;
+        m->mask = g->mask ? g->mask[e] : 0;
+    }
+    if (!is_kinetic_boundary(g, p)) return c;
+    const int kind = g->flags[p] == ORC_WALL ? ORC_IMG_WALL : ORC_IMG_FAR;
+    const int64_t nr = c;
+    for (int64_t j = 0; j < nr; ++j) {
+        const orc_member *r = &mem[j];
+        if (r->dn == 0.0) continue;
+        orc_member *m = &mem[c++];
+        m->i = r->i;
+        m->image = kind;
+        m->dx = r->dx - 2.0 * r->dn * nnx;
+        m->dy = r->dy - 2.0 * r->dn * nny;
+        m->ds = r->ds;
+        m->dn = -r->dn;
+        m->mask = (uint8_t)((r->mask & (ORC_XPOS | ORC_XNEG)) | ((r->mask & ORC_YPOS) ? ORC_YNEG : 0u) |
+                            ((r->mask & ORC_YNEG) ? ORC_YPOS : 0u));
+    }
+    return c;
+}
+
+/* reflect the vector (a, b) across the line with unit normal (nx, ny) */
+static void reflect(double *a, double *b, double nx, double ny)
+{
+    double c = *a * nx + *b * ny;
+    *a = *a - 2.0 * c * nx;
+    *b = *b - 2.0 * c * ny;
+}
+
+/* q and its gradient (nullable inputs give zero) carried by a member of the
+ * stencil of P_0 = p */
+static void member_state(const orc_geom *g, int64_t p, const orc_member *m, const double *q,
+                         const double *qx, const double *qy, double qi[4], double gx[4], double gy[4])
+{
+    const int64_t n = g->n;
+    if (m->image == ORC_IMG_FAR) {
+        for (int k = 0; k < 4; ++k) { qi[k] = g->qinf[k]; gx[k] = 0.0; gy[k] = 0.0; }
+        return;
+    }
+    for (int k = 0; k < 4; ++k) {
+        qi[k] = q[k * n + m->i];
+        gx[k] = qx ? qx[k * n + m->i] : 0.0;
+        gy[k] = qy ? qy[k * n + m->i] : 0.0;
+    }
+    if (m->image == ORC_IMG_WALL) {
+        const double nx = g->nx[p], ny = g->ny[p];
+        reflect(&qi[1], &qi[2], nx, ny);                              /* velocity part of q */
+        for (int k = 0; k < 4; ++k) reflect(&gx[k], &gy[k], nx, ny);  /* d/dx of the image */
+        reflect(&gx[1], &gx[2], nx, ny);                              /* and its velocity part */
+        reflect(&gy[1], &gy[2], nx, ny);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* q_derivatives(): E15 with the modified variables of E14, solved by inner */
 /* iterations. Iteration 0 is the first-order least-squares gradient (E9    */
 /* with dq in place of dF~); each of the `inner` iterations that follow     */
@@ -194,26 +317,27 @@ void orc_euler_flux(double gamma, double rho, double un, double ut, double p, do
 /* squares gradient is rotation-equivariant, so this is done in the global  */
 /* (x, y) frame and qx, qy are global-frame derivatives.                    */
 /* ------------------------------------------------------------------------ */
-int orc_q_derivatives_pass(int64_t n, const double *x, const double *y,
-                            const int32_t *off, const int32_t *idx,
-                            const double *q, const double *qx_old, const double *qy_old,
-                            double *qx, double *qy)
+static int q_derivatives_pass(const orc_geom *g, const double *q, const double *qx_old,
+                              const double *qy_old, double *qx, double *qy, orc_member *mem)
 {
+    const int64_t n = g->n;
     for (int64_t p = 0; p < n; ++p) {
         double sxx = 0.0, sxy = 0.0, syy = 0.0;
         double sxq[4] = {0, 0, 0, 0}, syq[4] = {0, 0, 0, 0};
-        for (int64_t e = off[p]; e < off[p + 1]; ++e) {
-            int64_t i = idx[e];
-            double dx = x[i] - x[p];
-            double dy = y[i] - y[p];
+        const int64_t cnt = stencil_members(g, p, mem);
+        for (int64_t j = 0; j < cnt; ++j) {
+            const orc_member *m = &mem[j];
+            double dx = m->dx, dy = m->dy;
+            double qi[4], gxi[4], gyi[4];
+            member_state(g, p, m, q, qx_old, qy_old, qi, gxi, gyi);
             sxx += dx * dx;
             sxy += dx * dy;
             syy += dy * dy;
             for (int k = 0; k < 4; ++k) {
-                double dq = q[k * n + i] - q[k * n + p];
+                double dq = qi[k] - q[k * n + p];
                 if (qx_old) {
-                    dq = dq - 0.5 * (dx * (qx_old[k * n + i] - qx_old[k * n + p])
-                                     + dy * (qy_old[k * n + i] - qy_old[k * n + p]));
+                    dq = dq - 0.5 * (dx * (gxi[k] - qx_old[k * n + p])
+                                     + dy * (gyi[k] - qy_old[k * n + p]));
                 }
                 sxq[k] += dx * dq;
                 syq[k] += dy * dq;
@@ -229,23 +353,55 @@ int orc_q_derivatives_pass(int64_t n, const double *x, const double *y,
     return ORC_OK;
 }
 
+static int q_derivatives(const orc_geom *g, const double *q, int inner, double *qx, double *qy)
+{
+    orc_member *mem = (orc_member *)malloc((size_t)(2 * max_degree(g) + 1) * sizeof(orc_member));
+    if (!mem) return -1;
+    int rc = q_derivatives_pass(g, q, NULL, NULL, qx, qy, mem);
+    size_t bytes = (size_t)4 * (size_t)g->n * sizeof(double);
+    double *ox = NULL, *oy = NULL;
+    if (rc == ORC_OK && inner > 0) {
+        ox = (double *)malloc(bytes);
+        oy = (double *)malloc(bytes);
+        if (!ox || !oy) rc = -1;
+    }
+    for (int it = 0; it < inner && rc == ORC_OK; ++it) {
+        memcpy(ox, qx, bytes);
+        memcpy(oy, qy, bytes);
+        rc = q_derivatives_pass(g, q, ox, oy, qx, qy, mem);
+    }
+    free(ox); free(oy); free(mem);
+    return rc;
+}
+
+static orc_geom plain_geom(int64_t n, const double *x, const double *y, const int32_t *off,
+                           const int32_t *idx)
+{
+    orc_geom g;
+    memset(&g, 0, sizeof g);
+    g.n = n; g.x = x; g.y = y; g.off = off; g.idx = idx;
+    return g;
+}
+
+int orc_q_derivatives_pass(int64_t n, const double *x, const double *y,
+                           const int32_t *off, const int32_t *idx,
+                           const double *q, const double *qx_old, const double *qy_old,
+                           double *qx, double *qy)
+{
+    orc_geom g = plain_geom(n, x, y, off, idx);
+    orc_member *mem = (orc_member *)malloc((size_t)(2 * max_degree(&g) + 1) * sizeof(orc_member));
+    if (!mem) return -1;
+    int rc = q_derivatives_pass(&g, q, qx_old, qy_old, qx, qy, mem);
+    free(mem);
+    return rc;
+}
+
 int orc_q_derivatives(int64_t n, const double *x, const double *y,
                       const int32_t *off, const int32_t *idx,
                       const double *q, int inner, double *qx, double *qy)
 {
-    int rc = orc_q_derivatives_pass(n, x, y, off, idx, q, NULL, NULL, qx, qy);
-    if (rc) return rc;
-    if (inner <= 0) return ORC_OK;
-    size_t bytes = (size_t)4 * (size_t)n * sizeof(double);
-    double *ox = (double *)malloc(bytes), *oy = (double *)malloc(bytes);
-    if (!ox || !oy) { free(ox); free(oy); return -1; }
-    for (int it = 0; it < inner && rc == ORC_OK; ++it) {
-        memcpy(ox, qx, bytes);
-        memcpy(oy, qy, bytes);
-        rc = orc_q_derivatives_pass(n, x, y, off, idx, q, ox, oy, qx, qy);
-    }
-    free(ox); free(oy);
-    return rc;
+    orc_geom g = plain_geom(n, x, y, off, idx);
+    return q_derivatives(&g, q, inner, qx, qy);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -264,35 +420,39 @@ static double venkat(double D, double d, double eps2)
     return (D * D + eps2 + 2.0 * D * d) / (D * D + 2.0 * d * d + D * d + eps2);
 }
 
-int orc_limit_gradients(int64_t n, const double *x, const double *y, const int32_t *off,
-                        const int32_t *idx, const double *q, double K, double *qx, double *qy)
+static int limit_gradients(const orc_geom *g, const double *q, double K, double *qx, double *qy)
 {
+    const int64_t n = g->n;
+    orc_member *mem = (orc_member *)malloc((size_t)(2 * max_degree(g) + 1) * sizeof(orc_member));
+    if (!mem) return -1;
     for (int64_t p = 0; p < n; ++p) {
+        const int64_t cnt = stencil_members(g, p, mem);
         double h = INFINITY;
-        for (int64_t e = off[p]; e < off[p + 1]; ++e) {
-            int64_t i = idx[e];
-            double d = sqrt((x[i] - x[p]) * (x[i] - x[p]) + (y[i] - y[p]) * (y[i] - y[p]));
+        for (int64_t j = 0; j < cnt; ++j) {
+            double d = sqrt(mem[j].dx * mem[j].dx + mem[j].dy * mem[j].dy);
             if (d < h) h = d;
         }
         double eps2 = (K * h) * (K * h) * (K * h);
-        for (int k = 0; k < 4; ++k) {
-            double q0 = q[k * n + p], qmax = q0, qmin = q0;
-            for (int64_t e = off[p]; e < off[p + 1]; ++e) {
-                double qi = q[k * n + idx[e]];
-                if (qi > qmax) qmax = qi;
-                if (qi < qmin) qmin = qi;
+        double qmax[4], qmin[4];
+        for (int k = 0; k < 4; ++k) qmax[k] = qmin[k] = q[k * n + p];
+        for (int64_t j = 0; j < cnt; ++j) {
+            double qi[4], gxi[4], gyi[4];
+            member_state(g, p, &mem[j], q, NULL, NULL, qi, gxi, gyi);
+            for (int k = 0; k < 4; ++k) {
+                if (qi[k] > qmax[k]) qmax[k] = qi[k];
+                if (qi[k] < qmin[k]) qmin[k] = qi[k];
             }
+        }
+        for (int k = 0; k < 4; ++k) {
+            double q0 = q[k * n + p];
             double phi = 1.0;
-            for (int64_t e = off[p]; e < off[p + 1]; ++e) {
-                int64_t i = idx[e];
-                double dx = x[i] - x[p];
-                double dy = y[i] - y[p];
-                double half = 0.5 * (dx * qx[k * n + p] + dy * qy[k * n + p]);
+            for (int64_t j = 0; j < cnt; ++j) {
+                double half = 0.5 * (mem[j].dx * qx[k * n + p] + mem[j].dy * qy[k * n + p]);
                 for (int sgn = -1; sgn <= 1; sgn += 2) {
                     double d = sgn * half;
                     double f = 1.0;
-                    if (d > 0.0) f = venkat(qmax - q0, d, eps2);
-                    else if (d < 0.0) f = venkat(qmin - q0, d, eps2);
+                    if (d > 0.0) f = venkat(qmax[k] - q0, d, eps2);
+                    else if (d < 0.0) f = venkat(qmin[k] - q0, d, eps2);
                     if (f < phi) phi = f;
                 }
             }
@@ -300,7 +460,15 @@ int orc_limit_gradients(int64_t n, const double *x, const double *y, const int32
             qy[k * n + p] *= phi;
         }
     }
+    free(mem);
     return ORC_OK;
+}
+
+int orc_limit_gradients(int64_t n, const double *x, const double *y, const int32_t *off,
+                        const int32_t *idx, const double *q, double K, double *qx, double *qy)
+{
+    orc_geom g = plain_geom(n, x, y, off, idx);
+    return limit_gradients(&g, q, K, qx, qy);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -318,6 +486,8 @@ int orc_limit_gradients(int64_t n, const double *x, const double *y, const int32
 /* back to (x, y).                                                          */
 /* Boundary reading (the paper states none): wall points (n into the fluid) */
 /* drop dGn+/dn, which has no upwind points; far-field points get R = 0.    */
+/* In the kinetic boundary mode both use all four terms on the stencil     */
+/* augmented by their mirror images (stencil members above).               */
 /* If `scale` is not NULL it receives, per point and component, the sum    */
 /* over the terms of |LS weight_i| (|G(q~_i)| + |G(q~_0)|): the magnitude   */
 /* of what is summed before cancellation (used to scale rounding tests).    */
@@ -340,43 +510,56 @@ static void frame_split_flux(double gamma, const double prim[4], double tx, doub
     }
 }
 
-int orc_flux_residual(int64_t n, double gamma,
-                      const double *x, const double *y, const double *nx, const double *ny,
-                      const int32_t *flags, const int32_t *off, const int32_t *idx,
-                      const uint8_t *mask, const double *q, const double *qx,
-                      const double *qy, int order, double *R, double *scale)
+/* q~ of E14 at a member (order 2; order 1: q~ = q) and at P_0 towards it */
+static void reconstruct(const orc_geom *g, int64_t p, const orc_member *m, const double *q,
+                        const double *qx, const double *qy, int order, double qt_i[4], double qt_0[4])
+{
+    const int64_t n = g->n;
+    double qi[4], gxi[4], gyi[4];
+    member_state(g, p, m, q, qx, qy, qi, gxi, gyi);
+    for (int k = 0; k < 4; ++k) {
+        if (order == 2) {
+            qt_i[k] = qi[k] - 0.5 * (m->dx * gxi[k] + m->dy * gyi[k]);
+            qt_0[k] = q[k * n + p] - 0.5 * (m->dx * qx[k * n + p] + m->dy * qy[k * n + p]);
+        } else {
+            qt_i[k] = qi[k];
+            qt_0[k] = q[k * n + p];
+        }
+    }
+}
+
+static int flux_residual(const orc_geom *g, double gamma, const double *q, const double *qx,
+                         const double *qy, int order, double *R, double *scale)
 {
     static const uint8_t sub_bit[4] = {ORC_XPOS, ORC_XNEG, ORC_YPOS, ORC_YNEG};
     static const int sub_dir[4] = {0, 0, 1, 1};
     static const int sub_sign[4] = {+1, -1, +1, -1};
-    for (int64_t p = 0; p < n; ++p) {
+    const int64_t n = g->n;
+    orc_member *mem = (orc_member *)malloc((size_t)(2 * max_degree(g) + 1) * sizeof(orc_member));
+    if (!mem) return -1;
+    int rc = ORC_OK;
+    for (int64_t p = 0; p < n && rc == ORC_OK; ++p) {
         double Rl[4] = {0, 0, 0, 0}, Sc[4] = {0, 0, 0, 0};
-        int flag = flags[p];
-        if (flag != ORC_FARFIELD) {
-            double tx = ny[p], ty = -nx[p], nnx = nx[p], nny = ny[p];
-            for (int sub = 0; sub < 4; ++sub) {
-                if (flag == ORC_WALL && sub == 2) continue; /* no dGn+/dn at the wall */
+        int flag = g->flags[p];
+        int kinetic = is_kinetic_boundary(g, p);
+        if (flag != ORC_FARFIELD || kinetic) {
+            double tx = g->ny[p], ty = -g->nx[p], nnx = g->nx[p], nny = g->ny[p];
+            const int64_t cnt = stencil_members(g, p, mem);
+            for (int sub = 0; sub < 4 && rc == ORC_OK; ++sub) {
+                /* plain reading: no dGn+/dn at the wall */
+                if (flag == ORC_WALL && !kinetic && sub == 2) continue;
                 double sss = 0.0, ssn = 0.0, snn = 0.0;
                 double ssG[4] = {0, 0, 0, 0}, snG[4] = {0, 0, 0, 0};
-                for (int64_t e = off[p]; e < off[p + 1]; ++e) {
-                    if (!(mask[e] & sub_bit[sub])) continue;
-                    int64_t i = idx[e];
-                    double dx = x[i] - x[p];
-                    double dy = y[i] - y[p];
-                    double ds = dx * tx + dy * ty;
-                    double dn = dx * nnx + dy * nny;
+                for (int64_t j = 0; j < cnt; ++j) {
+                    const orc_member *m = &mem[j];
+                    if (!(m->mask & sub_bit[sub])) continue;
+                    double ds = m->ds, dn = m->dn;
                     double qt_i[4], qt_0[4], pr_i[4], pr_0[4], Gi[4], G0[4];
-                    for (int k = 0; k < 4; ++k) {
-                        if (order == 2) {
-                            qt_i[k] = q[k * n + i] - 0.5 * (dx * qx[k * n + i] + dy * qy[k * n + i]);
-                            qt_0[k] = q[k * n + p] - 0.5 * (dx * qx[k * n + p] + dy * qy[k * n + p]);
-                        } else {
-                            qt_i[k] = q[k * n + i];
-                            qt_0[k] = q[k * n + p];
-                        }
+                    reconstruct(g, p, m, q, qx, qy, order, qt_i, qt_0);
+                    if (!prim_from_q(gamma, qt_i, pr_i) || !prim_from_q(gamma, qt_0, pr_0)) {
+                        rc = ORC_ERR_NONPHYSICAL;
+                        break;
                     }
-                    if (!prim_from_q(gamma, qt_i, pr_i) || !prim_from_q(gamma, qt_0, pr_0))
-                        return ORC_ERR_NONPHYSICAL;
                     frame_split_flux(gamma, pr_i, tx, ty, nnx, nny, sub_dir[sub], sub_sign[sub], Gi);
                     frame_split_flux(gamma, pr_0, tx, ty, nnx, nny, sub_dir[sub], sub_sign[sub], G0);
                     sss += ds * ds;
@@ -388,8 +571,9 @@ int orc_flux_residual(int64_t n, double gamma,
                         snG[k] += dn * dG;
                     }
                 }
+                if (rc) break;
                 double det = sss * snn - ssn * ssn;
-                if (!(det > ORC_DET_EPS * sss * snn)) return ORC_ERR_DEGENERATE;
+                if (!(det > ORC_DET_EPS * sss * snn)) { rc = ORC_ERR_DEGENERATE; break; }
                 for (int k = 0; k < 4; ++k) {
                     double d;
                     if (sub_dir[sub] == 0) d = (snn * ssG[k] - ssn * snG[k]) / det;
@@ -397,25 +581,14 @@ int orc_flux_residual(int64_t n, double gamma,
                     Rl[k] += d;
                 }
                 if (scale) {
-                    for (int64_t e = off[p]; e < off[p + 1]; ++e) {
-                        if (!(mask[e] & sub_bit[sub])) continue;
-                        int64_t i = idx[e];
-                        double dx = x[i] - x[p];
-                        double dy = y[i] - y[p];
-                        double ds = dx * tx + dy * ty;
-                        double dn = dx * nnx + dy * nny;
+                    for (int64_t j = 0; j < cnt; ++j) {
+                        const orc_member *m = &mem[j];
+                        if (!(m->mask & sub_bit[sub])) continue;
+                        double ds = m->ds, dn = m->dn;
                         double w = (sub_dir[sub] == 0) ? (snn * ds - ssn * dn) / det
                                                        : (sss * dn - ssn * ds) / det;
                         double qt_i[4], qt_0[4], pr_i[4], pr_0[4], Gi[4], G0[4];
-                        for (int k = 0; k < 4; ++k) {
-                            if (order == 2) {
-                                qt_i[k] = q[k * n + i] - 0.5 * (dx * qx[k * n + i] + dy * qy[k * n + i]);
-                                qt_0[k] = q[k * n + p] - 0.5 * (dx * qx[k * n + p] + dy * qy[k * n + p]);
-                            } else {
-                                qt_i[k] = q[k * n + i];
-                                qt_0[k] = q[k * n + p];
-                            }
-                        }
+                        reconstruct(g, p, m, q, qx, qy, order, qt_i, qt_0);
                         prim_from_q(gamma, qt_i, pr_i);
                         prim_from_q(gamma, qt_0, pr_0);
                         frame_split_flux(gamma, pr_i, tx, ty, nnx, nny, sub_dir[sub], sub_sign[sub], Gi);
@@ -426,10 +599,10 @@ int orc_flux_residual(int64_t n, double gamma,
             }
         }
         /* rotate the momentum components from (s, n) back to (x, y) */
-        double tx = ny[p], ty = -nx[p];
+        double tx = g->ny[p], ty = -g->nx[p];
         R[0 * n + p] = Rl[0];
-        R[1 * n + p] = Rl[1] * tx + Rl[2] * nx[p];
-        R[2 * n + p] = Rl[1] * ty + Rl[2] * ny[p];
+        R[1 * n + p] = Rl[1] * tx + Rl[2] * g->nx[p];
+        R[2 * n + p] = Rl[1] * ty + Rl[2] * g->ny[p];
         R[3 * n + p] = Rl[3];
         if (scale) {
             scale[0 * n + p] = Sc[0];
@@ -438,7 +611,19 @@ int orc_flux_residual(int64_t n, double gamma,
             scale[3 * n + p] = Sc[3];
         }
     }
-    return ORC_OK;
+    free(mem);
+    return rc;
+}
+
+int orc_flux_residual(int64_t n, double gamma,
+                      const double *x, const double *y, const double *nx, const double *ny,
+                      const int32_t *flags, const int32_t *off, const int32_t *idx,
+                      const uint8_t *mask, const double *q, const double *qx,
+                      const double *qy, int order, double *R, double *scale)
+{
+    orc_geom g = plain_geom(n, x, y, off, idx);
+    g.nx = nx; g.ny = ny; g.flags = flags; g.mask = mask;
+    return flux_residual(&g, gamma, q, qx, qy, order, R, scale);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -480,16 +665,17 @@ void orc_freestream(double gamma, double mach, double aoa_deg, double U[4])
 }
 
 /* boundary treatment after every update (reading): wall points lose their
- * normal momentum, far-field points are held at the free stream */
+ * normal momentum, far-field points are held at the free stream (plain
+ * mode) or updated like the other points (kinetic boundary mode) */
 static void apply_boundary(int64_t n, const int32_t *flags, const double *nx,
-                           const double *ny, const double Uinf[4], double *U)
+                           const double *ny, const double Uinf[4], int kinetic, double *U)
 {
     for (int64_t p = 0; p < n; ++p) {
         if (flags[p] == ORC_WALL) {
             double mn = U[1 * n + p] * nx[p] + U[2 * n + p] * ny[p];
             U[1 * n + p] = U[1 * n + p] - mn * nx[p];
             U[2 * n + p] = U[2 * n + p] - mn * ny[p];
-        } else if (flags[p] == ORC_FARFIELD) {
+        } else if (flags[p] == ORC_FARFIELD && !kinetic) {
             for (int k = 0; k < 4; ++k) U[k * n + p] = Uinf[k];
         }
     }
@@ -511,9 +697,9 @@ double orc_residue(int64_t n, const double *R)
 typedef int (*orc_residual_fn)(const double *U, double *R, void *user);
 
 /* E16, forward Euler with the local time step: U^{n+1} = U^n - dt R(U^n) */
-int orc_euler_step(int64_t n, const int32_t *flags, const double *nx, const double *ny,
-                   const double Uinf[4], const double *dt, double *U,
-                   orc_residual_fn res, void *user, double *R0_out)
+static int euler_step(int64_t n, const int32_t *flags, const double *nx, const double *ny,
+                      const double Uinf[4], int kinetic, const double *dt, double *U,
+                      orc_residual_fn res, void *user, double *R0_out)
 {
     double *R = (double *)malloc((size_t)4 * n * sizeof(double));
     if (!R) return -1;
@@ -522,11 +708,18 @@ int orc_euler_step(int64_t n, const int32_t *flags, const double *nx, const doub
         for (int k = 0; k < 4; ++k)
             for (int64_t p = 0; p < n; ++p)
                 U[k * n + p] = U[k * n + p] - dt[p] * R[k * n + p];
-        apply_boundary(n, flags, nx, ny, Uinf, U);
+        apply_boundary(n, flags, nx, ny, Uinf, kinetic, U);
         if (R0_out) memcpy(R0_out, R, (size_t)4 * n * sizeof(double));
     }
     free(R);
     return rc;
+}
+
+int orc_euler_step(int64_t n, const int32_t *flags, const double *nx, const double *ny,
+                   const double Uinf[4], const double *dt, double *U,
+                   orc_residual_fn res, void *user, double *R0_out)
+{
+    return euler_step(n, flags, nx, ny, Uinf, 0, dt, U, res, user, R0_out);
 }
 
 /* Classical four-stage Runge-Kutta with the local dt frozen at U^n (not in
@@ -534,9 +727,9 @@ int orc_euler_step(int64_t n, const int32_t *flags, const double *nx, const doub
  *   U1 = U^n - dt/2 R(U^n), U2 = U^n - dt/2 R(U1), U3 = U^n - dt R(U2),
  *   U^{n+1} = U^n - dt/6 (R(U^n) + 2 R(U1) + 2 R(U2) + R(U3)),
  * the boundary treatment applied after every stage. */
-int orc_rk4_step(int64_t n, const int32_t *flags, const double *nx, const double *ny,
-                 const double Uinf[4], const double *dt, double *U,
-                 orc_residual_fn res, void *user, double *R0_out)
+static int rk4_step(int64_t n, const int32_t *flags, const double *nx, const double *ny,
+                    const double Uinf[4], int kinetic, const double *dt, double *U,
+                    orc_residual_fn res, void *user, double *R0_out)
 {
     size_t bytes = (size_t)4 * n * sizeof(double);
     double *Un = (double *)malloc(bytes), *Us = (double *)malloc(bytes);
@@ -549,17 +742,17 @@ int orc_rk4_step(int64_t n, const int32_t *flags, const double *nx, const double
     if (rc) goto done;
     for (int k = 0; k < 4; ++k)
         for (int64_t p = 0; p < n; ++p) Us[k * n + p] = Un[k * n + p] - 0.5 * dt[p] * R0[k * n + p];
-    apply_boundary(n, flags, nx, ny, Uinf, Us);
+    apply_boundary(n, flags, nx, ny, Uinf, kinetic, Us);
     rc = res(Us, R1, user);
     if (rc) goto done;
     for (int k = 0; k < 4; ++k)
         for (int64_t p = 0; p < n; ++p) Us[k * n + p] = Un[k * n + p] - 0.5 * dt[p] * R1[k * n + p];
-    apply_boundary(n, flags, nx, ny, Uinf, Us);
+    apply_boundary(n, flags, nx, ny, Uinf, kinetic, Us);
     rc = res(Us, R2, user);
     if (rc) goto done;
     for (int k = 0; k < 4; ++k)
         for (int64_t p = 0; p < n; ++p) Us[k * n + p] = Un[k * n + p] - dt[p] * R2[k * n + p];
-    apply_boundary(n, flags, nx, ny, Uinf, Us);
+    apply_boundary(n, flags, nx, ny, Uinf, kinetic, Us);
     rc = res(Us, R3, user);
     if (rc) goto done;
     for (int k = 0; k < 4; ++k)
@@ -567,11 +760,18 @@ int orc_rk4_step(int64_t n, const int32_t *flags, const double *nx, const double
             int64_t a = k * n + p;
             U[a] = Un[a] - dt[p] / 6.0 * (R0[a] + 2.0 * R1[a] + 2.0 * R2[a] + R3[a]);
         }
-    apply_boundary(n, flags, nx, ny, Uinf, U);
+    apply_boundary(n, flags, nx, ny, Uinf, kinetic, U);
     if (R0_out) memcpy(R0_out, R0, bytes);
 done:
     free(Un); free(Us); free(R0); free(R1); free(R2); free(R3);
     return rc;
+}
+
+int orc_rk4_step(int64_t n, const int32_t *flags, const double *nx, const double *ny,
+                 const double Uinf[4], const double *dt, double *U,
+                 orc_residual_fn res, void *user, double *R0_out)
+{
+    return rk4_step(n, flags, nx, ny, Uinf, 0, dt, U, res, user, R0_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -579,11 +779,8 @@ done:
 /* flux_residual (Algorithm 1).                                             */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    int64_t n;
+    orc_geom g;
     double gamma;
-    const double *x, *y, *nx, *ny;
-    const int32_t *flags, *off, *idx;
-    const uint8_t *mask;
     int order, inner;
     double limiter_K; /* > 0: Venkatakrishnan limiter with this K */
     double *q, *qx, *qy;
@@ -592,25 +789,48 @@ typedef struct {
 static int scheme_residual(const double *U, double *R, void *user)
 {
     orc_scheme *s = (orc_scheme *)user;
-    int rc = orc_q_variables(s->n, s->gamma, U, s->q);
+    int rc = orc_q_variables(s->g.n, s->gamma, U, s->q);
     if (rc) return rc;
     if (s->order == 2) {
-        rc = orc_q_derivatives(s->n, s->x, s->y, s->off, s->idx, s->q, s->inner, s->qx, s->qy);
+        rc = q_derivatives(&s->g, s->q, s->inner, s->qx, s->qy);
         if (rc) return rc;
-        if (s->limiter_K > 0.0)
-            orc_limit_gradients(s->n, s->x, s->y, s->off, s->idx, s->q, s->limiter_K, s->qx, s->qy);
+        if (s->limiter_K > 0.0) limit_gradients(&s->g, s->q, s->limiter_K, s->qx, s->qy);
     }
-    return orc_flux_residual(s->n, s->gamma, s->x, s->y, s->nx, s->ny, s->flags, s->off,
-                             s->idx, s->mask, s->q, s->qx, s->qy, s->order, R, NULL);
+    return flux_residual(&s->g, s->gamma, s->q, s->qx, s->qy, s->order, R, NULL);
 }
 
-/* one residual evaluation R(U); qx, qy (nullable) receive the derivatives */
-int orc_residual(int64_t n, double gamma, const double *x, const double *y,
-                 const double *nx, const double *ny, const int32_t *flags,
-                 const int32_t *off, const int32_t *idx, const uint8_t *mask,
-                 int order, int inner, double limiter_K, const double *U, double *R,
-                 double *scale, double *qx_out, double *qy_out)
+/* q of the free stream, by the same conversion as a point held at U_inf */
+static void freestream_q(double gamma, double mach, double aoa_deg, double q[4])
 {
+    double U[4], pr[4];
+    orc_freestream(gamma, mach, aoa_deg, U);
+    prim_from_U(gamma, U, pr);
+    q_from_prim(gamma, pr, q);
+}
+
+static orc_geom scheme_geom(int64_t n, const double *x, const double *y, const double *nx,
+                            const double *ny, const int32_t *flags, const int32_t *off,
+                            const int32_t *idx, const uint8_t *mask, int boundary, double gamma,
+                            double mach, double aoa_deg)
+{
+    orc_geom g = plain_geom(n, x, y, off, idx);
+    g.nx = nx; g.ny = ny; g.flags = flags; g.mask = mask;
+    g.kinetic = boundary == 1;
+    if (g.kinetic) freestream_q(gamma, mach, aoa_deg, g.qinf);
+    return g;
+}
+
+/* one residual evaluation R(U); qx, qy (nullable) receive the derivatives.
+ * boundary: 0 plain reading, 1 kinetic boundary mode (mach and aoa_deg give
+ * the free stream of the far-field images) */
+int orc_residual_bc(int64_t n, double gamma, const double *x, const double *y,
+                    const double *nx, const double *ny, const int32_t *flags,
+                    const int32_t *off, const int32_t *idx, const uint8_t *mask,
+                    int order, int inner, double limiter_K, int boundary, double mach,
+                    double aoa_deg, const double *U, double *R, double *scale,
+                    double *qx_out, double *qy_out)
+{
+    orc_geom g = scheme_geom(n, x, y, nx, ny, flags, off, idx, mask, boundary, gamma, mach, aoa_deg);
     size_t bytes = (size_t)4 * n * sizeof(double);
     double *q = (double *)malloc(bytes), *qx = (double *)calloc(4 * (size_t)n, sizeof(double));
     double *qy = (double *)calloc(4 * (size_t)n, sizeof(double));
@@ -619,16 +839,26 @@ int orc_residual(int64_t n, double gamma, const double *x, const double *y,
     rc = orc_q_variables(n, gamma, U, q);
     if (rc) goto done;
     if (order == 2) {
-        rc = orc_q_derivatives(n, x, y, off, idx, q, inner, qx, qy);
+        rc = q_derivatives(&g, q, inner, qx, qy);
         if (rc) goto done;
-        if (limiter_K > 0.0) orc_limit_gradients(n, x, y, off, idx, q, limiter_K, qx, qy);
+        if (limiter_K > 0.0) limit_gradients(&g, q, limiter_K, qx, qy);
     }
-    rc = orc_flux_residual(n, gamma, x, y, nx, ny, flags, off, idx, mask, q, qx, qy, order, R, scale);
+    rc = flux_residual(&g, gamma, q, qx, qy, order, R, scale);
     if (qx_out) memcpy(qx_out, qx, bytes);
     if (qy_out) memcpy(qy_out, qy, bytes);
 done:
     free(q); free(qx); free(qy);
     return rc;
+}
+
+int orc_residual(int64_t n, double gamma, const double *x, const double *y,
+                 const double *nx, const double *ny, const int32_t *flags,
+                 const int32_t *off, const int32_t *idx, const uint8_t *mask,
+                 int order, int inner, double limiter_K, const double *U, double *R,
+                 double *scale, double *qx_out, double *qy_out)
+{
+    return orc_residual_bc(n, gamma, x, y, nx, ny, flags, off, idx, mask, order, inner, limiter_K, 0,
+                           0.0, 0.0, U, R, scale, qx_out, qy_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -670,19 +900,20 @@ int orc_forces(int64_t n, double gamma, double mach, double aoa_deg, const doubl
 /* The solver loop of Algorithm 1: per iteration q_variables,               */
 /* q_derivatives, flux_residual, timestep, state_update, residue.           */
 /* scheme 0: forward Euler (E16); scheme 1: RK4 (reading above).            */
+/* boundary 0: plain reading; 1: kinetic boundary mode (stencil members).  */
 /* U[4][n] holds the initial state on entry and the final one on exit;      */
 /* res_history[it] (nullable) receives residue() of R(U^it).                */
 /* ------------------------------------------------------------------------ */
-int orc_solve(int64_t n, double gamma, const double *x, const double *y,
-              const double *nx, const double *ny, const int32_t *flags,
-              const int32_t *off, const int32_t *idx, const uint8_t *mask,
-              int order, int inner, double limiter_K, int scheme, double cfl, double mach,
-              double aoa_deg, int n_iters, double *U, double *res_history)
+int orc_solve_bc(int64_t n, double gamma, const double *x, const double *y,
+                 const double *nx, const double *ny, const int32_t *flags,
+                 const int32_t *off, const int32_t *idx, const uint8_t *mask,
+                 int order, int inner, double limiter_K, int boundary, int scheme, double cfl,
+                 double mach, double aoa_deg, int n_iters, double *U, double *res_history)
 {
     size_t bytes = (size_t)4 * n * sizeof(double);
     orc_scheme s;
-    s.n = n; s.gamma = gamma; s.x = x; s.y = y; s.nx = nx; s.ny = ny;
-    s.flags = flags; s.off = off; s.idx = idx; s.mask = mask;
+    s.g = scheme_geom(n, x, y, nx, ny, flags, off, idx, mask, boundary, gamma, mach, aoa_deg);
+    s.gamma = gamma;
     s.order = order; s.inner = inner; s.limiter_K = limiter_K;
     s.q = (double *)malloc(bytes);
     s.qx = (double *)calloc(4 * (size_t)n, sizeof(double));
@@ -697,12 +928,22 @@ int orc_solve(int64_t n, double gamma, const double *x, const double *y,
     for (int it = 0; it < n_iters && rc == ORC_OK; ++it) {
         rc = orc_timestep(n, gamma, cfl, x, y, off, idx, U, dt);
         if (rc) break;
-        if (scheme == 1) rc = orc_rk4_step(n, flags, nx, ny, Uinf, dt, U, scheme_residual, &s, R0);
-        else rc = orc_euler_step(n, flags, nx, ny, Uinf, dt, U, scheme_residual, &s, R0);
+        if (scheme == 1) rc = rk4_step(n, flags, nx, ny, Uinf, s.g.kinetic, dt, U, scheme_residual, &s, R0);
+        else rc = euler_step(n, flags, nx, ny, Uinf, s.g.kinetic, dt, U, scheme_residual, &s, R0);
         if (rc) break;
         if (res_history) res_history[it] = orc_residue(n, R0);
     }
 done:
     free(s.q); free(s.qx); free(s.qy); free(dt); free(R0);
     return rc;
+}
+
+int orc_solve(int64_t n, double gamma, const double *x, const double *y,
+              const double *nx, const double *ny, const int32_t *flags,
+              const int32_t *off, const int32_t *idx, const uint8_t *mask,
+              int order, int inner, double limiter_K, int scheme, double cfl, double mach,
+              double aoa_deg, int n_iters, double *U, double *res_history)
+{
+    return orc_solve_bc(n, gamma, x, y, nx, ny, flags, off, idx, mask, order, inner, limiter_K, 0, scheme,
+                        cfl, mach, aoa_deg, n_iters, U, res_history);
 }
