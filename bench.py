@@ -307,7 +307,7 @@ def measure_form(args, cloud, precision, dist, sampler):
     solver = lskum.Solver(cloud, order=args.order, inner_iters=args.inner, time_scheme=scheme,
                           cfl=args.cfl, mach=args.mach, aoa_deg=args.aoa, reorder=args.reorder,
                           limiter_K=args.limiter, precision=1 if precision == "mixed" else 0,
-                          stream=stream.cuda_stream)
+                          stream=stream.cuda_stream, boundary=getattr(args, "boundary", 0))
     # start from a developed-looking, non-uniform state: after an impulsive
     # start most of the cloud is still exactly uniform, where a perturbation
     # dG vanishes identically, and a few iterations would not be representative
@@ -640,6 +640,7 @@ def run_ours(args, rank, world, local):
             if r.get("tuning"):
                 out["tuning"] = r["tuning"]
             out["config"] = {k: getattr(a, k) for k in ("scheme", "mach", "aoa", "limiter", "reorder")}
+            out["config"]["boundary"] = "kinetic" if getattr(a, "boundary", 0) else "plain"
             out["config"]["points"] = nn
             return out
 
@@ -654,6 +655,11 @@ def run_ours(args, rank, world, local):
         forms["mixed_input_order"]["speedup_of_morton"] = forms["mixed"]["value"] / forms["mixed_input_order"]["value"]
         forms["mixed_rcm"] = variant("mixed", cloud, reorder=2)
         forms["mixed_rcm"]["speedup_of_morton"] = forms["mixed"]["value"] / forms["mixed_rcm"]["value"]
+        # the kinetic boundary mode (mirror images at the wall and far-field points)
+        kin = {p_: variant(p_, cloud, boundary=1) for p_ in ("fp64", "mixed")}
+        for p_ in ("fp64", "mixed"):
+            kin[p_]["relative_to_plain"] = kin[p_]["value"] / forms[p_]["value"]
+        forms["kinetic_boundary"] = kin
         # throughput at 10M points
         W10, L10 = CLOUDS["naca0012_10m"]
         c10 = naca0012_cloud(W10, L10, shuffle=bool(args.shuffle))

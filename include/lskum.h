@@ -48,7 +48,7 @@ typedef enum {
 /* point flags */
 #define LSKUM_POINT_INTERIOR 0
 #define LSKUM_POINT_WALL 1     /* on the body; normal points into the fluid */
-#define LSKUM_POINT_FARFIELD 2 /* outer boundary; held at the free stream */
+#define LSKUM_POINT_FARFIELD 2 /* outer boundary; normal points out of the domain */
 
 /* sub-stencil bits of lskum_get_stencil_masks (Sec. 2, after E12), measured in
  * the point's frame: tangent t = (ny, -nx), normal n = (nx, ny) */
@@ -80,7 +80,29 @@ typedef struct {
                        * f(D, d) = (D^2 + e^2 + 2Dd)/(D^2 + 2d^2 + Dd + e^2), d+ the largest
                        * |(P_i - P_0).grad q|/2, D+- = max/min of q over P_0 and N(P_0) minus
                        * q_0, e^2 = (K h)^3, h the nearest-neighbour distance */
+    int boundary;     /* LSKUM_BOUNDARY_PLAIN or LSKUM_BOUNDARY_KINETIC (below) */
 } lskum_config;
+
+/*
+ * Boundary treatment (the paper cites kinetic wall and far-field conditions
+ * after E10 without stating them).
+ * LSKUM_BOUNDARY_PLAIN: a wall point drops dGy+/dy (no upwind points inside
+ *   the body) and loses its normal momentum after every update; far-field
+ *   points are held at the free stream.
+ * LSKUM_BOUNDARY_KINETIC: a wall or far-field point P_0 also sees the mirror
+ *   image of each neighbour P_i across its tangent line (local offsets
+ *   (ds_i, -dn_i); a neighbour with dn_i = 0 is its own image and adds none).
+ *   At a wall point the image carries the specularly reflected gas (the
+ *   velocity part of q and every gradient reflected across the line); at a
+ *   far-field point it carries the free stream with zero gradient. The point
+ *   then takes the interior formulas on the augmented stencil: q-derivatives
+ *   (E15), limiter, all four split-flux derivatives (E10-E12). Far-field
+ *   points are updated like interior points; wall points still lose their
+ *   normal momentum. The derivative calls (lskum_residual_vjp,
+ *   lskum_step_vjp) need LSKUM_BOUNDARY_PLAIN.
+ */
+#define LSKUM_BOUNDARY_PLAIN 0
+#define LSKUM_BOUNDARY_KINETIC 1
 
 typedef struct lskum_ctx lskum_ctx;
 
@@ -101,7 +123,9 @@ typedef struct lskum_ctx lskum_ctx;
  * Validates the CSR (LSKUM_ERR_CONNECTIVITY) and every needed stencil: the full
  * stencil at every point, N_x+, N_x-, N_y+, N_y- at interior points and N_x+,
  * N_x-, N_y- at wall points must have det > 1e-10 * Sxx * Syy
- * (LSKUM_ERR_DEGENERATE_STENCIL; the message names the first bad point).
+ * (LSKUM_ERR_DEGENERATE_STENCIL; the message names the first bad point). In
+ * the kinetic boundary mode wall and far-field points need all five stencils,
+ * each augmented by the mirror images.
  * Initialises the state to the free stream. Synchronises.
  */
 lskum_status lskum_create(int64_t n, const double *x, const double *y, const double *nx,
@@ -162,14 +186,16 @@ const char *lskum_last_error(const lskum_ctx *ctx);
  *   res_history  host float64[n_iters] or NULL: residue of each iteration,
  *                sqrt(sum_p R_rho(U^n)_p^2) / n
  * Wall points lose their normal momentum after every update; far-field points
- * are held at the free stream. Synchronises once at the end. On
+ * are held at the free stream (plain boundary mode) or updated (kinetic
+ * mode). Synchronises once at the end. On
  * LSKUM_ERR_NONPHYSICAL the state is rolled back to its value at entry.
  */
 lskum_status lskum_step(lskum_ctx *ctx, int n_iters, double *res_history);
 
 /*
  * Residual R(U) = dGx+/dx + dGx-/dx + dGy+/dy + dGy-/dy of E10 (q~ of E14 for
- * order 2), momentum in global (x, y) components; far-field points get 0.
+ * order 2), momentum in global (x, y) components; far-field points get 0 in
+ * the plain boundary mode.
  *   U  device float64[4*n] in input order, or NULL for the context's state
  *   R  device float64[4*n] in input order (written)
  * Does not change the context's state (its scratch buffers are reused).

@@ -40,6 +40,17 @@ struct lskum_ctx {
     double *dmin = nullptr;
     int32_t *off = nullptr, *idx = nullptr, *off_in = nullptr;
     double2 *lsw = nullptr, *fxw = nullptr, *hd = nullptr;
+    // kinetic boundary mode: mirror images of the neighbours of wall and
+    // far-field points (CSR per internal point) and each case's free-stream q
+    bool kinetic = false;
+    int64_t nimg = 0;
+    int32_t *ioff = nullptr, *iidx = nullptr;
+    uint8_t *imask = nullptr;
+    double2 *ilsw = nullptr, *ifxw = nullptr, *ihd = nullptr;
+    double *qinf = nullptr;
+    float *qinf_f = nullptr;
+    float2 *ilsw_f = nullptr;
+    float4 *igf = nullptr;
     int32_t *perm = nullptr, *inv = nullptr;
     int32_t *wall = nullptr;
     double *wall_ds = nullptr;
@@ -122,17 +133,25 @@ struct lskum_ctx {
 
     DevGeom geom() const
     {
-        DevGeom g;
+        DevGeom g{};
         g.n = n; g.xy = xy; g.nrm = nrm; g.flag = flag; g.dmin = dmin;
         g.off = off; g.idx = idx; g.mask = mask; g.lsw = lsw; g.fxw = fxw; g.hd = hd;
+        if (kinetic) {
+            g.ioff = ioff; g.iidx = iidx; g.imask = imask; g.ilsw = ilsw; g.ifxw = ifxw; g.ihd = ihd;
+            g.qinf = qinf; g.pcase = pcase;
+        }
         return g;
     }
 
     MixedGeom mgeom() const
     {
-        MixedGeom g;
+        MixedGeom g{};
         g.n = n; g.nrm = nrm_f; g.flag = flag; g.dmin = dmin_f; g.off = off;
         g.slice_off = slice_off; g.sidx = s_idx; g.ga = s_ga; g.gm = gm; g.gf = s_gf; g.fxw64 = s_fxw64;
+        if (kinetic) {
+            g.ioff = ioff; g.iidx = iidx; g.imask = imask; g.ilsw = ilsw_f; g.igf = igf; g.ifxw64 = ifxw;
+            g.qinf = qinf_f; g.pcase = pcase;
+        }
         return g;
     }
 };
@@ -490,7 +509,56 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     CK(c, dalloc(c, &bad, 2));
     const int bad_init[2] = {0, 0x7fffffff};
     CK(c, cudaMemcpyAsync(bad, bad_init, sizeof bad_init, cudaMemcpyHostToDevice, s));
-    LAUNCH(c, launch_geometry(n, c->xy, c->nrm, c->flag, c->off, c->idx, c->mask, c->lsw, c->fxw, c->dmin, bad, s));
+    LAUNCH(c, launch_geometry(n, c->xy, c->nrm, c->flag, c->off, c->idx, c->mask, c->lsw, c->fxw, c->dmin, bad,
+                              ImageEdges{}, s));
+    if (c->kinetic) {
+        // the mirror images: one per neighbour off the tangent line (a split
+        // bit in y) of each wall and far-field point, x+- kept, y+- swapped
+        std::vector<int32_t> off_h(n + 1), idx_h(nnz);
+        std::vector<uint8_t> mask_h(std::max<int64_t>(nnz, 1)), flag_h(n);
+        CK(c, cudaMemcpyAsync(off_h.data(), c->off, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(c, cudaMemcpyAsync(idx_h.data(), c->idx, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(c, cudaMemcpyAsync(mask_h.data(), c->mask, nnz, cudaMemcpyDeviceToHost, s));
+        CK(c, cudaMemcpyAsync(flag_h.data(), c->flag, n, cudaMemcpyDeviceToHost, s));
+        CK(c, cudaStreamSynchronize(s));
+        std::vector<int32_t> ioff_h(n + 1, 0), iidx_h;
+        std::vector<uint8_t> imask_h;
+        for (int64_t p = 0; p < n; ++p) {
+            const uint8_t f = flag_h[p] & 3;
+            if (f == FLAG_WALL || f == FLAG_FARFIELD) {
+                for (int32_t e = off_h[p]; e < off_h[p + 1]; ++e) {
+                    const uint8_t m = mask_h[e];
+                    if (!(m & (M_YPOS | M_YNEG))) continue;
+                    iidx_h.push_back(idx_h[e]);
+                    imask_h.push_back((uint8_t)((m & (M_XPOS | M_XNEG)) | ((m & M_YPOS) ? M_YNEG : 0) |
+                                                ((m & M_YNEG) ? M_YPOS : 0) |
+                                                (f == FLAG_WALL ? M_IMG_WALL : M_IMG_FAR)));
+                }
+            }
+            ioff_h[p + 1] = (int32_t)iidx_h.size();
+        }
+        c->nimg = (int64_t)iidx_h.size();
+        const int64_t ni = std::max<int64_t>(c->nimg, 1);
+        CK(c, dalloc(c, &c->ioff, n + 1));
+        CK(c, dalloc(c, &c->iidx, ni));
+        CK(c, dalloc(c, &c->imask, ni));
+        CK(c, dalloc(c, &c->ilsw, ni));
+        CK(c, dalloc(c, &c->ifxw, ni));
+        CK(c, dalloc(c, &c->ihd, ni));
+        CK(c, cudaMemcpyAsync(c->ioff, ioff_h.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        if (c->nimg > 0) {
+            CK(c, cudaMemcpyAsync(c->iidx, iidx_h.data(), c->nimg * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            CK(c, cudaMemcpyAsync(c->imask, imask_h.data(), c->nimg, cudaMemcpyHostToDevice, s));
+        }
+        // the weights again, now over the augmented stencils (the split of the
+        // first pass is recomputed identically)
+        CK(c, cudaMemcpyAsync(bad, bad_init, sizeof bad_init, cudaMemcpyHostToDevice, s));
+        ImageEdges im;
+        im.off = c->ioff; im.idx = c->iidx; im.mask = c->imask;
+        im.lsw = c->ilsw; im.fxw = c->ifxw; im.hd = c->ihd; im.kinetic = 1;
+        LAUNCH(c, launch_geometry(n, c->xy, c->nrm, c->flag, c->off, c->idx, c->mask, c->lsw, c->fxw, c->dmin,
+                                  bad, im, s));
+    }
     if (!c->mixed) {
         CK(c, dalloc(c, &c->hd, std::max<int64_t>(nnz, 1)));
         LAUNCH(c, launch_half_offsets(n, c->xy, c->off, c->idx, c->hd, s));
@@ -577,7 +645,12 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
         CK(c, dalloc(c, &cnt, 1));
         CK(c, cudaMemsetAsync(cnt, 0, sizeof(int), s));
         CK(c, dalloc(c, &c->gm, n));
-        LAUNCH(c, launch_mixed_prep(c->geom(), c->flag, c->nrm_f, c->dmin_f, c->gm, dxy, lsw, fxw, cnt, s));
+        if (c->kinetic) {
+            CK(c, dalloc(c, &c->ilsw_f, std::max<int64_t>(c->nimg, 1)));
+            CK(c, dalloc(c, &c->igf, std::max<int64_t>(c->nimg, 1)));
+        }
+        LAUNCH(c, launch_mixed_prep(c->geom(), c->flag, c->nrm_f, c->dmin_f, c->gm, dxy, lsw, fxw, c->ilsw_f, c->igf,
+                                    cnt, s));
         CK(c, cudaMemcpyAsync(&c->n_fp64_closure, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
         std::vector<int32_t> off_h(n + 1);
         CK(c, cudaMemcpyAsync(off_h.data(), c->off, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -621,6 +694,23 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     CK(c, cudaMemsetAsync(c->qgA, 0, 2 * 8 * n * qbytes, s));
     const int st_init[2] = {0, 0x7fffffff};
     CK(c, cudaMemcpyAsync(c->status, st_init, sizeof st_init, cudaMemcpyHostToDevice, s));
+    if (c->kinetic) {
+        // each case's free-stream q by the same kernel that turns states into q
+        const double *uinf = c->case_uinf;
+        if (!uinf) {
+            double *u1 = nullptr;
+            CK(c, dalloc(c, &u1, 4));
+            CK(c, cudaMemcpyAsync(u1, c->gas.Uinf, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+            uinf = u1;
+        }
+        if (c->mixed) {
+            CK(c, dalloc(c, &c->qinf_f, 4 * c->ncases));
+            LAUNCH(c, launch_q_from_U_mixed(c->ncases, c->gas, uinf, c->qinf_f, c->status, s));
+        } else {
+            CK(c, dalloc(c, &c->qinf, 4 * c->ncases));
+            LAUNCH(c, launch_q_from_U(c->ncases, c->gas, uinf, c->qinf, c->status, s));
+        }
+    }
     if (c->ncases > 1) LAUNCH(c, launch_fill_state_cases(n, c->pcase, c->case_uinf, c->U, s));
     else LAUNCH(c, launch_fill_state(n, c->gas.Uinf, c->U, s));
     lskum_status st = refresh_q(c, c->U, c->q_cur);
@@ -643,6 +733,8 @@ static lskum_status check_config(const lskum_config *cfg, int64_t n)
     if (cfg->reorder < 0 || cfg->reorder > 2) return fail(nullptr, LSKUM_ERR_ARG, "reorder must be 0, 1 or 2");
     if (!(cfg->limiter_K >= 0.0) || !std::isfinite(cfg->limiter_K))
         return fail(nullptr, LSKUM_ERR_ARG, "limiter_K must be finite and >= 0");
+    if (cfg->boundary != LSKUM_BOUNDARY_PLAIN && cfg->boundary != LSKUM_BOUNDARY_KINETIC)
+        return fail(nullptr, LSKUM_ERR_ARG, "boundary must be 0 (plain) or 1 (kinetic)");
     return LSKUM_OK;
 }
 
@@ -687,6 +779,7 @@ extern "C" lskum_status lskum_create(int64_t n, const double *x, const double *y
     c->n_wall = n_wall;
     c->cfg = *cfg;
     c->mixed = cfg->precision == 1;
+    c->kinetic = cfg->boundary == LSKUM_BOUNDARY_KINETIC;
     c->stream = (cudaStream_t)cuda_stream;
     c->gas.gamma = cfg->gamma;
     c->gas.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
@@ -776,6 +869,7 @@ extern "C" lskum_status lskum_create_batch(int n_cases, const lskum_case *cases,
     c->cfg.mach = cases[0].mach;
     c->cfg.aoa_deg = cases[0].aoa_deg;
     c->mixed = cfg->precision == 1;
+    c->kinetic = cfg->boundary == LSKUM_BOUNDARY_KINETIC;
     c->stream = (cudaStream_t)cuda_stream;
     c->gas.gamma = cfg->gamma;
     c->gas.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
@@ -1269,6 +1363,8 @@ static lskum_status vjp_begin(lskum_ctx *c)
 {
     if (c->cfg.order == 2 && c->cfg.limiter_K != 0.0)
         return fail(c, LSKUM_ERR_ARG, "derivatives need limiter_K = 0 (the limiter is not differentiated)");
+    if (c->kinetic)
+        return fail(c, LSKUM_ERR_ARG, "derivatives need boundary = 0 (the mirror images are not differentiated)");
     lskum_status st = vjp_workspace(c);
     if (st != LSKUM_OK) return st;
     if ((st = reset_status(c)) != LSKUM_OK) return st;

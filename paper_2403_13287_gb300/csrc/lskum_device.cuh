@@ -28,6 +28,10 @@ namespace lskum {
 
 enum : uint8_t { FLAG_INTERIOR = 0, FLAG_WALL = 1, FLAG_FARFIELD = 2 };
 enum : uint8_t { M_XPOS = 1, M_XNEG = 2, M_YPOS = 4, M_YNEG = 8 };
+// kinetic boundary mode: the member is the mirror image of a neighbour across
+// the tangent line of P_0, carrying the reflected gas (wall) or the free
+// stream with zero gradient (far field)
+enum : uint8_t { M_IMG_WALL = 16, M_IMG_FAR = 32 };
 
 enum : int { STATUS_NONPHYSICAL = 1, STATUS_DEGENERATE = 2 };
 
@@ -43,7 +47,28 @@ struct DevGeom {
     const double2 *__restrict__ lsw;
     const double2 *__restrict__ fxw;
     const double2 *__restrict__ hd;  // FP64 contexts: per edge (P_i - P_0)/2, or nullptr
+    // kinetic boundary mode (all nullptr otherwise): the mirror images of the
+    // neighbours of each wall and far-field point, per point in CSR form
+    // (rows are empty at interior points); an image of P_i has local offsets
+    // (ds_i, -dn_i) and the x+- membership of P_i with y+ and y- swapped
+    const int32_t *__restrict__ ioff;    // [n+1]
+    const int32_t *__restrict__ iidx;    // the neighbour whose image this is
+    const uint8_t *__restrict__ imask;   // sub-stencil bits | M_IMG_WALL or M_IMG_FAR
+    const double2 *__restrict__ ilsw;    // full-stencil weights of the images
+    const double2 *__restrict__ ifxw;    // sub-stencil weights of the images
+    const double2 *__restrict__ ihd;     // FP64 contexts: half offsets of the images
+    const double *__restrict__ qinf;     // [cases][4] q of each case's free stream
+    const uint16_t *__restrict__ pcase;  // per point: its case in a batch, or nullptr
 };
+
+// reflection of the vector (a, b) across the line with unit normal n
+template <typename T>
+__device__ __forceinline__ void reflect2(T &a, T &b, T nx, T ny)
+{
+    const T c = a * nx + b * ny;
+    a = a - T(2) * c * nx;
+    b = b - T(2) * c * ny;
+}
 
 // Free-stream and gas constants handed to every kernel.
 struct Gas {

@@ -20,10 +20,42 @@ __device__ __forceinline__ double venkat(double D, double d, double eps2)
     return (D * D + eps2 + 2.0 * D * d) / (D * D + 2.0 * d * d + D * d + eps2);
 }
 
+// Kinetic boundary mode: the q carried by the image (entry e of the image
+// CSR) of a neighbour P_i of P_0, reconstructed (E14) with the image's half
+// offset hs when recon: the reflection across the tangent line (normal n0)
+// of P_i's own reconstruction q_i - h.grad q_i, h the reflection of hs
+// (reflecting the gas reflects q1, q2 and every gradient, and the image of
+// a field at the image of a point is the reflection of its value there);
+// the free stream qf for a far-field image (zero gradient).
+__device__ __forceinline__ void image_q(const DevGeom &g, int e, uint8_t m, double2 n0, const double *qf,
+                                       const double *__restrict__ q, const double *__restrict__ qg, double2 hs,
+                                       bool recon, double qi[4])
+{
+    if (m & M_IMG_FAR) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qi[k] = qf[k];
+        return;
+    }
+    const int i = g.iidx[e];
+    load4(q, i, qi);
+    if (recon) {
+        double2 h = hs;
+        reflect2(h.x, h.y, n0.x, n0.y);
+        double gi[8];
+        load8(qg, i, gi);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qi[k] = fma(-h.y, gi[4 + k], fma(-h.x, gi[k], qi[k]));
+    }
+    reflect2(qi[1], qi[2], n0.x, n0.y);
+}
+
 // limK > 0 on the final pass: scale each component of the new gradient by
 // Venkatakrishnan's limiter. f(D, d) is >= 1 for 0 < d <= D/2 and decreasing
 // beyond, so its minimum over every reconstruction shift +-(P_i - P_0).grad/2
 // is its value at the largest shift d+ on each side.
+// KIN: the kinetic boundary mode (mirror images in g.ioff...; a separate
+// instantiation keeps the plain kernel's registers as they are)
+template <bool KIN>
 __global__ void __launch_bounds__(128) k_qgrad(DevGeom g, const double *__restrict__ q,
                                                const double *__restrict__ qg_old,
                                                double *__restrict__ qg_new, double limK)
@@ -75,6 +107,35 @@ __global__ void __launch_bounds__(128) k_qgrad(DevGeom g, const double *__restri
             sy[k] += a.y * dq[k];
         }
     }
+    if constexpr (KIN) {
+        // kinetic boundary mode: the mirror images of the neighbours
+        const int f0 = g.ioff[p], f1 = g.ioff[p + 1];
+        if (f0 < f1) {
+            const double2 n0 = g.nrm[p];
+            const double *qf = g.qinf + 4 * (g.pcase ? (int)g.pcase[p] : 0);
+            for (int e = f0; e < f1; ++e) {
+                const uint8_t m = g.imask[e];
+                const double2 a = g.ilsw[e];
+                double qi[4], dq[4];
+                image_q(g, e, m, n0, qf, q, qg_old, g.ihd[e], inner, qi);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dq[k] = qi[k] - q0[k];
+                if (limit) {
+                    if (inner) image_q(g, e, m, n0, qf, q, qg_old, g.ihd[e], false, qi);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        qmax[k] = fmax(qmax[k], qi[k]);
+                        qmin[k] = fmin(qmin[k], qi[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    sx[k] += a.x * dq[k];
+                    sy[k] += a.y * dq[k];
+                }
+            }
+        }
+    }
     if (inner) {
         // sum_e a_e (d_e . g_0) = g_0, since the weights a_e = M^-1 d_e with
         // M = sum_e d_e d_e^T give sum_e a_e d_e^T = I: the +1/2 d_e . g_0 of
@@ -92,6 +153,13 @@ __global__ void __launch_bounds__(128) k_qgrad(DevGeom g, const double *__restri
             const double dx = xyi.x - xy0.x, dy = xyi.y - xy0.y;
 #pragma unroll
             for (int k = 0; k < 4; ++k) dmax[k] = fmax(dmax[k], fabs(0.5 * (dx * sx[k] + dy * sy[k])));
+        }
+        if constexpr (KIN) {
+            for (int e = g.ioff[p]; e < g.ioff[p + 1]; ++e) {
+                const double2 h = g.ihd[e];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dmax[k] = fmax(dmax[k], fabs(h.x * sx[k] + h.y * sy[k]));
+            }
         }
         const double h = g.dmin[p] * limK;
         const double eps2 = h * h * h;
@@ -144,6 +212,50 @@ __device__ __forceinline__ void flag_nonphysical(int *status, int64_t p)
     atomicMin(status + 1, (int)p);
 }
 
+// One member's term of E11: w_s [Gs(q~_i) - Gs(q~_0)] + w_n [Gn(q~_i) - Gn(q~_0)],
+// Gs = Gx+ or Gx- and Gn = Gy+ or Gy- by the member's sub-stencil bits m,
+// in the frame (t, n) of P_0; R in the order [mass, s-momentum, n-momentum, energy].
+__device__ __forceinline__ void edge_residual(const double qti[4], const double qt0[4], uint8_t m, double2 w,
+                                              double2 n0, double tx, double ty, const Gas &gas, double R[4],
+                                              bool &ok)
+{
+    // equal reconstructed states have dG = 0 exactly (compared as bit patterns,
+    // on the integer pipe; +0 against -0 only costs a flux evaluation giving dG = 0)
+    if (((__double_as_longlong(qti[0]) ^ __double_as_longlong(qt0[0])) |
+         (__double_as_longlong(qti[1]) ^ __double_as_longlong(qt0[1])) |
+         (__double_as_longlong(qti[2]) ^ __double_as_longlong(qt0[2])) |
+         (__double_as_longlong(qti[3]) ^ __double_as_longlong(qt0[3]))) == 0)
+        return;
+    Prim si, s0;
+    ok &= prim_from_q(qti, gas, si);
+    ok &= prim_from_q(qt0, gas, s0);
+    const double us_i = si.u * tx + si.v * ty, un_i = si.u * n0.x + si.v * n0.y;
+    const double us_0 = s0.u * tx + s0.v * ty, un_0 = s0.u * n0.x + s0.v * n0.y;
+    if (w.x != 0.0) {
+        const double sg = (m & M_XPOS) ? 1.0 : -1.0;
+        double Gi[4], G0[4];
+        split_flux(sg, si, us_i, un_i, Gi);
+        split_flux(sg, s0, us_0, un_0, G0);
+        // dG = G(q~_i) - G(q~_0) from the two rounded fluxes: an unfused
+        // subtraction, so equal states give exactly zero (a contracted
+        // fma(rho_i, m_i, -rho_0 m_0) would leave a product's rounding)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) R[k] += w.x * __dsub_rn(Gi[k], G0[k]);
+    }
+    if (w.y != 0.0) {
+        const double sg = (m & M_YPOS) ? 1.0 : -1.0;
+        double Gi[4], G0[4];
+        split_flux(sg, si, un_i, us_i, Gi);
+        split_flux(sg, s0, un_0, us_0, G0);
+        // Gn components are [mass, n-momentum, s-momentum, energy]
+        R[0] += w.y * __dsub_rn(Gi[0], G0[0]);
+        R[1] += w.y * __dsub_rn(Gi[2], G0[2]);
+        R[2] += w.y * __dsub_rn(Gi[1], G0[1]);
+        R[3] += w.y * __dsub_rn(Gi[3], G0[3]);
+    }
+}
+
+template <bool KIN>
 __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
 {
     const DevGeom &g = P.g;
@@ -152,7 +264,8 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
     const bool live = p < g.n;
     uint8_t flag = FLAG_FARFIELD;
     if (live) flag = g.flag[p] & 3;  // bit 7 marks FP64 closures in mixed contexts
-    if (live && flag != FLAG_FARFIELD) {
+    // far-field points are held at the free stream, except in the kinetic boundary mode
+    if (live && (flag != FLAG_FARFIELD || KIN)) {
         const double2 xy0 = g.xy[p];
         const double2 n0 = g.nrm[p];
         const double tx = n0.y, ty = -n0.x;
@@ -189,39 +302,21 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
                     qt0[k] = fma(-h.y, g0[4 + k], fma(-h.x, g0[k], qt0[k]));
                 }
             }
-            // equal reconstructed states have dG = 0 exactly (compared as bit patterns,
-            // on the integer pipe; +0 against -0 only costs a flux evaluation giving dG = 0)
-            if (((__double_as_longlong(qti[0]) ^ __double_as_longlong(qt0[0])) |
-                 (__double_as_longlong(qti[1]) ^ __double_as_longlong(qt0[1])) |
-                 (__double_as_longlong(qti[2]) ^ __double_as_longlong(qt0[2])) |
-                 (__double_as_longlong(qti[3]) ^ __double_as_longlong(qt0[3]))) == 0)
-                continue;
-            Prim si, s0;
-            ok &= prim_from_q(qti, P.gas, si);
-            ok &= prim_from_q(qt0, P.gas, s0);
-            const double us_i = si.u * tx + si.v * ty, un_i = si.u * n0.x + si.v * n0.y;
-            const double us_0 = s0.u * tx + s0.v * ty, un_0 = s0.u * n0.x + s0.v * n0.y;
-            if (w.x != 0.0) {
-                const double sg = (m & M_XPOS) ? 1.0 : -1.0;
-                double Gi[4], G0[4];
-                split_flux(sg, si, us_i, un_i, Gi);
-                split_flux(sg, s0, us_0, un_0, G0);
-                // dG = G(q~_i) - G(q~_0) from the two rounded fluxes: an unfused
-                // subtraction, so equal states give exactly zero (a contracted
-                // fma(rho_i, m_i, -rho_0 m_0) would leave a product's rounding)
+            edge_residual(qti, qt0, m, w, n0, tx, ty, P.gas, R, ok);
+        }
+        if constexpr (KIN) {
+            // kinetic boundary mode: the mirror images of the neighbours
+            const int f0 = g.ioff[p], f1 = g.ioff[p + 1];
+            const double *qf = g.qinf + 4 * (g.pcase ? (int)g.pcase[p] : 0);
+            for (int e = f0; e < f1; ++e) {
+                const double2 w = g.ifxw[e];
+                const uint8_t m = g.imask[e];
+                const double2 hs = g.ihd[e];
+                double qti[4], qt0[4];
+                image_q(g, e, m, n0, qf, P.q, P.qg, hs, second, qti);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) R[k] += w.x * __dsub_rn(Gi[k], G0[k]);
-            }
-            if (w.y != 0.0) {
-                const double sg = (m & M_YPOS) ? 1.0 : -1.0;
-                double Gi[4], G0[4];
-                split_flux(sg, si, un_i, us_i, Gi);
-                split_flux(sg, s0, un_0, us_0, G0);
-                // Gn components are [mass, n-momentum, s-momentum, energy]
-                R[0] += w.y * __dsub_rn(Gi[0], G0[0]);
-                R[1] += w.y * __dsub_rn(Gi[2], G0[2]);
-                R[2] += w.y * __dsub_rn(Gi[1], G0[1]);
-                R[3] += w.y * __dsub_rn(Gi[3], G0[3]);
+                for (int k = 0; k < 4; ++k) qt0[k] = second ? fma(-hs.y, g0[4 + k], fma(-hs.x, g0[k], q0[k])) : q0[k];
+                edge_residual(qti, qt0, m, w, n0, tx, ty, P.gas, R, ok);
             }
         }
         if (!ok) flag_nonphysical(P.status, p);
@@ -284,7 +379,7 @@ __global__ void __launch_bounds__(128) k_flux_update(FluxParams P)
             const double mn = Unew[1] * n0.x + Unew[2] * n0.y;
             Unew[1] = Unew[1] - mn * n0.x;
             Unew[2] = Unew[2] - mn * n0.y;
-        } else if (flag == FLAG_FARFIELD) {
+        } else if (flag == FLAG_FARFIELD && !KIN) {
             const double *Ui = P.case_uinf ? P.case_uinf + 4 * (int)P.pcase[p] : P.gas.Uinf;
 #pragma unroll
             for (int k = 0; k < 4; ++k) Unew[k] = Ui[k];
@@ -428,7 +523,8 @@ static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t -
 cudaError_t launch_qgrad(const DevGeom &g, const double *q, const double *qg_old, double *qg_new,
                          double limiter_K, cudaStream_t s)
 {
-    k_qgrad<<<blocks_for(g.n, 128), 128, 0, s>>>(g, q, qg_old, qg_new, limiter_K);
+    if (g.ioff) k_qgrad<true><<<blocks_for(g.n, 128), 128, 0, s>>>(g, q, qg_old, qg_new, limiter_K);
+    else k_qgrad<false><<<blocks_for(g.n, 128), 128, 0, s>>>(g, q, qg_old, qg_new, limiter_K);
     return cudaGetLastError();
 }
 
@@ -443,7 +539,8 @@ cudaError_t launch_flux(const DevGeom &g, const Gas &gas, const FluxLaunch &L, c
     P.dt = L.dt; P.R = L.R; P.norm_part = L.norm_part; P.status = L.status;
     P.pcase = L.pcase; P.case_uinf = L.case_uinf;
     P.cfl = L.cfl; P.order = L.order; P.mode = L.mode; P.stage = L.stage;
-    k_flux_update<<<blocks_for(g.n, 128), 128, 0, s>>>(P);
+    if (g.ioff) k_flux_update<true><<<blocks_for(g.n, 128), 128, 0, s>>>(P);
+    else k_flux_update<false><<<blocks_for(g.n, 128), 128, 0, s>>>(P);
     return cudaGetLastError();
 }
 

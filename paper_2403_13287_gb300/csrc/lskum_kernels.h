@@ -48,10 +48,19 @@ cudaError_t launch_forces(int64_t nwall, const Gas &gas, double qinf, const int3
 // error text for calls without a context (lskum_api.cu)
 void set_global_error(const char *msg);
 
-// create-time geometry (lskum_setup.cu)
+// create-time geometry (lskum_setup.cu). im: the mirror images of the
+// kinetic boundary mode (im.off == nullptr: none); kinetic = the mode is on
+// (wall and far-field points then need all four sub-stencils)
+struct ImageEdges {
+    const int32_t *off = nullptr, *idx = nullptr;
+    const uint8_t *mask = nullptr;
+    double2 *lsw = nullptr, *fxw = nullptr, *hd = nullptr;
+    int kinetic = 0;
+};
 cudaError_t launch_geometry(int64_t n, const double2 *xy, const double2 *nrm, const uint8_t *flag,
                             const int32_t *off, const int32_t *idx, uint8_t *mask, double2 *lsw,
-                            double2 *fxw, double *dmin, int *bad, cudaStream_t s);
+                            double2 *fxw, double *dmin, int *bad, const ImageEdges &im, cudaStream_t s);
+
 cudaError_t morton_permutation(int64_t n, const double2 *xy, double xmin, double ymin, double scale,
                                int32_t *perm, cudaStream_t s);
 cudaError_t launch_permute_points(int64_t n, const int32_t *perm, const double *x, const double *y,

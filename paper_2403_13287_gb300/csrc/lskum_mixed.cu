@@ -21,20 +21,24 @@ namespace lskum {
 // --------------------------------------------------------------------------
 static constexpr double kAmpLimit = 16.0;
 
-__global__ void __launch_bounds__(128) k_mixed_prep(int64_t n, const double2 *__restrict__ xy,
-                                                    const double2 *__restrict__ nrm,
-                                                    const double *__restrict__ dmin,
-                                                    const int32_t *__restrict__ off,
-                                                    const int32_t *__restrict__ idx,
-                                                    const uint8_t *__restrict__ mask,
-                                                    const double2 *__restrict__ lsw,
-                                                    const double2 *__restrict__ fxw,
-                                                    uint8_t *__restrict__ flag, float2 *__restrict__ nrm_f,
-                                                    float *__restrict__ dmin_f, float4 *__restrict__ gm,
-                                                    float2 *__restrict__ dxy_f,
+// kinetic boundary mode: the images (g.ioff != nullptr) enter the sums and
+// the amplification test like neighbours, at their mirrored offsets
+__global__ void __launch_bounds__(128) k_mixed_prep(DevGeom g, uint8_t *__restrict__ flag,
+                                                    float2 *__restrict__ nrm_f, float *__restrict__ dmin_f,
+                                                    float4 *__restrict__ gm, float2 *__restrict__ dxy_f,
                                                     float2 *__restrict__ lsw_f, float2 *__restrict__ fxw_f,
+                                                    float2 *__restrict__ ilsw_f, float4 *__restrict__ igf,
                                                     int *n_fp64)
 {
+    const int64_t n = g.n;
+    const double2 *__restrict__ xy = g.xy;
+    const double2 *__restrict__ nrm = g.nrm;
+    const double *__restrict__ dmin = g.dmin;
+    const int32_t *__restrict__ off = g.off;
+    const int32_t *__restrict__ idx = g.idx;
+    const uint8_t *__restrict__ mask = g.mask;
+    const double2 *__restrict__ lsw = g.lsw;
+    const double2 *__restrict__ fxw = g.fxw;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const double2 P0 = xy[p];
@@ -58,6 +62,27 @@ __global__ void __launch_bounds__(128) k_mixed_prep(int64_t n, const double2 *__
         if (m & M_YNEG) amp[3] += fabs(w.y) * d;
     }
     const double2 n0 = nrm[p];
+    if (g.ioff) {
+        for (int e = g.ioff[p]; e < g.ioff[p + 1]; ++e) {
+            const double2 Pi = xy[g.iidx[e]];
+            double dx = Pi.x - P0.x, dy = Pi.y - P0.y;
+            const double dn = dx * n0.x + dy * n0.y;
+            dx = dx - 2.0 * dn * n0.x;
+            dy = dy - 2.0 * dn * n0.y;
+            Sxx += dx * dx;
+            Sxy += dx * dy;
+            Syy += dy * dy;
+            const double d = sqrt(dx * dx + dy * dy);
+            const double2 a = g.ilsw[e], w = g.ifxw[e];
+            ilsw_f[e] = make_float2((float)a.x, (float)a.y);
+            igf[e] = make_float4((float)dx, (float)dy, (float)w.x, (float)w.y);
+            const uint8_t m = g.imask[e];
+            if (m & M_XPOS) amp[0] += fabs(w.x) * d;
+            if (m & M_XNEG) amp[1] += fabs(w.x) * d;
+            if (m & M_YPOS) amp[2] += fabs(w.y) * d;
+            if (m & M_YNEG) amp[3] += fabs(w.y) * d;
+        }
+    }
     nrm_f[p] = make_float2((float)n0.x, (float)n0.y);
     gm[p] = make_float4((float)Sxx, (float)Sxy, (float)Syy, 0.0f);
     dmin_f[p] = (float)dmin[p];
@@ -69,11 +94,11 @@ __global__ void __launch_bounds__(128) k_mixed_prep(int64_t n, const double2 *__
 }
 
 cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, float *dmin_f, float4 *gm,
-                              float2 *dxy_f, float2 *lsw_f, float2 *fxw_f, int *n_fp64, cudaStream_t s)
+                              float2 *dxy_f, float2 *lsw_f, float2 *fxw_f, float2 *ilsw_f, float4 *igf,
+                              int *n_fp64, cudaStream_t s)
 {
-    k_mixed_prep<<<(unsigned)((g.n + 127) / 128), 128, 0, s>>>(g.n, g.xy, g.nrm, g.dmin, g.off, g.idx, g.mask,
-                                                               g.lsw, g.fxw, flag, nrm_f, dmin_f, gm, dxy_f,
-                                                               lsw_f, fxw_f, n_fp64);
+    k_mixed_prep<<<(unsigned)((g.n + 127) / 128), 128, 0, s>>>(g, flag, nrm_f, dmin_f, gm, dxy_f, lsw_f, fxw_f,
+                                                               ilsw_f, igf, n_fp64);
     return cudaGetLastError();
 }
 
@@ -134,10 +159,38 @@ cudaError_t launch_sell_fill(int64_t n, const int32_t *off, const int32_t *slice
     return cudaGetLastError();
 }
 
+// Kinetic boundary mode: the q carried by the image (entry e of the image
+// CSR) of a neighbour P_i of P_0 (see image_q of the FP64 kernels), with
+// d the image's offset: the reflection across the tangent line of P_i's own
+// reconstruction q_i - d_i.grad q_i / 2 (d_i the reflection of d) when
+// recon, else of q_i; the free stream qf for a far-field image.
+__device__ __forceinline__ void image_q_f(const MixedGeom &g, int e, uint8_t m, float2 n0, const float *qf,
+                                          const float *__restrict__ q, const float *__restrict__ qg, float2 d,
+                                          bool recon, float qi[4])
+{
+    if (m & M_IMG_FAR) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qi[k] = qf[k];
+        return;
+    }
+    const int i = g.iidx[e];
+    load4f(q, i, qi);
+    if (recon) {
+        reflect2(d.x, d.y, n0.x, n0.y);
+        float gi[8];
+        load8f(qg, i, gi);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qi[k] = qi[k] - 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
+    }
+    reflect2(qi[1], qi[2], n0.x, n0.y);
+}
+
 // --------------------------------------------------------------------------
 // q_derivatives() in FP32 (E15; same arithmetic as k_qgrad)
 // --------------------------------------------------------------------------
-template <int THREADS, int MINB>
+// KIN: the kinetic boundary mode (a separate instantiation keeps the plain
+// kernels' registers as they are)
+template <int THREADS, int MINB, bool KIN>
 __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, const float *__restrict__ q,
                                                                const float *__restrict__ qg_old,
                                                                float *__restrict__ qg_new, float limK)
@@ -187,6 +240,41 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
             sy[k] += a.y * dq[k];
         }
     }
+    if constexpr (KIN) {
+        // kinetic boundary mode: the mirror images of the neighbours
+        const int f0 = g.ioff[p], f1 = g.ioff[p + 1];
+        if (f0 < f1) {
+            const float2 n0 = g.nrm[p];
+            const float *qf = g.qinf + 4 * (g.pcase ? (int)g.pcase[p] : 0);
+            for (int e = f0; e < f1; ++e) {
+                const uint8_t m = g.imask[e];
+                const float2 a = g.ilsw[e];
+                const float4 r = g.igf[e];
+                const float2 d = make_float2(r.x, r.y);
+                float qi[4], dq[4];
+                image_q_f(g, e, m, n0, qf, q, qg_old, d, inner, qi);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dq[k] = qi[k] - q0[k];
+                if (inner) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) dq[k] = dq[k] + 0.5f * (d.x * g0[k] + d.y * g0[4 + k]);
+                }
+                if (limit) {
+                    if (inner) image_q_f(g, e, m, n0, qf, q, qg_old, d, false, qi);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        qmax[k] = fmaxf(qmax[k], qi[k]);
+                        qmin[k] = fminf(qmin[k], qi[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    sx[k] += a.x * dq[k];
+                    sy[k] += a.y * dq[k];
+                }
+            }
+        }
+    }
     if (limit) {
         float dmax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int s = 0; s < deg; ++s) {
@@ -194,6 +282,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
             const float2 d = make_float2(M.x * a.x + M.y * a.y, M.y * a.x + M.z * a.y);
 #pragma unroll
             for (int k = 0; k < 4; ++k) dmax[k] = fmaxf(dmax[k], fabsf(0.5f * (d.x * sx[k] + d.y * sy[k])));
+        }
+        if constexpr (KIN) {
+            for (int e = g.ioff[p]; e < g.ioff[p + 1]; ++e) {
+                const float4 r = g.igf[e];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dmax[k] = fmaxf(dmax[k], fabsf(0.5f * (r.x * sx[k] + r.y * sy[k])));
+            }
         }
         const float h = g.dmin[p] * limK;
         const float eps2 = h * h * h;
@@ -225,9 +320,56 @@ __device__ __forceinline__ void flag_nonphysical_m(int *status, int64_t p)
     atomicMin(status + 1, (int)p);
 }
 
+// One member's term of E11 in FP32 (the weights' FP64 copy w64[e] at points
+// with an FP64 closure), frame (t, n) of P_0, R in the order [mass,
+// s-momentum, n-momentum, energy]; see edge_residual of the FP64 kernels.
+__device__ __forceinline__ void edge_residual_f(const float qti[4], const float qt0[4], uint32_t m, float2 w,
+                                                bool fp64, const double2 *__restrict__ w64, int64_t e, float2 n0,
+                                                float tx, float ty, float inv_gm1, int g14, float R[4],
+                                                double R64[4], bool &ok)
+{
+    // equal reconstructed states have dG = 0 exactly; the two flux
+    // evaluations may be compiled along different paths (the q~_0 one
+    // partly hoisted), so equality is decided on q~, not on G
+    if (qti[0] == qt0[0] && qti[1] == qt0[1] && qti[2] == qt0[2] && qti[3] == qt0[3]) return;
+    PrimF si, s0;
+    ok &= prim_from_q_f(qti, inv_gm1, g14, si);
+    ok &= prim_from_q_f(qt0, inv_gm1, g14, s0);
+    const float us_i = si.u * tx + si.v * ty, un_i = si.u * n0.x + si.v * n0.y;
+    const float us_0 = s0.u * tx + s0.v * ty, un_0 = s0.u * n0.x + s0.v * n0.y;
+    float dGs[4] = {0, 0, 0, 0}, dGn[4] = {0, 0, 0, 0};
+    if (w.x != 0.0f) {
+        const float sg = (m & M_XPOS) ? 1.0f : -1.0f;
+        float Gi[4], G0[4];
+        split_flux_f(sg, si, us_i, un_i, Gi);
+        split_flux_f(sg, s0, us_0, un_0, G0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dGs[k] = __fsub_rn(Gi[k], G0[k]);
+    }
+    if (w.y != 0.0f) {
+        const float sg = (m & M_YPOS) ? 1.0f : -1.0f;
+        float Gi[4], G0[4];
+        split_flux_f(sg, si, un_i, us_i, Gi);
+        split_flux_f(sg, s0, un_0, us_0, G0);
+        // Gn components are [mass, n-momentum, s-momentum, energy]
+        dGn[0] = __fsub_rn(Gi[0], G0[0]);
+        dGn[1] = __fsub_rn(Gi[2], G0[2]);
+        dGn[2] = __fsub_rn(Gi[1], G0[1]);
+        dGn[3] = __fsub_rn(Gi[3], G0[3]);
+    }
+    if (fp64) {
+        const double2 ww = w64[e];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) R64[k] += ww.x * (double)dGs[k] + ww.y * (double)dGn[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) R[k] += w.x * dGs[k] + w.y * dGn[k];
+    }
+}
+
 // PF: software-pipelined neighbour loop (the next slot's record, index and
 // neighbour values are loaded while the current slot's fluxes are evaluated)
-template <int THREADS, int MINB, bool PF>
+template <int THREADS, int MINB, bool PF, bool KIN>
 __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxParams P)
 {
     const MixedGeom &g = P.g;
@@ -239,7 +381,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
     const bool fp64 = (fl & FLAG_FP64_CLOSURE) != 0;
     float Rl[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // residual, global frame
     double R64g[4] = {0.0, 0.0, 0.0, 0.0};   // FP64-closure points
-    if (live && flag != FLAG_FARFIELD) {
+    // far-field points are held at the free stream, except in the kinetic boundary mode
+    if (live && (flag != FLAG_FARFIELD || KIN)) {
         const int deg = g.off[p + 1] - g.off[p];
         const int64_t base = g.slice_off[p >> 5] + (p & 31);
         const float2 n0 = g.nrm[p];
@@ -317,42 +460,22 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
                     }
                 }
             }
-            // equal reconstructed states have dG = 0 exactly; the two flux
-            // evaluations may be compiled along different paths (the q~_0 one
-            // partly hoisted), so equality is decided on q~, not on G
-            if (qti[0] == qt0[0] && qti[1] == qt0[1] && qti[2] == qt0[2] && qti[3] == qt0[3]) continue;
-            PrimF si, s0;
-            ok &= prim_from_q_f(qti, P.inv_gm1, P.g14, si);
-            ok &= prim_from_q_f(qt0, P.inv_gm1, P.g14, s0);
-            const float us_i = si.u * tx + si.v * ty, un_i = si.u * n0.x + si.v * n0.y;
-            const float us_0 = s0.u * tx + s0.v * ty, un_0 = s0.u * n0.x + s0.v * n0.y;
-            float dGs[4] = {0, 0, 0, 0}, dGn[4] = {0, 0, 0, 0};
-            if (w.x != 0.0f) {
-                const float sg = (m & M_XPOS) ? 1.0f : -1.0f;
-                float Gi[4], G0[4];
-                split_flux_f(sg, si, us_i, un_i, Gi);
-                split_flux_f(sg, s0, us_0, un_0, G0);
+            edge_residual_f(qti, qt0, m, w, fp64, g.fxw64, e, n0, tx, ty, P.inv_gm1, P.g14, R, R64, ok);
+        }
+        if constexpr (KIN) {
+            // kinetic boundary mode: the mirror images of the neighbours
+            const int f0 = g.ioff[p], f1 = g.ioff[p + 1];
+            const float *qf = g.qinf + 4 * (g.pcase ? (int)g.pcase[p] : 0);
+            for (int e = f0; e < f1; ++e) {
+                const float4 rec = g.igf[e];
+                const float2 d = make_float2(rec.x, rec.y), w = make_float2(rec.z, rec.w);
+                const uint8_t m = g.imask[e];
+                float qti[4], qt0[4];
+                image_q_f(g, e, m, n0, qf, P.q, P.qg, d, second, qti);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) dGs[k] = __fsub_rn(Gi[k], G0[k]);
-            }
-            if (w.y != 0.0f) {
-                const float sg = (m & M_YPOS) ? 1.0f : -1.0f;
-                float Gi[4], G0[4];
-                split_flux_f(sg, si, un_i, us_i, Gi);
-                split_flux_f(sg, s0, un_0, us_0, G0);
-                // Gn components are [mass, n-momentum, s-momentum, energy]
-                dGn[0] = __fsub_rn(Gi[0], G0[0]);
-                dGn[1] = __fsub_rn(Gi[2], G0[2]);
-                dGn[2] = __fsub_rn(Gi[1], G0[1]);
-                dGn[3] = __fsub_rn(Gi[3], G0[3]);
-            }
-            if (fp64) {
-                const double2 w64 = g.fxw64[e];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) R64[k] += w64.x * (double)dGs[k] + w64.y * (double)dGn[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) R[k] += w.x * dGs[k] + w.y * dGn[k];
+                for (int k = 0; k < 4; ++k)
+                    qt0[k] = second ? q0[k] - 0.5f * (d.x * g0[k] + d.y * g0[4 + k]) : q0[k];
+                edge_residual_f(qti, qt0, m, w, fp64, g.ifxw64, e, n0, tx, ty, P.inv_gm1, P.g14, R, R64, ok);
             }
         }
         if (!ok) flag_nonphysical_m(P.status, p);
@@ -434,7 +557,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
             const double mn = Unew[1] * n0.x + Unew[2] * n0.y;
             Unew[1] = Unew[1] - mn * n0.x;
             Unew[2] = Unew[2] - mn * n0.y;
-        } else if (flag == FLAG_FARFIELD) {
+        } else if (flag == FLAG_FARFIELD && !KIN) {
             const double *Ui = P.case_uinf ? P.case_uinf + 4 * (int)P.pcase[p] : P.Uinf;
 #pragma unroll
             for (int k = 0; k < 4; ++k) Unew[k] = Ui[k];
@@ -485,31 +608,39 @@ __global__ void __launch_bounds__(256) k_grad_out_f(int64_t n, const int32_t *__
 
 // launch-shape variants of the two hot kernels, chosen by the autotuner:
 // (threads per block, minimum resident blocks per SM for the register cap)
-template <int T, int M>
+template <int T, int M, bool KIN>
 static cudaError_t qgrad_v(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new, float limK,
                            cudaStream_t s)
 {
-    k_qgrad_mixed<T, M><<<(unsigned)((g.n + T - 1) / T), T, 0, s>>>(g, q, qg_old, qg_new, limK);
+    k_qgrad_mixed<T, M, KIN><<<(unsigned)((g.n + T - 1) / T), T, 0, s>>>(g, q, qg_old, qg_new, limK);
     return cudaGetLastError();
 }
 
-template <int T, int M, bool PF>
+template <int T, int M, bool PF, bool KIN>
 static cudaError_t flux_v(const MixedFluxParams &P, cudaStream_t s)
 {
-    k_flux_update_mixed<T, M, PF><<<(unsigned)((P.g.n + T - 1) / T), T, 0, s>>>(P);
+    k_flux_update_mixed<T, M, PF, KIN><<<(unsigned)((P.g.n + T - 1) / T), T, 0, s>>>(P);
     return cudaGetLastError();
 }
 
 using QgradFn = cudaError_t (*)(const MixedGeom &, const float *, const float *, float *, float, cudaStream_t);
 using FluxFn = cudaError_t (*)(const MixedFluxParams &, cudaStream_t);
 
-static const QgradFn kQgradVariants[] = {qgrad_v<128, 8>, qgrad_v<64, 16>, qgrad_v<256, 4>, qgrad_v<128, 6>,
-                                         qgrad_v<256, 3>, qgrad_v<96, 10>};
-static const FluxFn kFluxVariants[] = {
-    flux_v<128, 7, false>, flux_v<64, 14, false>, flux_v<256, 3, false>, flux_v<128, 6, false>,
-    flux_v<128, 8, false>, flux_v<256, 4, false>, flux_v<128, 7, true>,  flux_v<64, 14, true>,
-    flux_v<256, 3, true>,  flux_v<128, 6, true>,  flux_v<128, 8, true>,  flux_v<256, 4, true>,
-    flux_v<128, 5, true>,  flux_v<128, 4, true>};
+// [plain, kinetic boundary mode][variant]
+template <bool K>
+struct VariantTable {
+    static constexpr QgradFn qgrad[] = {qgrad_v<128, 8, K>, qgrad_v<64, 16, K>, qgrad_v<256, 4, K>,
+                                        qgrad_v<128, 6, K>, qgrad_v<256, 3, K>, qgrad_v<96, 10, K>};
+    static constexpr FluxFn flux[] = {
+        flux_v<128, 7, false, K>, flux_v<64, 14, false, K>, flux_v<256, 3, false, K>, flux_v<128, 6, false, K>,
+        flux_v<128, 8, false, K>, flux_v<256, 4, false, K>, flux_v<128, 7, true, K>,  flux_v<64, 14, true, K>,
+        flux_v<256, 3, true, K>,  flux_v<128, 6, true, K>,  flux_v<128, 8, true, K>,  flux_v<256, 4, true, K>,
+        flux_v<128, 5, true, K>,  flux_v<128, 4, true, K>};
+};
+static const QgradFn *const kQgradVariants[2] = {VariantTable<false>::qgrad, VariantTable<true>::qgrad};
+static const FluxFn *const kFluxVariants[2] = {VariantTable<false>::flux, VariantTable<true>::flux};
+static constexpr int kNumQgradVariants = sizeof VariantTable<false>::qgrad / sizeof(QgradFn);
+static constexpr int kNumFluxVariants = sizeof VariantTable<false>::flux / sizeof(FluxFn);
 static const int kQgradShape[][2] = {{128, 8}, {64, 16}, {256, 4}, {128, 6}, {256, 3}, {96, 10}};
 // flux shapes 6-11 repeat 0-5 with the software-pipelined neighbour loop,
 // 12-13 give that loop more registers
@@ -519,8 +650,7 @@ static const int kFluxShape[][2] = {{128, 7}, {64, 14}, {256, 3}, {128, 6}, {128
 
 int mixed_variants(int kernel_class)
 {
-    return kernel_class == 0 ? (int)(sizeof kFluxVariants / sizeof kFluxVariants[0])
-                             : (int)(sizeof kQgradVariants / sizeof kQgradVariants[0]);
+    return kernel_class == 0 ? kNumFluxVariants : kNumQgradVariants;
 }
 
 void mixed_variant_shape(int kernel_class, int v, int *threads, int *min_blocks)
@@ -533,16 +663,14 @@ void mixed_variant_shape(int kernel_class, int v, int *threads, int *min_blocks)
 cudaError_t launch_qgrad_mixed(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new,
                                double limiter_K, cudaStream_t s, int variant)
 {
-    if (variant < 0 || variant >= (int)(sizeof kQgradVariants / sizeof kQgradVariants[0]))
-        return cudaErrorInvalidValue;
-    return kQgradVariants[variant](g, q, qg_old, qg_new, (float)limiter_K, s);
+    if (variant < 0 || variant >= kNumQgradVariants) return cudaErrorInvalidValue;
+    return kQgradVariants[g.ioff ? 1 : 0][variant](g, q, qg_old, qg_new, (float)limiter_K, s);
 }
 
 cudaError_t launch_flux_mixed(const MixedFluxParams &P, cudaStream_t s, int variant)
 {
-    if (variant < 0 || variant >= (int)(sizeof kFluxVariants / sizeof kFluxVariants[0]))
-        return cudaErrorInvalidValue;
-    return kFluxVariants[variant](P, s);
+    if (variant < 0 || variant >= kNumFluxVariants) return cudaErrorInvalidValue;
+    return kFluxVariants[P.g.ioff ? 1 : 0][variant](P, s);
 }
 
 cudaError_t launch_q_from_U_mixed(int64_t n, const Gas &gas, const double *U, float *q, int *status,

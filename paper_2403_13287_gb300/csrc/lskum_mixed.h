@@ -26,6 +26,16 @@ struct MixedGeom {
                                           // matrix M; the slot's offset is d = M a
     const float4 *__restrict__ gf;        // per slot: (dx, dy, w_s, w_n) sub-stencil weights
     const double2 *__restrict__ fxw64;    // per slot: FP64 sub-stencil weights
+    // kinetic boundary mode (all nullptr otherwise): mirror images of the
+    // neighbours of wall and far-field points, CSR per point (see DevGeom)
+    const int32_t *__restrict__ ioff;
+    const int32_t *__restrict__ iidx;
+    const uint8_t *__restrict__ imask;
+    const float2 *__restrict__ ilsw;      // full-stencil weights (the offset is d = M a)
+    const float4 *__restrict__ igf;       // (dx, dy, w_s, w_n) of the image
+    const double2 *__restrict__ ifxw64;   // FP64 sub-stencil weights of the image
+    const float *__restrict__ qinf;       // [cases][4] q of each case's free stream
+    const uint16_t *__restrict__ pcase;   // per point: its case in a batch, or nullptr
 };
 
 static constexpr int32_t kSlotIndexMask = 0x0fffffff;  // mixed layout: n < 2^28
@@ -51,8 +61,10 @@ struct MixedFluxParams {
     int order, mode, stage;
 };
 
+// ilsw_f/igf receive the FP32 weights and offsets of the images (kinetic mode, else nullptr)
 cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, float *dmin_f, float4 *gm,
-                              float2 *dxy_f, float2 *lsw_f, float2 *fxw_f, int *n_fp64, cudaStream_t s);
+                              float2 *dxy_f, float2 *lsw_f, float2 *fxw_f, float2 *ilsw_f, float4 *igf,
+                              int *n_fp64, cudaStream_t s);
 cudaError_t launch_sell_fill(int64_t n, const int32_t *off, const int32_t *slice_off, const int32_t *idx,
                              const uint8_t *mask, const float2 *dxy, const float2 *lsw, const float2 *fxw,
                              const double2 *fxw64, const MixedGeom &m, cudaStream_t s);

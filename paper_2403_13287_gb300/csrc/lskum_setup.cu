@@ -19,6 +19,28 @@ static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / 
 //   sub-stencil k: w_s = (Snn_k ds - Ssn_k dn)/det_k, w_n = (Sss_k dn - Ssn_k ds)/det_k
 // A sub-stencil that the point's residual does not use gets weight 0: far-field
 // points use none, wall points drop y+ (no upwind points inside the body).
+// Kinetic boundary mode (ioff != nullptr): a wall or far-field point also has
+// the mirror images of its neighbours (CSR ioff/iidx/imask, built from the
+// split of a first pass), at local offsets (ds, -dn) and global offsets
+// (dx - 2 dn nx, dy - 2 dn ny); they enter every sum after the neighbours,
+// and such a point uses all four sub-stencils.
+__device__ __forceinline__ void edge_offsets(double2 P0, double2 N0, double2 Pi, double &dx, double &dy, double &ds,
+                                             double &dn)
+{
+    dx = __dsub_rn(Pi.x, P0.x);
+    dy = __dsub_rn(Pi.y, P0.y);
+    ds = __dsub_rn(__dmul_rn(dx, N0.y), __dmul_rn(dy, N0.x));
+    dn = __dadd_rn(__dmul_rn(dx, N0.x), __dmul_rn(dy, N0.y));
+}
+
+__device__ __forceinline__ void image_offsets(double2 N0, double &dx, double &dy, double &ds, double &dn)
+{
+    dx = __dsub_rn(dx, __dmul_rn(2.0 * dn, N0.x));
+    dy = __dsub_rn(dy, __dmul_rn(2.0 * dn, N0.y));
+    dn = -dn;
+    (void)ds;
+}
+
 __global__ void __launch_bounds__(128) k_geometry(int64_t n, const double2 *__restrict__ xy,
                                                   const double2 *__restrict__ nrm,
                                                   const uint8_t *__restrict__ flag,
@@ -26,7 +48,7 @@ __global__ void __launch_bounds__(128) k_geometry(int64_t n, const double2 *__re
                                                   const int32_t *__restrict__ idx,
                                                   uint8_t *__restrict__ mask, double2 *__restrict__ lsw,
                                                   double2 *__restrict__ fxw, double *__restrict__ dmin,
-                                                  int *bad)
+                                                  int *bad, ImageEdges im)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -37,12 +59,10 @@ __global__ void __launch_bounds__(128) k_geometry(int64_t n, const double2 *__re
     double ss[4] = {0, 0, 0, 0}, sn[4] = {0, 0, 0, 0}, nn[4] = {0, 0, 0, 0};
     double d2min = 1.0 / 0.0;
     const int e0 = off[p], e1 = off[p + 1];
+    const int i0 = im.off ? im.off[p] : 0, i1 = im.off ? im.off[p + 1] : 0;
     for (int e = e0; e < e1; ++e) {
-        const double2 Pi = xy[idx[e]];
-        const double dx = __dsub_rn(Pi.x, P0.x);
-        const double dy = __dsub_rn(Pi.y, P0.y);
-        const double ds = __dsub_rn(__dmul_rn(dx, N0.y), __dmul_rn(dy, N0.x));
-        const double dn = __dadd_rn(__dmul_rn(dx, N0.x), __dmul_rn(dy, N0.y));
+        double dx, dy, ds, dn;
+        edge_offsets(P0, N0, xy[idx[e]], dx, dy, ds, dn);
         uint8_t m = 0;
         if (ds < 0.0) m |= M_XPOS;
         if (ds > 0.0) m |= M_XNEG;
@@ -59,14 +79,28 @@ __global__ void __launch_bounds__(128) k_geometry(int64_t n, const double2 *__re
         const double d2 = dx * dx + dy * dy;
         d2min = d2 < d2min ? d2 : d2min;
     }
+    for (int e = i0; e < i1; ++e) {
+        double dx, dy, ds, dn;
+        edge_offsets(P0, N0, xy[im.idx[e]], dx, dy, ds, dn);
+        image_offsets(N0, dx, dy, ds, dn);
+        const uint8_t m = im.mask[e];
+        Sxx += dx * dx;
+        Sxy += dx * dy;
+        Syy += dy * dy;
+        const int ks = (m & M_XPOS) ? 0 : ((m & M_XNEG) ? 1 : -1);
+        const int kn = (m & M_YPOS) ? 2 : ((m & M_YNEG) ? 3 : -1);
+        if (ks >= 0) { ss[ks] += ds * ds; sn[ks] += ds * dn; nn[ks] += dn * dn; }
+        if (kn >= 0) { ss[kn] += ds * ds; sn[kn] += ds * dn; nn[kn] += dn * dn; }
+    }
     dmin[p] = sqrt(d2min);
     const double detF = Sxx * Syy - Sxy * Sxy;
     bool good = detF > 1e-10 * Sxx * Syy;
     bool need[4];
     double det[4];
+    const bool kinetic = im.kinetic && f != FLAG_INTERIOR;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        need[k] = (f == FLAG_INTERIOR) || (f == FLAG_WALL && k != 2);
+        need[k] = (f == FLAG_INTERIOR) || kinetic || (f == FLAG_WALL && k != 2);
         det[k] = ss[k] * nn[k] - sn[k] * sn[k];
         if (need[k] && !(det[k] > 1e-10 * ss[k] * nn[k])) good = false;
     }
@@ -75,11 +109,8 @@ __global__ void __launch_bounds__(128) k_geometry(int64_t n, const double2 *__re
         atomicMin(bad + 1, (int)p);
     }
     for (int e = e0; e < e1; ++e) {
-        const double2 Pi = xy[idx[e]];
-        const double dx = __dsub_rn(Pi.x, P0.x);
-        const double dy = __dsub_rn(Pi.y, P0.y);
-        const double ds = __dsub_rn(__dmul_rn(dx, N0.y), __dmul_rn(dy, N0.x));
-        const double dn = __dadd_rn(__dmul_rn(dx, N0.x), __dmul_rn(dy, N0.y));
+        double dx, dy, ds, dn;
+        edge_offsets(P0, N0, xy[idx[e]], dx, dy, ds, dn);
         const uint8_t m = mask[e];
         lsw[e] = make_double2((Syy * dx - Sxy * dy) / detF, (Sxx * dy - Sxy * dx) / detF);
         const int ks = (m & M_XPOS) ? 0 : ((m & M_XNEG) ? 1 : -1);
@@ -89,13 +120,27 @@ __global__ void __launch_bounds__(128) k_geometry(int64_t n, const double2 *__re
         if (kn >= 0 && need[kn]) wn = (ss[kn] * dn - sn[kn] * ds) / det[kn];
         fxw[e] = make_double2(ws, wn);
     }
+    for (int e = i0; e < i1; ++e) {
+        double dx, dy, ds, dn;
+        edge_offsets(P0, N0, xy[im.idx[e]], dx, dy, ds, dn);
+        image_offsets(N0, dx, dy, ds, dn);
+        const uint8_t m = im.mask[e];
+        im.lsw[e] = make_double2((Syy * dx - Sxy * dy) / detF, (Sxx * dy - Sxy * dx) / detF);
+        const int ks = (m & M_XPOS) ? 0 : ((m & M_XNEG) ? 1 : -1);
+        const int kn = (m & M_YPOS) ? 2 : ((m & M_YNEG) ? 3 : -1);
+        double ws = 0.0, wn = 0.0;
+        if (ks >= 0) ws = (nn[ks] * ds - sn[ks] * dn) / det[ks];
+        if (kn >= 0) wn = (ss[kn] * dn - sn[kn] * ds) / det[kn];
+        im.fxw[e] = make_double2(ws, wn);
+        if (im.hd) im.hd[e] = make_double2(0.5 * dx, 0.5 * dy);
+    }
 }
 
 cudaError_t launch_geometry(int64_t n, const double2 *xy, const double2 *nrm, const uint8_t *flag,
                             const int32_t *off, const int32_t *idx, uint8_t *mask, double2 *lsw,
-                            double2 *fxw, double *dmin, int *bad, cudaStream_t s)
+                            double2 *fxw, double *dmin, int *bad, const ImageEdges &im, cudaStream_t s)
 {
-    k_geometry<<<nblk(n, 128), 128, 0, s>>>(n, xy, nrm, flag, off, idx, mask, lsw, fxw, dmin, bad);
+    k_geometry<<<nblk(n, 128), 128, 0, s>>>(n, xy, nrm, flag, off, idx, mask, lsw, fxw, dmin, bad, im);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,9 @@ LSKUM_ERR_OOM = 5
 LSKUM_ERR_NONPHYSICAL = 6
 LSKUM_ERR_TIMEOUT = 7
 
+LSKUM_BOUNDARY_PLAIN = 0
+LSKUM_BOUNDARY_KINETIC = 1
+
 LSKUM_KERNEL_FLUX = 0
 LSKUM_KERNEL_QGRAD = 1
 
@@ -37,7 +40,7 @@ class lskum_config(ctypes.Structure):
                 ("time_scheme", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("mach", ctypes.c_double), ("aoa_deg", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("precision", ctypes.c_int),
-                ("reorder", ctypes.c_int), ("limiter_K", ctypes.c_double)]
+                ("reorder", ctypes.c_int), ("limiter_K", ctypes.c_double), ("boundary", ctypes.c_int)]
 
 
 class LskumError(RuntimeError):
@@ -150,12 +153,12 @@ class Solver:
     """A q-LSKUM context (lskum_ctx) on the current CUDA device."""
 
     def __init__(self, cloud, order=2, inner_iters=3, time_scheme=1, cfl=0.2, mach=0.63,
-                 aoa_deg=2.0, gamma=1.4, precision=0, reorder=0, limiter_K=0.0, stream=None):
+                 aoa_deg=2.0, gamma=1.4, precision=0, reorder=0, limiter_K=0.0, stream=None, boundary=0):
         L = load()
         self._L = L
         self.n = int(cloud["n"])
         self.cfg = lskum_config(order, inner_iters, time_scheme, cfl, mach, aoa_deg, gamma,
-                                precision, reorder, limiter_K)
+                                precision, reorder, limiter_K, boundary)
         self._keep = {k: np.ascontiguousarray(cloud[k], dtype=np.float64) for k in ("x", "y", "nx", "ny")}
         for k in ("flags", "nbr_offsets", "nbr_idx"):
             self._keep[k] = np.ascontiguousarray(cloud[k], dtype=np.int32)
@@ -177,14 +180,14 @@ class Solver:
 
     @classmethod
     def batch(cls, cases, order=2, inner_iters=3, time_scheme=1, cfl=0.2, gamma=1.4, precision=1, reorder=1,
-              limiter_K=0.0, stream=None):
+              limiter_K=0.0, stream=None, boundary=0):
         """One context over several independent solves (lskum_create_batch).
         cases: a list of (cloud, mach, aoa_deg); clouds may repeat."""
         self = cls.__new__(cls)
         L = load()
         self._L = L
         self.cfg = lskum_config(order, inner_iters, time_scheme, cfl, cases[0][1], cases[0][2], gamma,
-                                precision, reorder, limiter_K)
+                                precision, reorder, limiter_K, boundary)
         keep, arr = {}, (lskum_case * len(cases))()
         for k, (cloud, mach, aoa) in enumerate(cases):
             key = id(cloud)

@@ -3,11 +3,13 @@ include/lskum.h declares (no GPU needed; no compute call is made)."""
 import ctypes
 import os
 import re
+import subprocess
 
 from paper_2403_13287_gb300 import build as lbuild
 from paper_2403_13287_gb300 import lskum
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lskum.h")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lskum.h")
 
 
 def declared_functions():
@@ -31,19 +33,40 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
-def test_config_struct_matches_header_layout():
-    # order, inner_iters, time_scheme (3 ints, padded to 16), 4 doubles, 2 ints, 1 double
-    assert ctypes.sizeof(lskum.lskum_config) == 64
-    assert lskum.lskum_config.cfl.offset == 16
-    assert lskum.lskum_config.precision.offset == 48
-    assert lskum.lskum_config.limiter_K.offset == 56
+def test_config_struct_matches_header_layout(tmp_path):
+    """ctypes' lskum_config against the C compiler's layout of the header's"""
+    fields = [f[0] for f in lskum.lskum_config._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "lskum.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(lskum_config));\n'
+                   + "".join('  printf("%%zu\\n", offsetof(lskum_config, %s));\n' % f for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(lskum.lskum_config)
+    assert got[1:] == [getattr(lskum.lskum_config, f).offset for f in fields]
 
 
 def test_create_rejects_bad_arguments_without_touching_the_gpu():
     L = lskum.load()
     ctx = ctypes.c_void_p()
-    cfg = lskum.lskum_config(2, 3, 1, 0.2, 0.5, 0.0, 1.4, 0, 0, 0.0)
+    cfg = lskum.lskum_config(2, 3, 1, 0.2, 0.5, 0.0, 1.4, 0, 0, 0.0, 0)
     st = L.lskum_create(0, None, None, None, None, None, None, None, 0, None, ctypes.byref(cfg), None,
                         ctypes.byref(ctx))
     assert st == lskum.LSKUM_ERR_ARG and not ctx.value
     assert b"out of range" in L.lskum_last_error(None)
+
+
+def test_create_rejects_an_unknown_boundary_mode_without_touching_the_gpu():
+    import numpy as np
+    L = lskum.load()
+    ctx = ctypes.c_void_p()
+    cfg = lskum.lskum_config(2, 3, 1, 0.2, 0.5, 0.0, 1.4, 0, 0, 0.0, 2)
+    x = np.zeros(3); nx = np.ones(3)
+    fl = np.zeros(3, np.int32); off = np.array([0, 2, 4, 6], np.int32); idx = np.array([1, 2, 0, 2, 0, 1], np.int32)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    st = L.lskum_create(3, p(x), p(x), p(nx), p(x), p(fl), p(off), p(idx), 0, None, ctypes.byref(cfg), None,
+                        ctypes.byref(ctx))
+    assert st == lskum.LSKUM_ERR_ARG and not ctx.value
+    assert b"boundary" in L.lskum_last_error(None)
