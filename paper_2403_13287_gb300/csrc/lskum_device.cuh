@@ -123,8 +123,9 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
     if (!finite_positive(beta)) return false;
     s.rsb = rsqrt(beta);
     const double ib = s.rsb * s.rsb;       // 1/beta, so 1/q4 = -ib/2 without a division
-    s.u = 0.5 * qt[1] * ib;
-    s.v = 0.5 * qt[2] * ib;
+    const double hib = 0.5 * ib;           // (exact halving: u = q1 hib rounds as 0.5 q1 ib)
+    s.u = qt[1] * hib;
+    s.v = qt[2] * hib;
     s.sqb = beta * s.rsb;
     const double ke = beta * (s.u * s.u + s.v * s.v);
     if (gas.g14) {
@@ -133,7 +134,7 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
     } else {
         s.rho = exp_tab(qt[0] - log(beta) * gas.inv_gm1 + ke);
     }
-    s.p = 0.5 * s.rho * ib;
+    s.p = s.rho * hib;
     // per unit mass: p/rho = 1/(2 beta), rho E = p/(gamma-1) + rho |u|^2/2
     const double hu2 = 0.5 * (s.u * s.u + s.v * s.v);
     s.h = fma(0.5 * (gas.inv_gm1 + 1.0), ib, hu2);
@@ -143,12 +144,12 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
 }
 
 // erf(S) and exp(-S^2) together, from one row of a Taylor table: on the grid
-// s_k = k/32 (0 <= s_k <= 6) the row holds the degree-8 Taylor coefficients
-// of both functions in d = |S| - s_k (|d| <= 1/64), so each is one Horner
+// s_k = k/128 (0 <= s_k <= 6) the row holds the degree-6 Taylor coefficients
+// of both functions in d = |S| - s_k (|d| <= 1/256), so each is one Horner
 // chain with an absolute error of about one unit in the last place of 1
 // (gen_fp64_tables.py; the first omitted terms are below 1e-18). The nearest
 // grid index comes from the top bits of |S| by integer operations, so the
-// FP64 pipe sees one subtraction and 16 fused multiply-adds. |S| >= 6:
+// FP64 pipe sees one subtraction and 12 fused multiply-adds. |S| >= 6:
 // erf = +-1 (erfc(6) = 2e-17) and exp(-S^2) directly.
 __device__ __forceinline__ void erf_exp(double S, double &erfS, double &eS)
 {
@@ -184,21 +185,32 @@ __device__ __forceinline__ void erf_exp(double S, double &erfS, double &eS)
     eS = e;
 }
 
+// the sign of x flipped when sbit is the sign bit (x unchanged for sbit = 0):
+// a multiplication by -1 or +1 done on the integer pipe
+__device__ __forceinline__ double flip_sign(double x, unsigned long long sbit)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)sbit);
+}
+
+static constexpr unsigned long long kSignBit = 0x8000000000000000ull;
+
 // Kinetic split flux along a direction: normal velocity un, transverse ut,
-// sign +1 for G+, -1 for G- (half-range moments of the Maxwellian):
+// sgn = +1 for G+, -1 for G- (half-range moments of the Maxwellian):
 //   S = un sqrt(beta), A = (1 + sgn erf S)/2, B = exp(-S^2)/(2 sqrt(pi beta))
 //   G = [rho(un A + sgn B), (p + rho un^2) A + sgn rho un B,
 //        rho ut (un A + sgn B), (rhoE + p) un A + sgn (rhoE + p/2) B]
 // evaluated as Q = rho A, W = sgn rho B: G0 = un Q + W, G1 = p A + un G0,
-// G2 = ut G0, G3 = h un Q + e2 W (h, e2 per unit mass, from the primitive state)
-__device__ __forceinline__ void split_flux(double sgn, const Prim &s, double un, double ut, double G[4])
+// G2 = ut G0, G3 = h un Q + e2 W (h, e2 per unit mass, from the primitive state).
+// sbit = 0 for G+, kSignBit for G-: the products by sgn are sign flips.
+__device__ __forceinline__ void split_flux(unsigned long long sbit, const Prim &s, double un, double ut,
+                                           double G[4])
 {
     const double S = un * s.sqb;
     double erfS, eS;
     erf_exp(S, erfS, eS);
-    const double A = fma(0.5 * sgn, erfS, 0.5);
+    const double A = fma(0.5, flip_sign(erfS, sbit), 0.5);
     const double Q = s.rho * A;
-    const double W = s.rho * (eS * (sgn * s.rsbc));
+    const double W = s.rho * (eS * flip_sign(s.rsbc, sbit));
     G[0] = fma(un, Q, W);
     G[1] = fma(un, G[0], s.p * A);
     G[2] = ut * G[0];
@@ -289,8 +301,9 @@ __device__ __forceinline__ bool prim_from_q_f(const float qt[4], float inv_gm1, 
     if (!(beta > 0.0f)) return false;
     s.rsb = rsqrtf(beta);
     const float ib = s.rsb * s.rsb;  // 1/beta, so 1/q4 = -ib/2 without a division
-    s.u = 0.5f * qt[1] * ib;
-    s.v = 0.5f * qt[2] * ib;
+    const float hib = 0.5f * ib;     // (exact halving: u = q1 hib rounds as 0.5 q1 ib)
+    s.u = qt[1] * hib;
+    s.v = qt[2] * hib;
     s.sqb = beta * s.rsb;
     const float u2 = s.u * s.u + s.v * s.v;
     const float ke = beta * u2;
@@ -298,7 +311,7 @@ __device__ __forceinline__ bool prim_from_q_f(const float qt[4], float inv_gm1, 
     // the FP32 budget of the form
     if (g14) s.rho = __expf(qt[0] + ke) * s.rsb * (ib * ib);
     else s.rho = __expf(qt[0] - __logf(beta) * inv_gm1 + ke);
-    s.p = 0.5f * s.rho * ib;
+    s.p = s.rho * hib;
     s.h = fmaf(0.5f * (inv_gm1 + 1.0f), ib, 0.5f * u2);
     s.e2 = fmaf(0.5f * (inv_gm1 + 0.5f), ib, 0.5f * u2);
     s.rsbc = s.rsb * 0.28209479177387814f;

@@ -232,7 +232,7 @@ __device__ __forceinline__ void edge_residual(const double qti[4], const double 
     const double us_i = si.u * tx + si.v * ty, un_i = si.u * n0.x + si.v * n0.y;
     const double us_0 = s0.u * tx + s0.v * ty, un_0 = s0.u * n0.x + s0.v * n0.y;
     if (w.x != 0.0) {
-        const double sg = (m & M_XPOS) ? 1.0 : -1.0;
+        const unsigned long long sg = (m & M_XPOS) ? 0ull : kSignBit;
         double Gi[4], G0[4];
         split_flux(sg, si, us_i, un_i, Gi);
         split_flux(sg, s0, us_0, un_0, G0);
@@ -243,7 +243,7 @@ __device__ __forceinline__ void edge_residual(const double qti[4], const double 
         for (int k = 0; k < 4; ++k) R[k] += w.x * __dsub_rn(Gi[k], G0[k]);
     }
     if (w.y != 0.0) {
-        const double sg = (m & M_YPOS) ? 1.0 : -1.0;
+        const unsigned long long sg = (m & M_YPOS) ? 0ull : kSignBit;
         double Gi[4], G0[4];
         split_flux(sg, si, un_i, us_i, Gi);
         split_flux(sg, s0, un_0, us_0, G0);

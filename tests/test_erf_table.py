@@ -35,27 +35,31 @@ def test_table_is_the_generator_output(tmp_path):
 
 def test_table_reproduces_erf_and_exp():
     T = _table()
-    assert T.shape == (193, 20)
-    assert np.all(T[:, 0] == np.arange(193) / 32.0)
+    step, deg = 128, 6
+    assert T.shape == (6 * step + 1, 2 * deg + 4)
+    assert np.all(T[:, 0] == np.arange(6 * step + 1) / step)
     S = np.linspace(-6.0, 6.0, 400001)
     a = np.abs(S)
-    k = np.minimum(np.rint(a * 32).astype(int), 192)
+    k = np.minimum(np.rint(a * step).astype(int), 6 * step)
     d = a - T[k, 0]
-    c = T[k, 1:10]
-    e = T[k, 10:19]
-    erf = c[:, 8]
-    ex = e[:, 8]
-    for n in range(7, -1, -1):
+    c = T[k, 1:deg + 2]
+    e = T[k, deg + 2:2 * deg + 3]
+    erf = c[:, deg]
+    ex = e[:, deg]
+    for n in range(deg - 1, -1, -1):
         erf = erf * d + c[:, n]
         ex = ex * d + e[:, n]
     erf = np.copysign(erf, S)
     ref_erf = np.array([math.erf(x) for x in S])
     assert np.max(np.abs(erf - ref_erf)) <= 2.3e-16
     assert np.max(np.abs(ex - np.exp(-S * S))) <= 2.3e-16
+    # relative to erf itself near 0 too (a few ulp)
+    small = np.abs(S) < 0.5
+    assert np.max(np.abs(erf - ref_erf)[small] / np.maximum(np.abs(ref_erf[small]), 1e-300)) <= 1e-15
     # half a grid step off the nodes as well (the largest |d| of the device)
-    off = (np.arange(192) + 0.5) / 32.0
+    off = (np.arange(6 * step) + 0.5) / step
     assert np.max(np.abs(np.array([math.erf(x) for x in off]) -
-                         np.array([np.polyval(T[j, 9:0:-1], 1 / 64) for j in range(192)]))) <= 2.3e-16
+                         np.array([np.polyval(T[j, deg + 1:0:-1], 0.5 / step) for j in range(6 * step)]))) <= 2.3e-16
 
 
 def _exp_consts():
