@@ -187,7 +187,7 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
 # profiles/launch_list_naca0012_2p5m_fp64.md).
 FP64_INSTR_PER_EDGE_FLUX = 241.61
 FP64_FLOPS_PER_EDGE_FLUX = 367.90
-FLUX_DRAM_BYTES_PER_POINT = 598.6
+FLUX_DRAM_BYTES_PER_POINT = 598.0
 # FP64 peak: ncu's DFMA unit count, 304 FP64 thread-instructions per cycle
 # (each DFMA 2 flops), at the 2070 MHz maximum SM clock
 FP64_PEAK_GINSTR = 304 * 2.070
@@ -375,7 +375,7 @@ def measure_e2e(solver, n, steps, dist):
 # DRAM bytes per point of one launch of the mixed kernels on the 2.5M-point
 # workload, from a full-size single-pass ncu capture of the current kernels
 # (profiles/mixed_kernels_naca0012_2p5m.md); None where not captured
-MIXED_TRAFFIC_PER_POINT = {"flux": 345.0, "qgrad": 181.2}
+MIXED_TRAFFIC_PER_POINT = {"flux": 345.2, "qgrad": 181.7}
 
 
 def form_summary(args, r, n, dbar, world, precision, peaks, peak_src):
