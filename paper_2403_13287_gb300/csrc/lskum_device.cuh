@@ -358,6 +358,16 @@ __device__ __forceinline__ void store4f(float *a, int64_t p, const float v[4])
     reinterpret_cast<float4 *>(a)[p] = make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// the 8 floats of row p of a read-only [n][8] array (32-byte aligned rows) as
+// one 256-bit load through the non-coherent path: half the load instructions
+// of two float4 loads for the neighbour gathers
+__device__ __forceinline__ void gather8f(const float *a, int64_t p, float v[8])
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(a + 8 * p));
+}
+
 __device__ __forceinline__ void load8f(const float *a, int64_t p, float v[8])
 {
     const float4 *a4 = reinterpret_cast<const float4 *>(a);

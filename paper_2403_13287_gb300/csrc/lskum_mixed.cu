@@ -178,7 +178,7 @@ __device__ __forceinline__ void image_q_f(const MixedGeom &g, int e, uint8_t m, 
     if (recon) {
         reflect2(d.x, d.y, n0.x, n0.y);
         float gi[8];
-        load8f(qg, i, gi);
+        gather8f(qg, i, gi);
 #pragma unroll
         for (int k = 0; k < 4; ++k) qi[k] = qi[k] - 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
     }
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
         }
         if (inner) {
             float gi[8];
-            load8f(qg_old, i, gi);
+            gather8f(qg_old, i, gi);
             const float2 d = make_float2(M.x * a.x + M.y * a.y, M.y * a.x + M.z * a.y);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
                 im_n = g.sidx[base];
                 const int i = im_n & kSlotIndexMask;
                 load4f(P.q, i, q_n);
-                if (second) load8f(P.qg, i, g_n);
+                if (second) gather8f(P.qg, i, g_n);
             }
         }
         for (int s = 0; s < deg; ++s) {
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
                     im_n = g.sidx[e + 32];
                     const int in = im_n & kSlotIndexMask;
                     load4f(P.q, in, q_n);
-                    if (second) load8f(P.qg, in, g_n);
+                    if (second) gather8f(P.qg, in, g_n);
                 }
                 w = make_float2(rec.z, rec.w);
                 if (w.x == 0.0f && w.y == 0.0f) continue;
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
                 if (second) {
                     d = make_float2(rec.x, rec.y);
                     float gi[8];
-                    load8f(P.qg, i, gi);
+                    gather8f(P.qg, i, gi);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         qti[k] = qti[k] - 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
