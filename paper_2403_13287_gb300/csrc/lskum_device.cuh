@@ -347,6 +347,82 @@ __device__ __forceinline__ void split_flux_f(float sgn, const PrimF &s, float un
     G[3] = fmaf(s.h * un, Q, s.e2 * W);
 }
 
+// ---------------------------------------------------------------------------
+// The same FP32 forms on a pair of states at once: the two ends of a stencil
+// edge (x: q~_i, y: q~_0) take identical arithmetic, so each multiply, add
+// and fused multiply-add of the pair is one packed FP32x2 instruction
+// (FFMA2 / FMUL2 / FADD2 of sm_100 and later, round to nearest like the
+// scalar ones); the special functions (reciprocal square root, exp,
+// reciprocal) stay per component.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 pr2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+struct PrimF2 {
+    float2 rho, u, v, p, sqb, h, e2, rsbc;
+};
+
+__device__ __forceinline__ bool prim_from_q_f2(const float2 qt[4], float inv_gm1, bool g14, PrimF2 &s)
+{
+    const float2 beta = mul2(pr2(-0.5f), qt[3]);
+    if (!(beta.x > 0.0f && beta.y > 0.0f)) return false;
+    const float2 rsb = make_float2(rsqrtf(beta.x), rsqrtf(beta.y));
+    const float2 ib = mul2(rsb, rsb);     // 1/beta
+    const float2 hib = mul2(pr2(0.5f), ib);
+    s.u = mul2(qt[1], hib);
+    s.v = mul2(qt[2], hib);
+    s.sqb = mul2(beta, rsb);
+    const float2 u2 = fma2(s.u, s.u, mul2(s.v, s.v));
+    const float2 ex = fma2(beta, u2, qt[0]);
+    if (g14) {
+        const float2 e = make_float2(__expf(ex.x), __expf(ex.y));
+        s.rho = mul2(mul2(e, rsb), mul2(ib, ib));
+    } else {
+        const float2 lb = make_float2(__logf(beta.x), __logf(beta.y));
+        const float2 a = fma2(lb, pr2(-inv_gm1), ex);
+        s.rho = make_float2(__expf(a.x), __expf(a.y));
+    }
+    s.p = mul2(s.rho, hib);
+    const float2 hu2 = mul2(pr2(0.5f), u2);
+    s.h = fma2(pr2(0.5f * (inv_gm1 + 1.0f)), ib, hu2);
+    s.e2 = fma2(pr2(0.5f * (inv_gm1 + 0.5f)), ib, hu2);
+    s.rsbc = mul2(rsb, pr2(0.28209479177387814f));
+    return isfinite(s.rho.x) && s.rho.x > 0.0f && isfinite(s.rho.y) && s.rho.y > 0.0f;
+}
+
+// half_range_A on the pair
+__device__ __forceinline__ float2 half_range_A2(float sgn, float2 S, float2 e)
+{
+    const float2 x = make_float2(fabsf(S.x), fabsf(S.y));
+    const float2 den = fma2(pr2(0.3275911f), x, pr2(1.0f));
+    const float2 t = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+    float2 poly = fma2(t, pr2(1.061405429f), pr2(-1.453152027f));
+    poly = fma2(t, poly, pr2(1.421413741f));
+    poly = fma2(t, poly, pr2(-0.284496736f));
+    poly = fma2(t, poly, pr2(0.254829592f));
+    const float2 small = mul2(mul2(pr2(0.5f), mul2(t, poly)), e);  // (1 - erf|S|)/2
+    const float2 large = fma2(small, pr2(-1.0f), pr2(1.0f));
+    // A+ is the large one for S > 0, A- for S < 0
+    return make_float2(sgn * S.x >= 0.0f ? large.x : small.x, sgn * S.y >= 0.0f ? large.y : small.y);
+}
+
+// split_flux_f on the pair
+__device__ __forceinline__ void split_flux_f2(float sgn, const PrimF2 &s, float2 un, float2 ut, float2 G[4])
+{
+    const float2 S = mul2(un, s.sqb);
+    const float2 S2 = mul2(S, S);
+    const float2 e = make_float2(__expf(-S2.x), __expf(-S2.y));
+    const float2 A = half_range_A2(sgn, S, e);
+    const float2 Q = mul2(s.rho, A);
+    const float2 W = mul2(s.rho, mul2(e, mul2(pr2(sgn), s.rsbc)));
+    G[0] = fma2(un, Q, W);
+    G[1] = fma2(un, G[0], mul2(s.p, A));
+    G[2] = mul2(ut, G[0]);
+    G[3] = fma2(mul2(s.h, un), Q, mul2(s.e2, W));
+}
+
 __device__ __forceinline__ void load4f(const float *a, int64_t p, float v[4])
 {
     const float4 t = reinterpret_cast<const float4 *>(a)[p];

@@ -320,42 +320,57 @@ __device__ __forceinline__ void flag_nonphysical_m(int *status, int64_t p)
     atomicMin(status + 1, (int)p);
 }
 
+// q~ of E14 at both ends of a slot as pairs (x: the neighbour, y: P_0):
+// q - (d.grad q)/2 with d the slot's offset (order 2), else q; scalar
+// arithmetic written straight into the pair registers
+__device__ __forceinline__ void recon_pair(const float qi[4], const float gi[8], const float q0[4],
+                                           const float g0[8], float2 d, bool second, float2 qt[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (second) {
+            qt[k].x = qi[k] - 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
+            qt[k].y = q0[k] - 0.5f * (d.x * g0[k] + d.y * g0[4 + k]);
+        } else {
+            qt[k] = make_float2(qi[k], q0[k]);
+        }
+    }
+}
+
 // One member's term of E11 in FP32 (the weights' FP64 copy w64[e] at points
 // with an FP64 closure), frame (t, n) of P_0, R in the order [mass,
 // s-momentum, n-momentum, energy]; see edge_residual of the FP64 kernels.
-__device__ __forceinline__ void edge_residual_f(const float qti[4], const float qt0[4], uint32_t m, float2 w,
-                                                bool fp64, const double2 *__restrict__ w64, int64_t e, float2 n0,
+// Both ends are evaluated as one pair (packed FP32x2 arithmetic).
+__device__ __forceinline__ void edge_residual_f(const float2 qt[4], uint32_t m, float2 w, bool fp64,
+                                                const double2 *__restrict__ w64, int64_t e, float2 n0,
                                                 float tx, float ty, float inv_gm1, int g14, float R[4],
                                                 double R64[4], bool &ok)
 {
     // equal reconstructed states have dG = 0 exactly; the two flux
-    // evaluations may be compiled along different paths (the q~_0 one
-    // partly hoisted), so equality is decided on q~, not on G
-    if (qti[0] == qt0[0] && qti[1] == qt0[1] && qti[2] == qt0[2] && qti[3] == qt0[3]) return;
-    PrimF si, s0;
-    ok &= prim_from_q_f(qti, inv_gm1, g14, si);
-    ok &= prim_from_q_f(qt0, inv_gm1, g14, s0);
-    const float us_i = si.u * tx + si.v * ty, un_i = si.u * n0.x + si.v * n0.y;
-    const float us_0 = s0.u * tx + s0.v * ty, un_0 = s0.u * n0.x + s0.v * n0.y;
+    // evaluations may be compiled along different paths, so equality is
+    // decided on q~, not on G
+    if (qt[0].x == qt[0].y && qt[1].x == qt[1].y && qt[2].x == qt[2].y && qt[3].x == qt[3].y) return;
+    PrimF2 s;
+    ok &= prim_from_q_f2(qt, inv_gm1, g14, s);
+    const float2 us = fma2(s.v, pr2(ty), mul2(s.u, pr2(tx)));
+    const float2 un = fma2(s.v, pr2(n0.y), mul2(s.u, pr2(n0.x)));
     float dGs[4] = {0, 0, 0, 0}, dGn[4] = {0, 0, 0, 0};
     if (w.x != 0.0f) {
         const float sg = (m & M_XPOS) ? 1.0f : -1.0f;
-        float Gi[4], G0[4];
-        split_flux_f(sg, si, us_i, un_i, Gi);
-        split_flux_f(sg, s0, us_0, un_0, G0);
+        float2 G[4];
+        split_flux_f2(sg, s, us, un, G);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) dGs[k] = __fsub_rn(Gi[k], G0[k]);
+        for (int k = 0; k < 4; ++k) dGs[k] = __fsub_rn(G[k].x, G[k].y);
     }
     if (w.y != 0.0f) {
         const float sg = (m & M_YPOS) ? 1.0f : -1.0f;
-        float Gi[4], G0[4];
-        split_flux_f(sg, si, un_i, us_i, Gi);
-        split_flux_f(sg, s0, un_0, us_0, G0);
+        float2 G[4];
+        split_flux_f2(sg, s, un, us, G);
         // Gn components are [mass, n-momentum, s-momentum, energy]
-        dGn[0] = __fsub_rn(Gi[0], G0[0]);
-        dGn[1] = __fsub_rn(Gi[2], G0[2]);
-        dGn[2] = __fsub_rn(Gi[1], G0[1]);
-        dGn[3] = __fsub_rn(Gi[3], G0[3]);
+        dGn[0] = __fsub_rn(G[0].x, G[0].y);
+        dGn[1] = __fsub_rn(G[2].x, G[2].y);
+        dGn[2] = __fsub_rn(G[1].x, G[1].y);
+        dGn[3] = __fsub_rn(G[3].x, G[3].y);
     }
     if (fp64) {
         const double2 ww = w64[e];
@@ -408,15 +423,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
         }
         for (int s = 0; s < deg; ++s) {
             const int64_t e = base + 32 * s;
-            float qti[4], qt0[4];
+            float2 qt[4];
             uint32_t m;
             float2 w, d;
             if constexpr (PF) {
                 const float4 rec = rec_n;
                 const int32_t im = im_n;
-                float gi[8];
+                float qi[4], gi[8];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) qti[k] = q_n[k];
+                for (int k = 0; k < 4; ++k) qi[k] = q_n[k];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) gi[k] = g_n[k];
                 if (s + 1 < deg) {
@@ -429,16 +444,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
                 w = make_float2(rec.z, rec.w);
                 if (w.x == 0.0f && w.y == 0.0f) continue;
                 m = (uint32_t)im >> 28;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) qt0[k] = q0[k];
-                if (second) {
-                    d = make_float2(rec.x, rec.y);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        qti[k] = qti[k] - 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
-                        qt0[k] = qt0[k] - 0.5f * (d.x * g0[k] + d.y * g0[4 + k]);
-                    }
-                }
+                d = make_float2(rec.x, rec.y);
+                recon_pair(qi, gi, q0, g0, d, second, qt);
             } else {
                 const float4 rec = g.gf[e];
                 w = make_float2(rec.z, rec.w);
@@ -446,21 +453,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
                 const int32_t im = g.sidx[e];
                 const int i = im & kSlotIndexMask;
                 m = (uint32_t)im >> 28;
-                load4f(P.q, i, qti);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) qt0[k] = q0[k];
-                if (second) {
-                    d = make_float2(rec.x, rec.y);
-                    float gi[8];
-                    gather8f(P.qg, i, gi);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        qti[k] = qti[k] - 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
-                        qt0[k] = qt0[k] - 0.5f * (d.x * g0[k] + d.y * g0[4 + k]);
-                    }
-                }
+                float qi[4], gi[8];
+                load4f(P.q, i, qi);
+                if (second) gather8f(P.qg, i, gi);
+                d = make_float2(rec.x, rec.y);
+                recon_pair(qi, gi, q0, g0, d, second, qt);
             }
-            edge_residual_f(qti, qt0, m, w, fp64, g.fxw64, e, n0, tx, ty, P.inv_gm1, P.g14, R, R64, ok);
+            edge_residual_f(qt, m, w, fp64, g.fxw64, e, n0, tx, ty, P.inv_gm1, P.g14, R, R64, ok);
         }
         if constexpr (KIN) {
             // kinetic boundary mode: the mirror images of the neighbours
@@ -470,12 +469,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
                 const float4 rec = g.igf[e];
                 const float2 d = make_float2(rec.x, rec.y), w = make_float2(rec.z, rec.w);
                 const uint8_t m = g.imask[e];
-                float qti[4], qt0[4];
+                float qti[4];
                 image_q_f(g, e, m, n0, qf, P.q, P.qg, d, second, qti);
+                float2 qt[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    qt0[k] = second ? q0[k] - 0.5f * (d.x * g0[k] + d.y * g0[4 + k]) : q0[k];
-                edge_residual_f(qti, qt0, m, w, fp64, g.ifxw64, e, n0, tx, ty, P.inv_gm1, P.g14, R, R64, ok);
+                    qt[k] = make_float2(qti[k], second ? q0[k] - 0.5f * (d.x * g0[k] + d.y * g0[4 + k]) : q0[k]);
+                edge_residual_f(qt, m, w, fp64, g.ifxw64, e, n0, tx, ty, P.inv_gm1, P.g14, R, R64, ok);
             }
         }
         if (!ok) flag_nonphysical_m(P.status, p);
@@ -635,7 +635,8 @@ struct VariantTable {
         flux_v<128, 7, false, K>, flux_v<64, 14, false, K>, flux_v<256, 3, false, K>, flux_v<128, 6, false, K>,
         flux_v<128, 8, false, K>, flux_v<256, 4, false, K>, flux_v<128, 7, true, K>,  flux_v<64, 14, true, K>,
         flux_v<256, 3, true, K>,  flux_v<128, 6, true, K>,  flux_v<128, 8, true, K>,  flux_v<256, 4, true, K>,
-        flux_v<128, 5, true, K>,  flux_v<128, 4, true, K>};
+        flux_v<128, 5, true, K>,  flux_v<128, 4, true, K>,  flux_v<64, 8, true, K>,   flux_v<96, 6, true, K>,
+        flux_v<128, 3, true, K>};
 };
 static const QgradFn *const kQgradVariants[2] = {VariantTable<false>::qgrad, VariantTable<true>::qgrad};
 static const FluxFn *const kFluxVariants[2] = {VariantTable<false>::flux, VariantTable<true>::flux};
@@ -643,10 +644,10 @@ static constexpr int kNumQgradVariants = sizeof VariantTable<false>::qgrad / siz
 static constexpr int kNumFluxVariants = sizeof VariantTable<false>::flux / sizeof(FluxFn);
 static const int kQgradShape[][2] = {{128, 8}, {64, 16}, {256, 4}, {128, 6}, {256, 3}, {96, 10}};
 // flux shapes 6-11 repeat 0-5 with the software-pipelined neighbour loop,
-// 12-13 give that loop more registers
+// 12-16 give that loop more registers
 static const int kFluxShape[][2] = {{128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4},
                                     {128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4},
-                                    {128, 5}, {128, 4}};
+                                    {128, 5}, {128, 4}, {64, 8},  {96, 6},  {128, 3}};
 
 int mixed_variants(int kernel_class)
 {

@@ -123,7 +123,7 @@ def test_batch_arguments(clouds):
     assert e.value.status == LSKUM_ERR_ARG
     s1 = Solver(a, precision=1)
     with pytest.raises(LskumError) as e:
-        s1.set_tuning(14, 0)
+        s1.set_tuning(1000, 0)
     assert e.value.status == LSKUM_ERR_ARG
     f64 = Solver(a, precision=0)
     with pytest.raises(LskumError) as e:
