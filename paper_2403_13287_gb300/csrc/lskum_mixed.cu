@@ -190,7 +190,10 @@ __device__ __forceinline__ void image_q_f(const MixedGeom &g, int e, uint8_t m, 
 // --------------------------------------------------------------------------
 // KIN: the kinetic boundary mode (a separate instantiation keeps the plain
 // kernels' registers as they are)
-template <int THREADS, int MINB, bool KIN>
+// PASS: bit 1 an inner iteration (qg_old is read), bit 0 the limiter's pass;
+// one instantiation per kind of pass keeps each one's registers to what it
+// uses (the limiter's extrema and the previous iterate only where needed)
+template <int THREADS, int MINB, bool KIN, int PASS>
 __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, const float *__restrict__ q,
                                                                const float *__restrict__ qg_old,
                                                                float *__restrict__ qg_new, float limK)
@@ -201,9 +204,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
     const int64_t base = g.slice_off[p >> 5] + (p & 31);
     float q0[4], g0[8], sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
     load4f(q, p, q0);
-    const bool inner = qg_old != nullptr;
-    const bool limit = limK > 0.0f;
-    if (inner) load8f(qg_old, p, g0);
+    constexpr bool inner = (PASS & 2) != 0;
+    constexpr bool limit = (PASS & 1) != 0;
     // the slot's offset d = M a (a = M^-1 d): recovered from the weights, so
     // a slot carries 8 bytes of geometry instead of 16
     float4 M = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -230,9 +232,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
             float gi[8];
             gather8f(qg_old, i, gi);
             const float2 d = make_float2(M.x * a.x + M.y * a.y, M.y * a.x + M.z * a.y);
+            // the previous iterate at P_0 is taken out of the sum (below)
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                dq[k] = dq[k] - 0.5f * (d.x * (gi[k] - g0[k]) + d.y * (gi[4 + k] - g0[4 + k]));
+            for (int k = 0; k < 4; ++k) dq[k] = dq[k] - 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -255,10 +257,6 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
                 image_q_f(g, e, m, n0, qf, q, qg_old, d, inner, qi);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) dq[k] = qi[k] - q0[k];
-                if (inner) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) dq[k] = dq[k] + 0.5f * (d.x * g0[k] + d.y * g0[4 + k]);
-                }
                 if (limit) {
                     if (inner) image_q_f(g, e, m, n0, qf, q, qg_old, d, false, qi);
 #pragma unroll
@@ -273,6 +271,17 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
                     sy[k] += a.y * dq[k];
                 }
             }
+        }
+    }
+    if (inner) {
+        // sum_e a_e (d_e . g_0) = g_0 (the weights satisfy sum_e a_e d_e^T = I,
+        // to FP32 rounding), so the +1/2 d_e . g_0 of every corrected
+        // difference (E14) adds up to g_0 / 2
+        load8f(qg_old, p, g0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            sx[k] += 0.5f * g0[k];
+            sy[k] += 0.5f * g0[4 + k];
         }
     }
     if (limit) {
@@ -612,7 +621,14 @@ template <int T, int M, bool KIN>
 static cudaError_t qgrad_v(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new, float limK,
                            cudaStream_t s)
 {
-    k_qgrad_mixed<T, M, KIN><<<(unsigned)((g.n + T - 1) / T), T, 0, s>>>(g, q, qg_old, qg_new, limK);
+    const unsigned nb = (unsigned)((g.n + T - 1) / T);
+    const int pass = (qg_old ? 2 : 0) | (limK > 0.0f ? 1 : 0);
+    switch (pass) {
+    case 0: k_qgrad_mixed<T, M, KIN, 0><<<nb, T, 0, s>>>(g, q, qg_old, qg_new, limK); break;
+    case 1: k_qgrad_mixed<T, M, KIN, 1><<<nb, T, 0, s>>>(g, q, qg_old, qg_new, limK); break;
+    case 2: k_qgrad_mixed<T, M, KIN, 2><<<nb, T, 0, s>>>(g, q, qg_old, qg_new, limK); break;
+    default: k_qgrad_mixed<T, M, KIN, 3><<<nb, T, 0, s>>>(g, q, qg_old, qg_new, limK); break;
+    }
     return cudaGetLastError();
 }
 
