@@ -89,7 +89,7 @@ struct Prim {
 
 // exp(x), table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157):
 // x = n ln2/64 + r, |r| <= ln2/128, n = 64 m + j, exp(x) = 2^m 2^(j/64) p(r)
-// with p the degree-5 Taylor polynomial (gen_fp64_tables.py): 11 FP64
+// with p the degree-5 Taylor polynomial (gen_fp64_tables.py): 10 FP64
 // instructions. |x| >= 708 (or NaN) goes to the library exp.
 __device__ __forceinline__ double exp_tab(double x)
 {
@@ -105,8 +105,10 @@ __device__ __forceinline__ double exp_tab(double x)
     p = fma(p, r, 0.5);
     p = fma(p, r, 1.0);
     p = fma(p, r, 1.0);
-    const double two_m = __hiloint2double(((n >> 6) + 1023) << 20, 0);
-    return __ldg(&kExp2Table[n & 63]) * p * two_m;
+    // 2^(j/64) p(r) lies in [1/2, 2]; the factor 2^m (|x| < 708 keeps the
+    // result normal) is an addition to its exponent field on the integer pipe
+    const double tp = __ldg(&kExp2Table[n & 63]) * p;
+    return __hiloint2double(__double2hiint(tp) + (n >> 6) * (1 << 20), __double2loint(tp));
 }
 
 // a double strictly between 0 and +inf (not 0, negative, inf or NaN), tested
