@@ -3,7 +3,7 @@
 1. erf(S) and exp(-S^2), Taylor coefficients on a grid.
 
 The FP64 split fluxes need erf(S) and exp(-S^2) of the same S. On the grid
-s_k = k/128, k = 0..768 (0 <= s <= 6), each row holds s_k and the degree-6
+s_k = k/256, k = 0..1536 (0 <= s <= 6), each row holds s_k and the degree-5
 Taylor coefficients in d = s - s_k of
 
     erf(s_k + d)      : c_n = erf^(n)(s_k) / n!
@@ -11,11 +11,11 @@ Taylor coefficients in d = s - s_k of
 
 (H_n the physicists' Hermite polynomials, d^n/dx^n exp(-x^2) =
 (-1)^n H_n(x) exp(-x^2), and erf' = 2/sqrt(pi) exp(-x^2), so
-c_n = 2/sqrt(pi) e_{n-1} / n for n >= 1). With |d| <= 1/256 the first
-omitted terms are below 1e-18, so each function comes out of one table row
-and two Horner chains of 6 steps to about one unit in the last place of 1
+c_n = 2/sqrt(pi) e_{n-1} / n for n >= 1). With |d| <= 1/512 the first
+omitted terms are below 1e-17, so each function comes out of one table row
+and two Horner chains of 5 steps to about one unit in the last place of 1
 (a finer grid with a lower degree: fewer FP64 operations per evaluation
-for a larger table, 96 KB, whose rows in use stay cached). The values
+for a larger table, 168 KB, whose rows in use stay cached). The values
 are computed with mpmath at 50 significant digits and written as exactly
 rounded hexadecimal doubles.
 
@@ -33,9 +33,9 @@ import os
 import mpmath as mp
 
 mp.mp.dps = 50
-STEP = 128         # grid points per unit of s
-KMAX = 768         # s_k up to 6
-DEG = 6
+STEP = 256         # grid points per unit of s
+KMAX = 1536        # s_k up to 6
+DEG = 5
 
 
 def hermite(n, x):

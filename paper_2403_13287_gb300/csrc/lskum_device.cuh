@@ -82,9 +82,10 @@ struct Gas {
 //   beta = -q4/2, u = q2/(2 beta), v = q3/(2 beta),
 //   rho = exp(q1 + beta (u^2 + v^2)) beta^(-1/(gamma-1)), p = rho/(2 beta)
 struct Prim {
-    double rho, u, v, p, rsb, sqb;  // rsb = 1/sqrt(beta), sqb = sqrt(beta)
-    double h, e2;                   // (rho E + p)/rho and (rho E + p/2)/rho
-    double rsbc;                    // rsb / (2 sqrt(pi))
+    double u, v, rsb, sqb;  // rsb = 1/sqrt(beta), sqb = sqrt(beta)
+    double hrho, hp;        // rho/2, p/2
+    double h, e2;           // (rho E + p)/rho and (rho E + p/2)/rho
+    double rrc;             // rho rsb / (2 sqrt(pi)), so that rho B = rrc exp(-S^2)
 };
 
 // exp(x), table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157):
@@ -130,28 +131,30 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
     s.v = qt[2] * hib;
     s.sqb = beta * s.rsb;
     const double ke = beta * (s.u * s.u + s.v * s.v);
+    double rho;
     if (gas.g14) {
         // beta^-2.5 = beta^-1/2 (1/beta)^2
-        s.rho = exp_tab(qt[0] + ke) * s.rsb * (ib * ib);
+        rho = exp_tab(qt[0] + ke) * s.rsb * (ib * ib);
     } else {
-        s.rho = exp_tab(qt[0] - log(beta) * gas.inv_gm1 + ke);
+        rho = exp_tab(qt[0] - log(beta) * gas.inv_gm1 + ke);
     }
-    s.p = s.rho * hib;
+    s.hrho = 0.5 * rho;
+    s.hp = s.hrho * hib;                   // p/2 = rho/(4 beta)
     // per unit mass: p/rho = 1/(2 beta), rho E = p/(gamma-1) + rho |u|^2/2
     const double hu2 = 0.5 * (s.u * s.u + s.v * s.v);
     s.h = fma(0.5 * (gas.inv_gm1 + 1.0), ib, hu2);
     s.e2 = fma(0.5 * (gas.inv_gm1 + 0.5), ib, hu2);
-    s.rsbc = s.rsb * 0.28209479177387814;  // 1/(2 sqrt(pi))
-    return finite_positive(s.rho);
+    s.rrc = rho * (s.rsb * 0.28209479177387814);  // 1/(2 sqrt(pi))
+    return finite_positive(rho);
 }
 
 // erf(S) and exp(-S^2) together, from one row of a Taylor table: on the grid
-// s_k = k/128 (0 <= s_k <= 6) the row holds the degree-6 Taylor coefficients
-// of both functions in d = |S| - s_k (|d| <= 1/256), so each is one Horner
+// s_k = k/256 (0 <= s_k <= 6) the row holds the degree-5 Taylor coefficients
+// of both functions in d = |S| - s_k (|d| <= 1/512), so each is one Horner
 // chain with an absolute error of about one unit in the last place of 1
-// (gen_fp64_tables.py; the first omitted terms are below 1e-18). The nearest
+// (gen_fp64_tables.py; the first omitted terms are below 1e-17). The nearest
 // grid index comes from the top bits of |S| by integer operations, so the
-// FP64 pipe sees one subtraction and 12 fused multiply-adds. |S| >= 6:
+// FP64 pipe sees one subtraction and 10 fused multiply-adds. |S| >= 6:
 // erf = +-1 (erfc(6) = 2e-17) and exp(-S^2) directly.
 __device__ __forceinline__ void erf_exp(double S, double &erfS, double &eS)
 {
@@ -201,20 +204,21 @@ static constexpr unsigned long long kSignBit = 0x8000000000000000ull;
 //   S = un sqrt(beta), A = (1 + sgn erf S)/2, B = exp(-S^2)/(2 sqrt(pi beta))
 //   G = [rho(un A + sgn B), (p + rho un^2) A + sgn rho un B,
 //        rho ut (un A + sgn B), (rhoE + p) un A + sgn (rhoE + p/2) B]
-// evaluated as Q = rho A, W = sgn rho B: G0 = un Q + W, G1 = p A + un G0,
-// G2 = ut G0, G3 = h un Q + e2 W (h, e2 per unit mass, from the primitive state).
-// sbit = 0 for G+, kSignBit for G-: the products by sgn are sign flips.
+// evaluated as Q = rho A = rho/2 (1 + sgn erf S), W = sgn rho B:
+// G0 = un Q + W, G1 = p A + un G0, G2 = ut G0, G3 = h un Q + e2 W (h, e2
+// per unit mass, from the primitive state). sbit = 0 for G+, kSignBit for
+// G-: the products by sgn are sign flips.
 __device__ __forceinline__ void split_flux(unsigned long long sbit, const Prim &s, double un, double ut,
                                            double G[4])
 {
     const double S = un * s.sqb;
     double erfS, eS;
     erf_exp(S, erfS, eS);
-    const double A = fma(0.5, flip_sign(erfS, sbit), 0.5);
-    const double Q = s.rho * A;
-    const double W = s.rho * (eS * flip_sign(s.rsbc, sbit));
+    const double fe = flip_sign(erfS, sbit);
+    const double Q = fma(s.hrho, fe, s.hrho);
+    const double W = eS * flip_sign(s.rrc, sbit);
     G[0] = fma(un, Q, W);
-    G[1] = fma(un, G[0], s.p * A);
+    G[1] = fma(un, G[0], fma(s.hp, fe, s.hp));
     G[2] = ut * G[0];
     G[3] = fma(s.h * un, Q, s.e2 * W);
 }
@@ -363,7 +367,7 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 struct PrimF2 {
-    float2 rho, u, v, p, sqb, h, e2, rsbc;
+    float2 rho, u, v, p, sqb, h, e2, rrc;  // rrc = rho rsb / (2 sqrt(pi))
 };
 
 __device__ __forceinline__ bool prim_from_q_f2(const float2 qt[4], float inv_gm1, bool g14, PrimF2 &s)
@@ -390,7 +394,7 @@ __device__ __forceinline__ bool prim_from_q_f2(const float2 qt[4], float inv_gm1
     const float2 hu2 = mul2(pr2(0.5f), u2);
     s.h = fma2(pr2(0.5f * (inv_gm1 + 1.0f)), ib, hu2);
     s.e2 = fma2(pr2(0.5f * (inv_gm1 + 0.5f)), ib, hu2);
-    s.rsbc = mul2(rsb, pr2(0.28209479177387814f));
+    s.rrc = mul2(s.rho, mul2(rsb, pr2(0.28209479177387814f)));
     return isfinite(s.rho.x) && s.rho.x > 0.0f && isfinite(s.rho.y) && s.rho.y > 0.0f;
 }
 
@@ -418,7 +422,7 @@ __device__ __forceinline__ void split_flux_f2(float sgn, const PrimF2 &s, float2
     const float2 e = make_float2(__expf(-S2.x), __expf(-S2.y));
     const float2 A = half_range_A2(sgn, S, e);
     const float2 Q = mul2(s.rho, A);
-    const float2 W = mul2(s.rho, mul2(e, mul2(pr2(sgn), s.rsbc)));
+    const float2 W = mul2(e, mul2(pr2(sgn), s.rrc));
     G[0] = fma2(un, Q, W);
     G[1] = fma2(un, G[0], mul2(s.p, A));
     G[2] = mul2(ut, G[0]);

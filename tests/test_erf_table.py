@@ -35,7 +35,7 @@ def test_table_is_the_generator_output(tmp_path):
 
 def test_table_reproduces_erf_and_exp():
     T = _table()
-    step, deg = 128, 6
+    step, deg = 256, 5
     assert T.shape == (6 * step + 1, 2 * deg + 4)
     assert np.all(T[:, 0] == np.arange(6 * step + 1) / step)
     S = np.linspace(-6.0, 6.0, 400001)
