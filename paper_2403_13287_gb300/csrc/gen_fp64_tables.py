@@ -20,11 +20,11 @@ are computed with mpmath at 50 significant digits and written as exactly
 rounded hexadecimal doubles.
 
 2. exp(x), table-driven (P. T. P. Tang, ACM Trans. Math. Software 15 (1989)
-144-157): x = n ln2/64 + r with |r| <= ln2/128 and n = 64 m + j, so
-exp(x) = 2^m 2^(j/64) p(r), p the degree-5 Taylor polynomial of exp
-(truncation below 4e-17). The table holds 2^(j/64), j = 0..63, exactly
-rounded; ln2/64 is split into a head with 32 significant bits (so that
-n * head is exact for |n| < 2^21) and the rounded remainder.
+144-157): x = n ln2/512 + r with |r| <= ln2/1024 and n = 512 m + j, so
+exp(x) = 2^m 2^(j/512) p(r), p the degree-4 Taylor polynomial of exp
+(truncation below 2e-18). The table holds 2^(j/512), j = 0..511, exactly
+rounded (4 KB); ln2/512 is split into a head with 32 significant bits (so
+that n * head is exact for |n| < 2^21) and the rounded remainder.
 
 Run from the repository root:  python paper_2403_13287_gb300/csrc/gen_fp64_tables.py
 """
@@ -36,6 +36,7 @@ mp.mp.dps = 50
 STEP = 256         # grid points per unit of s
 KMAX = 1536        # s_k up to 6
 DEG = 5
+EXP_N = 512        # entries of the 2^(j/N) table
 
 
 def hermite(n, x):
@@ -76,21 +77,22 @@ def main():
         vals = [float(v).hex() for v in r] + ["0x0.0p+0"]
         lines.append("    {" + ", ".join(vals) + "},")
     lines.append("};")
-    # exp: 2^(j/64) and the split of ln2/64
-    L = mp.log(2) / 64
+    # exp: 2^(j/512) and the split of ln2/512
+    L = mp.log(2) / EXP_N
     m_, e_ = mp.frexp(L)                       # L = m_ 2^e_, 1/2 <= m_ < 1
     head = mp.ldexp(mp.floor(mp.ldexp(m_, 32)), e_ - 32)
     tail = L - head
     lines += [
         "",
-        "// exp(x) = 2^m 2^(j/64) p(r), x = (64 m + j) ln2/64 + r (Tang's table-driven method)",
-        "#define LSKUM_EXP_INV_L %s   // 64/ln2" % float(64 / mp.log(2)).hex(),
-        "#define LSKUM_EXP_L_HI %s    // ln2/64, 32 significant bits" % float(head).hex(),
-        "#define LSKUM_EXP_L_LO %s    // ln2/64 - LSKUM_EXP_L_HI" % float(tail).hex(),
-        "__device__ __align__(16) const double kExp2Table[64] = {",
+        "// exp(x) = 2^m 2^(j/%d) p(r), x = (%d m + j) ln2/%d + r (Tang's table-driven method)" % (EXP_N, EXP_N, EXP_N),
+        "#define LSKUM_EXP_N %d" % EXP_N,
+        "#define LSKUM_EXP_INV_L %s   // %d/ln2" % (float(EXP_N / mp.log(2)).hex(), EXP_N),
+        "#define LSKUM_EXP_L_HI %s    // ln2/%d, 32 significant bits" % (float(head).hex(), EXP_N),
+        "#define LSKUM_EXP_L_LO %s    // ln2/%d - LSKUM_EXP_L_HI" % (float(tail).hex(), EXP_N),
+        "__device__ __align__(16) const double kExp2Table[%d] = {" % EXP_N,
     ]
-    vals = [float(mp.mpf(2) ** (mp.mpf(j) / 64)).hex() for j in range(64)]
-    for j in range(0, 64, 4):
+    vals = [float(mp.mpf(2) ** (mp.mpf(j) / EXP_N)).hex() for j in range(EXP_N)]
+    for j in range(0, EXP_N, 4):
         lines.append("    " + ", ".join(vals[j:j + 4]) + ",")
     lines.append("};")
     with open(os.path.join(here, "fp64_tables.h"), "w") as f:

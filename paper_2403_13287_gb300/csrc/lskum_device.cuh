@@ -89,8 +89,8 @@ struct Prim {
 };
 
 // exp(x), table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157):
-// x = n ln2/64 + r, |r| <= ln2/128, n = 64 m + j, exp(x) = 2^m 2^(j/64) p(r)
-// with p the degree-5 Taylor polynomial (gen_fp64_tables.py): 10 FP64
+// x = n ln2/512 + r, |r| <= ln2/1024, n = 512 m + j, exp(x) = 2^m 2^(j/512) p(r)
+// with p the degree-4 Taylor polynomial (gen_fp64_tables.py): 9 FP64
 // instructions. |x| >= 708 (or NaN) goes to the library exp.
 __device__ __forceinline__ double exp_tab(double x)
 {
@@ -101,15 +101,14 @@ __device__ __forceinline__ double exp_tab(double x)
     const double kd = t - magic;
     double r = fma(-kd, LSKUM_EXP_L_HI, x);
     r = fma(-kd, LSKUM_EXP_L_LO, r);
-    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-    p = fma(p, r, 1.0 / 6.0);
+    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     p = fma(p, r, 0.5);
     p = fma(p, r, 1.0);
     p = fma(p, r, 1.0);
-    // 2^(j/64) p(r) lies in [1/2, 2]; the factor 2^m (|x| < 708 keeps the
+    // 2^(j/512) p(r) lies in [1/2, 2]; the factor 2^m (|x| < 708 keeps the
     // result normal) is an addition to its exponent field on the integer pipe
-    const double tp = __ldg(&kExp2Table[n & 63]) * p;
-    return __hiloint2double(__double2hiint(tp) + (n >> 6) * (1 << 20), __double2loint(tp));
+    const double tp = __ldg(&kExp2Table[n & (LSKUM_EXP_N - 1)]) * p;
+    return __hiloint2double(__double2hiint(tp) + (n >> 9) * (1 << 20), __double2loint(tp));
 }
 
 // a double strictly between 0 and +inf (not 0, negative, inf or NaN), tested

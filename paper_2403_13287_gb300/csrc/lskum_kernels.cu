@@ -231,7 +231,8 @@ __device__ __forceinline__ void edge_residual(const double qti[4], const double 
     ok &= prim_from_q(qt0, gas, s0);
     const double us_i = si.u * tx + si.v * ty, un_i = si.u * n0.x + si.v * n0.y;
     const double us_0 = s0.u * tx + s0.v * ty, un_0 = s0.u * n0.x + s0.v * n0.y;
-    if (w.x != 0.0) {
+    // w != 0 tested on the bits (integer pipe; +-0 are the zeros)
+    if ((__double_as_longlong(w.x) & ~(long long)kSignBit) != 0) {
         const unsigned long long sg = (m & M_XPOS) ? 0ull : kSignBit;
         double Gi[4], G0[4];
         split_flux(sg, si, us_i, un_i, Gi);
@@ -242,7 +243,7 @@ __device__ __forceinline__ void edge_residual(const double qti[4], const double 
 #pragma unroll
         for (int k = 0; k < 4; ++k) R[k] += w.x * __dsub_rn(Gi[k], G0[k]);
     }
-    if (w.y != 0.0) {
+    if ((__double_as_longlong(w.y) & ~(long long)kSignBit) != 0) {
         const unsigned long long sg = (m & M_YPOS) ? 0ull : kSignBit;
         double Gi[4], G0[4];
         split_flux(sg, si, un_i, us_i, Gi);

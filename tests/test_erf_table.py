@@ -75,17 +75,18 @@ def test_exp_table_reproduces_exp():
     """The table-driven exp of the device, step by step in double precision
     (numpy rounds each operation; the device fuses multiply-adds)."""
     inv_l, l_hi, l_lo, T = _exp_consts()
-    assert T.shape == (64,) and T[0] == 1.0 and np.all(np.diff(T) > 0)
-    assert np.all(np.abs(T - np.array([2.0 ** (j / 64) for j in range(64)])) <= np.spacing(T))
-    # the head of ln2/64 has 32 significant bits, so n * head is exact for |n| < 2^21
+    N = 512
+    assert T.shape == (N,) and T[0] == 1.0 and np.all(np.diff(T) > 0)
+    assert np.all(np.abs(T - np.array([2.0 ** (j / N) for j in range(N)])) <= np.spacing(T))
+    # the head of ln2/512 has 32 significant bits, so n * head is exact for |n| < 2^21
     m, e = math.frexp(l_hi)
     assert m * 2.0 ** 32 == int(m * 2.0 ** 32)
-    assert abs((l_hi + l_lo) - math.log(2) / 64) <= 1e-18
+    assert abs((l_hi + l_lo) - math.log(2) / N) <= 1e-19
     x = np.concatenate([np.linspace(-700.0, 700.0, 200001), np.linspace(-5.0, 5.0, 200001)])
     kd = np.rint(x * inv_l)
     n = kd.astype(np.int64)
     r = (x - kd * l_hi) - kd * l_lo
-    p = ((((r / 120 + 1 / 24) * r + 1 / 6) * r + 0.5) * r + 1) * r + 1
-    got = T[n & 63] * p * np.ldexp(1.0, (n >> 6).astype(np.int32))
+    p = (((r / 24 + 1 / 6) * r + 0.5) * r + 1) * r + 1
+    got = T[n & (N - 1)] * p * np.ldexp(1.0, (n >> 9).astype(np.int32))
     rel = np.abs(got - np.exp(x)) / np.exp(x)
     assert np.max(rel) <= 4.5e-16
