@@ -293,72 +293,13 @@ __device__ __forceinline__ bool q_from_U(const double U[4], const Gas &gas, doub
 }
 
 // ---------------------------------------------------------------------------
-// FP32 forms for the mixed-precision kernels (same formulas as above)
-// ---------------------------------------------------------------------------
-struct PrimF {
-    float rho, u, v, p, rsb, sqb;
-    float h, e2, rsbc;  // (rho E + p)/rho, (rho E + p/2)/rho, rsb / (2 sqrt(pi))
-};
-
-__device__ __forceinline__ bool prim_from_q_f(const float qt[4], float inv_gm1, bool g14, PrimF &s)
-{
-    const float beta = -0.5f * qt[3];
-    if (!(beta > 0.0f)) return false;
-    s.rsb = rsqrtf(beta);
-    const float ib = s.rsb * s.rsb;  // 1/beta, so 1/q4 = -ib/2 without a division
-    const float hib = 0.5f * ib;     // (exact halving: u = q1 hib rounds as 0.5 q1 ib)
-    s.u = qt[1] * hib;
-    s.v = qt[2] * hib;
-    s.sqb = beta * s.rsb;
-    const float u2 = s.u * s.u + s.v * s.v;
-    const float ke = beta * u2;
-    // __expf: relative error about |arg| * 6e-8 here (|arg| < ~20), within
-    // the FP32 budget of the form
-    if (g14) s.rho = __expf(qt[0] + ke) * s.rsb * (ib * ib);
-    else s.rho = __expf(qt[0] - __logf(beta) * inv_gm1 + ke);
-    s.p = s.rho * hib;
-    s.h = fmaf(0.5f * (inv_gm1 + 1.0f), ib, 0.5f * u2);
-    s.e2 = fmaf(0.5f * (inv_gm1 + 0.5f), ib, 0.5f * u2);
-    s.rsbc = s.rsb * 0.28209479177387814f;
-    return isfinite(s.rho) && s.rho > 0.0f;
-}
-
-// A+- = (1 +- erf S)/2 with erfc from Abramowitz & Stegun 7.1.26 (Hastings):
-// erfc(x) = (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2), t = 1/(1 + p x),
-// x >= 0, |error| <= 1.5e-7, about one FP32 ulp of 1. exp(-S^2) is shared with
-// B, and the smaller of A+ and A- is formed directly (no 1 - erf cancellation).
-__device__ __forceinline__ float half_range_A(float sgn, float S, float e)
-{
-    const float x = fabsf(S);
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
-    const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f),
-                                        -0.284496736f), 0.254829592f);
-    const float small = 0.5f * poly * e;  // (1 - erf|S|)/2
-    // A+ is the large one for S > 0, A- for S < 0
-    return (sgn * S >= 0.0f) ? 1.0f - small : small;
-}
-
-// same regrouping as split_flux: Q = rho A, W = sgn rho B
-__device__ __forceinline__ void split_flux_f(float sgn, const PrimF &s, float un, float ut, float G[4])
-{
-    const float S = un * s.sqb;
-    const float e = __expf(-S * S);
-    const float A = half_range_A(sgn, S, e);
-    const float Q = s.rho * A;
-    const float W = s.rho * (e * (sgn * s.rsbc));
-    G[0] = fmaf(un, Q, W);
-    G[1] = fmaf(un, G[0], s.p * A);
-    G[2] = ut * G[0];
-    G[3] = fmaf(s.h * un, Q, s.e2 * W);
-}
-
-// ---------------------------------------------------------------------------
-// The same FP32 forms on a pair of states at once: the two ends of a stencil
-// edge (x: q~_i, y: q~_0) take identical arithmetic, so each multiply, add
-// and fused multiply-add of the pair is one packed FP32x2 instruction
-// (FFMA2 / FMUL2 / FADD2 of sm_100 and later, round to nearest like the
-// scalar ones); the special functions (reciprocal square root, exp,
-// reciprocal) stay per component.
+// FP32 forms for the mixed-precision flux kernel (same formulas as above), on
+// a pair of states at once: the two ends of a stencil edge (x: q~_i,
+// y: q~_0) take identical arithmetic, so each multiply, add and fused
+// multiply-add of the pair is one packed FP32x2 instruction (FFMA2 / FMUL2 /
+// FADD2 of sm_100 and later, round to nearest like the scalar ones); the
+// special functions (reciprocal square root, exp, reciprocal) stay per
+// component.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 pr2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -366,7 +307,9 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 struct PrimF2 {
-    float2 rho, u, v, p, sqb, h, e2, rrc;  // rrc = rho rsb / (2 sqrt(pi))
+    float2 rho, u, v, p, sqb;
+    float2 h, e2;  // (rho E + p)/rho, (rho E + p/2)/rho
+    float2 rrc;    // rho rsb / (2 sqrt(pi)), so that rho B = rrc exp(-S^2)
 };
 
 __device__ __forceinline__ bool prim_from_q_f2(const float2 qt[4], float inv_gm1, bool g14, PrimF2 &s)
@@ -381,6 +324,8 @@ __device__ __forceinline__ bool prim_from_q_f2(const float2 qt[4], float inv_gm1
     s.sqb = mul2(beta, rsb);
     const float2 u2 = fma2(s.u, s.u, mul2(s.v, s.v));
     const float2 ex = fma2(beta, u2, qt[0]);
+    // __expf: relative error about |arg| * 6e-8 here (|arg| < ~20), within
+    // the FP32 budget of the form
     if (g14) {
         const float2 e = make_float2(__expf(ex.x), __expf(ex.y));
         s.rho = mul2(mul2(e, rsb), mul2(ib, ib));
@@ -397,7 +342,10 @@ __device__ __forceinline__ bool prim_from_q_f2(const float2 qt[4], float inv_gm1
     return isfinite(s.rho.x) && s.rho.x > 0.0f && isfinite(s.rho.y) && s.rho.y > 0.0f;
 }
 
-// half_range_A on the pair
+// A+- = (1 +- erf S)/2 with erfc from Abramowitz & Stegun 7.1.26 (Hastings):
+// erfc(x) = (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2), t = 1/(1 + p x),
+// x >= 0, |error| <= 1.5e-7, about one FP32 ulp of 1. exp(-S^2) is shared with
+// B, and the smaller of A+ and A- is formed directly (no 1 - erf cancellation).
 __device__ __forceinline__ float2 half_range_A2(float sgn, float2 S, float2 e)
 {
     const float2 x = make_float2(fabsf(S.x), fabsf(S.y));
@@ -413,7 +361,7 @@ __device__ __forceinline__ float2 half_range_A2(float sgn, float2 S, float2 e)
     return make_float2(sgn * S.x >= 0.0f ? large.x : small.x, sgn * S.y >= 0.0f ? large.y : small.y);
 }
 
-// split_flux_f on the pair
+// the split flux of both states, regrouped as split_flux: Q = rho A, W = sgn rho B
 __device__ __forceinline__ void split_flux_f2(float sgn, const PrimF2 &s, float2 un, float2 ut, float2 G[4])
 {
     const float2 S = mul2(un, s.sqb);
