@@ -376,6 +376,13 @@ def measure_e2e(solver, n, steps, dist):
 # workload, from a full-size single-pass ncu capture of the current kernels
 # (profiles/mixed_kernels_naca0012_2p5m.md); None where not captured
 MIXED_TRAFFIC_PER_POINT = {"flux": 351.0, "qgrad": 181.0}
+# warp instructions per stencil edge of the mixed flux kernel at its autotuned
+# shape (ncu smsp__inst_executed.sum, 640k-point capture,
+# profiles/k_flux_update_mixed_naca0012_640k.md): the kernel is bound by
+# instruction issue, 4 warp instructions per cycle per SM at the 2.07 GHz
+# maximum SM clock
+MIXED_FLUX_WARP_INSTR_PER_EDGE = 61303128 / 5167022
+ISSUE_PEAK_GINSTR = 152 * 4 * 2.070
 
 
 def form_summary(args, r, n, dbar, world, precision, peaks, peak_src):
@@ -389,6 +396,13 @@ def form_summary(args, r, n, dbar, world, precision, peaks, peak_src):
                      "traffic": tf * n if tf else None, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": fb, "avg_launch_ms": flux_avg_s * 1e3,
                      "share_of_kernel_time": r["flux_ms"] / (r["flux_ms"] + r["qg_ms"])}
+        # the issue view: warp instructions per launch over the duration
+        wi = MIXED_FLUX_WARP_INSTR_PER_EDGE * dbar * n
+        flux_roof["issue"] = {"achieved": wi / flux_avg_s / 1e9, "peak": ISSUE_PEAK_GINSTR,
+                              "unit": "G warp instructions/s",
+                              "frac": wi / flux_avg_s / 1e9 / ISSUE_PEAK_GINSTR,
+                              "warp_instructions_per_launch": wi,
+                              "peak_source": "derived: 4 warp instructions/cycle/SM x 152 SMs x 2.07 GHz"}
         roofline = flux_roof
         if r["qg_n"]:
             # launches per stage: one first-order pass, then the inner passes
