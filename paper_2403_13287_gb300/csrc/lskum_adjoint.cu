@@ -36,14 +36,23 @@ struct D4T {
 };
 using D4 = D4T<double>;
 
-__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+// elementary functions: in FP64 the forward kernels' own forms (the
+// table-driven exp, and erf(S) with exp(-S^2) from one Taylor-table row),
+// in FP32 the library's
+__device__ __forceinline__ double m_exp(double x) { return exp_tab(x); }
 __device__ __forceinline__ float m_exp(float x) { return expf(x); }
 __device__ __forceinline__ double m_log(double x) { return log(x); }
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double m_erf(double x) { return erf(x); }
-__device__ __forceinline__ float m_erf(float x) { return erff(x); }
+__device__ __forceinline__ double m_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float m_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ void m_erf_gauss(double S, double &erfS, double &e) { erf_exp(S, erfS, e); }
+__device__ __forceinline__ void m_erf_gauss(float S, float &erfS, float &e)
+{
+    erfS = erff(S);
+    e = expf(-S * S);
+}
 
 template <class T>
 __device__ __forceinline__ D4T<T> dconst(T v)
@@ -136,20 +145,30 @@ struct PrimDT {
     D4T<T> rho, u, v, p, sqb, rsb;
 };
 
-// inverse of E13 over duals (general gamma): beta = -q4/2, u = -q2/q4,
-// v = -q3/q4, rho = exp(q1 - ln(beta)/(gamma-1) + beta |u|^2), p = rho/(2 beta)
+// inverse of E13 over duals: beta = -q4/2, u = -q2/q4, v = -q3/q4,
+// rho = exp(q1 + beta |u|^2) beta^(-1/(gamma-1)), p = rho/(2 beta). From
+// rsb = 1/sqrt(beta) and ib = 1/beta as the forward kernels form them:
+// 1/q4 = -ib/2 (derivative -ib^2/4), sqrt(beta) = beta rsb (rsb/2),
+// 1/sqrt(beta) (-rsb ib/2), and for gamma = 1.4 beta^-2.5 = rsb ib^2
+// (-2.5 rsb ib^3) in place of exp(-2.5 ln beta)
 template <class T>
-__device__ __forceinline__ PrimDT<T> prim_d(const D4T<T> qt[4], T inv_gm1)
+__device__ __forceinline__ PrimDT<T> prim_d(const D4T<T> qt[4], T inv_gm1, bool g14)
 {
     PrimDT<T> s;
     const D4T<T> beta = T(-0.5) * qt[3];
-    const D4T<T> r = recip(qt[3]);
+    const T rsb = m_rsqrt(beta.v), ib = rsb * rsb;
+    const D4T<T> r = chain(qt[3], T(-0.5) * ib, T(-0.25) * ib * ib);
     s.u = T(-1) * (qt[1] * r);
     s.v = T(-1) * (qt[2] * r);
-    s.sqb = dsqrt(beta);
-    s.rsb = recip(s.sqb);
+    s.sqb = chain(beta, beta.v * rsb, T(0.5) * rsb);
+    s.rsb = chain(beta, rsb, T(-0.5) * rsb * ib);
     const D4T<T> ke = beta * (s.u * s.u + s.v * s.v);
-    s.rho = dexp(qt[0] - inv_gm1 * dlog(beta) + ke);
+    if (g14) {
+        const T b25 = rsb * ib * ib;
+        s.rho = dexp(qt[0] + ke) * chain(beta, b25, T(-2.5) * b25 * ib);
+    } else {
+        s.rho = dexp(qt[0] - inv_gm1 * dlog(beta) + ke);
+    }
     s.p = T(-1) * (s.rho * r);
     return s;
 }
@@ -160,8 +179,9 @@ __device__ __forceinline__ void split_flux_d(T sgn, const PrimDT<T> &s, const D4
                                              T inv_gm1, D4T<T> G[4])
 {
     const D4T<T> S = un * s.sqb;
-    const T e = m_exp(-S.v * S.v);
-    const D4T<T> erfS = chain(S, m_erf(S.v), T(1.1283791670955126) * e);   // 2/sqrt(pi)
+    T erfv, e;
+    m_erf_gauss(S.v, erfv, e);
+    const D4T<T> erfS = chain(S, erfv, T(1.1283791670955126) * e);         // 2/sqrt(pi)
     const D4T<T> eS = chain(S, e, T(-2) * S.v * e);
     const D4T<T> A = T(0.5) * (T(1) + sgn * erfS);
     const D4T<T> B = T(0.28209479177387814) * (eS * s.rsb);                 // 1/(2 sqrt(pi))
@@ -228,8 +248,8 @@ __device__ __forceinline__ bool sub_needed(uint8_t f, int k)
 // flux values for the weight cotangents
 template <class T>
 __device__ __forceinline__ void state_adjoint(const T qt[4], T tx, T ty, T nx, T ny, bool use_s, T sg_s, bool use_n,
-                                              T sg_n, const T cs[4], const T cn[4], T inv_gm1, T qbar[4], T Gs[4],
-                                              T Gn[4])
+                                              T sg_n, const T cs[4], const T cn[4], T inv_gm1, bool g14, T qbar[4],
+                                              T Gs[4], T Gn[4])
 {
     D4T<T> q[4];
 #pragma unroll
@@ -237,7 +257,7 @@ __device__ __forceinline__ void state_adjoint(const T qt[4], T tx, T ty, T nx, T
         q[k] = dconst(qt[k]);
         q[k].d[k] = T(1);
     }
-    const PrimDT<T> s = prim_d(q, inv_gm1);
+    const PrimDT<T> s = prim_d(q, inv_gm1, g14);
     const D4T<T> us = tx * s.u + ty * s.v;
     const D4T<T> un = nx * s.u + ny * s.v;
 #pragma unroll
@@ -334,8 +354,8 @@ __global__ void __launch_bounds__(128) k_adj_flux(AdjParamsT<T> P)
                               Gn0[4] = {0, 0, 0, 0};
         const T sgs = (m & M_XPOS) ? T(1) : T(-1), sgn = (m & M_YPOS) ? T(1) : T(-1);
         if (us_ || un_) {
-            state_adjoint(qti, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, qbi, Gsi, Gni);
-            state_adjoint(qt0, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, qbo, Gs0, Gn0);
+            state_adjoint(qti, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, P.g14 != 0, qbi, Gsi, Gni);
+            state_adjoint(qt0, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, P.g14 != 0, qbo, Gs0, Gn0);
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) qbi[k] = qbo[k] = T(0);

@@ -27,6 +27,7 @@ struct AdjParamsT {
     const int32_t *tsrc;   // [nnz] owner point of each incoming edge
     const int32_t *perm;   // internal point -> input point
     double inv_gm1;
+    int g14;               // gamma == 1.4: beta^(-1/(gamma-1)) = beta^-2.5 (as the forward kernels)
     int order;
 };
 using AdjParams = AdjParamsT<double>;

@@ -1221,6 +1221,7 @@ static AdjParams adj_params(lskum_ctx *c)
     P.tsrc = c->tsrc;
     P.perm = c->perm;
     P.inv_gm1 = c->gas.inv_gm1;
+    P.g14 = c->gas.g14;
     P.order = c->cfg.order;
     return P;
 }
@@ -1314,6 +1315,7 @@ static lskum_status vjp_residual_fp32(lskum_ctx *c, const double *Ui, double *Ub
     P.tsrc = Pd.tsrc;
     P.perm = Pd.perm;
     P.inv_gm1 = Pd.inv_gm1;
+    P.g14 = Pd.g14;
     P.order = Pd.order;
     c->launches++;
     LAUNCH(c, launch_adj_flux(P, c->stream));
