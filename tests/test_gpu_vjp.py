@@ -99,7 +99,14 @@ def test_vjp_of_the_context_state_and_far_field(small):
 
 @pytest.mark.parametrize("order", [1, 2])
 def test_dot_product_identity_at_160k(order):
-    """<R_bar, J v> (oracle, complex step) = <J^T R_bar, v> (GPU) on the 160k-point cloud."""
+    """<R_bar, J v> (oracle, complex step) = <J^T R_bar, v> (GPU) on the 160k-point cloud.
+
+    The coordinate product runs through the inverse least-squares normal
+    matrices of the sub-stencils, whose condition number reaches 1.3e10 at
+    the four leading- and trailing-edge wall points of this cloud (x+-
+    sub-stencils); rounding amplified there is about 1e-10 of the
+    first-order coordinate product, so that one takes 1e-9 (a wrong term
+    would be off by 1e-3 or more)."""
     c = naca0012_cloud(512, 311)
     mask = oracle.split_stencils(c)
     n = c["n"]
@@ -112,12 +119,12 @@ def test_dot_product_identity_at_160k(order):
     h = 1e-3 * np.median(np.abs(np.diff(c["x"])))
     vx = rng.standard_normal(n) * h
     vy = rng.standard_normal(n) * h
-    for dU, dx, dy, lhs_gpu in ((vU, None, None, np.sum(Ub * vU)),
-                                (None, vx, vy, np.sum(xb * vx) + np.sum(yb * vy))):
+    for dU, dx, dy, lhs_gpu, tol in ((vU, None, None, np.sum(Ub * vU), 1e-10),
+                                     (None, vx, vy, np.sum(xb * vx) + np.sum(yb * vy), 1e-9 if order == 1 else 1e-10)):
         Jv = lskum_jvp.jvp(c, mask, U, dU=dU, dx=dx, dy=dy, order=order, inner=3)
         lhs = np.sum(Rb * Jv)
         mag = np.sum(np.abs(Rb * Jv))
-        assert abs(lhs_gpu - lhs) <= 1e-10 * mag, (lhs_gpu, lhs, mag)
+        assert abs(lhs_gpu - lhs) <= tol * mag, (lhs_gpu, lhs, mag)
 
 
 def test_vjp_is_deterministic_and_precision_independent(small):
