@@ -182,12 +182,12 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
 # Per-unit figures of the FP64 fused flux kernel (ncu counters, 640k-point
 # capture, profiles/k_flux_update_fp64_naca0012_640k.md): executed FP64
 # instructions per stencil edge (every FP64 instruction, of which DFMA + DMUL +
-# DADD are 221.3) and the flops they carry (2 DFMA + DMUL + DADD); DRAM bytes
+# DADD are 217.9) and the flops they carry (2 DFMA + DMUL + DADD); DRAM bytes
 # per point of one full-size 2.5M launch (single-pass capture,
 # profiles/launch_list_naca0012_2p5m_fp64.md).
-FP64_INSTR_PER_EDGE_FLUX = 225.63
-FP64_FLOPS_PER_EDGE_FLUX = 345.93
-FLUX_DRAM_BYTES_PER_POINT = 598.0
+FP64_INSTR_PER_EDGE_FLUX = 222.28
+FP64_FLOPS_PER_EDGE_FLUX = 339.98
+FLUX_DRAM_BYTES_PER_POINT = 598.6
 # FP64 peak: ncu's DFMA unit count, 304 FP64 thread-instructions per cycle
 # (each DFMA 2 flops), at the 2070 MHz maximum SM clock
 FP64_PEAK_GINSTR = 304 * 2.070
@@ -381,7 +381,7 @@ MIXED_TRAFFIC_PER_POINT = {"flux": 351.0, "qgrad": 181.0}
 # profiles/k_flux_update_mixed_naca0012_640k.md): the kernel is bound by
 # instruction issue, 4 warp instructions per cycle per SM at the 2.07 GHz
 # maximum SM clock
-MIXED_FLUX_WARP_INSTR_PER_EDGE = 61303128 / 5167022
+MIXED_FLUX_WARP_INSTR_PER_EDGE = 61136978 / 5167022
 ISSUE_PEAK_GINSTR = 152 * 4 * 2.070
 
 

@@ -282,10 +282,13 @@ __device__ __forceinline__ void store8(double *a, int64_t p, const double v[8])
 __device__ __forceinline__ bool q_from_U(const double U[4], const Gas &gas, double q[4])
 {
     const double rho = U[0];
-    const double u = U[1] / rho, v = U[2] / rho;
+    const double irho = 1.0 / rho;
+    const double u = U[1] * irho, v = U[2] * irho;
     const double p = (gas.gamma - 1.0) * (U[3] - 0.5 * rho * (u * u + v * v));
     const double beta = 0.5 * rho / p;
-    q[0] = log(rho) + log(beta) * gas.inv_gm1 - beta * (u * u + v * v);
+    // gamma = 1.4: ln rho + 2.5 ln beta as one logarithm of rho beta^2 sqrt(beta)
+    const double lrb = gas.g14 ? log(rho * (beta * beta) * sqrt(beta)) : log(rho) + log(beta) * gas.inv_gm1;
+    q[0] = lrb - beta * (u * u + v * v);
     q[1] = 2.0 * beta * u;
     q[2] = 2.0 * beta * v;
     q[3] = -2.0 * beta;
