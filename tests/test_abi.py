@@ -70,3 +70,20 @@ def test_create_rejects_an_unknown_boundary_mode_without_touching_the_gpu():
                         ctypes.byref(ctx))
     assert st == lskum.LSKUM_ERR_ARG and not ctx.value
     assert b"boundary" in L.lskum_last_error(None)
+
+
+def test_create_rejects_clouds_beyond_the_layout_limits_without_touching_the_gpu():
+    """The mixed form packs a neighbour index into 28 bits: 2^28 points are
+    refused (before any input array is read), as is n = 2^31 in either form."""
+    import numpy as np
+    L = lskum.load()
+    ctx = ctypes.c_void_p()
+    x = np.zeros(4)
+    off = np.zeros(5, np.int32)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    for n, precision, what in ((1 << 28, 1, b"2^28"), (1 << 31, 0, b"out of range")):
+        cfg = lskum.lskum_config(2, 3, 1, 0.2, 0.5, 0.0, 1.4, precision, 0, 0.0, 0)
+        st = L.lskum_create(n, p(x), p(x), p(x), p(x), p(off), p(off), p(off), 0, None, ctypes.byref(cfg), None,
+                            ctypes.byref(ctx))
+        assert st == lskum.LSKUM_ERR_ARG and not ctx.value
+        assert what in L.lskum_last_error(None)
