@@ -59,6 +59,9 @@ struct lskum_ctx {
     // q and q-derivative buffers: double in the FP64 form, float in the mixed one
     void *q_cur = nullptr, *q_nxt = nullptr;
     void *qgA = nullptr, *qgB = nullptr;
+    // FP64 form, second order: the first-order q-derivatives kept for the
+    // inner passes, and the limiter's extremum measure
+    double *qgG1 = nullptr, *qext = nullptr;
     bool mixed = false;
     int n_fp64_closure = 0;
     // mixed form: FP32 geometry view
@@ -633,6 +636,10 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
         c->qgA = b;
         c->qgB = b + 8 * n * qbytes;
     }
+    if (!c->mixed && c->cfg.order == 2) {
+        CK(c, dalloc(c, &c->qgG1, 8 * n));
+        CK(c, dalloc(c, &c->qext, 4 * n));
+    }
     if (c->mixed) {
         // FP32 geometry in CSR order, then scattered into the SELL-32 layout
         CK(c, dalloc(c, &c->nrm_f, n));
@@ -923,10 +930,21 @@ static lskum_status gradients(lskum_ctx *c, const void *q, void **qg_out, int in
     } else {
         const DevGeom g = c->geom();
         const double *qd = (const double *)q;
-        TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, qd, nullptr, (double *)src, inner == 0 ? limK : 0.0, c->stream));
-        for (int k = 0; k < inner; ++k) {
-            TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, qd, (const double *)src, (double *)dst,
-                                                             k == inner - 1 ? limK : 0.0, c->stream));
+        if (inner == 0) {
+            TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, qd, nullptr, nullptr, (double *)src, nullptr, limK,
+                                                             c->stream));
+        } else {
+            // the first-order result stays in qgG1 for every inner pass, the
+            // iterates alternate between qgA and qgB
+            double *g1 = c->qgG1, *ext = limK > 0.0 ? c->qext : nullptr;
+            TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, qd, nullptr, nullptr, g1, ext, 0.0, c->stream));
+            const double *old = g1;
+            for (int k = 0; k < inner; ++k) {
+                TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, qd, old, g1, (double *)src, ext,
+                                                                 k == inner - 1 ? limK : 0.0, c->stream));
+                old = (const double *)src;
+                std::swap(src, dst);
+            }
             std::swap(src, dst);
         }
     }
@@ -1233,10 +1251,10 @@ static lskum_status vjp_forward(lskum_ctx *c, const double *Ui)
     const DevGeom g = c->geom();
     LAUNCH(c, launch_q_from_U(n, c->gas, Ui, c->vq, c->status, c->stream));
     if (c->cfg.order == 2) {
-        LAUNCH(c, launch_qgrad(g, c->vq, nullptr, c->vG, 0.0, c->stream));
+        LAUNCH(c, launch_qgrad(g, c->vq, nullptr, nullptr, c->vG, nullptr, 0.0, c->stream));
         for (int k = 1; k <= c->cfg.inner_iters; ++k)
-            LAUNCH(c, launch_qgrad(g, c->vq, c->vG + (int64_t)(k - 1) * 8 * n, c->vG + (int64_t)k * 8 * n, 0.0,
-                                   c->stream));
+            LAUNCH(c, launch_qgrad(g, c->vq, c->vG + (int64_t)(k - 1) * 8 * n, c->vG, c->vG + (int64_t)k * 8 * n,
+                                   nullptr, 0.0, c->stream));
     }
     return LSKUM_OK;
 }

@@ -49,48 +49,103 @@ __device__ __forceinline__ void image_q(const DevGeom &g, int e, uint8_t m, doub
     reflect2(qi[1], qi[2], n0.x, n0.y);
 }
 
-// limK > 0 on the final pass: scale each component of the new gradient by
-// Venkatakrishnan's limiter. f(D, d) is >= 1 for 0 < d <= D/2 and decreasing
-// beyond, so its minimum over every reconstruction shift +-(P_i - P_0).grad/2
-// is its value at the largest shift d+ on each side.
+// Order-preserving integer image of a double (anything but NaN): its IEEE
+// bits as a signed integer with the magnitude bits of negative values
+// inverted, so that integer order is numeric order (-0 just below +0); the
+// map is its own inverse. FP64 min/max issue at the FP64 rate on this part,
+// 1/64 of the integer ALU rate, so the stencil extrema take this form.
+__device__ __forceinline__ long long order_key(long long b) { return b ^ ((b >> 63) & 0x7fffffffffffffffLL); }
+__device__ __forceinline__ unsigned long long abs_bits(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
+// Kinds of q-derivative pass (the template argument PASS): QG_INNER an inner
+// iteration, QG_LIMIT the limiter applied at its end, QG_EXTREMA a first
+// pass that also stores the limiter's extremum measure for a limited inner
+// pass that follows.
+enum { QG_LIMIT = 1, QG_INNER = 2, QG_EXTREMA = 4 };
+
+// One pass, by kind:
+//   first:  G1 = sum_e a_e (q_i - q_0), the first-order solve;
+//   inner:  G1 - sum_e a_e (h_e . grad q_i) + grad q_0 / 2, which is the sum
+//           of a_e (q_i - q_0 - h_e . (grad q_i - grad q_0)) over the stencil
+//           (h_e the half offset (P_i - P_0)/2): the weights a_e = M^-1 d_e,
+//           M = sum_e d_e d_e^T, satisfy sum_e a_e d_e^T = I, so the terms in
+//           grad q_0 add up to grad q_0 / 2, and the first-order part is the
+//           stored G1 (g1) of the same state.
+// The limiter scales each component of the result by Venkatakrishnan's
+// phi = min over every reconstruction shift +-h_e.grad q of f(D, d), D the
+// stencil maximum minus q_0 for a positive shift, the minimum minus q_0 for
+// a negative one. With x = |D| and d = |shift|, f = N/M has N - M = d (x - 2d):
+// f < 1 exactly when x < 2d, and it increases in x up to x = 2d + sqrt(8d^2 +
+// eps^2) > 2d and stays above 1 beyond; for fixed x it decreases in d. So phi
+// is 1 unless x_m = min(D+, -D-) < 2 d_m, d_m the largest |h_e.grad q|, and
+// then it is f(x_m, d_m): one division per component.
 // KIN: the kinetic boundary mode (mirror images in g.ioff...; a separate
 // instantiation keeps the plain kernel's registers as they are)
-template <bool KIN>
+template <bool KIN, int PASS>
 __global__ void __launch_bounds__(128) k_qgrad(DevGeom g, const double *__restrict__ q,
-                                               const double *__restrict__ qg_old,
-                                               double *__restrict__ qg_new, double limK)
+                                               const double *__restrict__ qg_old, const double *__restrict__ g1,
+                                               double *__restrict__ qg_new, double *__restrict__ ext, double limK)
 {
+    constexpr bool INNER = (PASS & QG_INNER) != 0, LIMIT = (PASS & QG_LIMIT) != 0;
+    constexpr bool EXTR = !INNER && (PASS & (QG_LIMIT | QG_EXTREMA)) != 0;   // extrema found here
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.n) return;
-    double q0[4], g0[8], sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
-    load4(q, p, q0);
-    const bool inner = qg_old != nullptr;
-    const bool limit = limK > 0.0;
-    double2 xy0 = make_double2(0.0, 0.0);
-    if (inner) load8(qg_old, p, g0);
-    if (inner || limit) xy0 = g.xy[p];
-    double qmax[4] = {q0[0], q0[1], q0[2], q0[3]}, qmin[4] = {q0[0], q0[1], q0[2], q0[3]};
+    double sx[4], sy[4];
+    // order keys of the largest and smallest q_i - q_0 (P_0's own difference: +0)
+    long long kmax[4] = {0, 0, 0, 0}, kmin[4] = {0, 0, 0, 0};
     const int e0 = g.off[p], e1 = g.off[p + 1];
-    for (int e = e0; e < e1; ++e) {
-        const int i = g.idx[e];
-        const double2 a = g.lsw[e];
-        double qi[4];
-        load4(q, i, qi);
-        double dq[4];
+    double2 xy0 = make_double2(0.0, 0.0);
+    if ((INNER || LIMIT) && !g.hd) xy0 = g.xy[p];
+    if constexpr (!INNER) {
+        double q0[4];
+        load4(q, p, q0);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) dq[k] = qi[k] - q0[k];
-        if (limit) {
-            // stencil extrema for the limiter (only its pass needs them)
+        for (int k = 0; k < 4; ++k) sx[k] = sy[k] = 0.0;
+        auto add = [&](const double qi[4], double2 a) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                qmax[k] = fmax(qmax[k], qi[k]);
-                qmin[k] = fmin(qmin[k], qi[k]);
+                const double dq = qi[k] - q0[k];
+                if constexpr (EXTR) {
+                    const long long key = order_key(__double_as_longlong(dq));
+                    kmax[k] = max(kmax[k], key);
+                    kmin[k] = min(kmin[k], key);
+                }
+                sx[k] = fma(a.x, dq, sx[k]);
+                sy[k] = fma(a.y, dq, sy[k]);
+            }
+        };
+        for (int e = e0; e < e1; ++e) {
+            double qi[4];
+            load4(q, g.idx[e], qi);
+            add(qi, g.lsw[e]);
+        }
+        if constexpr (KIN) {
+            // kinetic boundary mode: the mirror images of the neighbours
+            const int f0 = g.ioff[p], f1 = g.ioff[p + 1];
+            if (f0 < f1) {
+                const double2 n0 = g.nrm[p];
+                const double *qf = g.qinf + 4 * (g.pcase ? (int)g.pcase[p] : 0);
+                for (int e = f0; e < f1; ++e) {
+                    double qi[4];
+                    image_q(g, e, g.imask[e], n0, qf, q, nullptr, make_double2(0.0, 0.0), false, qi);
+                    add(qi, g.ilsw[e]);
+                }
             }
         }
-        if (inner) {
-            // the previous iterate at P_0 is taken out of the sum below
-            double gi[8];
-            load8(qg_old, i, gi);
+    } else {
+        double t[8];
+        load8(g1, p, t);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            sx[k] = t[k];
+            sy[k] = t[4 + k];
+        }
+        for (int e = e0; e < e1; ++e) {
+            const int i = g.idx[e];
+            const double2 a = g.lsw[e];
             double2 h;
             if (g.hd) {
                 h = g.hd[e];
@@ -98,81 +153,89 @@ __global__ void __launch_bounds__(128) k_qgrad(DevGeom g, const double *__restri
                 const double2 xyi = g.xy[i];
                 h = make_double2(0.5 * (xyi.x - xy0.x), 0.5 * (xyi.y - xy0.y));
             }
+            double gi[8];
+            load8(qg_old, i, gi);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) dq[k] = fma(-h.y, gi[4 + k], fma(-h.x, gi[k], dq[k]));
+            for (int k = 0; k < 4; ++k) {
+                const double c = fma(h.y, gi[4 + k], h.x * gi[k]);
+                sx[k] = fma(-a.x, c, sx[k]);
+                sy[k] = fma(-a.y, c, sy[k]);
+            }
         }
+        if constexpr (KIN) {
+            // a wall image's q~ is the reflection of q_i - h.grad q_i, h the
+            // reflection of the image's half offset, so its correction is the
+            // reflection of h.grad q_i; far-field images carry no gradient
+            const int f0 = g.ioff[p], f1 = g.ioff[p + 1];
+            if (f0 < f1) {
+                const double2 n0 = g.nrm[p];
+                for (int e = f0; e < f1; ++e) {
+                    if (g.imask[e] & M_IMG_FAR) continue;
+                    const double2 a = g.ilsw[e];
+                    double2 h = g.ihd[e];
+                    reflect2(h.x, h.y, n0.x, n0.y);
+                    double gi[8], c[4];
+                    load8(qg_old, g.iidx[e], gi);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            sx[k] += a.x * dq[k];
-            sy[k] += a.y * dq[k];
-        }
-    }
-    if constexpr (KIN) {
-        // kinetic boundary mode: the mirror images of the neighbours
-        const int f0 = g.ioff[p], f1 = g.ioff[p + 1];
-        if (f0 < f1) {
-            const double2 n0 = g.nrm[p];
-            const double *qf = g.qinf + 4 * (g.pcase ? (int)g.pcase[p] : 0);
-            for (int e = f0; e < f1; ++e) {
-                const uint8_t m = g.imask[e];
-                const double2 a = g.ilsw[e];
-                double qi[4], dq[4];
-                image_q(g, e, m, n0, qf, q, qg_old, g.ihd[e], inner, qi);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) dq[k] = qi[k] - q0[k];
-                if (limit) {
-                    if (inner) image_q(g, e, m, n0, qf, q, qg_old, g.ihd[e], false, qi);
+                    for (int k = 0; k < 4; ++k) c[k] = fma(-h.y, gi[4 + k], -h.x * gi[k]);
+                    reflect2(c[1], c[2], n0.x, n0.y);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        qmax[k] = fmax(qmax[k], qi[k]);
-                        qmin[k] = fmin(qmin[k], qi[k]);
+                        sx[k] = fma(a.x, c[k], sx[k]);
+                        sy[k] = fma(a.y, c[k], sy[k]);
                     }
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    sx[k] += a.x * dq[k];
-                    sy[k] += a.y * dq[k];
                 }
             }
         }
-    }
-    if (inner) {
-        // sum_e a_e (d_e . g_0) = g_0, since the weights a_e = M^-1 d_e with
-        // M = sum_e d_e d_e^T give sum_e a_e d_e^T = I: the +1/2 d_e . g_0 of
-        // every corrected difference (E14) adds up to g_0 / 2
+        load8(qg_old, p, t);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            sx[k] += 0.5 * g0[k];
-            sy[k] += 0.5 * g0[4 + k];
+            sx[k] = fma(0.5, t[k], sx[k]);
+            sy[k] = fma(0.5, t[4 + k], sy[k]);
         }
     }
-    if (limit) {
-        double dmax[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int e = e0; e < e1; ++e) {
-            const double2 xyi = g.xy[g.idx[e]];
-            const double dx = xyi.x - xy0.x, dy = xyi.y - xy0.y;
+    // x_m = min(D+, -D-) per component
+    double xm[4];
+    if constexpr (EXTR) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) dmax[k] = fmax(dmax[k], fabs(0.5 * (dx * sx[k] + dy * sy[k])));
+        for (int k = 0; k < 4; ++k)
+            xm[k] = __longlong_as_double((long long)min((unsigned long long)kmax[k],
+                                                        abs_bits(__longlong_as_double(order_key(kmin[k])))));
+    }
+    if constexpr (LIMIT) {
+        if constexpr (INNER) load4(ext, p, xm);
+        unsigned long long dm[4] = {0, 0, 0, 0};   // bits of d_m (non-negative doubles order as integers)
+        for (int e = e0; e < e1; ++e) {
+            double2 h;
+            if (g.hd) {
+                h = g.hd[e];
+            } else {
+                const double2 xyi = g.xy[g.idx[e]];
+                h = make_double2(0.5 * (xyi.x - xy0.x), 0.5 * (xyi.y - xy0.y));
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dm[k] = max(dm[k], abs_bits(fma(h.x, sx[k], h.y * sy[k])));
         }
         if constexpr (KIN) {
             for (int e = g.ioff[p]; e < g.ioff[p + 1]; ++e) {
                 const double2 h = g.ihd[e];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) dmax[k] = fmax(dmax[k], fabs(h.x * sx[k] + h.y * sy[k]));
+                for (int k = 0; k < 4; ++k) dm[k] = max(dm[k], abs_bits(fma(h.x, sx[k], h.y * sy[k])));
             }
         }
-        const double h = g.dmin[p] * limK;
-        const double eps2 = h * h * h;
+        const double hK = g.dmin[p] * limK;
+        const double eps2 = hK * hK * hK;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            double phi = 1.0;
-            if (dmax[k] > 0.0) {
-                phi = fmin(phi, venkat(qmax[k] - q0[k], dmax[k], eps2));
-                phi = fmin(phi, venkat(qmin[k] - q0[k], -dmax[k], eps2));
+            const double d = __longlong_as_double((long long)dm[k]);
+            if (xm[k] < 2.0 * d) {
+                const double phi = venkat(xm[k], d, eps2);
+                sx[k] *= phi;
+                sy[k] *= phi;
             }
-            sx[k] *= phi;
-            sy[k] *= phi;
         }
+    } else if constexpr (EXTR) {
+        store4(ext, p, xm);
     }
     double out[8] = {sx[0], sx[1], sx[2], sx[3], sy[0], sy[1], sy[2], sy[3]};
     store8(qg_new, p, out);
@@ -521,11 +584,28 @@ __global__ void __launch_bounds__(256) k_forces(int64_t nwall, Gas gas, double q
 // ----------------------------------------------------------------------------
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-cudaError_t launch_qgrad(const DevGeom &g, const double *q, const double *qg_old, double *qg_new,
-                         double limiter_K, cudaStream_t s)
+template <bool KIN>
+static void qgrad_pass(int pass, const DevGeom &g, const double *q, const double *qg_old, const double *g1,
+                       double *qg_new, double *ext, double limK, cudaStream_t s)
 {
-    if (g.ioff) k_qgrad<true><<<blocks_for(g.n, 128), 128, 0, s>>>(g, q, qg_old, qg_new, limiter_K);
-    else k_qgrad<false><<<blocks_for(g.n, 128), 128, 0, s>>>(g, q, qg_old, qg_new, limiter_K);
+    const unsigned nb = blocks_for(g.n, 128);
+    switch (pass) {
+    case 0: k_qgrad<KIN, 0><<<nb, 128, 0, s>>>(g, q, qg_old, g1, qg_new, ext, limK); break;
+    case QG_EXTREMA: k_qgrad<KIN, QG_EXTREMA><<<nb, 128, 0, s>>>(g, q, qg_old, g1, qg_new, ext, limK); break;
+    case QG_LIMIT: k_qgrad<KIN, QG_LIMIT><<<nb, 128, 0, s>>>(g, q, qg_old, g1, qg_new, ext, limK); break;
+    case QG_INNER: k_qgrad<KIN, QG_INNER><<<nb, 128, 0, s>>>(g, q, qg_old, g1, qg_new, ext, limK); break;
+    default: k_qgrad<KIN, QG_INNER | QG_LIMIT><<<nb, 128, 0, s>>>(g, q, qg_old, g1, qg_new, ext, limK); break;
+    }
+}
+
+cudaError_t launch_qgrad(const DevGeom &g, const double *q, const double *qg_old, const double *g1,
+                         double *qg_new, double *ext, double limiter_K, cudaStream_t s)
+{
+    const bool inner = qg_old != nullptr, limit = limiter_K > 0.0;
+    if (inner && (!g1 || (limit && !ext))) return cudaErrorInvalidValue;
+    const int pass = inner ? (QG_INNER | (limit ? QG_LIMIT : 0)) : limit ? QG_LIMIT : ext ? QG_EXTREMA : 0;
+    if (g.ioff) qgrad_pass<true>(pass, g, q, qg_old, g1, qg_new, ext, limiter_K, s);
+    else qgrad_pass<false>(pass, g, q, qg_old, g1, qg_new, ext, limiter_K, s);
     return cudaGetLastError();
 }
 

@@ -27,8 +27,13 @@ struct FluxLaunch {
     int stage;
 };
 
-cudaError_t launch_qgrad(const DevGeom &g, const double *q, const double *qg_old, double *qg_new,
-                         double limiter_K, cudaStream_t s);
+// One q-derivative pass. First pass (qg_old == nullptr): the first-order
+// solve into qg_new, limited when limiter_K > 0, else with the limiter's
+// extremum measure ([n][4]) stored to ext when ext != nullptr. Inner pass:
+// needs g1, the first pass's result for the same q, and, when limiter_K > 0,
+// the ext a first pass stored (cudaErrorInvalidValue without them).
+cudaError_t launch_qgrad(const DevGeom &g, const double *q, const double *qg_old, const double *g1,
+                         double *qg_new, double *ext, double limiter_K, cudaStream_t s);
 cudaError_t launch_flux(const DevGeom &g, const Gas &gas, const FluxLaunch &L, cudaStream_t s);
 // residue of every case into out_base[*counter * ncases + c] (when 0 <= *counter < cap), then ++*counter;
 // part holds a pair of sums per warp of 32 points (residue_parts(n) values); chunk is scratch of
