@@ -157,14 +157,17 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
 // erf = +-1 (erfc(6) = 2e-17) and exp(-S^2) directly.
 __device__ __forceinline__ void erf_exp(double S, double &erfS, double &eS)
 {
-    const double a = fabs(S);
-    const int hi = __double2hiint(a);
-    if (hi >= 0x40180000) {  // a >= 6
+    // the words of |S| straight from S's bits: a materialised fabs would be
+    // an FP64 instruction
+    unsigned lo;
+    int hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(S));
+    hi &= 0x7fffffff;
+    if (hi >= 0x40180000) {  // |S| >= 6
         erfS = copysign(1.0, S);
         eS = exp(-S * S);
         return;
     }
-    const unsigned lo = (unsigned)__double2loint(a);
     // an FP32 copy of a (truncated mantissa) built from the FP64 bits
     const float af = hi < ((1023 - 30) << 20)
                          ? 0.0f
@@ -178,7 +181,7 @@ __device__ __forceinline__ void erf_exp(double S, double &erfS, double &eS)
         v[2 * j] = t.x;
         v[2 * j + 1] = t.y;
     }
-    const double d = a - v[0];
+    const double d = fabs(S) - v[0];   // |.| as an operand modifier of the subtraction
     double c = v[1 + LSKUM_ERF_DEG], e = v[2 + 2 * LSKUM_ERF_DEG];
 #pragma unroll
     for (int n = LSKUM_ERF_DEG - 1; n >= 0; --n) {
@@ -197,6 +200,16 @@ __device__ __forceinline__ double flip_sign(double x, unsigned long long sbit)
 }
 
 static constexpr unsigned long long kSignBit = 0x8000000000000000ull;
+
+// the magnitude bits of x (sign bit cleared) by an integer AND that the
+// compiler cannot turn into an FP64 absolute value, which would be issued on
+// the FP64 pipe
+__device__ __forceinline__ unsigned long long abs_bits(double x)
+{
+    unsigned long long b;
+    asm("and.b64 %0, %1, 0x7fffffffffffffff;" : "=l"(b) : "l"(__double_as_longlong(x)));
+    return b;
+}
 
 // Kinetic split flux along a direction: normal velocity un, transverse ut,
 // sgn = +1 for G+, -1 for G- (half-range moments of the Maxwellian):

@@ -14,10 +14,19 @@ namespace lskum {
 // with the previous iterate qg_old read at every point and the new one
 // written to qg_new (no point reads what this pass writes).
 // --------------------------------------------------------------------------
-// Venkatakrishnan's function f(D, d) = (D^2 + e^2 + 2Dd)/(D^2 + 2d^2 + Dd + e^2)
-__device__ __forceinline__ double venkat(double D, double d, double eps2)
+// 1/M for a positive normal M: the approximate reciprocal of PTX
+// (rcp.approx.ftz.f64) refined by two steps of Newton's iteration for 1/M,
+// r <- r + r (1 - M r), each of which squares the relative error; the
+// limiter's phi needs no correctly rounded quotient, and the limited
+// q-derivative parity tests hold it to far below 1e-12.
+__device__ __forceinline__ double rcp_newton(double M)
 {
-    return (D * D + eps2 + 2.0 * D * d) / (D * D + 2.0 * d * d + D * d + eps2);
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(M));
+    double e = fma(-M, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-M, r, 1.0);
+    return fma(r, e, r);
 }
 
 // Kinetic boundary mode: the q carried by the image (entry e of the image
@@ -55,10 +64,6 @@ __device__ __forceinline__ void image_q(const DevGeom &g, int e, uint8_t m, doub
 // map is its own inverse. FP64 min/max issue at the FP64 rate on this part,
 // 1/64 of the integer ALU rate, so the stencil extrema take this form.
 __device__ __forceinline__ long long order_key(long long b) { return b ^ ((b >> 63) & 0x7fffffffffffffffLL); }
-__device__ __forceinline__ unsigned long long abs_bits(double v)
-{
-    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
-}
 
 // Kinds of q-derivative pass (the template argument PASS): QG_INNER an inner
 // iteration, QG_LIMIT the limiter applied at its end, QG_EXTREMA a first
@@ -75,9 +80,10 @@ enum { QG_LIMIT = 1, QG_INNER = 2, QG_EXTREMA = 4 };
 //           grad q_0 add up to grad q_0 / 2, and the first-order part is the
 //           stored G1 (g1) of the same state.
 // The limiter scales each component of the result by Venkatakrishnan's
-// phi = min over every reconstruction shift +-h_e.grad q of f(D, d), D the
-// stencil maximum minus q_0 for a positive shift, the minimum minus q_0 for
-// a negative one. With x = |D| and d = |shift|, f = N/M has N - M = d (x - 2d):
+// phi = min over every reconstruction shift +-h_e.grad q of
+// f(D, d) = (D^2 + eps^2 + 2Dd) / (D^2 + 2d^2 + Dd + eps^2), D the stencil
+// maximum minus q_0 for a positive shift, the minimum minus q_0 for a
+// negative one, eps^2 = (K min_e |P_i - P_0|)^3. With x = |D| and d = |shift|, f = N/M has N - M = d (x - 2d):
 // f < 1 exactly when x < 2d, and it increases in x up to x = 2d + sqrt(8d^2 +
 // eps^2) > 2d and stays above 1 beyond; for fixed x it decreases in d. So phi
 // is 1 unless x_m = min(D+, -D-) < 2 d_m, d_m the largest |h_e.grad q|, and
@@ -227,12 +233,14 @@ __global__ void __launch_bounds__(128) k_qgrad(DevGeom g, const double *__restri
         const double eps2 = hK * hK * hK;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const double d = __longlong_as_double((long long)dm[k]);
-            if (xm[k] < 2.0 * d) {
-                const double phi = venkat(xm[k], d, eps2);
-                sx[k] *= phi;
-                sy[k] *= phi;
-            }
+            // f(x, d) = N / M, N = x (x + 2d) + eps^2, M = x (x + d) + (2d^2 + eps^2),
+            // evaluated for every component (warps diverge on x < 2d anyway)
+            const double x = xm[k], d = __longlong_as_double((long long)dm[k]), d2 = 2.0 * d;
+            const double N = fma(x, x + d2, eps2);
+            const double M = fma(x, x + d, fma(d2, d, eps2));
+            const double phi = x < d2 ? N * rcp_newton(M) : 1.0;
+            sx[k] *= phi;
+            sy[k] *= phi;
         }
     } else if constexpr (EXTR) {
         store4(ext, p, xm);
