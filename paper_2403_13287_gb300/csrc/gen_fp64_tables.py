@@ -3,7 +3,7 @@
 1. erf(S) and exp(-S^2), Taylor coefficients on a grid.
 
 The FP64 split fluxes need erf(S) and exp(-S^2) of the same S. On the grid
-s_k = k/256, k = 0..1536 (0 <= s <= 6), each row holds s_k and the degree-5
+s_k = k/1024, k = 0..6144 (0 <= s <= 6), each row holds s_k and the degree-4
 Taylor coefficients in d = s - s_k of
 
     erf(s_k + d)      : c_n = erf^(n)(s_k) / n!
@@ -11,13 +11,16 @@ Taylor coefficients in d = s - s_k of
 
 (H_n the physicists' Hermite polynomials, d^n/dx^n exp(-x^2) =
 (-1)^n H_n(x) exp(-x^2), and erf' = 2/sqrt(pi) exp(-x^2), so
-c_n = 2/sqrt(pi) e_{n-1} / n for n >= 1). With |d| <= 1/512 the first
-omitted terms are below 1e-17, so each function comes out of one table row
-and two Horner chains of 5 steps to about one unit in the last place of 1
-(a finer grid with a lower degree: fewer FP64 operations per evaluation
-for a larger table, 168 KB, whose rows in use stay cached). The values
-are computed with mpmath at 50 significant digits and written as exactly
-rounded hexadecimal doubles.
+c_n = 2/sqrt(pi) e_{n-1} / n for n >= 1). With |d| <= 1/2048 the first
+omitted terms, d^5/5! times |H_5(s) exp(-s^2)| <= 32 (or 2/sqrt(pi) |H_4|
+<= 14 for erf), are below 1e-17, so each function comes out of one table
+row and a Horner chain of 4 steps to about one unit in the last place of 1.
+The split fluxes take erf only through 1 +- erf(S), so this absolute error
+is the measure. A finer grid with a lower degree means fewer FP64
+operations per evaluation for a larger table (576 KB): the FP64 pipe, not
+the cache, bounds the kernels that use it. The values are computed with
+mpmath at 50 significant digits and written as exactly rounded
+hexadecimal doubles.
 
 2. exp(x), table-driven (P. T. P. Tang, ACM Trans. Math. Software 15 (1989)
 144-157): x = n ln2/512 + r with |r| <= ln2/1024 and n = 512 m + j, so
@@ -33,9 +36,9 @@ import os
 import mpmath as mp
 
 mp.mp.dps = 50
-STEP = 256         # grid points per unit of s
-KMAX = 1536        # s_k up to 6
-DEG = 5
+STEP = 1024        # grid points per unit of s
+KMAX = 6144        # s_k up to 6
+DEG = 4
 EXP_N = 512        # entries of the 2^(j/N) table
 
 

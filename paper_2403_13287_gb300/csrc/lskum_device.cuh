@@ -148,12 +148,12 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
 }
 
 // erf(S) and exp(-S^2) together, from one row of a Taylor table: on the grid
-// s_k = k/256 (0 <= s_k <= 6) the row holds the degree-5 Taylor coefficients
-// of both functions in d = |S| - s_k (|d| <= 1/512), so each is one Horner
+// s_k = k/1024 (0 <= s_k <= 6) the row holds the degree-4 Taylor coefficients
+// of both functions in d = |S| - s_k (|d| <= 1/2048), so each is one Horner
 // chain with an absolute error of about one unit in the last place of 1
 // (gen_fp64_tables.py; the first omitted terms are below 1e-17). The nearest
 // grid index comes from the top bits of |S| by integer operations, so the
-// FP64 pipe sees one subtraction and 10 fused multiply-adds. |S| >= 6:
+// FP64 pipe sees one subtraction and 8 fused multiply-adds. |S| >= 6:
 // erf = +-1 (erfc(6) = 2e-17) and exp(-S^2) directly.
 __device__ __forceinline__ void erf_exp(double S, double &erfS, double &eS)
 {
