@@ -23,11 +23,12 @@ mpmath at 50 significant digits and written as exactly rounded
 hexadecimal doubles.
 
 2. exp(x), table-driven (P. T. P. Tang, ACM Trans. Math. Software 15 (1989)
-144-157): x = n ln2/512 + r with |r| <= ln2/1024 and n = 512 m + j, so
-exp(x) = 2^m 2^(j/512) p(r), p the degree-4 Taylor polynomial of exp
-(truncation below 2e-18). The table holds 2^(j/512), j = 0..511, exactly
-rounded (4 KB); ln2/512 is split into a head with 32 significant bits (so
-that n * head is exact for |n| < 2^21) and the rounded remainder.
+144-157): x = n ln2/4096 + r with |r| <= ln2/8192 and n = 4096 m + j, so
+exp(x) = 2^m 2^(j/4096) p(r), p the degree-3 Taylor polynomial of exp
+(truncation r^4/24 below 3e-18). The table holds 2^(j/4096), j = 0..4095,
+exactly rounded (32 KB); ln2/4096 is split into a head with 31 significant
+bits (so that n * head is exact for |n| < 2^22, which covers |x| < 708) and
+the rounded remainder.
 
 Run from the repository root:  python paper_2403_13287_gb300/csrc/gen_fp64_tables.py
 """
@@ -39,7 +40,8 @@ mp.mp.dps = 50
 STEP = 1024        # grid points per unit of s
 KMAX = 6144        # s_k up to 6
 DEG = 4
-EXP_N = 512        # entries of the 2^(j/N) table
+EXP_N = 4096       # entries of the 2^(j/N) table
+EXP_HEAD_BITS = 31 # significant bits of the head of ln2/N
 
 
 def hermite(n, x):
@@ -83,14 +85,15 @@ def main():
     # exp: 2^(j/512) and the split of ln2/512
     L = mp.log(2) / EXP_N
     m_, e_ = mp.frexp(L)                       # L = m_ 2^e_, 1/2 <= m_ < 1
-    head = mp.ldexp(mp.floor(mp.ldexp(m_, 32)), e_ - 32)
+    head = mp.ldexp(mp.floor(mp.ldexp(m_, EXP_HEAD_BITS)), e_ - EXP_HEAD_BITS)
     tail = L - head
     lines += [
         "",
         "// exp(x) = 2^m 2^(j/%d) p(r), x = (%d m + j) ln2/%d + r (Tang's table-driven method)" % (EXP_N, EXP_N, EXP_N),
         "#define LSKUM_EXP_N %d" % EXP_N,
+        "#define LSKUM_EXP_LOG2N %d" % (EXP_N.bit_length() - 1),
         "#define LSKUM_EXP_INV_L %s   // %d/ln2" % (float(EXP_N / mp.log(2)).hex(), EXP_N),
-        "#define LSKUM_EXP_L_HI %s    // ln2/%d, 32 significant bits" % (float(head).hex(), EXP_N),
+        "#define LSKUM_EXP_L_HI %s    // ln2/%d, %d significant bits" % (float(head).hex(), EXP_N, EXP_HEAD_BITS),
         "#define LSKUM_EXP_L_LO %s    // ln2/%d - LSKUM_EXP_L_HI" % (float(tail).hex(), EXP_N),
         "__device__ __align__(16) const double kExp2Table[%d] = {" % EXP_N,
     ]

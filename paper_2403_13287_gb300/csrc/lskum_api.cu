@@ -790,6 +790,7 @@ extern "C" lskum_status lskum_create(int64_t n, const double *x, const double *y
     c->stream = (cudaStream_t)cuda_stream;
     c->gas.gamma = cfg->gamma;
     c->gas.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
+    c->gas.hc = 0.5 * (c->gas.inv_gm1 + 1.0);
     c->gas.g14 = cfg->gamma == 1.4;
     freestream(cfg->gamma, cfg->mach, cfg->aoa_deg, c->gas.Uinf);
     c->case_start_h = {0, n};
@@ -880,6 +881,7 @@ extern "C" lskum_status lskum_create_batch(int n_cases, const lskum_case *cases,
     c->stream = (cudaStream_t)cuda_stream;
     c->gas.gamma = cfg->gamma;
     c->gas.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
+    c->gas.hc = 0.5 * (c->gas.inv_gm1 + 1.0);
     c->gas.g14 = cfg->gamma == 1.4;
     freestream(cfg->gamma, cases[0].mach, cases[0].aoa_deg, c->gas.Uinf);
     lskum_status st = check_config(cfg, N);

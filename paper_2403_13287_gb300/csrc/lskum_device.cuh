@@ -74,41 +74,49 @@ __device__ __forceinline__ void reflect2(T &a, T &b, T nx, T ny)
 struct Gas {
     double gamma;
     double inv_gm1;  // 1/(gamma - 1)
+    double hc;       // gamma/(2 (gamma - 1)): enthalpy per unit mass h = hc/beta + |u|^2/2
     int g14;         // gamma == 1.4: beta^(-1/(gamma-1)) = beta^(-2.5) without log
     double Uinf[4];
 };
 
 // Primitive state of a (modified) q-vector, E13 inverted:
 //   beta = -q4/2, u = q2/(2 beta), v = q3/(2 beta),
-//   rho = exp(q1 + beta (u^2 + v^2)) beta^(-1/(gamma-1)), p = rho/(2 beta)
+//   rho = exp(q1 + beta (u^2 + v^2)) beta^(-1/(gamma-1)), p = rho/(2 beta),
+// with the velocity taken in the frame (t, n) of P_0.
 struct Prim {
-    double u, v, rsb, sqb;  // rsb = 1/sqrt(beta), sqb = sqrt(beta)
-    double hrho, hp;        // rho/2, p/2
-    double h, e2;           // (rho E + p)/rho and (rho E + p/2)/rho
-    double rrc;             // rho rsb / (2 sqrt(pi)), so that rho B = rrc exp(-S^2)
+    double us, un;  // u.t, u.n
+    double sqb;     // sqrt(beta)
+    double hrho;    // rho/2
+    double hp;      // p/2
+    double h;       // (rho E + p)/rho
+    double qb;      // 1/(4 beta) = h - (rho E + p/2)/rho
+    double rrc;     // rho/(2 sqrt(pi beta)), so that rho B = rrc exp(-S^2)
 };
 
-// exp(x), table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157):
-// x = n ln2/512 + r, |r| <= ln2/1024, n = 512 m + j, exp(x) = 2^m 2^(j/512) p(r)
-// with p the degree-4 Taylor polynomial (gen_fp64_tables.py): 9 FP64
-// instructions. |x| >= 708 (or NaN) goes to the library exp.
-__device__ __forceinline__ double exp_tab(double x)
+// exp(x) 2^k, table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157):
+// x = n ln2/4096 + r, |r| <= ln2/8192, n = 4096 m + j, exp(x) = 2^m 2^(j/4096) p(r)
+// with p the degree-3 Taylor polynomial (gen_fp64_tables.py): 8 FP64
+// instructions. The factor 2^(m+k) is an addition to the exponent field on
+// the integer pipe: for |x| < 706 and |k| <= 2 the biased exponent of the
+// result stays within [1, 2044] (2^(j/4096) p(r) lies in [1/2, 2] and
+// |m| <= 1019). |x| >= 706 (or NaN), found from the high word of x on the
+// integer pipe, goes to the library exp.
+__device__ __forceinline__ double exp_tab(double x, int k = 0)
 {
-    if (!(fabs(x) < 708.0)) return exp(x);
+    int xhi;
+    asm("{ .reg .b32 lo; mov.b64 {lo, %0}, %1; }" : "=r"(xhi) : "d"(x));
+    if ((xhi & 0x7fffffff) >= 0x40861000) return ldexp(exp(x), k);  // 0x40861000: high word of 706.0
     const double magic = 0x1.8p52;
     const double t = fma(x, LSKUM_EXP_INV_L, magic);
     const int n = __double2loint(t);  // round-to-nearest integer held in the low word
     const double kd = t - magic;
     double r = fma(-kd, LSKUM_EXP_L_HI, x);
     r = fma(-kd, LSKUM_EXP_L_LO, r);
-    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
-    p = fma(p, r, 0.5);
+    double p = fma(r, 1.0 / 6.0, 0.5);
     p = fma(p, r, 1.0);
     p = fma(p, r, 1.0);
-    // 2^(j/512) p(r) lies in [1/2, 2]; the factor 2^m (|x| < 708 keeps the
-    // result normal) is an addition to its exponent field on the integer pipe
     const double tp = __ldg(&kExp2Table[n & (LSKUM_EXP_N - 1)]) * p;
-    return __hiloint2double(__double2hiint(tp) + (n >> 9) * (1 << 20), __double2loint(tp));
+    return __hiloint2double(__double2hiint(tp) + ((n >> LSKUM_EXP_LOG2N) + k) * (1 << 20), __double2loint(tp));
 }
 
 // a double strictly between 0 and +inf (not 0, negative, inf or NaN), tested
@@ -119,32 +127,34 @@ __device__ __forceinline__ bool finite_positive(double x)
     return b > 0 && b < 0x7ff0000000000000ll;
 }
 
-__device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, Prim &s)
+// u.t = (q2 tx + q3 ty)/(2 beta) and u.n alike, straight from q (no u, v);
+// exp_tab(., -1) gives rho/2 without a multiplication.
+__device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, double tx, double ty, double2 n0,
+                                            Prim &s)
 {
     const double beta = -0.5 * qt[3];
     if (!finite_positive(beta)) return false;
-    s.rsb = rsqrt(beta);
-    const double ib = s.rsb * s.rsb;       // 1/beta, so 1/q4 = -ib/2 without a division
-    const double hib = 0.5 * ib;           // (exact halving: u = q1 hib rounds as 0.5 q1 ib)
-    s.u = qt[1] * hib;
-    s.v = qt[2] * hib;
-    s.sqb = beta * s.rsb;
-    const double ke = beta * (s.u * s.u + s.v * s.v);
-    double rho;
+    const double rsb = rsqrt(beta);
+    const double ib = rsb * rsb;           // 1/beta, so 1/q4 = -ib/2 without a division
+    const double hib = 0.5 * ib;
+    s.us = fma(qt[1], tx, qt[2] * ty) * hib;
+    s.un = fma(qt[1], n0.x, qt[2] * n0.y) * hib;
+    s.sqb = beta * rsb;
+    const double w2 = fma(s.us, s.us, s.un * s.un);   // |u|^2
+    double hrho;
     if (gas.g14) {
         // beta^-2.5 = beta^-1/2 (1/beta)^2
-        rho = exp_tab(qt[0] + ke) * s.rsb * (ib * ib);
+        hrho = exp_tab(fma(beta, w2, qt[0]), -1) * (rsb * (ib * ib));
     } else {
-        rho = exp_tab(qt[0] - log(beta) * gas.inv_gm1 + ke);
+        hrho = exp_tab(fma(beta, w2, qt[0] - log(beta) * gas.inv_gm1), -1);
     }
-    s.hrho = 0.5 * rho;
-    s.hp = s.hrho * hib;                   // p/2 = rho/(4 beta)
+    s.hrho = hrho;
+    s.hp = hrho * hib;                     // p/2 = rho/(4 beta)
     // per unit mass: p/rho = 1/(2 beta), rho E = p/(gamma-1) + rho |u|^2/2
-    const double hu2 = 0.5 * (s.u * s.u + s.v * s.v);
-    s.h = fma(0.5 * (gas.inv_gm1 + 1.0), ib, hu2);
-    s.e2 = fma(0.5 * (gas.inv_gm1 + 0.5), ib, hu2);
-    s.rrc = rho * (s.rsb * 0.28209479177387814);  // 1/(2 sqrt(pi))
-    return finite_positive(rho);
+    s.h = fma(gas.hc, ib, 0.5 * w2);
+    s.qb = 0.5 * hib;
+    s.rrc = hrho * (rsb * 0.5641895835477563);  // 1/sqrt(pi)
+    return finite_positive(hrho);
 }
 
 // erf(S) and exp(-S^2) together, from one row of a Taylor table: on the grid
@@ -217,9 +227,9 @@ __device__ __forceinline__ unsigned long long abs_bits(double x)
 //   G = [rho(un A + sgn B), (p + rho un^2) A + sgn rho un B,
 //        rho ut (un A + sgn B), (rhoE + p) un A + sgn (rhoE + p/2) B]
 // evaluated as Q = rho A = rho/2 (1 + sgn erf S), W = sgn rho B:
-// G0 = un Q + W, G1 = p A + un G0, G2 = ut G0, G3 = h un Q + e2 W (h, e2
-// per unit mass, from the primitive state). sbit = 0 for G+, kSignBit for
-// G-: the products by sgn are sign flips.
+// G0 = un Q + W, G1 = p A + un G0, G2 = ut G0, and with h = (rhoE + p)/rho,
+// e2 = (rhoE + p/2)/rho = h - 1/(4 beta): G3 = h un Q + e2 W = h G0 - W/(4 beta).
+// sbit = 0 for G+, kSignBit for G-: the products by sgn are sign flips.
 __device__ __forceinline__ void split_flux(unsigned long long sbit, const Prim &s, double un, double ut,
                                            double G[4])
 {
@@ -232,7 +242,7 @@ __device__ __forceinline__ void split_flux(unsigned long long sbit, const Prim &
     G[0] = fma(un, Q, W);
     G[1] = fma(un, G[0], fma(s.hp, fe, s.hp));
     G[2] = ut * G[0];
-    G[3] = fma(s.h * un, Q, s.e2 * W);
+    G[3] = fma(s.h, G[0], -s.qb * W);
 }
 
 // per-warp pair of residue partial sums (lo: lanes in the case of the warp's

@@ -298,10 +298,9 @@ __device__ __forceinline__ void edge_residual(const double qti[4], const double 
          (__double_as_longlong(qti[3]) ^ __double_as_longlong(qt0[3]))) == 0)
         return;
     Prim si, s0;
-    ok &= prim_from_q(qti, gas, si);
-    ok &= prim_from_q(qt0, gas, s0);
-    const double us_i = si.u * tx + si.v * ty, un_i = si.u * n0.x + si.v * n0.y;
-    const double us_0 = s0.u * tx + s0.v * ty, un_0 = s0.u * n0.x + s0.v * n0.y;
+    ok &= prim_from_q(qti, gas, tx, ty, n0, si);
+    ok &= prim_from_q(qt0, gas, tx, ty, n0, s0);
+    const double us_i = si.us, un_i = si.un, us_0 = s0.us, un_0 = s0.un;
     // w != 0 tested on the bits (integer pipe; +-0 are the zeros)
     if ((__double_as_longlong(w.x) & ~(long long)kSignBit) != 0) {
         const unsigned long long sg = (m & M_XPOS) ? 0ull : kSignBit;

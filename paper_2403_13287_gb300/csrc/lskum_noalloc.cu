@@ -165,6 +165,7 @@ extern "C" lskum_status lskum_q_derivatives_noalloc(int64_t n, const double *x, 
     Gas gas{};
     gas.gamma = gamma;
     gas.inv_gm1 = 1.0 / (gamma - 1.0);
+    gas.hc = 0.5 * (gas.inv_gm1 + 1.0);
     gas.g14 = gamma == 1.4;
     const unsigned b256 = (unsigned)((n + 255) / 256), b128 = (unsigned)((n + 127) / 128);
     k_na_q<<<b256, 256, 0, s>>>(n, gas, U, q, status);

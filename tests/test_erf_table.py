@@ -78,18 +78,26 @@ def test_exp_table_reproduces_exp():
     """The table-driven exp of the device, step by step in double precision
     (numpy rounds each operation; the device fuses multiply-adds)."""
     inv_l, l_hi, l_lo, T = _exp_consts()
-    N = 512
+    N = 4096
     assert T.shape == (N,) and T[0] == 1.0 and np.all(np.diff(T) > 0)
     assert np.all(np.abs(T - np.array([2.0 ** (j / N) for j in range(N)])) <= np.spacing(T))
-    # the head of ln2/512 has 32 significant bits, so n * head is exact for |n| < 2^21
+    # the head of ln2/4096 has 31 significant bits, so n * head is exact for
+    # |n| < 2^22 (|x| < 706 gives |n| < 4.18e6)
     m, e = math.frexp(l_hi)
-    assert m * 2.0 ** 32 == int(m * 2.0 ** 32)
-    assert abs((l_hi + l_lo) - math.log(2) / N) <= 1e-19
-    x = np.concatenate([np.linspace(-700.0, 700.0, 200001), np.linspace(-5.0, 5.0, 200001)])
+    assert m * 2.0 ** 31 == int(m * 2.0 ** 31)
+    assert abs((l_hi + l_lo) - math.log(2) / N) <= 1e-20
+    x = np.concatenate([np.linspace(-705.9, 705.9, 200001), np.linspace(-5.0, 5.0, 200001)])
     kd = np.rint(x * inv_l)
     n = kd.astype(np.int64)
+    assert np.max(np.abs(n)) < 2 ** 22
     r = (x - kd * l_hi) - kd * l_lo
-    p = (((r / 24 + 1 / 6) * r + 0.5) * r + 1) * r + 1
-    got = T[n & (N - 1)] * p * np.ldexp(1.0, (n >> 9).astype(np.int32))
-    rel = np.abs(got - np.exp(x)) / np.exp(x)
-    assert np.max(rel) <= 4.5e-16
+    assert np.max(np.abs(r)) <= math.log(2) / (2 * N) * (1 + 1e-9)
+    p = ((r / 6 + 0.5) * r + 1) * r + 1
+    # the exponent-field scaling by 2^(m + k), k = -1 as for rho/2, stays normal
+    for k in (0, -1):
+        sc = (n >> 12) + k
+        tp = T[n & (N - 1)] * p
+        assert np.all((np.frexp(tp)[1] - 1 + sc) >= -1022)
+        got = tp * np.ldexp(1.0, sc.astype(np.int32))
+        rel = np.abs(got - np.ldexp(np.exp(x), k)) / np.ldexp(np.exp(x), k)
+        assert np.max(rel) <= 4.5e-16
