@@ -59,9 +59,9 @@ struct lskum_ctx {
     // q and q-derivative buffers: double in the FP64 form, float in the mixed one
     void *q_cur = nullptr, *q_nxt = nullptr;
     void *qgA = nullptr, *qgB = nullptr;
-    // FP64 form, second order: the first-order q-derivatives kept for the
-    // inner passes, and the limiter's extremum measure
-    double *qgG1 = nullptr, *qext = nullptr;
+    // second order: the first-order q-derivatives kept for the inner passes
+    // ([n][8]) and the limiter's extremum measure ([n][4]), in the form's type
+    void *qgG1 = nullptr, *qext = nullptr;
     bool mixed = false;
     int n_fp64_closure = 0;
     // mixed form: FP32 geometry view
@@ -636,9 +636,11 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
         c->qgA = b;
         c->qgB = b + 8 * n * qbytes;
     }
-    if (!c->mixed && c->cfg.order == 2) {
-        CK(c, dalloc(c, &c->qgG1, 8 * n));
-        CK(c, dalloc(c, &c->qext, 4 * n));
+    if (c->cfg.order == 2) {
+        char *b = nullptr;
+        CK(c, dalloc(c, &b, 12 * n * qbytes));
+        c->qgG1 = b;
+        c->qext = b + 8 * n * qbytes;
     }
     if (c->mixed) {
         // FP32 geometry in CSR order, then scattered into the SELL-32 layout
@@ -921,12 +923,22 @@ static lskum_status gradients(lskum_ctx *c, const void *q, void **qg_out, int in
     if (c->mixed) {
         const MixedGeom g = c->mgeom();
         const float *qf = (const float *)q;
-        TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad_mixed(g, qf, nullptr, (float *)src, inner == 0 ? limK : 0.0,
-                                                               c->stream, c->var_qgrad));
-        for (int k = 0; k < inner; ++k) {
-            TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad_mixed(g, qf, (const float *)src, (float *)dst,
-                                                                   k == inner - 1 ? limK : 0.0, c->stream,
+        if (inner == 0) {
+            TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad_mixed(g, qf, nullptr, nullptr, (float *)src, nullptr, limK,
+                                                                   c->stream, c->var_qgrad));
+        } else {
+            // as in the FP64 form: the first-order result stays in qgG1
+            float *g1 = (float *)c->qgG1, *ext = limK > 0.0 ? (float *)c->qext : nullptr;
+            TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad_mixed(g, qf, nullptr, nullptr, g1, ext, 0.0, c->stream,
                                                                    c->var_qgrad));
+            const float *old = g1;
+            for (int k = 0; k < inner; ++k) {
+                TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad_mixed(g, qf, old, g1, (float *)src, ext,
+                                                                       k == inner - 1 ? limK : 0.0, c->stream,
+                                                                       c->var_qgrad));
+                old = (const float *)src;
+                std::swap(src, dst);
+            }
             std::swap(src, dst);
         }
     } else {
@@ -938,7 +950,7 @@ static lskum_status gradients(lskum_ctx *c, const void *q, void **qg_out, int in
         } else {
             // the first-order result stays in qgG1 for every inner pass, the
             // iterates alternate between qgA and qgB
-            double *g1 = c->qgG1, *ext = limK > 0.0 ? c->qext : nullptr;
+            double *g1 = (double *)c->qgG1, *ext = limK > 0.0 ? (double *)c->qext : nullptr;
             TIMED_LAUNCH(c, LSKUM_KERNEL_QGRAD, launch_qgrad(g, qd, nullptr, nullptr, g1, ext, 0.0, c->stream));
             const double *old = g1;
             for (int k = 0; k < inner; ++k) {
@@ -1312,10 +1324,10 @@ static lskum_status vjp_residual_fp32(lskum_ctx *c, const double *Ui, double *Ub
     const MixedGeom mg = c->mgeom();
     LAUNCH(c, launch_q_from_U_mixed(n, c->gas, Ui, c->fq, c->status, c->stream));
     if (second) {
-        LAUNCH(c, launch_qgrad_mixed(mg, c->fq, nullptr, c->fG, 0.0, c->stream, c->var_qgrad));
+        LAUNCH(c, launch_qgrad_mixed(mg, c->fq, nullptr, nullptr, c->fG, nullptr, 0.0, c->stream, c->var_qgrad));
         for (int k = 1; k <= K; ++k)
-            LAUNCH(c, launch_qgrad_mixed(mg, c->fq, c->fG + (int64_t)(k - 1) * 8 * n, c->fG + (int64_t)k * 8 * n, 0.0,
-                                         c->stream, c->var_qgrad));
+            LAUNCH(c, launch_qgrad_mixed(mg, c->fq, c->fG + (int64_t)(k - 1) * 8 * n, c->fG,
+                                         c->fG + (int64_t)k * 8 * n, nullptr, 0.0, c->stream, c->var_qgrad));
     }
     LAUNCH(c, launch_to_float(4 * n, c->vRb, c->fRb, c->stream));
     const AdjParams Pd = adj_params(c);
@@ -1633,11 +1645,11 @@ extern "C" lskum_status lskum_autotune(lskum_ctx *c, int reps, lskum_tuning *out
     int vq = 0, vf = 0;
     // q-derivative variants: one inner pass, reading the first-order gradient in gA
     lskum_status r = LSKUM_OK;
-    if (LAUNCH_OK(c, launch_qgrad_mixed(g, q, nullptr, gA, 0.0, c->stream, 0), r)) {
+    if (LAUNCH_OK(c, launch_qgrad_mixed(g, q, nullptr, nullptr, gA, nullptr, 0.0, c->stream, 0), r)) {
         for (int v = 0; v < mixed_variants(1) && r == LSKUM_OK; ++v) {
             double ms = 0.0;
             r = time_variant(c, reps, e0, e1,
-                             [&] { return launch_qgrad_mixed(g, q, gA, gB, 0.0, c->stream, v); }, &ms);
+                             [&] { return launch_qgrad_mixed(g, q, gA, gA, gB, nullptr, 0.0, c->stream, v); }, &ms);
             if (v == 0) def_q = ms;
             if (r == LSKUM_OK && ms < best_q) { best_q = ms; vq = v; }
         }

@@ -102,11 +102,6 @@ cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, fl
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ float venkat_f(float D, float d, float eps2)
-{
-    return (D * D + eps2 + 2.0f * D * d) / (D * D + 2.0f * d * d + D * d + eps2);
-}
-
 // --------------------------------------------------------------------------
 // Edge layout of the mixed kernels: sliced ELL with slices of 32 points
 // (SELL-32). One thread per point; a warp handles the 32 points of one slice,
@@ -186,105 +181,139 @@ __device__ __forceinline__ void image_q_f(const MixedGeom &g, int e, uint8_t m, 
 }
 
 // --------------------------------------------------------------------------
-// q_derivatives() in FP32 (E15; same arithmetic as k_qgrad)
+// q_derivatives() in FP32 (E15; the same passes as k_qgrad of the FP64 form)
 // --------------------------------------------------------------------------
 // KIN: the kinetic boundary mode (a separate instantiation keeps the plain
 // kernels' registers as they are)
-// PASS: bit 1 an inner iteration (qg_old is read), bit 0 the limiter's pass;
-// one instantiation per kind of pass keeps each one's registers to what it
-// uses (the limiter's extrema and the previous iterate only where needed)
+// PASS: bit 1 an inner iteration, G1 - sum_e a_e (d_e/2 . grad q_i) +
+// grad q_0 / 2 with G1 = g1 the first pass's result (so no q_i is gathered);
+// bit 0 the limiter at its end, phi = f(x_m, d_m) when x_m < 2 d_m, else 1
+// (x_m = min(D+, -D-), d_m the largest |d_e/2 . grad q|: see k_qgrad); bit 2
+// a first pass that stores x_m for a limited inner pass. One instantiation
+// per kind of pass keeps each one's registers to what it uses.
 template <int THREADS, int MINB, bool KIN, int PASS>
 __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, const float *__restrict__ q,
                                                                const float *__restrict__ qg_old,
-                                                               float *__restrict__ qg_new, float limK)
+                                                               const float *__restrict__ g1,
+                                                               float *__restrict__ qg_new, float *__restrict__ ext,
+                                                               float limK)
 {
+    constexpr bool INNER = (PASS & 2) != 0, LIMIT = (PASS & 1) != 0;
+    constexpr bool EXTR = !INNER && (PASS & 5) != 0;   // extrema found in this pass
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.n) return;
     const int deg = g.off[p + 1] - g.off[p];
     const int64_t base = g.slice_off[p >> 5] + (p & 31);
-    float q0[4], g0[8], sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
-    load4f(q, p, q0);
-    constexpr bool inner = (PASS & 2) != 0;
-    constexpr bool limit = (PASS & 1) != 0;
+    float sx[4], sy[4];
+    // largest and smallest q_i - q_0 (P_0's own difference: 0)
+    float dhi[4] = {0.0f, 0.0f, 0.0f, 0.0f}, dlo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     // the slot's offset d = M a (a = M^-1 d): recovered from the weights, so
     // a slot carries 8 bytes of geometry instead of 16
     float4 M = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (inner || limit) M = g.gm[p];
-    float qmax[4] = {q0[0], q0[1], q0[2], q0[3]}, qmin[4] = {q0[0], q0[1], q0[2], q0[3]};
-#pragma unroll 2
-    for (int s = 0; s < deg; ++s) {
-        const int64_t e = base + 32 * s;
-        const int i = g.sidx[e] & kSlotIndexMask;
-        const float2 a = g.ga[e];
-        float qi[4];
-        load4f(q, i, qi);
-        float dq[4];
+    if (INNER || LIMIT) M = g.gm[p];
+    if constexpr (!INNER) {
+        float q0[4];
+        load4f(q, p, q0);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) dq[k] = qi[k] - q0[k];
-        if (limit) {
+        for (int k = 0; k < 4; ++k) sx[k] = sy[k] = 0.0f;
+        auto add = [&](const float qi[4], float2 a) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                qmax[k] = fmaxf(qmax[k], qi[k]);
-                qmin[k] = fminf(qmin[k], qi[k]);
+                const float dq = qi[k] - q0[k];
+                if constexpr (EXTR) {
+                    dhi[k] = fmaxf(dhi[k], dq);
+                    dlo[k] = fminf(dlo[k], dq);
+                }
+                sx[k] += a.x * dq;
+                sy[k] += a.y * dq;
+            }
+        };
+#pragma unroll 2
+        for (int s = 0; s < deg; ++s) {
+            const int64_t e = base + 32 * s;
+            float qi[4];
+            load4f(q, g.sidx[e] & kSlotIndexMask, qi);
+            add(qi, g.ga[e]);
+        }
+        if constexpr (KIN) {
+            // kinetic boundary mode: the mirror images of the neighbours
+            const int f0 = g.ioff[p], f1 = g.ioff[p + 1];
+            if (f0 < f1) {
+                const float2 n0 = g.nrm[p];
+                const float *qf = g.qinf + 4 * (g.pcase ? (int)g.pcase[p] : 0);
+                for (int e = f0; e < f1; ++e) {
+                    float qi[4];
+                    image_q_f(g, e, g.imask[e], n0, qf, q, nullptr, make_float2(0.0f, 0.0f), false, qi);
+                    add(qi, g.ilsw[e]);
+                }
             }
         }
-        if (inner) {
-            float gi[8];
-            gather8f(qg_old, i, gi);
-            const float2 d = make_float2(M.x * a.x + M.y * a.y, M.y * a.x + M.z * a.y);
-            // the previous iterate at P_0 is taken out of the sum (below)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) dq[k] = dq[k] - 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
-        }
+    } else {
+        float t[8];
+        load8f(g1, p, t);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            sx[k] += a.x * dq[k];
-            sy[k] += a.y * dq[k];
+            sx[k] = t[k];
+            sy[k] = t[4 + k];
         }
-    }
-    if constexpr (KIN) {
-        // kinetic boundary mode: the mirror images of the neighbours
-        const int f0 = g.ioff[p], f1 = g.ioff[p + 1];
-        if (f0 < f1) {
-            const float2 n0 = g.nrm[p];
-            const float *qf = g.qinf + 4 * (g.pcase ? (int)g.pcase[p] : 0);
-            for (int e = f0; e < f1; ++e) {
-                const uint8_t m = g.imask[e];
-                const float2 a = g.ilsw[e];
-                const float4 r = g.igf[e];
-                const float2 d = make_float2(r.x, r.y);
-                float qi[4], dq[4];
-                image_q_f(g, e, m, n0, qf, q, qg_old, d, inner, qi);
+#pragma unroll 2
+        for (int s = 0; s < deg; ++s) {
+            const int64_t e = base + 32 * s;
+            const int i = g.sidx[e] & kSlotIndexMask;
+            const float2 a = g.ga[e];
+            const float2 d = make_float2(M.x * a.x + M.y * a.y, M.y * a.x + M.z * a.y);
+            float gi[8];
+            gather8f(qg_old, i, gi);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) dq[k] = qi[k] - q0[k];
-                if (limit) {
-                    if (inner) image_q_f(g, e, m, n0, qf, q, qg_old, d, false, qi);
+            for (int k = 0; k < 4; ++k) {
+                const float c = 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
+                sx[k] -= a.x * c;
+                sy[k] -= a.y * c;
+            }
+        }
+        if constexpr (KIN) {
+            // a wall image's q~ is the reflection of q_i - d'.grad q_i / 2, d'
+            // the reflection of the image's offset, so its correction is the
+            // reflection of d'.grad q_i / 2; far-field images carry no gradient
+            const int f0 = g.ioff[p], f1 = g.ioff[p + 1];
+            if (f0 < f1) {
+                const float2 n0 = g.nrm[p];
+                for (int e = f0; e < f1; ++e) {
+                    if (g.imask[e] & M_IMG_FAR) continue;
+                    const float2 a = g.ilsw[e];
+                    const float4 r = g.igf[e];
+                    float2 d = make_float2(r.x, r.y);
+                    reflect2(d.x, d.y, n0.x, n0.y);
+                    float gi[8], c[4];
+                    gather8f(qg_old, g.iidx[e], gi);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) c[k] = 0.5f * (d.x * gi[k] + d.y * gi[4 + k]);
+                    reflect2(c[1], c[2], n0.x, n0.y);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        qmax[k] = fmaxf(qmax[k], qi[k]);
-                        qmin[k] = fminf(qmin[k], qi[k]);
+                        sx[k] -= a.x * c[k];
+                        sy[k] -= a.y * c[k];
                     }
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    sx[k] += a.x * dq[k];
-                    sy[k] += a.y * dq[k];
                 }
             }
         }
-    }
-    if (inner) {
         // sum_e a_e (d_e . g_0) = g_0 (the weights satisfy sum_e a_e d_e^T = I,
         // to FP32 rounding), so the +1/2 d_e . g_0 of every corrected
         // difference (E14) adds up to g_0 / 2
-        load8f(qg_old, p, g0);
+        load8f(qg_old, p, t);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            sx[k] += 0.5f * g0[k];
-            sy[k] += 0.5f * g0[4 + k];
+            sx[k] += 0.5f * t[k];
+            sy[k] += 0.5f * t[4 + k];
         }
     }
-    if (limit) {
+    float xm[4];
+    if constexpr (EXTR) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) xm[k] = fminf(dhi[k], -dlo[k]);
+    }
+    if constexpr (LIMIT) {
+        if constexpr (INNER) load4f(ext, p, xm);
         float dmax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int s = 0; s < deg; ++s) {
             const float2 a = g.ga[base + 32 * s];
@@ -303,14 +332,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
         const float eps2 = h * h * h;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float phi = 1.0f;
-            if (dmax[k] > 0.0f) {
-                phi = fminf(phi, venkat_f(qmax[k] - q0[k], dmax[k], eps2));
-                phi = fminf(phi, venkat_f(qmin[k] - q0[k], -dmax[k], eps2));
-            }
+            // f(x, d) = (x (x + 2d) + eps^2) / (x (x + d) + 2d^2 + eps^2)
+            const float x = xm[k], d = dmax[k], d2 = 2.0f * d;
+            const float num = fmaf(x, x + d2, eps2);
+            const float den = fmaf(x, x + d, fmaf(d2, d, eps2));
+            const float phi = x < d2 ? num / den : 1.0f;
             sx[k] *= phi;
             sy[k] *= phi;
         }
+    } else if constexpr (EXTR) {
+        store4f(ext, p, xm);
     }
     const float out[8] = {sx[0], sx[1], sx[2], sx[3], sy[0], sy[1], sy[2], sy[3]};
     store8f(qg_new, p, out);
@@ -618,16 +649,18 @@ __global__ void __launch_bounds__(256) k_grad_out_f(int64_t n, const int32_t *__
 // launch-shape variants of the two hot kernels, chosen by the autotuner:
 // (threads per block, minimum resident blocks per SM for the register cap)
 template <int T, int M, bool KIN>
-static cudaError_t qgrad_v(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new, float limK,
-                           cudaStream_t s)
+static cudaError_t qgrad_v(const MixedGeom &g, const float *q, const float *qg_old, const float *g1, float *qg_new,
+                           float *ext, float limK, cudaStream_t s)
 {
     const unsigned nb = (unsigned)((g.n + T - 1) / T);
-    const int pass = (qg_old ? 2 : 0) | (limK > 0.0f ? 1 : 0);
+    const bool inner = qg_old != nullptr, limit = limK > 0.0f;
+    const int pass = inner ? (2 | (limit ? 1 : 0)) : limit ? 1 : ext ? 4 : 0;
     switch (pass) {
-    case 0: k_qgrad_mixed<T, M, KIN, 0><<<nb, T, 0, s>>>(g, q, qg_old, qg_new, limK); break;
-    case 1: k_qgrad_mixed<T, M, KIN, 1><<<nb, T, 0, s>>>(g, q, qg_old, qg_new, limK); break;
-    case 2: k_qgrad_mixed<T, M, KIN, 2><<<nb, T, 0, s>>>(g, q, qg_old, qg_new, limK); break;
-    default: k_qgrad_mixed<T, M, KIN, 3><<<nb, T, 0, s>>>(g, q, qg_old, qg_new, limK); break;
+    case 0: k_qgrad_mixed<T, M, KIN, 0><<<nb, T, 0, s>>>(g, q, qg_old, g1, qg_new, ext, limK); break;
+    case 1: k_qgrad_mixed<T, M, KIN, 1><<<nb, T, 0, s>>>(g, q, qg_old, g1, qg_new, ext, limK); break;
+    case 2: k_qgrad_mixed<T, M, KIN, 2><<<nb, T, 0, s>>>(g, q, qg_old, g1, qg_new, ext, limK); break;
+    case 4: k_qgrad_mixed<T, M, KIN, 4><<<nb, T, 0, s>>>(g, q, qg_old, g1, qg_new, ext, limK); break;
+    default: k_qgrad_mixed<T, M, KIN, 3><<<nb, T, 0, s>>>(g, q, qg_old, g1, qg_new, ext, limK); break;
     }
     return cudaGetLastError();
 }
@@ -639,7 +672,8 @@ static cudaError_t flux_v(const MixedFluxParams &P, cudaStream_t s)
     return cudaGetLastError();
 }
 
-using QgradFn = cudaError_t (*)(const MixedGeom &, const float *, const float *, float *, float, cudaStream_t);
+using QgradFn = cudaError_t (*)(const MixedGeom &, const float *, const float *, const float *, float *, float *,
+                                float, cudaStream_t);
 using FluxFn = cudaError_t (*)(const MixedFluxParams &, cudaStream_t);
 
 // [plain, kinetic boundary mode][variant]
@@ -677,11 +711,12 @@ void mixed_variant_shape(int kernel_class, int v, int *threads, int *min_blocks)
     *min_blocks = t[v][1];
 }
 
-cudaError_t launch_qgrad_mixed(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new,
-                               double limiter_K, cudaStream_t s, int variant)
+cudaError_t launch_qgrad_mixed(const MixedGeom &g, const float *q, const float *qg_old, const float *g1,
+                               float *qg_new, float *ext, double limiter_K, cudaStream_t s, int variant)
 {
     if (variant < 0 || variant >= kNumQgradVariants) return cudaErrorInvalidValue;
-    return kQgradVariants[g.ioff ? 1 : 0][variant](g, q, qg_old, qg_new, (float)limiter_K, s);
+    if (qg_old && (!g1 || (limiter_K > 0.0 && !ext))) return cudaErrorInvalidValue;
+    return kQgradVariants[g.ioff ? 1 : 0][variant](g, q, qg_old, g1, qg_new, ext, (float)limiter_K, s);
 }
 
 cudaError_t launch_flux_mixed(const MixedFluxParams &P, cudaStream_t s, int variant)

@@ -72,8 +72,11 @@ cudaError_t launch_sell_fill(int64_t n, const int32_t *off, const int32_t *slice
 // kernel_class 0 = flux, 1 = q-derivatives; variant 0 is the default
 int mixed_variants(int kernel_class);
 void mixed_variant_shape(int kernel_class, int variant, int *threads, int *min_blocks);
-cudaError_t launch_qgrad_mixed(const MixedGeom &g, const float *q, const float *qg_old, float *qg_new,
-                               double limiter_K, cudaStream_t s, int variant);
+// One q-derivative pass in FP32, with the same pass rules as launch_qgrad:
+// an inner pass (qg_old != nullptr) needs g1, the first pass's result for the
+// same q, and, when limited, the ext a first pass stored.
+cudaError_t launch_qgrad_mixed(const MixedGeom &g, const float *q, const float *qg_old, const float *g1,
+                               float *qg_new, float *ext, double limiter_K, cudaStream_t s, int variant);
 cudaError_t launch_flux_mixed(const MixedFluxParams &P, cudaStream_t s, int variant);
 cudaError_t launch_q_from_U_mixed(int64_t n, const Gas &gas, const double *U, float *q, int *status,
                                   cudaStream_t s);
