@@ -147,7 +147,13 @@ def algorithmic_bytes_per_point(kernel, dbar, order, scheme, stage_avg=True):
     if kernel == "qgrad_first":
         return 32 + 4 + dbar * (4 + 16) + 64
     if kernel == "qgrad_inner":
-        return 32 + 64 + 16 + 4 + dbar * (4 + 16 + 16) + 64
+        # first-order result G1 64, previous iterate 64, offset 4, per edge
+        # index 4 + weights 16 + half offset 16, new iterate 64 (no q)
+        return 64 + 64 + 4 + dbar * (4 + 16 + 16) + 64
+    if kernel == "qgrad_limit_extra":
+        # per stage with the limiter after inner passes: the extremum
+        # measure written by the first pass and read by the last, dmin
+        return 32 + 32 + 8
     raise ValueError(kernel)
 
 
@@ -159,10 +165,12 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
     averaged over the 4 stages: dt written (FP64) and dmin read (FP32) at
     stage 0, dt read at stages 1-3, the FP32 accumulator written at 0-2 and
     read at 1-3. q-derivative pass: own q 16, CSR offset 4, per slot the
-    index word 4 + (a_x, a_y) 8, the new derivatives 32; an inner pass also
-    reads its own previous derivatives 32 and the normal matrix (Sxx, Sxy,
-    Syy) 16 from which the slot offsets are recovered. Neighbour gathers are
-    served from cache."""
+    index word 4 + (a_x, a_y) 8, the new derivatives 32; an inner pass reads
+    the first pass's result 32 instead of q, its own previous derivatives 32
+    and the normal matrix (Sxx, Sxy, Syy) 16 from which the slot offsets are
+    recovered; with the limiter after inner passes, the first pass writes the
+    extremum measure 16 and the last reads it with dmin 4. Neighbour gathers
+    are served from cache."""
     if kernel == "flux":
         b = 16 + 8 + 1 + 4 + 32 + 32 + 16 + dbar * 20
         if order == 2:
@@ -175,7 +183,9 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
     if kernel == "qgrad_first":
         return 16 + 4 + dbar * 12 + 32
     if kernel == "qgrad_inner":
-        return 16 + 32 + 16 + 4 + dbar * 12 + 32
+        return 32 + 32 + 16 + 4 + dbar * 12 + 32
+    if kernel == "qgrad_limit_extra":
+        return 16 + 16 + 4
     raise ValueError(kernel)
 
 
@@ -187,7 +197,7 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
 # profiles/launch_list_naca0012_2p5m_fp64.md).
 FP64_INSTR_PER_EDGE_FLUX = 186.33
 FP64_FLOPS_PER_EDGE_FLUX = 293.04
-FLUX_DRAM_BYTES_PER_POINT = 598.6
+FLUX_DRAM_BYTES_PER_POINT = 598.2
 # FP64 peak: ncu's DFMA unit count, 304 FP64 thread-instructions per cycle
 # (each DFMA 2 flops), at the 2070 MHz maximum SM clock
 FP64_PEAK_GINSTR = 304 * 2.070
@@ -410,7 +420,7 @@ def measure_e2e(solver, n, steps, dist):
 # DRAM bytes per point of one launch of the mixed kernels on the 2.5M-point
 # workload, from a full-size single-pass ncu capture of the current kernels
 # (profiles/mixed_kernels_naca0012_2p5m.md); None where not captured
-MIXED_TRAFFIC_PER_POINT = {"flux": 351.0, "qgrad": 181.0}
+MIXED_TRAFFIC_PER_POINT = {"flux": 351.0, "qgrad": 192.7}
 # warp instructions per stencil edge of the mixed flux kernel at its autotuned
 # shape (ncu smsp__inst_executed.sum, 640k-point capture,
 # profiles/k_flux_update_mixed_naca0012_640k.md): the kernel is bound by
@@ -444,6 +454,8 @@ def form_summary(args, r, n, dbar, world, precision, peaks, peak_src):
             per_stage = args.inner + 1
             qb = (algorithmic_bytes_per_point_mixed("qgrad_first", dbar, args.order, args.scheme)
                   + args.inner * algorithmic_bytes_per_point_mixed("qgrad_inner", dbar, args.order, args.scheme)
+                  + (algorithmic_bytes_per_point_mixed("qgrad_limit_extra", dbar, args.order, args.scheme)
+                     if args.limiter > 0 and args.inner > 0 else 0.0)
                   ) / per_stage * n
             qg_avg_s = (r["qg_ms"] / r["qg_n"]) / 1e3
             qgbs = qb / qg_avg_s / 1e9
