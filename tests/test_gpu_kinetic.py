@@ -86,7 +86,7 @@ def test_mixed_residual_matches_oracle(small, order, limiter):
     assert np.all(np.abs(R - Ro) <= 3e-5 * S), np.max(np.abs(R - Ro) / S)
 
 
-@pytest.mark.parametrize("inner,limiter", [(0, 0.0), (3, 0.0), (3, 1.0)])
+@pytest.mark.parametrize("inner,limiter", [(0, 0.0), (3, 0.0), (0, 1.0), (1, 1.0), (3, 1.0)])
 def test_q_derivatives_match_oracle(small, inner, limiter):
     c, m = small
     U = _state(c, 0.63, 2.0, seed=4)

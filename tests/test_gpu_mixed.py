@@ -68,13 +68,17 @@ def test_mixed_residual_matches_oracle(small, order, limiter, reorder):
     assert err.max() > 1e-12
 
 
-def test_mixed_q_derivatives_match_oracle(small):
+@pytest.mark.parametrize("inner", [0, 1, 2, 3])
+@pytest.mark.parametrize("limiter", [0.0, 1.0])
+def test_mixed_q_derivatives_match_oracle(small, inner, limiter):
     U = _perturbed_state(small, 0.63, 2.0, seed=1)
-    s = _solver(small, order=2, inner_iters=3)
+    s = _solver(small, order=2, inner_iters=inner, limiter_K=limiter)
     qx, qy = s.q_derivatives(_dev(U))
     qx, qy = qx.cpu().numpy(), qy.cpu().numpy()
     q = oracle.q_variables(U)
-    ox, oy = oracle.q_derivatives(small, q, inner=3)
+    ox, oy = oracle.q_derivatives(small, q, inner=inner)
+    if limiter:
+        ox, oy = oracle.limit_gradients(small, q, ox, oy, limiter)
     off, idx = small["nbr_offsets"], small["nbr_idx"]
     rows = np.repeat(np.arange(small["n"]), np.diff(off))
     d = np.hypot(small["x"][idx] - small["x"][rows], small["y"][idx] - small["y"][rows])

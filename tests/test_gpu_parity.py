@@ -100,7 +100,11 @@ def _grad_scale(cloud, q, gx, gy):
     return S
 
 
-@pytest.mark.parametrize("inner,limiter", [(0, 0.0), (3, 0.0), (0, 1.0), (3, 1.0)])
+# inner 0 with the limiter: the first pass limits; 1: the one inner pass
+# reads the first-order solve as its previous iterate too; 2 and 3: the
+# iterates end in either buffer
+@pytest.mark.parametrize("inner,limiter", [(0, 0.0), (1, 0.0), (2, 0.0), (3, 0.0),
+                                           (0, 1.0), (1, 1.0), (2, 1.0), (3, 1.0)])
 def test_q_derivatives_match_oracle(small, inner, limiter):
     U = _perturbed_state(small, 0.63, 2.0, seed=1)
     s = _solver(small, order=2, inner_iters=inner, limiter_K=limiter)
