@@ -19,6 +19,7 @@
 //             points by one more gather;
 //   state     q_bar to U_bar through the E13 Jacobian.
 #include <cub/cub.cuh>
+#include <type_traits>
 
 #include "lskum_adjoint.h"
 
@@ -140,9 +141,18 @@ __device__ __forceinline__ D4T<T> dsqrt(const D4T<T> &a)
     return chain(a, s, T(0.5) / s);
 }
 
+// The FP64 product takes the split fluxes in the forward kernels' regrouped
+// form (fewer dual products); the FP32 product keeps the paper's form, whose
+// rounding its coordinate-cotangent tolerance was set on.
 template <class T>
 struct PrimDT {
-    D4T<T> rho, u, v, p, sqb, rsb;
+    D4T<T> u, v, sqb;
+    D4T<T> hrho;  // rho/2 (FP64)
+    D4T<T> hib;   // 1/(2 beta) = p/rho (FP64)
+    D4T<T> rrc;   // rho/(2 sqrt(pi beta)), so that rho B = rrc exp(-S^2) (FP64)
+    D4T<T> h;     // (rho E + p)/rho (FP64)
+    D4T<T> qb;    // 1/(4 beta) = h - (rho E + p/2)/rho (FP64)
+    D4T<T> rho, p, rsb;  // (FP32)
 };
 
 // inverse of E13 over duals: beta = -q4/2, u = -q2/q4, v = -q3/q4,
@@ -150,30 +160,46 @@ struct PrimDT {
 // rsb = 1/sqrt(beta) and ib = 1/beta as the forward kernels form them:
 // 1/q4 = -ib/2 (derivative -ib^2/4), sqrt(beta) = beta rsb (rsb/2),
 // 1/sqrt(beta) (-rsb ib/2), and for gamma = 1.4 beta^-2.5 = rsb ib^2
-// (-2.5 rsb ib^3) in place of exp(-2.5 ln beta)
+// (-2.5 rsb ib^3) in place of exp(-2.5 ln beta). Then the per-state factors
+// of the regrouped split fluxes (see split_flux_d).
 template <class T>
 __device__ __forceinline__ PrimDT<T> prim_d(const D4T<T> qt[4], T inv_gm1, bool g14)
 {
     PrimDT<T> s;
     const D4T<T> beta = T(-0.5) * qt[3];
     const T rsb = m_rsqrt(beta.v), ib = rsb * rsb;
-    const D4T<T> r = chain(qt[3], T(-0.5) * ib, T(-0.25) * ib * ib);
+    const D4T<T> r = chain(qt[3], T(-0.5) * ib, T(-0.25) * ib * ib);   // 1/q4 = -1/(2 beta)
     s.u = T(-1) * (qt[1] * r);
     s.v = T(-1) * (qt[2] * r);
     s.sqb = chain(beta, beta.v * rsb, T(0.5) * rsb);
-    s.rsb = chain(beta, rsb, T(-0.5) * rsb * ib);
-    const D4T<T> ke = beta * (s.u * s.u + s.v * s.v);
+    const D4T<T> rsbd = chain(beta, rsb, T(-0.5) * rsb * ib);
+    const D4T<T> w2 = s.u * s.u + s.v * s.v;
+    D4T<T> rho;
     if (g14) {
         const T b25 = rsb * ib * ib;
-        s.rho = dexp(qt[0] + ke) * chain(beta, b25, T(-2.5) * b25 * ib);
+        rho = dexp(qt[0] + beta * w2) * chain(beta, b25, T(-2.5) * b25 * ib);
     } else {
-        s.rho = dexp(qt[0] - inv_gm1 * dlog(beta) + ke);
+        rho = dexp(qt[0] - inv_gm1 * dlog(beta) + beta * w2);
     }
-    s.p = T(-1) * (s.rho * r);
+    if constexpr (std::is_same<T, double>::value) {
+        s.hrho = T(0.5) * rho;
+        s.hib = T(-1) * r;
+        s.rrc = T(0.5641895835477563) * (s.hrho * rsbd);                // 1/sqrt(pi)
+        // h = gamma/(gamma-1) p/rho + |u|^2/2, p/rho = 1/(2 beta)
+        s.h = (inv_gm1 + T(1)) * s.hib + T(0.5) * w2;
+        s.qb = T(0.5) * s.hib;
+    } else {
+        s.rho = rho;
+        s.p = T(-1) * (rho * r);
+        s.rsb = rsbd;
+    }
     return s;
 }
 
-// split flux along a direction over duals, in the paper's form
+// split flux along a direction over duals. FP64: regrouped as in the
+// forward kernels, S = un sqrt(beta), Q = rho A = rho/2 (1 + sgn erf S),
+// W = sgn rho B = sgn rrc exp(-S^2); G0 = un Q + W, G1 = un G0 + p A with
+// p A = Q/(2 beta), G2 = ut G0, G3 = h G0 - W/(4 beta). FP32: the paper's form.
 template <class T>
 __device__ __forceinline__ void split_flux_d(T sgn, const PrimDT<T> &s, const D4T<T> &un, const D4T<T> &ut,
                                              T inv_gm1, D4T<T> G[4])
@@ -181,16 +207,26 @@ __device__ __forceinline__ void split_flux_d(T sgn, const PrimDT<T> &s, const D4
     const D4T<T> S = un * s.sqb;
     T erfv, e;
     m_erf_gauss(S.v, erfv, e);
-    const D4T<T> erfS = chain(S, erfv, T(1.1283791670955126) * e);         // 2/sqrt(pi)
-    const D4T<T> eS = chain(S, e, T(-2) * S.v * e);
-    const D4T<T> A = T(0.5) * (T(1) + sgn * erfS);
-    const D4T<T> B = T(0.28209479177387814) * (eS * s.rsb);                 // 1/(2 sqrt(pi))
-    const D4T<T> rhoE = inv_gm1 * s.p + T(0.5) * (s.rho * (un * un + ut * ut));
-    const D4T<T> m = un * A + sgn * B;
-    G[0] = s.rho * m;
-    G[1] = (s.p + s.rho * un * un) * A + sgn * (s.rho * un * B);
-    G[2] = s.rho * ut * m;
-    G[3] = (rhoE + s.p) * un * A + sgn * ((rhoE + T(0.5) * s.p) * B);
+    if constexpr (std::is_same<T, double>::value) {
+        const D4T<T> fe = chain(S, sgn * erfv, sgn * T(1.1283791670955126) * e);   // sgn erf S; 2/sqrt(pi)
+        const D4T<T> W = chain(S, sgn * e, sgn * T(-2) * S.v * e) * s.rrc;
+        const D4T<T> Q = s.hrho + s.hrho * fe;
+        G[0] = un * Q + W;
+        G[1] = un * G[0] + Q * s.hib;
+        G[2] = ut * G[0];
+        G[3] = s.h * G[0] - s.qb * W;
+    } else {
+        const D4T<T> erfS = chain(S, erfv, T(1.1283791670955126) * e);     // 2/sqrt(pi)
+        const D4T<T> eS = chain(S, e, T(-2) * S.v * e);
+        const D4T<T> A = T(0.5) * (T(1) + sgn * erfS);
+        const D4T<T> B = T(0.28209479177387814) * (eS * s.rsb);             // 1/(2 sqrt(pi))
+        const D4T<T> rhoE = inv_gm1 * s.p + T(0.5) * (s.rho * (un * un + ut * ut));
+        const D4T<T> m = un * A + sgn * B;
+        G[0] = s.rho * m;
+        G[1] = (s.p + s.rho * un * un) * A + sgn * (s.rho * un * B);
+        G[2] = s.rho * ut * m;
+        G[3] = (rhoE + s.p) * un * A + sgn * ((rhoE + T(0.5) * s.p) * B);
+    }
 }
 
 __device__ __forceinline__ void ld4(const double *a, int64_t p, double v[4])
@@ -246,6 +282,7 @@ __device__ __forceinline__ bool sub_needed(uint8_t f, int k)
 // cotangent of one reconstructed state: sum over the split fluxes it feeds,
 // cs (frame order) against Gs and cn (frame order) against Gn, plus the
 // flux values for the weight cotangents
+
 template <class T>
 __device__ __forceinline__ void state_adjoint(const T qt[4], T tx, T ty, T nx, T ny, bool use_s, T sg_s, bool use_n,
                                               T sg_n, const T cs[4], const T cn[4], T inv_gm1, bool g14, T qbar[4],
