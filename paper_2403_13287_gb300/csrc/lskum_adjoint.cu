@@ -3,8 +3,10 @@
 // FP64, for the unlimited scheme of order 1 or 2.
 //
 // Reverse pass, every sum a gather (no atomics, bitwise reproducible):
-//   flux      per point (owner of its edges): the split-flux Jacobians at
-//             both reconstructed states (forward-mode duals, 4 tangents),
+//   flux      per point (owner of its edges): the transposed split-flux
+//             Jacobians at both reconstructed states applied to the
+//             cotangents (FP64: reverse mode through the regrouped split
+//             fluxes; FP32: forward-mode duals, 4 tangents), giving
 //             cotangents of the owner's q~_0, of each neighbour's q~_i (kept
 //             per edge) and of the sub-stencil weights;
 //   gather    per point over its incoming edges (transpose CSR): the
@@ -141,18 +143,12 @@ __device__ __forceinline__ D4T<T> dsqrt(const D4T<T> &a)
     return chain(a, s, T(0.5) / s);
 }
 
-// The FP64 product takes the split fluxes in the forward kernels' regrouped
-// form (fewer dual products); the FP32 product keeps the paper's form, whose
-// rounding its coordinate-cotangent tolerance was set on.
+// The dual-number forms below serve the FP32 product; the FP64 product runs
+// state_adjoint_rev (reverse mode through the forward kernels' regrouped
+// split fluxes).
 template <class T>
 struct PrimDT {
-    D4T<T> u, v, sqb;
-    D4T<T> hrho;  // rho/2 (FP64)
-    D4T<T> hib;   // 1/(2 beta) = p/rho (FP64)
-    D4T<T> rrc;   // rho/(2 sqrt(pi beta)), so that rho B = rrc exp(-S^2) (FP64)
-    D4T<T> h;     // (rho E + p)/rho (FP64)
-    D4T<T> qb;    // 1/(4 beta) = h - (rho E + p/2)/rho (FP64)
-    D4T<T> rho, p, rsb;  // (FP32)
+    D4T<T> rho, u, v, p, sqb, rsb;
 };
 
 // inverse of E13 over duals: beta = -q4/2, u = -q2/q4, v = -q3/q4,
@@ -160,46 +156,30 @@ struct PrimDT {
 // rsb = 1/sqrt(beta) and ib = 1/beta as the forward kernels form them:
 // 1/q4 = -ib/2 (derivative -ib^2/4), sqrt(beta) = beta rsb (rsb/2),
 // 1/sqrt(beta) (-rsb ib/2), and for gamma = 1.4 beta^-2.5 = rsb ib^2
-// (-2.5 rsb ib^3) in place of exp(-2.5 ln beta). Then the per-state factors
-// of the regrouped split fluxes (see split_flux_d).
+// (-2.5 rsb ib^3) in place of exp(-2.5 ln beta)
 template <class T>
 __device__ __forceinline__ PrimDT<T> prim_d(const D4T<T> qt[4], T inv_gm1, bool g14)
 {
     PrimDT<T> s;
     const D4T<T> beta = T(-0.5) * qt[3];
     const T rsb = m_rsqrt(beta.v), ib = rsb * rsb;
-    const D4T<T> r = chain(qt[3], T(-0.5) * ib, T(-0.25) * ib * ib);   // 1/q4 = -1/(2 beta)
+    const D4T<T> r = chain(qt[3], T(-0.5) * ib, T(-0.25) * ib * ib);
     s.u = T(-1) * (qt[1] * r);
     s.v = T(-1) * (qt[2] * r);
     s.sqb = chain(beta, beta.v * rsb, T(0.5) * rsb);
-    const D4T<T> rsbd = chain(beta, rsb, T(-0.5) * rsb * ib);
-    const D4T<T> w2 = s.u * s.u + s.v * s.v;
-    D4T<T> rho;
+    s.rsb = chain(beta, rsb, T(-0.5) * rsb * ib);
+    const D4T<T> ke = beta * (s.u * s.u + s.v * s.v);
     if (g14) {
         const T b25 = rsb * ib * ib;
-        rho = dexp(qt[0] + beta * w2) * chain(beta, b25, T(-2.5) * b25 * ib);
+        s.rho = dexp(qt[0] + ke) * chain(beta, b25, T(-2.5) * b25 * ib);
     } else {
-        rho = dexp(qt[0] - inv_gm1 * dlog(beta) + beta * w2);
+        s.rho = dexp(qt[0] - inv_gm1 * dlog(beta) + ke);
     }
-    if constexpr (std::is_same<T, double>::value) {
-        s.hrho = T(0.5) * rho;
-        s.hib = T(-1) * r;
-        s.rrc = T(0.5641895835477563) * (s.hrho * rsbd);                // 1/sqrt(pi)
-        // h = gamma/(gamma-1) p/rho + |u|^2/2, p/rho = 1/(2 beta)
-        s.h = (inv_gm1 + T(1)) * s.hib + T(0.5) * w2;
-        s.qb = T(0.5) * s.hib;
-    } else {
-        s.rho = rho;
-        s.p = T(-1) * (rho * r);
-        s.rsb = rsbd;
-    }
+    s.p = T(-1) * (s.rho * r);
     return s;
 }
 
-// split flux along a direction over duals. FP64: regrouped as in the
-// forward kernels, S = un sqrt(beta), Q = rho A = rho/2 (1 + sgn erf S),
-// W = sgn rho B = sgn rrc exp(-S^2); G0 = un Q + W, G1 = un G0 + p A with
-// p A = Q/(2 beta), G2 = ut G0, G3 = h G0 - W/(4 beta). FP32: the paper's form.
+// split flux along a direction over duals, in the paper's form
 template <class T>
 __device__ __forceinline__ void split_flux_d(T sgn, const PrimDT<T> &s, const D4T<T> &un, const D4T<T> &ut,
                                              T inv_gm1, D4T<T> G[4])
@@ -207,26 +187,16 @@ __device__ __forceinline__ void split_flux_d(T sgn, const PrimDT<T> &s, const D4
     const D4T<T> S = un * s.sqb;
     T erfv, e;
     m_erf_gauss(S.v, erfv, e);
-    if constexpr (std::is_same<T, double>::value) {
-        const D4T<T> fe = chain(S, sgn * erfv, sgn * T(1.1283791670955126) * e);   // sgn erf S; 2/sqrt(pi)
-        const D4T<T> W = chain(S, sgn * e, sgn * T(-2) * S.v * e) * s.rrc;
-        const D4T<T> Q = s.hrho + s.hrho * fe;
-        G[0] = un * Q + W;
-        G[1] = un * G[0] + Q * s.hib;
-        G[2] = ut * G[0];
-        G[3] = s.h * G[0] - s.qb * W;
-    } else {
-        const D4T<T> erfS = chain(S, erfv, T(1.1283791670955126) * e);     // 2/sqrt(pi)
-        const D4T<T> eS = chain(S, e, T(-2) * S.v * e);
-        const D4T<T> A = T(0.5) * (T(1) + sgn * erfS);
-        const D4T<T> B = T(0.28209479177387814) * (eS * s.rsb);             // 1/(2 sqrt(pi))
-        const D4T<T> rhoE = inv_gm1 * s.p + T(0.5) * (s.rho * (un * un + ut * ut));
-        const D4T<T> m = un * A + sgn * B;
-        G[0] = s.rho * m;
-        G[1] = (s.p + s.rho * un * un) * A + sgn * (s.rho * un * B);
-        G[2] = s.rho * ut * m;
-        G[3] = (rhoE + s.p) * un * A + sgn * ((rhoE + T(0.5) * s.p) * B);
-    }
+    const D4T<T> erfS = chain(S, erfv, T(1.1283791670955126) * e);         // 2/sqrt(pi)
+    const D4T<T> eS = chain(S, e, T(-2) * S.v * e);
+    const D4T<T> A = T(0.5) * (T(1) + sgn * erfS);
+    const D4T<T> B = T(0.28209479177387814) * (eS * s.rsb);                 // 1/(2 sqrt(pi))
+    const D4T<T> rhoE = inv_gm1 * s.p + T(0.5) * (s.rho * (un * un + ut * ut));
+    const D4T<T> m = un * A + sgn * B;
+    G[0] = s.rho * m;
+    G[1] = (s.p + s.rho * un * un) * A + sgn * (s.rho * un * B);
+    G[2] = s.rho * ut * m;
+    G[3] = (rhoE + s.p) * un * A + sgn * ((rhoE + T(0.5) * s.p) * B);
 }
 
 __device__ __forceinline__ void ld4(const double *a, int64_t p, double v[4])
@@ -323,6 +293,100 @@ __device__ __forceinline__ void state_adjoint(const T qt[4], T tx, T ty, T nx, T
     }
 }
 
+// FP64 form of state_adjoint in reverse mode: the split fluxes in the forward
+// kernels' regrouped form once, then their adjoint, so that
+// q_bar = sum over the needed directions of (dG/dq~)^T c without forming the
+// Jacobians. Primal, with (u_d, u_t) = (u.t, u.n) for the s direction and
+// (u.n, u.t) for the n direction:
+//   beta = -q4/2, r = beta^-1/2, hib = r^2/2 (= p/rho), u.t = (q2 tx + q3 ty) hib,
+//   sqb = beta r, w2 = |u|^2, rho/2 = exp(q1 + beta w2)/2 beta^(-1/(gamma-1)),
+//   h = (1/(gamma-1) + 1) hib + w2/2, qb = hib/2, rrc = (rho/2) r/sqrt(pi);
+//   S = u_d sqb, fe = sgn erf S, Q = rho/2 (1 + fe), W = sgn rrc exp(-S^2),
+//   G0 = u_d Q + W, G1 = u_d G0 + Q hib, G2 = u_t G0, G3 = h G0 - qb W.
+__device__ __forceinline__ void state_adjoint_rev(const double qt[4], double tx, double ty, double nx, double ny,
+                                                  bool use_s, double sg_s, bool use_n, double sg_n,
+                                                  const double cs[4], const double cn[4], double inv_gm1, bool g14,
+                                                  double qbar[4], double Gs[4], double Gn[4])
+{
+    const double beta = -0.5 * qt[3];
+    const double rsb = m_rsqrt(beta), ib = rsb * rsb, hib = 0.5 * ib;
+    const double qs = qt[1] * tx + qt[2] * ty, qn = qt[1] * nx + qt[2] * ny;
+    const double us = qs * hib, un = qn * hib;
+    const double sqb = beta * rsb;
+    const double w2 = us * us + un * un;
+    double hrho, fb = 1.0;   // fb = beta^-2.5 for gamma = 1.4
+    if (g14) {
+        fb = rsb * (ib * ib);
+        hrho = exp_tab(qt[0] + beta * w2, -1) * fb;
+    } else {
+        hrho = exp_tab(qt[0] + beta * w2 - inv_gm1 * m_log(beta), -1);
+    }
+    const double h = (inv_gm1 + 1.0) * hib + 0.5 * w2;
+    const double qb = 0.5 * hib;
+    const double rrc = hrho * rsb * 0.5641895835477563;   // 1/sqrt(pi)
+    double b_us = 0.0, b_un = 0.0, b_sqb = 0.0, b_hrho = 0.0, b_hib = 0.0, b_rrc = 0.0, b_h = 0.0, b_qb = 0.0;
+    // one direction: primal G (in the direction's order) and its adjoint for cotangent c
+    auto dir = [&](double ud, double ut, double sg, const double c[4], double G[4], double &b_ud, double &b_ut) {
+        const double S = ud * sqb;
+        double erfv, e;
+        erf_exp(S, erfv, e);
+        const double fe = sg * erfv;
+        const double Q = hrho + hrho * fe;
+        const double W = sg * e * rrc;
+        const double G0 = ud * Q + W;
+        G[0] = G0;
+        G[1] = ud * G0 + Q * hib;
+        G[2] = ut * G0;
+        G[3] = h * G0 - qb * W;
+        const double bG0 = c[0] + c[1] * ud + c[2] * ut + c[3] * h;
+        b_h += c[3] * G0;
+        b_qb -= c[3] * W;
+        b_ut += c[2] * G0;
+        b_hib += c[1] * Q;
+        const double bQ = c[1] * hib + bG0 * ud;
+        const double bW = bG0 - c[3] * qb;
+        b_ud += c[1] * G0 + bG0 * Q;
+        b_rrc += bW * sg * e;
+        b_hrho += bQ * (1.0 + fe);
+        // fe = sgn erf S (erf' = 2/sqrt(pi) e), e = exp(-S^2) (e' = -2 S e)
+        const double bS = (bQ * hrho * sg * 1.1283791670955126 - bW * sg * rrc * 2.0 * S) * e;
+        b_ud += bS * sqb;
+        b_sqb += bS * ud;
+    };
+    if (use_s) dir(us, un, sg_s, cs, Gs, b_us, b_un);
+    if (use_n) {
+        const double c[4] = {cn[0], cn[2], cn[1], cn[3]};   // Gn is [mass, n-momentum, s-momentum, energy]
+        double G[4];
+        dir(un, us, sg_n, c, G, b_un, b_us);
+        Gn[0] = G[0];
+        Gn[1] = G[2];
+        Gn[2] = G[1];
+        Gn[3] = G[3];
+    }
+    // per-state factors, in reverse
+    b_hrho += b_rrc * rsb * 0.5641895835477563;
+    double b_rsb = b_rrc * hrho * 0.5641895835477563;
+    b_hib += 0.5 * b_qb + (inv_gm1 + 1.0) * b_h;
+    double b_w2 = 0.5 * b_h;
+    const double bx = b_hrho * hrho;   // d(rho/2)/dx = rho/2 for the exponent's argument x
+    double b_beta = bx * w2;
+    if (g14) b_beta += bx * (-2.5 * ib);   // beta^-2.5: relative derivative -2.5/beta
+    else b_beta -= bx * inv_gm1 * ib;      // -ln(beta)/(gamma-1)
+    b_w2 += bx * beta;
+    b_us += 2.0 * us * b_w2;
+    b_un += 2.0 * un * b_w2;
+    b_beta += b_sqb * rsb;
+    b_rsb += b_sqb * beta;
+    const double b_qs = b_us * hib, b_qn = b_un * hib;
+    b_hib += b_us * qs + b_un * qn;
+    b_rsb += b_hib * rsb;                  // hib = rsb^2/2
+    b_beta -= 0.5 * b_rsb * rsb * ib;      // rsb = beta^-1/2
+    qbar[0] = bx;
+    qbar[1] = b_qs * tx + b_qn * nx;
+    qbar[2] = b_qs * ty + b_qn * ny;
+    qbar[3] = -0.5 * b_beta;
+}
+
 // ---------------------------------------------------------------------------
 // flux adjoint, owner side
 // ---------------------------------------------------------------------------
@@ -391,8 +455,13 @@ __global__ void __launch_bounds__(128) k_adj_flux(AdjParamsT<T> P)
                               Gn0[4] = {0, 0, 0, 0};
         const T sgs = (m & M_XPOS) ? T(1) : T(-1), sgn = (m & M_YPOS) ? T(1) : T(-1);
         if (us_ || un_) {
-            state_adjoint(qti, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, P.g14 != 0, qbi, Gsi, Gni);
-            state_adjoint(qt0, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, P.g14 != 0, qbo, Gs0, Gn0);
+            if constexpr (std::is_same<T, double>::value) {
+                state_adjoint_rev(qti, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, P.g14 != 0, qbi, Gsi, Gni);
+                state_adjoint_rev(qt0, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, P.g14 != 0, qbo, Gs0, Gn0);
+            } else {
+                state_adjoint(qti, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, P.g14 != 0, qbi, Gsi, Gni);
+                state_adjoint(qt0, tx, ty, nx, ny, us_, sgs, un_, sgn, cs, cn, inv_gm1, P.g14 != 0, qbo, Gs0, Gn0);
+            }
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) qbi[k] = qbo[k] = T(0);
