@@ -42,12 +42,12 @@ using D4 = D4T<double>;
 // elementary functions: in FP64 the forward kernels' own forms (the
 // table-driven exp, and erf(S) with exp(-S^2) from one Taylor-table row),
 // in FP32 the library's
-__device__ __forceinline__ double m_exp(double x) { return exp_tab(x); }
+[[maybe_unused]] __device__ __forceinline__ double m_exp(double x) { return exp_tab(x); }
 __device__ __forceinline__ float m_exp(float x) { return expf(x); }
 __device__ __forceinline__ double m_log(double x) { return log(x); }
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+[[maybe_unused]] __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float m_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ void m_erf_gauss(double S, double &erfS, double &e) { erf_exp(S, erfS, e); }
@@ -329,7 +329,7 @@ __device__ __forceinline__ void state_adjoint_rev(const double qt[4], double tx,
     auto dir = [&](double ud, double ut, double sg, const double c[4], double G[4], double &b_ud, double &b_ut) {
         const double S = ud * sqb;
         double erfv, e;
-        erf_exp(S, erfv, e);
+        m_erf_gauss(S, erfv, e);
         const double fe = sg * erfv;
         const double Q = hrho + hrho * fe;
         const double W = sg * e * rrc;
@@ -557,13 +557,19 @@ __global__ void __launch_bounds__(128) k_adj_grad(AdjParamsT<T> P, const T *__re
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.n) return;
     const bool inner = gprev != nullptr;
-    const T h = T(0.5);
-    T qb[4], gb[8], gpp[8], qp[4], gbo[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    T qb[4], gb[8], qp[4], gbo[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     ld4(P.qbar, p, qb);
     ld8(gbar_in, p, gb);
     ld4(P.q, p, qp);
-    if (inner) ld8(gprev, p, gpp);
     const double2 xyp = g.xy[p];
+    // an inner pass is sum_e a_e (q_i - q_0 - h_e.grad q_i) + grad q_0 / 2
+    // (h_e the half offset; the terms in grad q_0 add up to grad q_0 / 2 since
+    // sum_e a_e d_e^T = I, and the forward passes take them so), so grad q_0
+    // gets gb / 2 and neither the weights nor the offsets see grad q_0
+    if (inner) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) gbo[k] = T(0.5) * gb[k];
+    }
     // outgoing edges: owner terms, and the cotangents of a_e and of the offsets
     for (int e = g.off[p]; e < g.off[p + 1]; ++e) {
         const int i = g.idx[e];
@@ -571,12 +577,18 @@ __global__ void __launch_bounds__(128) k_adj_grad(AdjParamsT<T> P, const T *__re
         const T ax = T(ad.x), ay = T(ad.y);
         T qi[4], gi[8];
         ld4(P.q, i, qi);
-        T dx = T(0), dy = T(0);
+        T hx = T(0), hy = T(0);
         if (inner) {
             ld8(gprev, i, gi);
-            const double2 xyi = g.xy[i];
-            dx = T(xyi.x - xyp.x);
-            dy = T(xyi.y - xyp.y);
+            double2 hh;
+            if (g.hd) {
+                hh = g.hd[e];
+            } else {
+                const double2 xyi = g.xy[i];
+                hh = make_double2(0.5 * (xyi.x - xyp.x), 0.5 * (xyi.y - xyp.y));
+            }
+            hx = T(hh.x);
+            hy = T(hh.y);
         }
         T abx = T(0), aby = T(0), dbx = T(0), dby = T(0);
 #pragma unroll
@@ -584,12 +596,10 @@ __global__ void __launch_bounds__(128) k_adj_grad(AdjParamsT<T> P, const T *__re
             const T sb = ax * gb[k] + ay * gb[4 + k];
             T s = qi[k] - qp[k];
             if (inner) {
-                const T ddx = gi[k] - gpp[k], ddy = gi[4 + k] - gpp[4 + k];
-                s = s - h * (dx * ddx + dy * ddy);
-                gbo[k] += h * dx * sb;
-                gbo[4 + k] += h * dy * sb;
-                dbx -= h * sb * ddx;
-                dby -= h * sb * ddy;
+                s = s - (hx * gi[k] + hy * gi[4 + k]);
+                // d_e = 2 h_e: d_bar = -(sb/2) grad q_i
+                dbx -= T(0.5) * sb * gi[k];
+                dby -= T(0.5) * sb * gi[4 + k];
             }
             qb[k] -= sb;
             abx += s * gb[k];
@@ -613,19 +623,25 @@ __global__ void __launch_bounds__(128) k_adj_grad(AdjParamsT<T> P, const T *__re
         const T ax = T(ad.x), ay = T(ad.y);
         T gs[8];
         ld8(gbar_in, src, gs);
-        T dx = T(0), dy = T(0);
+        T hx = T(0), hy = T(0);
         if (inner) {
-            const double2 xys = g.xy[src];
-            dx = T(xyp.x - xys.x);
-            dy = T(xyp.y - xys.y);
+            double2 hh;
+            if (g.hd) {
+                hh = g.hd[e];
+            } else {
+                const double2 xys = g.xy[src];
+                hh = make_double2(0.5 * (xyp.x - xys.x), 0.5 * (xyp.y - xys.y));
+            }
+            hx = T(hh.x);
+            hy = T(hh.y);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const T sb = ax * gs[k] + ay * gs[4 + k];
             qb[k] += sb;
             if (inner) {
-                gbo[k] -= h * dx * sb;
-                gbo[4 + k] -= h * dy * sb;
+                gbo[k] -= hx * sb;
+                gbo[4 + k] -= hy * sb;
             }
         }
     }
