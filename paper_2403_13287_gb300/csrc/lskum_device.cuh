@@ -127,6 +127,13 @@ __device__ __forceinline__ bool finite_positive(double x)
     return b > 0 && b < 0x7ff0000000000000ll;
 }
 
+// x/2 for a positive normal x whose half is normal: the exponent field
+// decremented on the integer pipe, bitwise the FP64 product 0.5 x there
+__device__ __forceinline__ double half_of(double x)
+{
+    return __longlong_as_double(__double_as_longlong(x) - (1ll << 52));
+}
+
 // u.t = (q2 tx + q3 ty)/(2 beta) and u.n alike, straight from q (no u, v);
 // exp_tab(., -1) gives rho/2 without a multiplication.
 __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, double tx, double ty, double2 n0,
@@ -136,7 +143,11 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
     if (!finite_positive(beta)) return false;
     const double rsb = rsqrt(beta);
     const double ib = rsb * rsb;           // 1/beta, so 1/q4 = -ib/2 without a division
-    const double hib = 0.5 * ib;
+    // ib/2 and ib/4 are exact exponent decrements while ib/4 is normal (biased
+    // exponent of ib at least 3); beta above 1/16 of the largest double
+    // (p/rho below 1e-307) is reported non-physical instead
+    const bool ib_ok = (__double_as_longlong(ib) >> 52) > 2;
+    const double hib = half_of(ib);
     s.us = fma(qt[1], tx, qt[2] * ty) * hib;
     s.un = fma(qt[1], n0.x, qt[2] * n0.y) * hib;
     s.sqb = beta * rsb;
@@ -152,9 +163,9 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
     s.hp = hrho * hib;                     // p/2 = rho/(4 beta)
     // per unit mass: p/rho = 1/(2 beta), rho E = p/(gamma-1) + rho |u|^2/2
     s.h = fma(gas.hc, ib, 0.5 * w2);
-    s.qb = 0.5 * hib;
+    s.qb = half_of(hib);
     s.rrc = hrho * (rsb * 0.5641895835477563);  // 1/sqrt(pi)
-    return finite_positive(hrho);
+    return finite_positive(hrho) && ib_ok;
 }
 
 // erf(S) and exp(-S^2) together, from one row of a Taylor table: on the grid
