@@ -197,7 +197,7 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
 # profiles/launch_list_naca0012_2p5m_fp64.md).
 FP64_INSTR_PER_EDGE_FLUX = 182.33
 FP64_FLOPS_PER_EDGE_FLUX = 289.04
-FLUX_DRAM_BYTES_PER_POINT = 598.2
+FLUX_DRAM_BYTES_PER_POINT = 598.4
 # FP64 peak: ncu's DFMA unit count, 304 FP64 thread-instructions per cycle
 # (each DFMA 2 flops), at the 2070 MHz maximum SM clock
 FP64_PEAK_GINSTR = 304 * 2.070
