@@ -83,11 +83,12 @@ enum { QG_LIMIT = 1, QG_INNER = 2, QG_EXTREMA = 4 };
 // phi = min over every reconstruction shift +-h_e.grad q of
 // f(D, d) = (D^2 + eps^2 + 2Dd) / (D^2 + 2d^2 + Dd + eps^2), D the stencil
 // maximum minus q_0 for a positive shift, the minimum minus q_0 for a
-// negative one, eps^2 = (K min_e |P_i - P_0|)^3. With x = |D| and d = |shift|, f = N/M has N - M = d (x - 2d):
-// f < 1 exactly when x < 2d, and it increases in x up to x = 2d + sqrt(8d^2 +
-// eps^2) > 2d and stays above 1 beyond; for fixed x it decreases in d. So phi
-// is 1 unless x_m = min(D+, -D-) < 2 d_m, d_m the largest |h_e.grad q|, and
-// then it is f(x_m, d_m): one division per component.
+// negative one, eps^2 = (K min_e |P_i - P_0|)^3. With x = |D| and
+// d = |shift|, f = N/M has N - M = d (x - 2d): f < 1 exactly when x < 2d;
+// f increases in x up to x = 2d + sqrt(8d^2 + eps^2) > 2d and stays above 1
+// beyond; and for fixed x < 2d it decreases in d. So phi is 1 unless
+// x_m = min(D+, -D-) < 2 d_m, d_m the largest |h_e.grad q|, and then it is
+// f(x_m, d_m): one quotient per component (a reciprocal and two Newton steps).
 // KIN: the kinetic boundary mode (mirror images in g.ioff...; a separate
 // instantiation keeps the plain kernel's registers as they are)
 template <bool KIN, int PASS>
