@@ -127,6 +127,16 @@ __device__ __forceinline__ bool finite_positive(double x)
     return b > 0 && b < 0x7ff0000000000000ll;
 }
 
+// the magnitude bits of x (sign bit cleared) by an integer AND that the
+// compiler cannot turn into an FP64 absolute value, which would be issued on
+// the FP64 pipe
+__device__ __forceinline__ unsigned long long abs_bits(double x)
+{
+    unsigned long long b;
+    asm("and.b64 %0, %1, 0x7fffffffffffffff;" : "=l"(b) : "l"(__double_as_longlong(x)));
+    return b;
+}
+
 // x/2 for a positive normal x whose half is normal: the exponent field
 // decremented on the integer pipe, bitwise the FP64 product 0.5 x there
 __device__ __forceinline__ double half_of(double x)
@@ -139,8 +149,13 @@ __device__ __forceinline__ double half_of(double x)
 __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, double tx, double ty, double2 n0,
                                             Prim &s)
 {
-    const double beta = -0.5 * qt[3];
-    if (!finite_positive(beta)) return false;
+    // beta = -q4/2 as an exponent decrement of |q4|, bitwise the FP64 product:
+    // q4 must be negative and normal with a normal half; anything else (zero,
+    // positive, not finite, |q4| < 2^-1021, i.e. p/rho > 1e307) is non-physical
+    const long long b3 = __double_as_longlong(qt[3]);
+    const unsigned e3 = (unsigned)(b3 >> 52) & 0x7ffu;
+    if (!(b3 < 0 && e3 >= 2u && e3 < 0x7ffu)) return false;
+    const double beta = __longlong_as_double((long long)abs_bits(qt[3]) - (1ll << 52));
     const double rsb = rsqrt(beta);
     const double ib = rsb * rsb;           // 1/beta, so 1/q4 = -ib/2 without a division
     // ib/2 and ib/4 are exact exponent decrements while ib/4 is normal (biased
@@ -222,15 +237,6 @@ __device__ __forceinline__ double flip_sign(double x, unsigned long long sbit)
 
 static constexpr unsigned long long kSignBit = 0x8000000000000000ull;
 
-// the magnitude bits of x (sign bit cleared) by an integer AND that the
-// compiler cannot turn into an FP64 absolute value, which would be issued on
-// the FP64 pipe
-__device__ __forceinline__ unsigned long long abs_bits(double x)
-{
-    unsigned long long b;
-    asm("and.b64 %0, %1, 0x7fffffffffffffff;" : "=l"(b) : "l"(__double_as_longlong(x)));
-    return b;
-}
 
 // Kinetic split flux along a direction: normal velocity un, transverse ut,
 // sgn = +1 for G+, -1 for G- (half-range moments of the Maxwellian):
