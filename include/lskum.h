@@ -41,8 +41,8 @@ typedef enum {
     LSKUM_ERR_DEGENERATE_STENCIL = 3, /* a needed (sub-)stencil has a singular 2x2 least-squares matrix */
     LSKUM_ERR_CUDA = 4,               /* a CUDA runtime call failed */
     LSKUM_ERR_OOM = 5,                /* device allocation failed */
-    LSKUM_ERR_NONPHYSICAL = 6,        /* a state with rho <= 0, p <= 0 (FP64 form: p/rho below
-                                         1e-307) or a non-finite value appeared */
+    LSKUM_ERR_NONPHYSICAL = 6,        /* a state with rho <= 0, p <= 0 (FP64 form: p/rho outside
+                                         [1e-307, 1e307]) or a non-finite value appeared */
     LSKUM_ERR_TIMEOUT = 7             /* a bounded device-side wait ran out */
 } lskum_status;
 
