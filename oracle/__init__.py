@@ -18,6 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lskum_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+# the same source built with -fopenmp: the points of each pass shared out
+# among host threads (bitwise the same results), for timing on all cores
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 
 OK = 0
 ERR_DEGENERATE = 3
@@ -26,6 +29,8 @@ ERR_NONPHYSICAL = 6
 XPOS, XNEG, YPOS, YNEG = 1, 2, 4, 8
 
 _lib = None
+_libs = {}
+_threads = 1
 
 _d = ctypes.c_double
 _i64 = ctypes.c_int64
@@ -36,49 +41,84 @@ RESIDUAL_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/_build/liboracle.so (plain gcc, -O2, no FMA contraction)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (plain gcc, -O2, no
+    FMA contraction); openmp=True builds liboracle_omp.so from the same source
+    with -fopenmp (returns None if the compiler has no OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + ".tmp%d" % os.getpid()
+    out = _LIB_OMP if openmp else _LIB
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+        return out
+    tmp = out + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+           "-shared", "-Wall", "-fopenmp" if openmp else "-Wno-unknown-pragmas",
+           "-o", tmp, _SRC, "-lm"]
+    if openmp:
+        r = subprocess.run(cmd, capture_output=True)
+        if r.returncode != 0:
+            return None
+    else:
+        subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def set_threads(threads: int) -> int:
+    """Host threads for the oracle calls that follow: 1 (the default) uses the
+    serial build; more uses the OpenMP build (same bits). Returns the number
+    of threads in effect (1 if OpenMP is not available)."""
+    global _lib, _threads
+    threads = max(1, int(threads))
+    if threads > 1 and build(openmp=True) is None:
+        threads = 1
+    _threads = threads
+    _lib = None
+    L = lib()
+    return int(L.orc_set_threads(threads)) if threads > 1 else 1
+
+
+def threads() -> int:
+    return _threads
 
 
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        L = _lib
-        L.orc_split_stencils.argtypes = [_i64] + [_p] * 7
-        L.orc_q_variables.argtypes = [_i64, _d, _p, _p]
-        L.orc_U_from_q.argtypes = [_i64, _d, _p, _p]
-        L.orc_split_flux.argtypes = [_d, _d, _d, _d, _d, _int, _p]
-        L.orc_split_flux.restype = None
-        L.orc_euler_flux.argtypes = [_d, _d, _d, _d, _d, _p]
-        L.orc_euler_flux.restype = None
-        L.orc_q_derivatives.argtypes = [_i64, _p, _p, _p, _p, _p, _int, _p, _p]
-        L.orc_q_derivatives_pass.argtypes = [_i64] + [_p] * 9
-        L.orc_flux_residual.argtypes = [_i64, _d] + [_p] * 11 + [_int, _p, _p]
-        L.orc_timestep.argtypes = [_i64, _d, _d] + [_p] * 5 + [_p]
-        L.orc_freestream.argtypes = [_d, _d, _d, _p]
-        L.orc_freestream.restype = None
-        L.orc_residue.argtypes = [_i64, _p]
-        L.orc_residue.restype = _d
-        L.orc_euler_step.argtypes = [_i64, _p, _p, _p, _p, _p, _p, RESIDUAL_FN, _p, _p]
-        L.orc_rk4_step.argtypes = [_i64, _p, _p, _p, _p, _p, _p, RESIDUAL_FN, _p, _p]
-        L.orc_residual.argtypes = [_i64, _d] + [_p] * 8 + [_int, _int, _d] + [_p] * 5
-        L.orc_limit_gradients.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _p, _p]
-        L.orc_forces.argtypes = [_i64, _d, _d, _d, _p, _p, _p, _p, _p, _i64, _p, _p, _p, _p]
-        L.orc_solve.argtypes = ([_i64, _d] + [_p] * 8 + [_int, _int, _d, _int, _d, _d, _d, _int, _p, _p])
-        L.orc_residual_bc.argtypes = [_i64, _d] + [_p] * 8 + [_int, _int, _d, _int, _d, _d] + [_p] * 5
-        L.orc_solve_bc.argtypes = ([_i64, _d] + [_p] * 8 + [_int, _int, _d, _int, _int, _d, _d, _d, _int, _p, _p])
+        key = "omp" if _threads > 1 else "serial"
+        if key not in _libs:
+            _libs[key] = _declare(ctypes.CDLL(build(openmp=True) if key == "omp" else build()))
+        _lib = _libs[key]
     return _lib
+
+
+def _declare(L):
+    L.orc_set_threads.argtypes = [_int]
+    L.orc_set_threads.restype = _int
+    L.orc_split_stencils.argtypes = [_i64] + [_p] * 7
+    L.orc_q_variables.argtypes = [_i64, _d, _p, _p]
+    L.orc_U_from_q.argtypes = [_i64, _d, _p, _p]
+    L.orc_split_flux.argtypes = [_d, _d, _d, _d, _d, _int, _p]
+    L.orc_split_flux.restype = None
+    L.orc_euler_flux.argtypes = [_d, _d, _d, _d, _d, _p]
+    L.orc_euler_flux.restype = None
+    L.orc_q_derivatives.argtypes = [_i64, _p, _p, _p, _p, _p, _int, _p, _p]
+    L.orc_q_derivatives_pass.argtypes = [_i64] + [_p] * 9
+    L.orc_flux_residual.argtypes = [_i64, _d] + [_p] * 11 + [_int, _p, _p]
+    L.orc_timestep.argtypes = [_i64, _d, _d] + [_p] * 5 + [_p]
+    L.orc_freestream.argtypes = [_d, _d, _d, _p]
+    L.orc_freestream.restype = None
+    L.orc_residue.argtypes = [_i64, _p]
+    L.orc_residue.restype = _d
+    L.orc_euler_step.argtypes = [_i64, _p, _p, _p, _p, _p, _p, RESIDUAL_FN, _p, _p]
+    L.orc_rk4_step.argtypes = [_i64, _p, _p, _p, _p, _p, _p, RESIDUAL_FN, _p, _p]
+    L.orc_residual.argtypes = [_i64, _d] + [_p] * 8 + [_int, _int, _d] + [_p] * 5
+    L.orc_limit_gradients.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _p, _p]
+    L.orc_forces.argtypes = [_i64, _d, _d, _d, _p, _p, _p, _p, _p, _i64, _p, _p, _p, _p]
+    L.orc_solve.argtypes = ([_i64, _d] + [_p] * 8 + [_int, _int, _d, _int, _d, _d, _d, _int, _p, _p])
+    L.orc_residual_bc.argtypes = [_i64, _d] + [_p] * 8 + [_int, _int, _d, _int, _d, _d] + [_p] * 5
+    L.orc_solve_bc.argtypes = ([_i64, _d] + [_p] * 8 + [_int, _int, _d, _int, _int, _d, _d, _d, _int, _p, _p])
+    return L
 
 
 def _ptr(a):

@@ -16,11 +16,22 @@
  * without stating them; see "Stencil members".
  *
  * Arrays of 4 components are stored component-major: A[k*n + p].
+ *
+ * Points are independent within a pass (q_variables, each q_derivatives
+ * solve, the limiter, flux_residual, timestep, each state update): every
+ * point reads the previous pass's arrays and writes only its own entries.
+ * Built with -fopenmp (the host-core timing build) those loops share the
+ * points out among threads; each point's own sums still run serially in CSR
+ * order, so both builds give the same bits. Without -fopenmp the pragmas are
+ * ignored and every loop runs in input order.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_INTERIOR 0
 #define ORC_WALL 1
@@ -73,6 +84,18 @@ int orc_split_stencils(int64_t n, const double *x, const double *y,
     return ORC_OK;
 }
 
+/* threads of the OpenMP timing build (1 in the serial build) */
+int orc_set_threads(int threads)
+{
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+    return omp_get_max_threads();
+#else
+    (void)threads;
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* State conversions                                                        */
 /* ------------------------------------------------------------------------ */
@@ -123,15 +146,21 @@ static int prim_from_q(double gamma, const double q[4], double prim[4])
 /* q_variables() of Algorithm 1 applied to a conserved state U[4][n] */
 int orc_q_variables(int64_t n, double gamma, const double *U, double *q)
 {
+    int rc = ORC_OK;
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < n; ++p) {
         double u[4], pr[4], qq[4];
         for (int k = 0; k < 4; ++k) u[k] = U[k * n + p];
         prim_from_U(gamma, u, pr);
-        if (!(pr[0] > 0.0) || !(pr[3] > 0.0)) return ORC_ERR_NONPHYSICAL;
+        if (!(pr[0] > 0.0) || !(pr[3] > 0.0)) {
+#pragma omp atomic write
+            rc = ORC_ERR_NONPHYSICAL;
+            continue;
+        }
         q_from_prim(gamma, pr, qq);
         for (int k = 0; k < 4; ++k) q[k * n + p] = qq[k];
     }
-    return ORC_OK;
+    return rc;
 }
 
 /* inverse map, q[4][n] -> U[4][n] (used by the round-trip checks) */
@@ -317,47 +346,77 @@ static void member_state(const orc_geom *g, int64_t p, const orc_member *m, cons
 /* squares gradient is rotation-equivariant, so this is done in the global  */
 /* (x, y) frame and qx, qy are global-frame derivatives.                    */
 /* ------------------------------------------------------------------------ */
-static int q_derivatives_pass(const orc_geom *g, const double *q, const double *qx_old,
-                              const double *qy_old, double *qx, double *qy, orc_member *mem)
+static int q_derivatives_point(const orc_geom *g, int64_t p, const double *q, const double *qx_old,
+                               const double *qy_old, double *qx, double *qy, orc_member *mem)
 {
     const int64_t n = g->n;
-    for (int64_t p = 0; p < n; ++p) {
-        double sxx = 0.0, sxy = 0.0, syy = 0.0;
-        double sxq[4] = {0, 0, 0, 0}, syq[4] = {0, 0, 0, 0};
-        const int64_t cnt = stencil_members(g, p, mem);
-        for (int64_t j = 0; j < cnt; ++j) {
-            const orc_member *m = &mem[j];
-            double dx = m->dx, dy = m->dy;
-            double qi[4], gxi[4], gyi[4];
-            member_state(g, p, m, q, qx_old, qy_old, qi, gxi, gyi);
-            sxx += dx * dx;
-            sxy += dx * dy;
-            syy += dy * dy;
-            for (int k = 0; k < 4; ++k) {
-                double dq = qi[k] - q[k * n + p];
-                if (qx_old) {
-                    dq = dq - 0.5 * (dx * (gxi[k] - qx_old[k * n + p])
-                                     + dy * (gyi[k] - qy_old[k * n + p]));
-                }
-                sxq[k] += dx * dq;
-                syq[k] += dy * dq;
-            }
-        }
-        double det = sxx * syy - sxy * sxy;
-        if (!(det > ORC_DET_EPS * sxx * syy)) return ORC_ERR_DEGENERATE;
+    double sxx = 0.0, sxy = 0.0, syy = 0.0;
+    double sxq[4] = {0, 0, 0, 0}, syq[4] = {0, 0, 0, 0};
+    const int64_t cnt = stencil_members(g, p, mem);
+    for (int64_t j = 0; j < cnt; ++j) {
+        const orc_member *m = &mem[j];
+        double dx = m->dx, dy = m->dy;
+        double qi[4], gxi[4], gyi[4];
+        member_state(g, p, m, q, qx_old, qy_old, qi, gxi, gyi);
+        sxx += dx * dx;
+        sxy += dx * dy;
+        syy += dy * dy;
         for (int k = 0; k < 4; ++k) {
-            qx[k * n + p] = (syy * sxq[k] - sxy * syq[k]) / det;
-            qy[k * n + p] = (sxx * syq[k] - sxy * sxq[k]) / det;
+            double dq = qi[k] - q[k * n + p];
+            if (qx_old) {
+                dq = dq - 0.5 * (dx * (gxi[k] - qx_old[k * n + p])
+                                 + dy * (gyi[k] - qy_old[k * n + p]));
+            }
+            sxq[k] += dx * dq;
+            syq[k] += dy * dq;
         }
+    }
+    double det = sxx * syy - sxy * sxy;
+    if (!(det > ORC_DET_EPS * sxx * syy)) return ORC_ERR_DEGENERATE;
+    for (int k = 0; k < 4; ++k) {
+        qx[k * n + p] = (syy * sxq[k] - sxy * syq[k]) / det;
+        qy[k * n + p] = (sxx * syq[k] - sxy * sxq[k]) / det;
     }
     return ORC_OK;
 }
 
+/* room for the members of any stencil: the neighbours and their images */
+static size_t member_room(const orc_geom *g)
+{
+    return (size_t)(2 * max_degree(g) + 1) * sizeof(orc_member);
+}
+
+/* keep the first error a thread met (any one of them, with threads) */
+static void merge_status(int *rc, int mine)
+{
+    if (mine == ORC_OK) return;
+#pragma omp critical(orc_status)
+    {
+        if (*rc == ORC_OK) *rc = mine;
+    }
+}
+
+static int q_derivatives_pass(const orc_geom *g, const double *q, const double *qx_old,
+                              const double *qy_old, double *qx, double *qy)
+{
+    const size_t room = member_room(g);
+    int rc = ORC_OK;
+#pragma omp parallel
+    {
+        orc_member *mem = (orc_member *)malloc(room);
+        int mine = mem ? ORC_OK : -1;
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t p = 0; p < g->n; ++p)
+            if (mine == ORC_OK) mine = q_derivatives_point(g, p, q, qx_old, qy_old, qx, qy, mem);
+        free(mem);
+        merge_status(&rc, mine);
+    }
+    return rc;
+}
+
 static int q_derivatives(const orc_geom *g, const double *q, int inner, double *qx, double *qy)
 {
-    orc_member *mem = (orc_member *)malloc((size_t)(2 * max_degree(g) + 1) * sizeof(orc_member));
-    if (!mem) return -1;
-    int rc = q_derivatives_pass(g, q, NULL, NULL, qx, qy, mem);
+    int rc = q_derivatives_pass(g, q, NULL, NULL, qx, qy);
     size_t bytes = (size_t)4 * (size_t)g->n * sizeof(double);
     double *ox = NULL, *oy = NULL;
     if (rc == ORC_OK && inner > 0) {
@@ -368,9 +427,9 @@ static int q_derivatives(const orc_geom *g, const double *q, int inner, double *
     for (int it = 0; it < inner && rc == ORC_OK; ++it) {
         memcpy(ox, qx, bytes);
         memcpy(oy, qy, bytes);
-        rc = q_derivatives_pass(g, q, ox, oy, qx, qy, mem);
+        rc = q_derivatives_pass(g, q, ox, oy, qx, qy);
     }
-    free(ox); free(oy); free(mem);
+    free(ox); free(oy);
     return rc;
 }
 
@@ -389,11 +448,7 @@ int orc_q_derivatives_pass(int64_t n, const double *x, const double *y,
                            double *qx, double *qy)
 {
     orc_geom g = plain_geom(n, x, y, off, idx);
-    orc_member *mem = (orc_member *)malloc((size_t)(2 * max_degree(&g) + 1) * sizeof(orc_member));
-    if (!mem) return -1;
-    int rc = q_derivatives_pass(&g, q, qx_old, qy_old, qx, qy, mem);
-    free(mem);
-    return rc;
+    return q_derivatives_pass(&g, q, qx_old, qy_old, qx, qy);
 }
 
 int orc_q_derivatives(int64_t n, const double *x, const double *y,
@@ -420,48 +475,62 @@ static double venkat(double D, double d, double eps2)
     return (D * D + eps2 + 2.0 * D * d) / (D * D + 2.0 * d * d + D * d + eps2);
 }
 
-static int limit_gradients(const orc_geom *g, const double *q, double K, double *qx, double *qy)
+static void limit_point(const orc_geom *g, int64_t p, const double *q, double K, double *qx,
+                        double *qy, orc_member *mem)
 {
     const int64_t n = g->n;
-    orc_member *mem = (orc_member *)malloc((size_t)(2 * max_degree(g) + 1) * sizeof(orc_member));
-    if (!mem) return -1;
-    for (int64_t p = 0; p < n; ++p) {
-        const int64_t cnt = stencil_members(g, p, mem);
-        double h = INFINITY;
-        for (int64_t j = 0; j < cnt; ++j) {
-            double d = sqrt(mem[j].dx * mem[j].dx + mem[j].dy * mem[j].dy);
-            if (d < h) h = d;
-        }
-        double eps2 = (K * h) * (K * h) * (K * h);
-        double qmax[4], qmin[4];
-        for (int k = 0; k < 4; ++k) qmax[k] = qmin[k] = q[k * n + p];
-        for (int64_t j = 0; j < cnt; ++j) {
-            double qi[4], gxi[4], gyi[4];
-            member_state(g, p, &mem[j], q, NULL, NULL, qi, gxi, gyi);
-            for (int k = 0; k < 4; ++k) {
-                if (qi[k] > qmax[k]) qmax[k] = qi[k];
-                if (qi[k] < qmin[k]) qmin[k] = qi[k];
-            }
-        }
+    const int64_t cnt = stencil_members(g, p, mem);
+    double h = INFINITY;
+    for (int64_t j = 0; j < cnt; ++j) {
+        double d = sqrt(mem[j].dx * mem[j].dx + mem[j].dy * mem[j].dy);
+        if (d < h) h = d;
+    }
+    double eps2 = (K * h) * (K * h) * (K * h);
+    double qmax[4], qmin[4];
+    for (int k = 0; k < 4; ++k) qmax[k] = qmin[k] = q[k * n + p];
+    for (int64_t j = 0; j < cnt; ++j) {
+        double qi[4], gxi[4], gyi[4];
+        member_state(g, p, &mem[j], q, NULL, NULL, qi, gxi, gyi);
         for (int k = 0; k < 4; ++k) {
-            double q0 = q[k * n + p];
-            double phi = 1.0;
-            for (int64_t j = 0; j < cnt; ++j) {
-                double half = 0.5 * (mem[j].dx * qx[k * n + p] + mem[j].dy * qy[k * n + p]);
-                for (int sgn = -1; sgn <= 1; sgn += 2) {
-                    double d = sgn * half;
-                    double f = 1.0;
-                    if (d > 0.0) f = venkat(qmax[k] - q0, d, eps2);
-                    else if (d < 0.0) f = venkat(qmin[k] - q0, d, eps2);
-                    if (f < phi) phi = f;
-                }
-            }
-            qx[k * n + p] *= phi;
-            qy[k * n + p] *= phi;
+            if (qi[k] > qmax[k]) qmax[k] = qi[k];
+            if (qi[k] < qmin[k]) qmin[k] = qi[k];
         }
     }
-    free(mem);
-    return ORC_OK;
+    for (int k = 0; k < 4; ++k) {
+        double q0 = q[k * n + p];
+        double phi = 1.0;
+        for (int64_t j = 0; j < cnt; ++j) {
+            double half = 0.5 * (mem[j].dx * qx[k * n + p] + mem[j].dy * qy[k * n + p]);
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                double d = sgn * half;
+                double f = 1.0;
+                if (d > 0.0) f = venkat(qmax[k] - q0, d, eps2);
+                else if (d < 0.0) f = venkat(qmin[k] - q0, d, eps2);
+                if (f < phi) phi = f;
+            }
+        }
+        qx[k * n + p] *= phi;
+        qy[k * n + p] *= phi;
+    }
+}
+
+/* each point scales only its own gradients and reads only q, so the points
+ * are independent */
+static int limit_gradients(const orc_geom *g, const double *q, double K, double *qx, double *qy)
+{
+    const size_t room = member_room(g);
+    int rc = ORC_OK;
+#pragma omp parallel
+    {
+        orc_member *mem = (orc_member *)malloc(room);
+        int mine = mem ? ORC_OK : -1;
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t p = 0; p < g->n; ++p)
+            if (mine == ORC_OK) limit_point(g, p, q, K, qx, qy, mem);
+        free(mem);
+        merge_status(&rc, mine);
+    }
+    return rc;
 }
 
 int orc_limit_gradients(int64_t n, const double *x, const double *y, const int32_t *off,
@@ -528,90 +597,101 @@ static void reconstruct(const orc_geom *g, int64_t p, const orc_member *m, const
     }
 }
 
-static int flux_residual(const orc_geom *g, double gamma, const double *q, const double *qx,
-                         const double *qy, int order, double *R, double *scale)
+static const uint8_t sub_bit[4] = {ORC_XPOS, ORC_XNEG, ORC_YPOS, ORC_YNEG};
+static const int sub_dir[4] = {0, 0, 1, 1};
+static const int sub_sign[4] = {+1, -1, +1, -1};
+
+static int flux_residual_point(const orc_geom *g, int64_t p, double gamma, const double *q,
+                               const double *qx, const double *qy, int order, double *R,
+                               double *scale, orc_member *mem)
 {
-    static const uint8_t sub_bit[4] = {ORC_XPOS, ORC_XNEG, ORC_YPOS, ORC_YNEG};
-    static const int sub_dir[4] = {0, 0, 1, 1};
-    static const int sub_sign[4] = {+1, -1, +1, -1};
     const int64_t n = g->n;
-    orc_member *mem = (orc_member *)malloc((size_t)(2 * max_degree(g) + 1) * sizeof(orc_member));
-    if (!mem) return -1;
-    int rc = ORC_OK;
-    for (int64_t p = 0; p < n && rc == ORC_OK; ++p) {
-        double Rl[4] = {0, 0, 0, 0}, Sc[4] = {0, 0, 0, 0};
-        int flag = g->flags[p];
-        int kinetic = is_kinetic_boundary(g, p);
-        if (flag != ORC_FARFIELD || kinetic) {
-            double tx = g->ny[p], ty = -g->nx[p], nnx = g->nx[p], nny = g->ny[p];
-            const int64_t cnt = stencil_members(g, p, mem);
-            for (int sub = 0; sub < 4 && rc == ORC_OK; ++sub) {
-                /* plain reading: no dGn+/dn at the wall */
-                if (flag == ORC_WALL && !kinetic && sub == 2) continue;
-                double sss = 0.0, ssn = 0.0, snn = 0.0;
-                double ssG[4] = {0, 0, 0, 0}, snG[4] = {0, 0, 0, 0};
+    double Rl[4] = {0, 0, 0, 0}, Sc[4] = {0, 0, 0, 0};
+    int flag = g->flags[p];
+    int kinetic = is_kinetic_boundary(g, p);
+    if (flag != ORC_FARFIELD || kinetic) {
+        double tx = g->ny[p], ty = -g->nx[p], nnx = g->nx[p], nny = g->ny[p];
+        const int64_t cnt = stencil_members(g, p, mem);
+        for (int sub = 0; sub < 4; ++sub) {
+            /* plain reading: no dGn+/dn at the wall */
+            if (flag == ORC_WALL && !kinetic && sub == 2) continue;
+            double sss = 0.0, ssn = 0.0, snn = 0.0;
+            double ssG[4] = {0, 0, 0, 0}, snG[4] = {0, 0, 0, 0};
+            for (int64_t j = 0; j < cnt; ++j) {
+                const orc_member *m = &mem[j];
+                if (!(m->mask & sub_bit[sub])) continue;
+                double ds = m->ds, dn = m->dn;
+                double qt_i[4], qt_0[4], pr_i[4], pr_0[4], Gi[4], G0[4];
+                reconstruct(g, p, m, q, qx, qy, order, qt_i, qt_0);
+                if (!prim_from_q(gamma, qt_i, pr_i) || !prim_from_q(gamma, qt_0, pr_0))
+                    return ORC_ERR_NONPHYSICAL;
+                frame_split_flux(gamma, pr_i, tx, ty, nnx, nny, sub_dir[sub], sub_sign[sub], Gi);
+                frame_split_flux(gamma, pr_0, tx, ty, nnx, nny, sub_dir[sub], sub_sign[sub], G0);
+                sss += ds * ds;
+                ssn += ds * dn;
+                snn += dn * dn;
+                for (int k = 0; k < 4; ++k) {
+                    double dG = Gi[k] - G0[k];
+                    ssG[k] += ds * dG;
+                    snG[k] += dn * dG;
+                }
+            }
+            double det = sss * snn - ssn * ssn;
+            if (!(det > ORC_DET_EPS * sss * snn)) return ORC_ERR_DEGENERATE;
+            for (int k = 0; k < 4; ++k) {
+                double d;
+                if (sub_dir[sub] == 0) d = (snn * ssG[k] - ssn * snG[k]) / det;
+                else d = (sss * snG[k] - ssn * ssG[k]) / det;
+                Rl[k] += d;
+            }
+            if (scale) {
                 for (int64_t j = 0; j < cnt; ++j) {
                     const orc_member *m = &mem[j];
                     if (!(m->mask & sub_bit[sub])) continue;
                     double ds = m->ds, dn = m->dn;
+                    double w = (sub_dir[sub] == 0) ? (snn * ds - ssn * dn) / det
+                                                   : (sss * dn - ssn * ds) / det;
                     double qt_i[4], qt_0[4], pr_i[4], pr_0[4], Gi[4], G0[4];
                     reconstruct(g, p, m, q, qx, qy, order, qt_i, qt_0);
-                    if (!prim_from_q(gamma, qt_i, pr_i) || !prim_from_q(gamma, qt_0, pr_0)) {
-                        rc = ORC_ERR_NONPHYSICAL;
-                        break;
-                    }
+                    prim_from_q(gamma, qt_i, pr_i);
+                    prim_from_q(gamma, qt_0, pr_0);
                     frame_split_flux(gamma, pr_i, tx, ty, nnx, nny, sub_dir[sub], sub_sign[sub], Gi);
                     frame_split_flux(gamma, pr_0, tx, ty, nnx, nny, sub_dir[sub], sub_sign[sub], G0);
-                    sss += ds * ds;
-                    ssn += ds * dn;
-                    snn += dn * dn;
-                    for (int k = 0; k < 4; ++k) {
-                        double dG = Gi[k] - G0[k];
-                        ssG[k] += ds * dG;
-                        snG[k] += dn * dG;
-                    }
-                }
-                if (rc) break;
-                double det = sss * snn - ssn * ssn;
-                if (!(det > ORC_DET_EPS * sss * snn)) { rc = ORC_ERR_DEGENERATE; break; }
-                for (int k = 0; k < 4; ++k) {
-                    double d;
-                    if (sub_dir[sub] == 0) d = (snn * ssG[k] - ssn * snG[k]) / det;
-                    else d = (sss * snG[k] - ssn * ssG[k]) / det;
-                    Rl[k] += d;
-                }
-                if (scale) {
-                    for (int64_t j = 0; j < cnt; ++j) {
-                        const orc_member *m = &mem[j];
-                        if (!(m->mask & sub_bit[sub])) continue;
-                        double ds = m->ds, dn = m->dn;
-                        double w = (sub_dir[sub] == 0) ? (snn * ds - ssn * dn) / det
-                                                       : (sss * dn - ssn * ds) / det;
-                        double qt_i[4], qt_0[4], pr_i[4], pr_0[4], Gi[4], G0[4];
-                        reconstruct(g, p, m, q, qx, qy, order, qt_i, qt_0);
-                        prim_from_q(gamma, qt_i, pr_i);
-                        prim_from_q(gamma, qt_0, pr_0);
-                        frame_split_flux(gamma, pr_i, tx, ty, nnx, nny, sub_dir[sub], sub_sign[sub], Gi);
-                        frame_split_flux(gamma, pr_0, tx, ty, nnx, nny, sub_dir[sub], sub_sign[sub], G0);
-                        for (int k = 0; k < 4; ++k) Sc[k] += fabs(w) * (fabs(Gi[k]) + fabs(G0[k]));
-                    }
+                    for (int k = 0; k < 4; ++k) Sc[k] += fabs(w) * (fabs(Gi[k]) + fabs(G0[k]));
                 }
             }
         }
-        /* rotate the momentum components from (s, n) back to (x, y) */
-        double tx = g->ny[p], ty = -g->nx[p];
-        R[0 * n + p] = Rl[0];
-        R[1 * n + p] = Rl[1] * tx + Rl[2] * g->nx[p];
-        R[2 * n + p] = Rl[1] * ty + Rl[2] * g->ny[p];
-        R[3 * n + p] = Rl[3];
-        if (scale) {
-            scale[0 * n + p] = Sc[0];
-            scale[1 * n + p] = Sc[1] + Sc[2];
-            scale[2 * n + p] = Sc[1] + Sc[2];
-            scale[3 * n + p] = Sc[3];
-        }
     }
-    free(mem);
+    /* rotate the momentum components from (s, n) back to (x, y) */
+    double tx = g->ny[p], ty = -g->nx[p];
+    R[0 * n + p] = Rl[0];
+    R[1 * n + p] = Rl[1] * tx + Rl[2] * g->nx[p];
+    R[2 * n + p] = Rl[1] * ty + Rl[2] * g->ny[p];
+    R[3 * n + p] = Rl[3];
+    if (scale) {
+        scale[0 * n + p] = Sc[0];
+        scale[1 * n + p] = Sc[1] + Sc[2];
+        scale[2 * n + p] = Sc[1] + Sc[2];
+        scale[3 * n + p] = Sc[3];
+    }
+    return ORC_OK;
+}
+
+static int flux_residual(const orc_geom *g, double gamma, const double *q, const double *qx,
+                         const double *qy, int order, double *R, double *scale)
+{
+    const size_t room = member_room(g);
+    int rc = ORC_OK;
+#pragma omp parallel
+    {
+        orc_member *mem = (orc_member *)malloc(room);
+        int mine = mem ? ORC_OK : -1;
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t p = 0; p < g->n; ++p)
+            if (mine == ORC_OK) mine = flux_residual_point(g, p, gamma, q, qx, qy, order, R, scale, mem);
+        free(mem);
+        merge_status(&rc, mine);
+    }
     return rc;
 }
 
@@ -634,11 +714,17 @@ int orc_flux_residual(int64_t n, double gamma,
 int orc_timestep(int64_t n, double gamma, double cfl, const double *x, const double *y,
                  const int32_t *off, const int32_t *idx, const double *U, double *dt)
 {
+    int rc = ORC_OK;
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < n; ++p) {
         double u[4], pr[4];
         for (int k = 0; k < 4; ++k) u[k] = U[k * n + p];
         prim_from_U(gamma, u, pr);
-        if (!(pr[0] > 0.0) || !(pr[3] > 0.0)) return ORC_ERR_NONPHYSICAL;
+        if (!(pr[0] > 0.0) || !(pr[3] > 0.0)) {
+#pragma omp atomic write
+            rc = ORC_ERR_NONPHYSICAL;
+            continue;
+        }
         double speed = sqrt(pr[1] * pr[1] + pr[2] * pr[2]) + 3.0 * sqrt(pr[3] / pr[0]);
         double dmin = INFINITY;
         for (int64_t e = off[p]; e < off[p + 1]; ++e) {
@@ -650,7 +736,7 @@ int orc_timestep(int64_t n, double gamma, double cfl, const double *x, const dou
         }
         dt[p] = cfl * dmin / speed;
     }
-    return ORC_OK;
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -670,6 +756,7 @@ void orc_freestream(double gamma, double mach, double aoa_deg, double U[4])
 static void apply_boundary(int64_t n, const int32_t *flags, const double *nx,
                            const double *ny, const double Uinf[4], int kinetic, double *U)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < n; ++p) {
         if (flags[p] == ORC_WALL) {
             double mn = U[1 * n + p] * nx[p] + U[2 * n + p] * ny[p];
@@ -706,6 +793,7 @@ static int euler_step(int64_t n, const int32_t *flags, const double *nx, const d
     int rc = res(U, R, user);
     if (rc == ORC_OK) {
         for (int k = 0; k < 4; ++k)
+#pragma omp parallel for schedule(static)
             for (int64_t p = 0; p < n; ++p)
                 U[k * n + p] = U[k * n + p] - dt[p] * R[k * n + p];
         apply_boundary(n, flags, nx, ny, Uinf, kinetic, U);
@@ -741,21 +829,25 @@ static int rk4_step(int64_t n, const int32_t *flags, const double *nx, const dou
     rc = res(Un, R0, user);
     if (rc) goto done;
     for (int k = 0; k < 4; ++k)
+#pragma omp parallel for schedule(static)
         for (int64_t p = 0; p < n; ++p) Us[k * n + p] = Un[k * n + p] - 0.5 * dt[p] * R0[k * n + p];
     apply_boundary(n, flags, nx, ny, Uinf, kinetic, Us);
     rc = res(Us, R1, user);
     if (rc) goto done;
     for (int k = 0; k < 4; ++k)
+#pragma omp parallel for schedule(static)
         for (int64_t p = 0; p < n; ++p) Us[k * n + p] = Un[k * n + p] - 0.5 * dt[p] * R1[k * n + p];
     apply_boundary(n, flags, nx, ny, Uinf, kinetic, Us);
     rc = res(Us, R2, user);
     if (rc) goto done;
     for (int k = 0; k < 4; ++k)
+#pragma omp parallel for schedule(static)
         for (int64_t p = 0; p < n; ++p) Us[k * n + p] = Un[k * n + p] - dt[p] * R2[k * n + p];
     apply_boundary(n, flags, nx, ny, Uinf, kinetic, Us);
     rc = res(Us, R3, user);
     if (rc) goto done;
     for (int k = 0; k < 4; ++k)
+#pragma omp parallel for schedule(static)
         for (int64_t p = 0; p < n; ++p) {
             int64_t a = k * n + p;
             U[a] = Un[a] - dt[p] / 6.0 * (R0[a] + 2.0 * R1[a] + 2.0 * R2[a] + R3[a]);
