@@ -317,15 +317,20 @@ int64_t lskum_launch_count(const lskum_ctx *ctx);
  * handed a fixed memory budget. It needs no context either. The paper has no
  * counterpart: this is a plumbing variant of lskum_q_derivatives.
  *
- * Computes q (E13) from U and the least-squares q-derivatives of E15 (the
+ * Computes the q-variables from U and their least-squares derivatives, with
+ * the same arithmetic as lskum_q_derivatives of an unlimited context (the
  * first-order solve, then inner_iters Jacobi inner iterations), in the global
- * frame, with the 2x2 sums formed on the fly; no limiter. All pointers are
- * caller-owned device memory, in the caller's numbering:
+ * frame, with the 2x2 sums formed on the fly. All pointers are caller-owned
+ * device memory, in the caller's numbering:
  *   n                     number of points, 1 <= n <= LSKUM_NOALLOC_MAX_POINTS
  *   x, y                  float64[n]
- *   nbr_offsets, nbr_idx  int32[n+1], int32[nbr_offsets[n]]: a well-formed CSR
- *                         (the caller's responsibility; a neighbour index outside
- *                         [0, n) is skipped and reported as LSKUM_ERR_CONNECTIVITY)
+ *   nbr_offsets, nbr_idx  int32[n+1], int32[nbr_offsets[n]]: a CSR. nbr_idx must
+ *                         hold nbr_offsets[n] entries (the caller's
+ *                         responsibility: a plain pointer carries no size).
+ *                         A row that runs backwards, leaves [0, nbr_offsets[n]]
+ *                         or has more than LSKUM_MAX_DEGREE entries, and a
+ *                         neighbour index outside [0, n), are skipped by the
+ *                         kernels and reported as LSKUM_ERR_CONNECTIVITY
  *   U                     float64[4*n] conserved state (component-major)
  *   qx, qy                float64[4*n], written
  *   cuda_stream           cudaStream_t, or NULL for the legacy default stream
@@ -334,14 +339,17 @@ int64_t lskum_launch_count(const lskum_ctx *ctx);
  * (21 MB), which every GPU that loads the library holds until the process
  * exits. The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. All calls share the one array: calls whose
- * work overlaps on the GPU (other threads, other streams) race and must be
- * serialised by the caller. The call synchronises the stream at its end to
- * read its status word. A point whose stencil has a singular 2x2
- * least-squares matrix gets non-finite derivatives. Errors: LSKUM_ERR_ARG (n out of range, NULL pointer,
- * inner_iters outside [0, 1000]), LSKUM_ERR_CONNECTIVITY, LSKUM_ERR_NONPHYSICAL
- * (a point with rho <= 0 or p <= 0), LSKUM_ERR_CUDA; message via
- * lskum_last_error(NULL).
+ * before any stream capture. The address is kept for the life of the
+ * process: do not call this on a device after cudaDeviceReset there. All
+ * calls share the one array: calls whose work overlaps on the GPU (other
+ * threads, other streams) race and must be serialised by the caller. The
+ * status words at the head of the array are cleared at the start of every
+ * call; the rest is written before it is read. The call synchronises the
+ * stream at its end to read its status word. A point whose stencil has a
+ * singular 2x2 least-squares matrix gets non-finite derivatives.
+ * Errors: LSKUM_ERR_ARG (n out of range, NULL pointer, inner_iters outside
+ * [0, 1000]), LSKUM_ERR_CONNECTIVITY, LSKUM_ERR_NONPHYSICAL (a point with
+ * rho <= 0 or p <= 0), LSKUM_ERR_CUDA; message via lskum_last_error(NULL).
  */
 #define LSKUM_NOALLOC_MAX_POINTS 131072
 lskum_status lskum_q_derivatives_noalloc(int64_t n, const double *x, const double *y,
@@ -382,6 +390,19 @@ lskum_status lskum_set_tuning(lskum_ctx *ctx, int flux_variant, int qgrad_varian
  * with case k's free stream; cp receives its n_wall values in its contour order.
  */
 lskum_status lskum_case_forces(lskum_ctx *ctx, int k, double *cl, double *cd, double *cp);
+
+/*
+ * Measured arithmetic peak of the current device, for throughput reports (the
+ * paper has no counterpart: these are the denominators of the ALU rooflines of
+ * the flux kernels). kind 0: FP64 fused multiply-add; 1: FP32 fused
+ * multiply-add; 2: packed FP32x2 fused multiply-add (FFMA2). Runs `reps` timed
+ * launches (after one warm-up) of independent multiply-add chains filling
+ * every SM on cuda_stream (NULL: the legacy default stream) and writes the
+ * best rate in GFLOP/s (2 flops per multiply-add) to *gflops. Allocates and
+ * frees a 4 KB device buffer; synchronises. LSKUM_ERR_ARG for a kind outside
+ * 0..2, reps outside 1..100 or a NULL gflops.
+ */
+lskum_status lskum_probe_peak(int kind, int reps, void *cuda_stream, double *gflops);
 
 #define LSKUM_KERNEL_FLUX 0  /* fused flux residual + state update */
 #define LSKUM_KERNEL_QGRAD 1 /* one least-squares q-derivative pass */

@@ -2,11 +2,13 @@
 // statically sized __device__ array, so the call allocates no device memory.
 // It serves callers that cannot allocate where they call from (a caching
 // allocator that owns the GPU's memory, a loop that must not pay the device
-// synchronisation of cudaMalloc/cudaFree, a fixed memory budget).
+// synchronisation of cudaMalloc/cudaFree, a fixed memory budget). The paper
+// has no counterpart; this is a plumbing variant of lskum_q_derivatives.
 //
-// Arithmetic: q of E13 from U, then E15 (first-order least squares, then
-// Jacobi inner iterations with the dq~ of E14) in the global frame, the 2x2
-// sums formed on the fly from the coordinates (no precomputed weights).
+// Arithmetic: the q-variables from U, then the least-squares q-derivatives
+// (the first-order solve, then Jacobi inner iterations on the corrected
+// differences) in the global frame, the 2x2 sums formed on the fly from the
+// coordinates (no precomputed weights).
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
@@ -24,7 +26,7 @@ static constexpr int64_t kNoallocPerPoint = 4 + 8 + 8;
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocHeader + kNoallocPerPoint * LSKUM_NOALLOC_MAX_POINTS];
 
 // status word bits (int view of the header)
-enum : int { NA_NONPHYSICAL = 1, NA_BAD_INDEX = 2 };
+enum : int { NA_NONPHYSICAL = 1, NA_BAD_INDEX = 2, NA_BAD_OFFSETS = 4 };
 
 __global__ void __launch_bounds__(256) k_na_q(int64_t n, Gas gas, const double *__restrict__ U,
                                               double *__restrict__ q, int *status)
@@ -36,7 +38,7 @@ __global__ void __launch_bounds__(256) k_na_q(int64_t n, Gas gas, const double *
     store4(q, p, qq);
 }
 
-// One solve of E15 at every point. g_old == nullptr: first order. Output to
+// One least-squares solve at every point. g_old == nullptr: first order. Output to
 // g_new ([n][8] scratch) or, on the final pass, to qx/qy ([4][n], caller).
 __global__ void __launch_bounds__(128) k_na_grad(int64_t n, const double *__restrict__ x,
                                                  const double *__restrict__ y,
@@ -55,7 +57,13 @@ __global__ void __launch_bounds__(128) k_na_grad(int64_t n, const double *__rest
     const double x0 = x[p], y0 = y[p];
     double sxx = 0.0, sxy = 0.0, syy = 0.0;
     double sxq[4] = {0, 0, 0, 0}, syq[4] = {0, 0, 0, 0};
-    const int e0 = off[p], e1 = off[p + 1];
+    // a row outside [0, nbr_offsets[n]] or running backwards is skipped and
+    // reported, so that idx is only read inside its nbr_offsets[n] entries
+    const int e0 = off[p], e1 = off[p + 1], nnz = off[n];
+    if (e0 < 0 || e1 < e0 || e1 > nnz || e1 - e0 > LSKUM_MAX_DEGREE) {
+        atomicOr(status, NA_BAD_OFFSETS);
+        return;
+    }
     for (int e = e0; e < e1; ++e) {
         const int i = idx[e];
         if (i < 0 || i >= n) {
@@ -98,6 +106,9 @@ __global__ void __launch_bounds__(128) k_na_grad(int64_t n, const double *__rest
 
 // Device address of the scratch array, looked up once per device with that
 // device current (host code only sees a host-side stand-in for the symbol).
+// The address belongs to the device's primary context: the library must not
+// be used on a device after cudaDeviceReset there (the cached address would
+// be stale).
 static std::mutex g_noalloc_mutex;
 static double *g_noalloc_ptr[128];
 
@@ -182,6 +193,10 @@ extern "C" lskum_status lskum_q_derivatives_noalloc(int64_t n, const double *x, 
     static thread_local int st_h[2];
     NA_CK(cudaMemcpyAsync(st_h, status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
+    if (st_h[0] & NA_BAD_OFFSETS)
+        return na_fail(LSKUM_ERR_CONNECTIVITY,
+                       "nbr_offsets is not a CSR row array (a row runs backwards, leaves [0, nbr_offsets[n]] "
+                       "or has more than %d entries)", LSKUM_MAX_DEGREE);
     if (st_h[0] & NA_BAD_INDEX) return na_fail(LSKUM_ERR_CONNECTIVITY, "a neighbour index is outside [0, n)");
     if (st_h[0] & NA_NONPHYSICAL) return na_fail(LSKUM_ERR_NONPHYSICAL, "a state has rho <= 0 or p <= 0");
     return LSKUM_OK;

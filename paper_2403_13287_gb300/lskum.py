@@ -390,22 +390,68 @@ LSKUM_VJP_ACCUMULATE_XY = 1
 LSKUM_VJP_FP32 = 2
 
 
-def q_derivatives_noalloc(x, y, nbr_offsets, nbr_idx, U, qx, qy, gamma=1.4, inner_iters=3,
-                          stream=None):
-    """lskum_q_derivatives_noalloc on caller-owned CUDA tensors (no context,
-    no device allocation): x, y float64[n]; nbr_offsets int32[n+1]; nbr_idx
-    int32[nnz]; U float64[4, n]; qx, qy float64[4, n] written."""
-    import torch
+PROBE_FP64_FMA = 0
+PROBE_FP32_FMA = 1
+PROBE_FP32X2_FMA = 2
+
+
+def probe_peak(kind, reps=5, stream=None):
+    """Measured FMA peak of the current device in GFLOP/s (lskum_probe_peak):
+    kind 0 FP64, 1 FP32, 2 packed FP32x2."""
+    L = load()
+    if not hasattr(L, "_probe_ready"):
+        L.lskum_probe_peak.argtypes = [_int, _int, _p, ctypes.POINTER(ctypes.c_double)]
+        L.lskum_probe_peak.restype = _int
+        L._probe_ready = True
+    g = ctypes.c_double()
+    stream_ptr = _stream_ptr(stream)
+    st = L.lskum_probe_peak(int(kind), int(reps), _p(stream_ptr) if stream_ptr else None, ctypes.byref(g))
+    if st != LSKUM_OK:
+        raise LskumError(st, "lskum_probe_peak failed")
+    return g.value
+
+
+def _noalloc_lib():
     L = load()
     if not hasattr(L, "_noalloc_ready"):
         L.lskum_q_derivatives_noalloc.argtypes = [_i64, _p, _p, _p, _p, _p, ctypes.c_double, _int,
                                                   _p, _p, _p]
         L.lskum_q_derivatives_noalloc.restype = _int
         L._noalloc_ready = True
+    return L
+
+
+def q_derivatives_noalloc(x, y, nbr_offsets, nbr_idx, U, qx, qy, gamma=1.4, inner_iters=3,
+                          stream=None):
+    """lskum_q_derivatives_noalloc on caller-owned CUDA tensors (no context,
+    no device allocation): x, y float64[n]; nbr_offsets int32[n+1]; nbr_idx
+    int32[nnz]; U float64[4, n]; qx, qy float64[4, n] written."""
+    import torch
+    L = _noalloc_lib()
     for t, dt in ((nbr_offsets, torch.int32), (nbr_idx, torch.int32)):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
             raise TypeError("expected a contiguous int32 CUDA tensor")
     n = int(x.shape[0])
+    # sizes and devices: the C entry sees plain pointers and cannot check them
+    for t in (x, y, U, qx, qy):
+        _dev_ptr(t)                       # contiguous float64 CUDA tensors, else TypeError
+    need = ((x, n), (y, n), (nbr_offsets, n + 1), (U, 4 * n), (qx, 4 * n), (qy, 4 * n))
+    for t, size in need:
+        if t.numel() != size:
+            raise LskumError(LSKUM_ERR_ARG, "an array has %d entries where %d are needed" % (t.numel(), size))
+    dev = torch.cuda.current_device()
+    for t in (x, y, nbr_offsets, nbr_idx, U, qx, qy):
+        if t.device.index != dev:
+            raise LskumError(LSKUM_ERR_ARG, "an array is on cuda:%d, the current device is cuda:%d"
+                             % (t.device.index, dev))
+    # the CSR rows: non-decreasing from 0, and nbr_idx long enough for them
+    # (one scalar read back)
+    bad = (nbr_offsets[0] != 0) | (nbr_offsets[1:] < nbr_offsets[:-1]).any()
+    nnz = int(torch.where(bad, torch.full_like(nbr_offsets[-1], -1), nbr_offsets[-1]).item())
+    if nnz < 0:
+        raise LskumError(LSKUM_ERR_CONNECTIVITY, "nbr_offsets does not start at 0 or decreases")
+    if nbr_idx.numel() < nnz:
+        raise LskumError(LSKUM_ERR_ARG, "nbr_idx has %d entries, nbr_offsets[n] = %d" % (nbr_idx.numel(), nnz))
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     st = L.lskum_q_derivatives_noalloc(n, _dev_ptr(x), _dev_ptr(y), _p(nbr_offsets.data_ptr()),
