@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblskum.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["lskum_api.cu", "lskum_kernels.cu", "lskum_setup.cu", "lskum_noalloc.cu", "lskum_mixed.cu",
-           "lskum_adjoint.cu"]
+           "lskum_adjoint.cu", "lskum_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

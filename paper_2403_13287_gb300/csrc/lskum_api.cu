@@ -71,6 +71,10 @@ struct lskum_ctx {
     float2 *s_ga = nullptr;
     float4 *s_gf = nullptr, *gm = nullptr;
     double2 *s_fxw64 = nullptr;
+    // staged flux variants: per tile the neighbours outside it, per slot its staged row
+    int32_t *tile_off = nullptr, *tile_idx = nullptr;
+    uint16_t *s_loc = nullptr;
+    int64_t tile_overflow = 0;     // slots whose neighbour is beyond a tile's staging cap
     double *dt = nullptr, *Rt = nullptr, *Ut = nullptr, *Ucm = nullptr;
     double *norm_part = nullptr;   // residue_parts(n) values: a pair of sums per warp
     double *norm_chunk = nullptr;  // ncases * maxchunks chunk sums of the residue reduction
@@ -151,6 +155,7 @@ struct lskum_ctx {
         MixedGeom g{};
         g.n = n; g.nrm = nrm_f; g.flag = flag; g.dmin = dmin_f; g.off = off;
         g.slice_off = slice_off; g.sidx = s_idx; g.ga = s_ga; g.gm = gm; g.gf = s_gf; g.fxw64 = s_fxw64;
+        g.tile_off = tile_off; g.tile_idx = tile_idx; g.sloc = s_loc;
         if (kinetic) {
             g.ioff = ioff; g.iidx = iidx; g.imask = imask; g.ilsw = ilsw_f; g.igf = igf; g.ifxw64 = ifxw;
             g.qinf = qinf_f; g.pcase = pcase;
@@ -414,6 +419,76 @@ static void rcm_permutation(int64_t n, const int32_t *off, const int32_t *idx, s
         std::reverse(order.begin() + a, order.end());
     }
     perm.assign(order.begin(), order.end());
+}
+
+// Staged flux variants: for every tile of kTile consecutive points (internal
+// numbering), the neighbours outside the tile, each once and in increasing
+// order, and for every SELL slot the row of its neighbour in the tile's
+// staged block: the tile's own points are rows 0..kTile-1, its first
+// kHaloCap outside neighbours rows kTile.., a neighbour beyond that cap is
+// kSlotGlobal (read from global memory). Padding slots get the point's own row.
+static lskum_status build_tiles(lskum_ctx *c, const std::vector<int32_t> &off_h, const std::vector<int32_t> &so)
+{
+    const int64_t n = c->n, nnz = off_h[n];
+    const cudaStream_t s = c->stream;
+    std::vector<int32_t> idx_h(std::max<int64_t>(nnz, 1));
+    std::vector<uint8_t> mask_h(std::max<int64_t>(nnz, 1));
+    if (nnz > 0) {
+        CK(c, cudaMemcpyAsync(idx_h.data(), c->idx, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(c, cudaMemcpyAsync(mask_h.data(), c->mask, nnz * sizeof(uint8_t), cudaMemcpyDeviceToHost, s));
+    }
+    CK(c, cudaStreamSynchronize(s));
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    const int64_t nslot = std::max<int32_t>(so.back(), 1);
+    std::vector<int32_t> toff(ntiles + 1, 0), tidx;
+    tidx.reserve((size_t)ntiles * 96);
+    std::vector<uint16_t> sloc(nslot, 0);
+    std::vector<int32_t> outside;
+    int64_t overflow = 0;
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const int64_t p0 = t * kTile, p1 = std::min<int64_t>(n, p0 + kTile);
+        outside.clear();
+        for (int64_t p = p0; p < p1; ++p)
+            for (int32_t e = off_h[p]; e < off_h[p + 1]; ++e)
+                if (idx_h[e] < p0 || idx_h[e] >= p1) outside.push_back(idx_h[e]);
+        std::sort(outside.begin(), outside.end());
+        outside.erase(std::unique(outside.begin(), outside.end()), outside.end());
+        if ((int64_t)toff[t] + (int64_t)outside.size() > 0x7fffffff)
+            return fail(c, LSKUM_ERR_ARG, "too many stencil entries for the staged tiles");
+        toff[t + 1] = toff[t] + (int32_t)outside.size();
+        tidx.insert(tidx.end(), outside.begin(), outside.end());
+        for (int64_t p = p0; p < p1; ++p) {
+            const int64_t base = so[p >> 5] + (p & 31);
+            const int deg = off_h[p + 1] - off_h[p];
+            const int depth = (so[(p >> 5) + 1] - so[p >> 5]) >> 5;
+            for (int k = 0; k < depth; ++k) {
+                uint16_t v = (uint16_t)(p - p0);
+                if (k < deg) {
+                    const int32_t e = off_h[p] + k, i = idx_h[e];
+                    int row;
+                    if (i >= p0 && i < p1) {
+                        row = (int)(i - p0);
+                    } else {
+                        const int64_t r = std::lower_bound(outside.begin(), outside.end(), i) - outside.begin();
+                        row = r < kHaloCap ? kTile + (int)r : kSlotGlobal;
+                        overflow += r >= kHaloCap;
+                    }
+                    v = (uint16_t)(row | ((mask_h[e] & 0xf) << 12));
+                }
+                sloc[base + 32 * k] = v;
+            }
+        }
+    }
+    c->tile_overflow = overflow;
+    CK(c, dalloc(c, &c->tile_off, ntiles + 1));
+    CK(c, dalloc(c, &c->tile_idx, std::max<int64_t>((int64_t)tidx.size(), 1)));
+    CK(c, dalloc(c, &c->s_loc, nslot));
+    CK(c, cudaMemcpyAsync(c->tile_off, toff.data(), (ntiles + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (!tidx.empty())
+        CK(c, cudaMemcpyAsync(c->tile_idx, tidx.data(), tidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(c->s_loc, sloc.data(), nslot * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+    CK(c, cudaStreamSynchronize(s));
+    return LSKUM_OK;
 }
 
 static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, const double *nx,
@@ -685,6 +760,8 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
         CK(c, cudaFreeAsync(dxy, s));
         CK(c, cudaFreeAsync(lsw, s));
         CK(c, cudaFreeAsync(fxw, s));
+        lskum_status st = build_tiles(c, off_h, so);
+        if (st != LSKUM_OK) return st;
         CK(c, cudaStreamSynchronize(s));
     }
     CK(c, dalloc(c, &c->dt, n));

@@ -377,6 +377,19 @@ __device__ __forceinline__ void recon_pair(const float qi[4], const float gi[8],
     }
 }
 
+// q and grad q of row r of a staged tile (shared memory)
+__device__ __forceinline__ void row_f(const float4 *sq, const float4 *sg, int r, bool second, float q[4],
+                                      float gq[8])
+{
+    const float4 a = sq[r];
+    q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+    if (second) {
+        const float4 b = sg[2 * r], c = sg[2 * r + 1];
+        gq[0] = b.x; gq[1] = b.y; gq[2] = b.z; gq[3] = b.w;
+        gq[4] = c.x; gq[5] = c.y; gq[6] = c.z; gq[7] = c.w;
+    }
+}
+
 // One member's term of E11 in FP32 (the weights' FP64 copy w64[e] at points
 // with an FP64 closure), frame (t, n) of P_0, R in the order [mass,
 // s-momentum, n-momentum, energy]; see edge_residual of the FP64 kernels.
@@ -423,13 +436,41 @@ __device__ __forceinline__ void edge_residual_f(const float2 qt[4], uint32_t m, 
 }
 
 // PF: software-pipelined neighbour loop (the next slot's record, index and
-// neighbour values are loaded while the current slot's fluxes are evaluated)
-template <int THREADS, int MINB, bool PF, bool KIN>
+// neighbour values are loaded while the current slot's fluxes are evaluated).
+// STAGE: the CTA is one tile of kTile points. It first copies the q and
+// grad q of its own points and of up to kHaloCap neighbours outside the tile
+// (each once, the list made at create) into shared memory with independent
+// loads, then runs the neighbour loop on those rows: no gathered value is
+// read from global memory inside the loop, only the streamed slot records
+// (a neighbour beyond the cap is read from global memory as before).
+template <int THREADS, int MINB, bool PF, bool KIN, bool STAGE = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxParams P)
 {
     const MixedGeom &g = P.g;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = p < g.n;
+    const float4 *sq = nullptr, *sg = nullptr;
+    if constexpr (STAGE) {
+        static_assert(THREADS == kTile, "a staged CTA is one tile");
+        __shared__ float4 s_q[kTile + kHaloCap];
+        __shared__ float4 s_g[2 * (kTile + kHaloCap)];
+        const int h0 = g.tile_off[blockIdx.x];
+        const int nh = min(g.tile_off[blockIdx.x + 1] - h0, kHaloCap);
+        const bool second = P.order == 2;
+        for (int r = threadIdx.x; r < kTile + nh; r += kTile) {
+            const int64_t i = r < kTile ? (int64_t)blockIdx.x * kTile + r : (int64_t)g.tile_idx[h0 + r - kTile];
+            if (i < g.n) {
+                s_q[r] = __ldg(reinterpret_cast<const float4 *>(P.q) + i);
+                if (second) {
+                    s_g[2 * r] = __ldg(reinterpret_cast<const float4 *>(P.qg) + 2 * i);
+                    s_g[2 * r + 1] = __ldg(reinterpret_cast<const float4 *>(P.qg) + 2 * i + 1);
+                }
+            }
+        }
+        __syncthreads();
+        sq = s_q;
+        sg = s_g;
+    }
     uint8_t fl = FLAG_FARFIELD;
     if (live) fl = g.flag[p];
     const uint8_t flag = fl & 3;
@@ -443,16 +484,51 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
         const float2 n0 = g.nrm[p];
         const float tx = n0.y, ty = -n0.x;
         float q0[4], g0[8];
-        load4f(P.q, p, q0);
         const bool second = P.order == 2;
-        if (second) load8f(P.qg, p, g0);
+        if constexpr (STAGE) {
+            row_f(sq, sg, threadIdx.x, second, q0, g0);
+        } else {
+            load4f(P.q, p, q0);
+            if (second) load8f(P.qg, p, g0);
+        }
         float R[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         double R64[4] = {0.0, 0.0, 0.0, 0.0};
         bool ok = true;
         float4 rec_n = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         int32_t im_n = 0;
         float q_n[4] = {0, 0, 0, 0}, g_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if constexpr (PF) {
+        if constexpr (STAGE) {
+            // only the slot records are prefetched; the rows are in shared memory
+            uint16_t sl_n = 0;
+            if (deg > 0) {
+                rec_n = g.gf[base];
+                sl_n = g.sloc[base];
+            }
+            for (int s = 0; s < deg; ++s) {
+                const int64_t e = base + 32 * s;
+                const float4 rec = rec_n;
+                const uint16_t sl = sl_n;
+                if (s + 1 < deg) {
+                    rec_n = g.gf[e + 32];
+                    sl_n = g.sloc[e + 32];
+                }
+                const float2 w = make_float2(rec.z, rec.w);
+                if (w.x == 0.0f && w.y == 0.0f) continue;
+                const uint32_t m = (uint32_t)sl >> 12;
+                const int row = sl & kSlotRowMask;
+                float qi[4], gi[8];
+                if (row != kSlotGlobal) {
+                    row_f(sq, sg, row, second, qi, gi);
+                } else {
+                    const int i = g.sidx[e] & kSlotIndexMask;
+                    load4f(P.q, i, qi);
+                    if (second) gather8f(P.qg, i, gi);
+                }
+                float2 qt[4];
+                recon_pair(qi, gi, q0, g0, make_float2(rec.x, rec.y), second, qt);
+                edge_residual_f(qt, m, w, fp64, g.fxw64, e, n0, tx, ty, P.inv_gm1, P.g14, R, R64, ok);
+            }
+        } else if constexpr (PF) {
             if (deg > 0) {
                 rec_n = g.gf[base];
                 im_n = g.sidx[base];
@@ -461,7 +537,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
                 if (second) gather8f(P.qg, i, g_n);
             }
         }
-        for (int s = 0; s < deg; ++s) {
+        if constexpr (!STAGE) for (int s = 0; s < deg; ++s) {
             const int64_t e = base + 32 * s;
             float2 qt[4];
             uint32_t m;
@@ -665,10 +741,11 @@ static cudaError_t qgrad_v(const MixedGeom &g, const float *q, const float *qg_o
     return cudaGetLastError();
 }
 
-template <int T, int M, bool PF, bool KIN>
+template <int T, int M, bool PF, bool KIN, bool STAGE = false>
 static cudaError_t flux_v(const MixedFluxParams &P, cudaStream_t s)
 {
-    k_flux_update_mixed<T, M, PF, KIN><<<(unsigned)((P.g.n + T - 1) / T), T, 0, s>>>(P);
+    if (STAGE && (!P.g.tile_off || !P.g.tile_idx || !P.g.sloc)) return cudaErrorInvalidValue;
+    k_flux_update_mixed<T, M, PF, KIN, STAGE><<<(unsigned)((P.g.n + T - 1) / T), T, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -686,7 +763,10 @@ struct VariantTable {
         flux_v<128, 8, false, K>, flux_v<256, 4, false, K>, flux_v<128, 7, true, K>,  flux_v<64, 14, true, K>,
         flux_v<256, 3, true, K>,  flux_v<128, 6, true, K>,  flux_v<128, 8, true, K>,  flux_v<256, 4, true, K>,
         flux_v<128, 5, true, K>,  flux_v<128, 4, true, K>,  flux_v<64, 8, true, K>,   flux_v<96, 6, true, K>,
-        flux_v<128, 3, true, K>};
+        flux_v<128, 3, true, K>,
+        // staged tiles (one 64-point tile per CTA, rows in shared memory)
+        flux_v<64, 14, true, K, true>, flux_v<64, 16, true, K, true>, flux_v<64, 12, true, K, true>,
+        flux_v<64, 10, true, K, true>, flux_v<64, 8, true, K, true>};
 };
 static const QgradFn *const kQgradVariants[2] = {VariantTable<false>::qgrad, VariantTable<true>::qgrad};
 static const FluxFn *const kFluxVariants[2] = {VariantTable<false>::flux, VariantTable<true>::flux};
@@ -694,10 +774,16 @@ static constexpr int kNumQgradVariants = sizeof VariantTable<false>::qgrad / siz
 static constexpr int kNumFluxVariants = sizeof VariantTable<false>::flux / sizeof(FluxFn);
 static const int kQgradShape[][2] = {{128, 8}, {64, 16}, {256, 4}, {128, 6}, {256, 3}, {96, 10}};
 // flux shapes 6-11 repeat 0-5 with the software-pipelined neighbour loop,
-// 12-16 give that loop more registers
+// 12-16 give that loop more registers, 17-21 stage each tile's rows in
+// shared memory
+static constexpr int kFirstStagedFlux = 17;
 static const int kFluxShape[][2] = {{128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4},
                                     {128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4},
-                                    {128, 5}, {128, 4}, {64, 8},  {96, 6},  {128, 3}};
+                                    {128, 5}, {128, 4}, {64, 8},  {96, 6},  {128, 3},
+                                    {64, 14}, {64, 16}, {64, 12}, {64, 10}, {64, 8}};
+static_assert(sizeof kFluxShape / sizeof kFluxShape[0] == kNumFluxVariants, "one shape per flux variant");
+
+int mixed_first_staged_variant() { return kFirstStagedFlux; }
 
 int mixed_variants(int kernel_class)
 {

@@ -36,9 +36,22 @@ struct MixedGeom {
     const double2 *__restrict__ ifxw64;   // FP64 sub-stencil weights of the image
     const float *__restrict__ qinf;       // [cases][4] q of each case's free stream
     const uint16_t *__restrict__ pcase;   // per point: its case in a batch, or nullptr
+    // staged flux variants: tiles of kTile points (tile t = points
+    // [kTile t, kTile t + kTile)); the neighbours outside a tile, each once,
+    // at tile_idx[tile_off[t] ..] (the first kHaloCap are staged); per slot
+    // sloc = its row in the tile's staged block (own points 0..kTile-1, then
+    // the staged outside neighbours) | sub-stencil bits << 12, the row being
+    // kSlotGlobal where the neighbour was not staged
+    const int32_t *__restrict__ tile_off;
+    const int32_t *__restrict__ tile_idx;
+    const uint16_t *__restrict__ sloc;
 };
 
 static constexpr int32_t kSlotIndexMask = 0x0fffffff;  // mixed layout: n < 2^28
+static constexpr int kTile = 64;                        // points per staged tile (= its CTA)
+static constexpr int kHaloCap = 160;                    // outside neighbours staged per tile
+static constexpr uint16_t kSlotGlobal = 0x1ff;          // sloc row: not staged
+static constexpr uint16_t kSlotRowMask = 0x1ff;
 
 struct MixedFluxParams {
     MixedGeom g;
@@ -68,6 +81,9 @@ cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, fl
 cudaError_t launch_sell_fill(int64_t n, const int32_t *off, const int32_t *slice_off, const int32_t *idx,
                              const uint8_t *mask, const float2 *dxy, const float2 *lsw, const float2 *fxw,
                              const double2 *fxw64, const MixedGeom &m, cudaStream_t s);
+// first staged flux variant (the variants from there on read MixedGeom's
+// tile arrays)
+int mixed_first_staged_variant();
 // launch-shape variants (threads per block, minimum resident blocks per SM);
 // kernel_class 0 = flux, 1 = q-derivatives; variant 0 is the default
 int mixed_variants(int kernel_class);
