@@ -49,13 +49,27 @@ def parse():
     ap.add_argument("--reorder", type=int, default=1, help="0 input order, 1 Morton, 2 reverse Cuthill-McKee")
     ap.add_argument("--shuffle", type=int, default=1, help="present the cloud in random point order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ref-extra", dest="ref_extra", action="store_false",
+                    help="reference arm: skip the serial and all-core 160k-point oracle runs")
     ap.add_argument("--single-form", action="store_true", help="time only --precision's form")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solves form")
+    ap.add_argument("--no-error", action="store_true", help="skip the mixed form's error against FP64")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint form")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the forward-Euler, input-order and 10M-point forms")
     ap.add_argument("--tuning", default="auto",
                     help="mixed launch shapes: 'auto' (autotune on the cloud) or 'F,Q' (flux, q-derivative variant)")
+    ap.add_argument("--residuals-only", type=int, default=0, metavar="N",
+                    help="no timing: create the configured form (--precision, --tuning), set the timed start "
+                         "state and evaluate the residual N times (a short program for ncu captures)")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="instead of timing: the mixed form's converged error against FP64 at 160k and 2.5M points")
+    ap.add_argument("--acc-iters-160k", type=int, default=60000)
+    ap.add_argument("--acc-cfl-160k", type=float, default=1.0)
+    ap.add_argument("--acc-iters-2p5m", type=int, default=60000)
+    ap.add_argument("--acc-cfl-2p5m", type=float, default=0.8)
+    ap.add_argument("--acc-iters-fp64-restart", type=int, default=20000)
+    ap.add_argument("--acc-chunk", type=int, default=2000)
     ap.add_argument("--batch-clouds", type=int, default=16)
     ap.add_argument("--batch-conditions", type=int, default=3)
     return ap.parse_args()
@@ -204,100 +218,139 @@ FP64_PEAK_GINSTR = 304 * 2.070
 FP64_PEAK_GFLOPS = 2 * FP64_PEAK_GINSTR
 
 
-def roofline_fp64(flux_avg_s, n, dbar, fb, achieved_gbs, peaks, peak_src):
+def roofline_fp64(flux_avg_s, n, dbar, fb, achieved_gbs, peaks, peak_src, fp64_measured=None):
     """The FP64 flux kernel is bound by the FP64 pipe: its issue rate of FP64
     instructions (a DMUL or DADD takes a slot as a DFMA does) against the
-    pipe's 304 per cycle; the flop rate and the HBM view beside it."""
+    pipe's 304 per cycle; the same rate against the FP64 multiply-add rate
+    measured on this GPU (lskum_probe_peak, GFLOP/s / 2); the flop rate and
+    the HBM view beside it, the latter also as flat keys."""
     instr = FP64_INSTR_PER_EDGE_FLUX * dbar * n
     flops = FP64_FLOPS_PER_EDGE_FLUX * dbar * n
     achieved = instr / flux_avg_s / 1e9
     gflops = flops / flux_avg_s / 1e9
-    return {"bound": "alu", "kernel": "k_flux_update", "achieved": achieved,
-            "peak": FP64_PEAK_GINSTR, "unit": "G FP64 instructions/s", "frac": achieved / FP64_PEAK_GINSTR,
-            "traffic": FLUX_DRAM_BYTES_PER_POINT * n,
-            "fp64_instructions_per_launch": instr, "flops_per_launch": flops,
-            "gflops": gflops, "gflops_peak": FP64_PEAK_GFLOPS, "gflops_frac": gflops / FP64_PEAK_GFLOPS,
-            "avg_launch_ms": flux_avg_s * 1e3,
-            "peak_source": "derived: 304 FP64 instructions/cycle x 2.07 GHz (ncu unit count, max SM clock)",
-            "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved_gbs / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": fb,
-                    "peak_source": peak_src}}
+    r = {"bound": "alu", "kernel": "k_flux_update", "achieved": achieved,
+         "peak": FP64_PEAK_GINSTR, "unit": "G FP64 instructions/s", "frac": achieved / FP64_PEAK_GINSTR,
+         "traffic": FLUX_DRAM_BYTES_PER_POINT * n,
+         "fp64_instructions_per_launch": instr, "flops_per_launch": flops,
+         "gflops": gflops, "gflops_peak": FP64_PEAK_GFLOPS, "gflops_frac": gflops / FP64_PEAK_GFLOPS,
+         "avg_launch_ms": flux_avg_s * 1e3,
+         "peak_source": "derived: 304 FP64 instructions/cycle x 2.07 GHz (ncu unit count, max SM clock)",
+         "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
+         "hbm_frac": achieved_gbs / peaks["hbm_gbs"], "hbm_algorithmic_bytes_per_launch": fb,
+         "hbm_traffic_bytes_per_launch": FLUX_DRAM_BYTES_PER_POINT * n, "hbm_peak_source": peak_src,
+         "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": achieved_gbs / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": fb,
+                 "peak_source": peak_src}}
+    if fp64_measured:
+        r["fp64_fma_measured_gflops"] = fp64_measured
+        r["frac_of_measured_fma_rate"] = achieved / (fp64_measured / 2.0)
+        r["gflops_frac_of_measured"] = gflops / fp64_measured
+    return r
 
 
 # ----------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle on the host cores
 # ----------------------------------------------------------------------------
-def wedge_sample(cloud, shuffled, frac=8, seed=2403_13287):
-    """A bounded sample of the workload for the CPU oracle: the points of the
-    first W/frac grid rays (all layers, wall to far field) of the cloud, as a
-    cloud of its own in the cloud's own (shuffled) point order. Points that
-    lose a neighbour to the cut are far-field points of the sample (no
-    residual of their own), so every point that is evaluated keeps its whole
-    stencil."""
-    import numpy as np
-    W, L, n = cloud["W"], cloud["L"], cloud["n"]
-    inv = np.arange(n)
-    if shuffled:
-        perm = np.random.Generator(np.random.PCG64(seed + 1)).permutation(n)   # as cloudgen's shuffle
-        inv[perm] = np.arange(n)
-    old = (np.arange(L + 1)[:, None] * W + np.arange(W // frac)[None, :]).ravel()
-    pts = np.sort(inv[old])
-    loc = np.full(n, -1, dtype=np.int64)
-    loc[pts] = np.arange(len(pts))
-    off, idx = cloud["nbr_offsets"], cloud["nbr_idx"]
-    rows, flags = [], cloud["flags"][pts].copy()
-    for k, p in enumerate(pts):
-        nb = loc[idx[off[p]:off[p + 1]]]
-        if np.any(nb < 0):
-            flags[k] = 2
-        rows.append(nb[nb >= 0])
-    sub_off = np.zeros(len(pts) + 1, np.int32)
-    sub_off[1:] = np.cumsum([len(r) for r in rows])
-    return {"n": len(pts), "x": cloud["x"][pts], "y": cloud["y"][pts], "nx": cloud["nx"][pts],
-            "ny": cloud["ny"][pts], "flags": flags.astype(np.int32), "nbr_offsets": sub_off,
-            "nbr_idx": np.concatenate(rows).astype(np.int32), "wall_order": np.zeros(0, np.int32)}, pts
+def host_cpu():
+    """(logical CPUs this process may use, CPU model name)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return cores, model or platform.machine()
+
+
+def oracle_iterations(cloud, mask, U, args, iters, threads):
+    """Time `iters` single iterations of the oracle's solver loop (timestep,
+    the scheme's residual evaluations, the update, the residue) on `threads`
+    host threads; returns the per-iteration wall times and the final state."""
+    import oracle
+    oracle.set_threads(threads)
+    scheme = 1 if args.scheme == "rk4" else 0
+    times = []
+    for _ in range(iters):
+        t0 = time.perf_counter()
+        U, _ = oracle.solve(cloud, mask, U, 1, order=args.order, inner=args.inner, scheme=scheme, cfl=args.cfl,
+                            mach=args.mach, aoa_deg=args.aoa, limiter=args.limiter)
+        times.append(time.perf_counter() - t0)
+    return times, U
 
 
 def run_reference(args, rank, world):
+    """The FP64 CPU oracle on this host's cores, on the whole configured
+    cloud: every step is one full iteration of the oracle's solver loop,
+    with the points of each pass shared out among all host threads (its
+    OpenMP build, bitwise the serial one). Also reported: the serial oracle
+    and the all-core oracle on the 160k-point cloud (median of 3 runs each)."""
     if rank != 0:
         return 0
-    import numpy as np
-    import oracle
-    from paper_2403_13287_gb300.cloudgen import CLOUDS, naca0012_cloud
+    import statistics
 
+    import oracle
+    from paper_2403_13287_gb300.cloudgen import CLOUDS, naca0012_cloud, smooth_state
+
+    cores, model = host_cpu()
     W, L = CLOUDS[args.workload]
     cloud = naca0012_cloud(W, L, shuffle=bool(args.shuffle))
     n = cloud["n"]
-    from paper_2403_13287_gb300.cloudgen import smooth_state
+    mask = oracle.split_stencils(cloud)
     U = smooth_state(cloud, args.mach, args.aoa, amp=0.05, seed=7)
-    # each step: one residual evaluation of a bounded sample (1/8 of the rays)
-    sub, pts = wedge_sample(cloud, bool(args.shuffle))
-    mask = oracle.split_stencils(sub)
-    Us = np.ascontiguousarray(U[:, pts])
-    evals = 4 if args.scheme == "rk4" else 1
-    times = []
-    for it in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        oracle.residual(sub, mask, Us, order=args.order, inner=args.inner, limiter=args.limiter)
-        dt = time.perf_counter() - t0
-        if it >= args.warmup:
-            times.append(dt)
-    t_res = sum(times) / len(times)
-    value = sub["n"] / (evals * t_res)
-    sample = ("one residual evaluation (q_variables, q_derivatives with %d inner iterations, "
-              "flux_residual) per step over a %d-point sample of the %d-point cloud (the first 1/8 of "
-              "its grid rays, wall to far field, in the cloud's own point order), scaled by 1/%d for one "
-              "%s iteration" % (args.inner, sub["n"], n, evals, args.scheme.upper()))
+    threads = oracle.set_threads(cores)
+    _, U = oracle_iterations(cloud, mask, U, args, args.warmup, threads)
+    t0 = time.perf_counter()
+    times, U = oracle_iterations(cloud, mask, U, args, args.steps, threads)
+    total = time.perf_counter() - t0
+    value = n * args.steps / total
+    # the 160k-point cloud: serial (2 iterations) and all cores (10), median of 3
+    extra = {}
+    W2, L2 = CLOUDS["naca0012_160k"]
+    c2 = naca0012_cloud(W2, L2, shuffle=bool(args.shuffle)) if args.ref_extra else None
+    m2 = oracle.split_stencils(c2) if c2 else None
+    U2 = smooth_state(c2, args.mach, args.aoa, amp=0.05, seed=7) if c2 else None
+    for key, thr, its in ((("serial_160k", 1, 2), ("all_cores_160k", threads, 10)) if c2 else ()):
+        runs = []
+        for _ in range(3):
+            ts, _ = oracle_iterations(c2, m2, U2, args, its, thr)
+            runs.append(c2["n"] * its / sum(ts))
+        extra[key] = {"value": statistics.median(runs), "unit": UNIT, "threads": thr, "iterations": its,
+                      "runs": runs, "points": int(c2["n"])}
+    oracle.set_threads(1)
+    sample = ("the whole %d-point cloud, one full %s iteration of the oracle's solver loop per step "
+              "(timestep, %d residual evaluations with q_derivatives (%d inner iterations) and "
+              "flux_residual, the update, the residue) on %d host threads (OpenMP over points, bitwise "
+              "the serial oracle); %s" % (n, args.scheme.upper(), 4 if args.scheme == "rk4" else 1, args.inner,
+                                          threads, model))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t_res * evals * n / sub["n"], "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
         "config": {"workload": args.workload, "points": n, "order": args.order,
                    "inner_iters": args.inner, "limiter_K": args.limiter, "scheme": args.scheme, "mach": args.mach,
-                   "aoa_deg": args.aoa},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                   "aoa_deg": args.aoa, "cfl": args.cfl},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "nproc": cores, "cpu_model": model,
+                         "ms_per_iteration_median": 1e3 * statistics.median(times)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_160k": extra,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -322,18 +375,20 @@ def replicas_value(points, steps, ms, world):
 
 
 def cpu_baseline_sample(cloud, mask, args):
-    """The oracle as it stands, on one host core: one residual evaluation of
-    the full cloud (about 10-30 s), scaled to an iteration."""
-    import oracle
+    """The oracle as it stands on all host cores (its OpenMP build, bitwise
+    the serial one): one full iteration of its solver loop over the whole
+    cloud from the timed form's start state."""
     from paper_2403_13287_gb300.cloudgen import smooth_state
+    cores, model = host_cpu()
     U = smooth_state(cloud, args.mach, args.aoa, amp=0.05, seed=7)
-    t0 = time.perf_counter()
-    oracle.residual(cloud, mask, U, order=args.order, inner=args.inner, limiter=args.limiter)
-    t = time.perf_counter() - t0
-    evals = 4 if args.scheme == "rk4" else 1
-    return {"value": cloud["n"] / (evals * t), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one residual evaluation of all %d points (%.1f s), scaled by 1/%d for one %s "
-                      "iteration" % (cloud["n"], t, evals, args.scheme.upper())}
+    import oracle
+    threads = oracle.set_threads(cores)
+    times, _ = oracle_iterations(cloud, mask, U, args, 1, threads)
+    oracle.set_threads(1)
+    return {"value": cloud["n"] / times[0], "unit": UNIT, "cores": threads, "kind": "oracle",
+            "nproc": cores, "cpu_model": model,
+            "sample": "one full %s iteration of the oracle's solver loop over all %d points (%.1f s) on %d host "
+                      "threads" % (args.scheme.upper(), cloud["n"], times[0], threads)}
 
 
 # ----------------------------------------------------------------------------
@@ -430,7 +485,7 @@ MIXED_FLUX_WARP_INSTR_PER_EDGE = 61136978 / 5167022
 ISSUE_PEAK_GINSTR = 152 * 4 * 2.070
 
 
-def form_summary(args, r, n, dbar, world, precision, peaks, peak_src):
+def form_summary(args, r, n, dbar, world, precision, peaks, peak_src, probes=None):
     flux_avg_s = (r["flux_ms"] / max(r["flux_n"], 1)) / 1e3
     if precision == "mixed":
         fb = algorithmic_bytes_per_point_mixed("flux", dbar, args.order, args.scheme) * n
@@ -473,12 +528,246 @@ def form_summary(args, r, n, dbar, world, precision, peaks, peak_src):
     else:
         fb = algorithmic_bytes_per_point("flux", dbar, args.order, args.scheme) * n
         gbs = fb / flux_avg_s / 1e9
-        roofline = roofline_fp64(flux_avg_s, n, dbar, fb, gbs, peaks, peak_src)
-    return {"value": replicas_value(n, args.steps, r["ms"], world), "ms_per_step": r["ms"] / args.steps,
+        roofline = roofline_fp64(flux_avg_s, n, dbar, fb, gbs, peaks, peak_src,
+                                 (probes or {}).get("fp64_fma_gflops"))
+    value = replicas_value(n, args.steps, r["ms"], world)
+    return {"value": value, "edge_iterations_per_s": value * dbar, "ms_per_step": r["ms"] / args.steps,
             "dtype": "f32/f64 mixed" if precision == "mixed" else "f64", "roofline": roofline,
             "kernels": {"k_flux_update": {"launches": r["flux_n"], "total_ms": r["flux_ms"]},
                         "k_qgrad": {"launches": r["qg_n"], "total_ms": r["qg_ms"]}},
             "gpu_launches": r["launches"]}
+
+
+def rel(a, b, scale=None):
+    s = abs(b) if scale is None else abs(scale)
+    return abs(a - b) / s if s > 0 else None
+
+
+def compare_forms(cloud, mach, aoa, cfl, limiter, iters, order, inner, tuning, U0, stream):
+    """The mixed form against the FP64 form from the same start state after
+    `iters` iterations: Cl, Cd (relative; at alpha = 0, Cl against |Cd|), the
+    wall Cp, the residue histories and the states; and the residual of both
+    forms at the FP64 end state."""
+    import numpy as np
+    import torch
+
+    from paper_2403_13287_gb300 import lskum
+    out = {}
+    res = {}
+    for prec in (0, 1):
+        s = lskum.Solver(cloud, order=order, inner_iters=inner, time_scheme=1, cfl=cfl, mach=mach, aoa_deg=aoa,
+                         reorder=1, limiter_K=limiter, precision=prec, stream=stream)
+        if prec == 1 and tuning:
+            s.set_tuning(tuning["flux_variant"], tuning["qgrad_variant"])
+        if U0 is not None:
+            s.set_state(U0)
+        h = s.step(iters)
+        cl, cd, cp = s.forces()
+        res[prec] = {"solver": s, "hist": h, "cl": cl, "cd": cd, "cp": cp, "U": s.get_state()}
+    f, m = res[0], res[1]
+    Ud = torch.from_numpy(f["U"]).cuda()
+    R64 = f["solver"].residual(Ud).cpu().numpy()
+    Rm = m["solver"].residual(Ud).cpu().numpy()
+    for r in res.values():
+        r["solver"].close()
+    # at alpha = 0 the lift vanishes by symmetry (up to the cloud's jitter):
+    # its error is measured against |Cd|
+    small_cl = aoa == 0.0
+    h64, hm = f["hist"], m["hist"]
+    # the residue histories are compared while the FP64 residue is above the
+    # mixed form's FP32 floor (1e-4 of its maximum)
+    live = h64 > 1e-4 * h64.max()
+    live[0] = False
+    out.update({
+        "iterations": iters, "cl_fp64": f["cl"], "cd_fp64": f["cd"], "cl_mixed": m["cl"], "cd_mixed": m["cd"],
+        "cl_rel_err": rel(m["cl"], f["cl"], f["cd"] if small_cl else None),
+        "cl_err_scale": "|Cd| (Cl ~ 0)" if small_cl else "|Cl|",
+        "cd_rel_err": rel(m["cd"], f["cd"]),
+        "cp_max_abs_err": float(np.max(np.abs(m["cp"] - f["cp"]))),
+        "residue_history_max_rel_gap": float(np.max(np.abs(hm[live] - h64[live]) / h64[live])),
+        "residue_history_compared_iterations": int(live.sum()),
+        "residue_last_fp64": float(h64[-1]), "residue_last_mixed": float(hm[-1]),
+        "residue_drop_fp64": float(h64[-1] / h64.max()), "residue_drop_mixed": float(hm[-1] / hm.max()),
+        "state_max_rel_err": float(np.max(np.abs(m["U"] - f["U"]) / (np.abs(f["U"]) + 1e-3))),
+        "residual_at_fp64_state": {"max_abs_err_over_max_abs": float(np.abs(Rm - R64).max() / np.abs(R64).max()),
+                                   "rel_l2": float(np.linalg.norm(Rm - R64) / np.linalg.norm(R64))},
+    })
+    return out
+
+
+def summary_of(line, forms):
+    """The headline figures of every form in a few flat keys (printed last on
+    the line, so a truncated tail still shows them)."""
+    out = {"value": line["value"], "edge_iterations_per_s": line.get("edge_iterations_per_s"),
+           "roofline_frac": line["roofline"].get("frac"), "roofline_hbm_frac": line["roofline"].get("hbm_frac")}
+    for k in ("fp64", "mixed"):
+        f = forms.get(k)
+        if f:
+            out[k + "_value"] = f["value"]
+            out[k + "_ms_per_step"] = f["ms_per_step"]
+    mx = forms.get("mixed")
+    if mx:
+        ro = mx["roofline"]
+        fl = ro if ro.get("kernel") == "k_flux_update_mixed" else ro.get("other", {})
+        qg = ro if ro.get("kernel") == "k_qgrad_mixed" else ro.get("other", {})
+        out["mixed_flux_hbm_frac"] = fl.get("frac")
+        out["mixed_flux_ms_per_launch"] = fl.get("avg_launch_ms")
+        out["mixed_qgrad_hbm_frac"] = qg.get("frac")
+        err = mx.get("error")
+        if err:
+            c = err["converged_10k"]
+            out["mixed_converged_cl_rel_err"] = c["cl_rel_err"]
+            out["mixed_converged_cd_rel_err"] = c["cd_rel_err"]
+            out["mixed_converged_cp_max_abs_err"] = c["cp_max_abs_err"]
+            b = err["bench_cloud_after_timed_steps"]
+            out["mixed_residual_rel_l2_err"] = b["residual_at_fp64_state"]["rel_l2"]
+            out["mixed_cd_rel_err_after_timed_steps"] = b["cd_rel_err"]
+    for k in ("mixed_speedup_vs_fp64", "batched_speedup_vs_fp64"):
+        if k in forms:
+            out[k] = forms[k]
+    if "batched" in forms:
+        out["batched_value"] = forms["batched"]["value"]
+        out["batched_speedup_vs_sequential"] = forms["batched"]["speedup_vs_sequential"]
+    if "mixed_10m" in forms:
+        out["mixed_10m_value"] = forms["mixed_10m"]["value"]
+    cb = line.get("cpu_baseline")
+    if cb:
+        out["cpu_baseline_value"] = cb["value"]
+        out["cpu_baseline_cores"] = cb["cores"]
+    return out
+
+
+def measure_mixed_error(args, cloud, tuning, stream):
+    """The error of the mixed form beside its speedup: on the bench cloud
+    after the warm-up plus timed iterations from the timed start state, and
+    on a 10k-point cloud under the same conditions (CFL 1.5) run until the
+    residue has fallen by more than eight decades (converged Cl, Cd, Cp)."""
+    from paper_2403_13287_gb300.cloudgen import naca0012_cloud, smooth_state
+    U0 = smooth_state(cloud, args.mach, args.aoa, amp=0.05, seed=7)
+    short = compare_forms(cloud, args.mach, args.aoa, args.cfl, args.limiter, args.warmup + args.steps,
+                          args.order, args.inner, tuning, U0, stream)
+    small = naca0012_cloud(128, 77, seed=11)
+    conv = compare_forms(small, args.mach, args.aoa, 1.5, args.limiter, 12000, args.order, args.inner, None,
+                         None, stream)
+    conv["cloud"] = "naca0012 128x77 (9,984 points), seed 11, from the free stream, CFL 1.5"
+    return {"bench_cloud_after_timed_steps": short, "converged_10k": conv}
+
+
+def converge(solver, iters, chunk):
+    """Step `solver` `iters` iterations in chunks; the residue history and
+    (iteration, Cl, Cd) after every chunk."""
+    import numpy as np
+    hist, forces = [], []
+    done = 0
+    while done < iters:
+        h = solver.step(min(chunk, iters - done))
+        done += len(h)
+        hist.append(h)
+        cl, cd, _ = solver.forces(want_cp=False)
+        forces.append((done, cl, cd))
+    return np.concatenate(hist), forces
+
+
+def run_residuals_only(args):
+    """Evaluate the residual of the configured form args.residuals_only times
+    from the timed start state (a small, fixed program to profile)."""
+    import torch
+
+    from paper_2403_13287_gb300 import lskum
+    from paper_2403_13287_gb300.cloudgen import CLOUDS, naca0012_cloud, smooth_state
+    torch.cuda.set_device(0)
+    W, L = CLOUDS[args.workload]
+    cloud = naca0012_cloud(W, L, shuffle=bool(args.shuffle))
+    s = lskum.Solver(cloud, order=args.order, inner_iters=args.inner, time_scheme=1 if args.scheme == "rk4" else 0,
+                     cfl=args.cfl, mach=args.mach, aoa_deg=args.aoa, reorder=args.reorder, limiter_K=args.limiter,
+                     precision=1 if args.precision == "mixed" else 0)
+    if args.precision == "mixed" and args.tuning != "auto":
+        fv, qv = (int(v) for v in args.tuning.split(","))
+        s.set_tuning(fv, qv)
+    U = torch.from_numpy(smooth_state(cloud, args.mach, args.aoa, amp=0.05, seed=7)).cuda()
+    for _ in range(args.residuals_only):
+        s.residual(U)
+    torch.cuda.synchronize()
+    s.close()
+    print(json.dumps({"residuals": args.residuals_only, "workload": args.workload, "points": int(cloud["n"]),
+                      "precision": args.precision, "tuning": args.tuning}))
+    return 0
+
+
+def run_accuracy(args):
+    """The mixed form's accuracy at convergence against the FP64 form on the
+    160k- and 2.5M-point clouds (second order, 3 inner iterations, RK4,
+    M 1.2, alpha 0, limiter K = 1): FP64 and mixed from the free stream on
+    the 160k cloud; on the 2.5M cloud the mixed form from the free stream,
+    then the FP64 form continued from the mixed form's converged state until
+    its own forces settle. Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_2403_13287_gb300 import lskum
+    from paper_2403_13287_gb300.cloudgen import CLOUDS, naca0012_cloud
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    mach, aoa, lim = args.mach, args.aoa, args.limiter
+    out = {"metric": "mixed-precision error against FP64 at convergence", "mach": mach, "aoa_deg": aoa,
+           "limiter_K": lim, "order": args.order, "inner_iters": args.inner, "scheme": "rk4"}
+
+    def solver(cloud, prec, cfl):
+        s = lskum.Solver(cloud, order=args.order, inner_iters=args.inner, time_scheme=1, cfl=cfl, mach=mach,
+                         aoa_deg=aoa, reorder=1, limiter_K=lim, precision=prec, stream=stream)
+        if prec == 1:
+            s.autotune(reps=3)
+        return s
+
+    def record(h, f, cp, t):
+        return {"iterations": int(len(h)), "seconds": t, "residue_max": float(h.max()),
+                "residue_last": float(h[-1]), "residue_drop": float(h[-1] / h.max()),
+                "cl": f[-1][1], "cd": f[-1][2],
+                "force_change_last_chunk": [abs(f[-1][1] - f[-2][1]), abs(f[-1][2] - f[-2][2])] if len(f) > 1
+                else None, "forces": f[::max(1, len(f) // 12)] + f[-1:], "cp": cp}
+
+    def errors(r64, rm):
+        small_cl = aoa == 0.0
+        return {"cl_rel_err": rel(rm["cl"], r64["cl"], r64["cd"] if small_cl else None),
+                "cl_err_scale": "|Cd| (Cl ~ 0)" if small_cl else "|Cl|",
+                "cd_rel_err": rel(rm["cd"], r64["cd"]),
+                "cp_max_abs_err": float(np.max(np.abs(np.array(rm["cp"]) - np.array(r64["cp"]))))}
+
+    for name, iters, cfl in (("naca0012_160k", args.acc_iters_160k, args.acc_cfl_160k),
+                             ("naca0012_2p5m", args.acc_iters_2p5m, args.acc_cfl_2p5m)):
+        if iters <= 0:
+            continue
+        W, L = CLOUDS[name]
+        cloud = naca0012_cloud(W, L)
+        res = {"points": int(cloud["n"]), "cfl": cfl}
+        try:
+            t0 = time.time()
+            sm = solver(cloud, 1, cfl)
+            hm, fm = converge(sm, iters, args.acc_chunk)
+            cl, cd, cp = sm.forces()
+            res["mixed"] = record(hm, fm, cp.tolist(), time.time() - t0)
+            Um = sm.get_state()
+            sm.close()
+            t0 = time.time()
+            s64 = solver(cloud, 0, cfl)
+            if name == "naca0012_2p5m":
+                s64.set_state(Um)
+                h64, f64 = converge(s64, args.acc_iters_fp64_restart, args.acc_chunk)
+                res["fp64_started_from"] = "the mixed form's state after %d iterations" % iters
+            else:
+                h64, f64 = converge(s64, iters, args.acc_chunk)
+            cl, cd, cp = s64.forces()
+            res["fp64"] = record(h64, f64, cp.tolist(), time.time() - t0)
+            s64.close()
+            res["error"] = errors(res["fp64"], res["mixed"])
+            for k in ("mixed", "fp64"):
+                res[k].pop("cp")
+        except lskum.LskumError as e:
+            res["failed"] = str(e)
+        out[name] = res
+        print(json.dumps({name: res}), file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def batch_workload(n_clouds, n_cond, seed=240313292):
@@ -547,7 +836,19 @@ def measure_batched(args, dist, sampler):
     ms_b = timed(lambda: B.step(args.steps, history=False))
     launches = B.launch_count() - l0
     clocks = sampler.stop() if sampler else None
+    # idle share of the graph-replayed iteration: its time minus the summed
+    # CUDA-event durations of its flux and q-derivative kernels (timed in a
+    # separate, directly launched run; the residue kernels count as idle)
+    B.profile(True)
+    B.step(args.steps, history=False)
+    fms, fn = B.kernel_time(lskum.LSKUM_KERNEL_FLUX)
+    qms, qn = B.kernel_time(lskum.LSKUM_KERNEL_QGRAD)
+    B.profile(False)
     B.close()
+    gaps = {"graph_ms_per_iteration": ms_b / args.steps,
+            "kernel_ms_per_iteration": (fms + qms) / args.steps,
+            "launches_per_iteration": (fn + qn) / args.steps,
+            "idle_share": max(0.0, 1.0 - (fms + qms) / ms_b)}
 
     singles = []
     for k, (c, m, a) in enumerate(cases):
@@ -566,7 +867,7 @@ def measure_batched(args, dist, sampler):
     return {"value": value_b, "unit": UNIT, "ms_per_step": ms_b / args.steps, "dtype": "f32/f64 mixed",
             "cases": len(cases), "points": npts, "cloud_sizes": [sizes[0], sizes[-1]],
             "clouds": args.batch_clouds, "conditions_per_cloud": args.batch_conditions,
-            "gpu_launches": launches, "tuning": tuning, "clocks": clocks,
+            "gpu_launches": launches, "tuning": tuning, "clocks": clocks, "launch_gaps": gaps,
             "sequential": {"value": value_s, "ms_per_step": ms_s / args.steps,
                            "note": "one context per case, stepped one after another with the same "
                                    "launch shapes; small cases then run from L2"},
@@ -667,23 +968,32 @@ def run_ours(args, rank, world, local):
     primary = args.precision
     other = "mixed" if primary == "fp64" else "fp64"
     peaks, peak_src = measured_peaks()
+    from paper_2403_13287_gb300 import lskum as _lskum
+    probes = {"fp64_fma_gflops": _lskum.probe_peak(_lskum.PROBE_FP64_FMA),
+              "fp32_fma_gflops": _lskum.probe_peak(_lskum.PROBE_FP32_FMA),
+              "fp32x2_fma_gflops": _lskum.probe_peak(_lskum.PROBE_FP32X2_FMA)}
 
     rp = measure_form(args, cloud, primary, dist, ClockSampler(local) if rank == 0 else None)
     tuning = rp.get("tuning")
     e2e_value = world * measure_e2e(rp["solver"], n, max(1, args.steps), dist)
     rp["solver"].close()
-    forms = {primary: form_summary(args, rp, n, dbar, world, primary, peaks, peak_src)}
+    forms = {primary: form_summary(args, rp, n, dbar, world, primary, peaks, peak_src, probes)}
     if not args.single_form:
         ro = measure_form(args, cloud, other, dist, ClockSampler(local) if rank == 0 else None)
         ro["solver"].close()
-        forms[other] = form_summary(args, ro, n, dbar, world, other, peaks, peak_src)
+        forms[other] = form_summary(args, ro, n, dbar, world, other, peaks, peak_src, probes)
         forms[other]["clocks"] = ro["clocks"]
         if ro.get("tuning"):
             forms[other]["tuning"] = ro["tuning"]
         forms["mixed_speedup_vs_fp64"] = forms["mixed"]["value"] / forms["fp64"]["value"]
+        if not args.no_error:
+            forms["mixed"]["error"] = measure_mixed_error(
+                args, cloud, forms["mixed"].get("tuning") or tuning, torch.cuda.current_stream().cuda_stream)
     if not args.no_batch and not args.single_form:
         forms["batched"] = measure_batched(args, dist, ClockSampler(local) if rank == 0 else None)
         forms["batched_speedup_vs_fp64"] = forms["batched"]["value"] / forms["fp64"]["value"]
+        forms["batched"]["error"] = ("the mixed form's (forms.mixed.error): every case of a batch gives, bit for "
+                                     "bit, the states of a mixed context of its own (tests/test_gpu_batch.py)")
     if not args.no_adjoint and not args.single_form:
         forms["adjoint"] = measure_adjoint(args, dist, ClockSampler(local) if rank == 0 else None)
     if not args.no_extra and not args.single_form:
@@ -696,7 +1006,7 @@ def run_ours(args, rank, world, local):
             r = measure_form(a, cl, precision, dist, ClockSampler(local) if rank == 0 else None)
             r["solver"].close()
             nn = cl["n"]
-            out = form_summary(a, r, nn, cl["nbr_offsets"][-1] / nn, world, precision, peaks, peak_src)
+            out = form_summary(a, r, nn, cl["nbr_offsets"][-1] / nn, world, precision, peaks, peak_src, probes)
             out["clocks"] = r["clocks"]
             if r.get("tuning"):
                 out["tuning"] = r["tuning"]
@@ -743,9 +1053,11 @@ def run_ours(args, rank, world, local):
                    "l2": "inputs larger than L2 (working set ~%.1f GB)" % (
                        (n * 380 + cloud["nbr_offsets"][-1] * 37) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
+        "edge_iterations_per_s": main["edge_iterations_per_s"],
         "roofline": main["roofline"],
         "kernels": main["kernels"],
         "gpu_launches": main["gpu_launches"],
+        "measured_fma_peaks_gflops": probes,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n * 8,
                 "d2h_bytes_per_step": 4 * n * 8 + 8},
         "clocks": rp["clocks"],
@@ -757,6 +1069,7 @@ def run_ours(args, rank, world, local):
         import oracle
         m = oracle.split_stencils(cloud)
         line["cpu_baseline"] = cpu_baseline_sample(cloud, m, args)
+    line["summary"] = summary_of(line, forms)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -770,6 +1083,10 @@ def main():
         print("warning: --gpus %d but WORLD_SIZE %d" % (args.gpus, world), file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.accuracy:
+        return run_accuracy(args)
+    if args.residuals_only:
+        return run_residuals_only(args)
     return run_ours(args, rank, world, local)
 
 
