@@ -1,10 +1,21 @@
-"""Long runs (1000-1500 iterations) against stored oracle results (needs a GPU).
+"""Long runs against stored oracle results (needs a GPU).
 
-tests/golden/converged_*.json are written by tests/golden/make_converged.py,
-which runs only the FP64 CPU oracle. The FP64 CUDA path must reproduce its
-Cl, Cd and Cp to 1e-8 (round-off carried through the iterations); the mixed
-form must meet the accuracy target of its design, converged Cl and Cd within
-1e-4 of max(|Cl|, |Cd|).
+tests/golden/*.json are written by tests/golden/make_converged.py, which runs
+only the FP64 CPU oracle.
+
+converged_*.json are solves run until the residue has fallen by more than
+eight decades from its largest value. The FP64 CUDA path must reproduce their
+Cl, Cd and wall Cp to 1e-8 (round-off carried through the iterations) and
+their residue history wherever it is still above the round-off floor. The
+mixed form must meet its accuracy target at convergence: Cl and Cd each
+within 1e-4 of themselves (where Cl ~ 0 at alpha = 0, within 1e-4 of |Cd|),
+wall Cp within 1e-4 of the stagnation value.
+
+run_naca0012_160k_*.json is the 160k-point transonic workload (second order,
+3 inner iterations, RK4, M 0.85, alpha 1, limiter K = 1, CFL 0.2) over its
+2000 iterations with the whole residue history. The FP64 path matches it to
+1e-8; the mixed form's gap over those 2000 (unconverged) iterations is
+bounded at 1e-3 relative in the residue history and in Cl and Cd.
 """
 import glob
 import json
@@ -17,7 +28,9 @@ from paper_2403_13287_gb300.cloudgen import naca0012_cloud
 
 pytestmark = pytest.mark.gpu
 
-GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "converged_*.json")))
+HERE = os.path.join(os.path.dirname(__file__), "golden")
+CONVERGED = sorted(glob.glob(os.path.join(HERE, "converged_*.json")))
+RUN160K = os.path.join(HERE, "run_naca0012_160k_m085_a1_rk4_lim1.json")
 
 
 def _run(g, precision):
@@ -32,26 +45,60 @@ def _run(g, precision):
     return cl, cd, cp, hist
 
 
-@pytest.mark.parametrize("path", GOLDEN, ids=[os.path.basename(p)[10:-5] for p in GOLDEN])
-def test_fp64_long_run_matches_oracle(path):
+def _ids(paths):
+    return [os.path.basename(p)[:-5] for p in paths]
+
+
+@pytest.mark.parametrize("path", CONVERGED, ids=_ids(CONVERGED))
+def test_fp64_converged_run_matches_oracle(path):
     g = json.load(open(path))
     cl, cd, cp, hist = _run(g, 0)
     scale = max(abs(g["cl"]), abs(g["cd"]))
     assert abs(cl - g["cl"]) <= 1e-8 * scale
     assert abs(cd - g["cd"]) <= 1e-8 * scale
     assert np.max(np.abs(cp - np.array(g["cp"]))) <= 1e-8
-    assert abs(hist[-1] - g["residue_last"]) <= 1e-6 * g["residue_last"]
+    ref = np.array(g["residue_every_100"])
+    got = hist[::100]
+    live = ref > 1e-7 * g["residue_max"]          # above the round-off floor of the iteration
+    assert live.sum() >= 10
+    assert np.all(np.abs(got[live] - ref[live]) <= 1e-6 * ref[live])
+    # converged on the GPU too
+    assert hist[-1] <= 1e-8 * hist.max()
 
 
-@pytest.mark.parametrize("path", GOLDEN, ids=[os.path.basename(p)[10:-5] for p in GOLDEN])
-def test_mixed_long_run_meets_accuracy_target(path):
+@pytest.mark.parametrize("path", CONVERGED, ids=_ids(CONVERGED))
+def test_mixed_converged_run_meets_accuracy_target(path):
     g = json.load(open(path))
     cl, cd, cp, hist = _run(g, 1)
-    # relative to the larger coefficient: inviscid drag on these clouds is a
-    # small difference of pressure forces (|Cd| << |Cl|), where a relative
-    # error of Cd alone says nothing about the solution
+    # Cl on its own scale; at alpha = 0 (Cl ~ 0 by symmetry, up to the
+    # cloud's jitter) on |Cd|
+    cl_scale = abs(g["cd"]) if g["aoa_deg"] == 0.0 else abs(g["cl"])
+    assert abs(cl - g["cl"]) <= 1e-4 * cl_scale, (cl, g["cl"])
+    assert abs(cd - g["cd"]) <= 1e-4 * abs(g["cd"]), (cd, g["cd"])
+    cp_ref = np.array(g["cp"])
+    assert np.max(np.abs(cp - cp_ref)) <= 1e-4 * np.max(np.abs(cp_ref))
+    # the mixed iteration converges too, to its own round-off floor
+    assert hist[-1] <= 1e-5 * hist.max()
+
+
+def test_fp64_160k_run_matches_oracle():
+    g = json.load(open(RUN160K))
+    cl, cd, cp, hist = _run(g, 0)
+    ref = np.array(g["residue_history"])
+    assert hist[0] == 0.0 and ref[0] == 0.0          # the free stream has R = 0 exactly
+    assert np.all(np.abs(hist[1:] - ref[1:]) <= 1e-8 * ref[1:])
     scale = max(abs(g["cl"]), abs(g["cd"]))
-    assert abs(cd - g["cd"]) <= 1e-4 * scale, (cd, g["cd"])
-    assert abs(cl - g["cl"]) <= 1e-4 * scale, (cl, g["cl"])
-    # surface pressure: report-level agreement
-    assert np.max(np.abs(cp - np.array(g["cp"]))) <= 1e-3
+    assert abs(cl - g["cl"]) <= 1e-8 * scale and abs(cd - g["cd"]) <= 1e-8 * scale
+    assert np.max(np.abs(cp - np.array(g["cp"]))) <= 1e-8
+
+
+def test_mixed_160k_run_gap_is_bounded():
+    g = json.load(open(RUN160K))
+    cl, cd, cp, hist = _run(g, 1)
+    ref = np.array(g["residue_history"])
+    gap = np.max(np.abs(hist[1:] - ref[1:]) / ref[1:])
+    print("mixed 160k over 2000 iterations: residue gap %.2e, Cl %.2e, Cd %.2e (relative), Cp %.2e" % (
+        gap, abs(cl - g["cl"]) / abs(g["cl"]), abs(cd - g["cd"]) / abs(g["cd"]),
+        np.max(np.abs(cp - np.array(g["cp"])))))
+    assert gap <= 1e-3
+    assert abs(cl - g["cl"]) <= 1e-3 * abs(g["cl"]) and abs(cd - g["cd"]) <= 1e-3 * abs(g["cd"])
