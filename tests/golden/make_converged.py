@@ -30,7 +30,7 @@ from paper_2403_13287_gb300.cloudgen import naca0012_cloud  # noqa: E402
 CASES = {
     "converged_naca0012_128x77_m120_a0_rk4_lim1": (128, 77, 11, 2, 1, 1.2, 0.0, 1.0, 1.5, 12000, "converged"),
     "converged_naca0012_128x77_m063_a2_rk4_o1": (128, 77, 11, 1, 1, 0.63, 2.0, 0.0, 1.0, 10000, "converged"),
-    "converged_naca0012_128x77_m085_a1_rk4_o1": (128, 77, 11, 1, 1, 0.85, 1.0, 0.0, 1.0, 26000, "converged"),
+    "converged_naca0012_128x77_m085_a1_rk4_o1": (128, 77, 11, 1, 1, 0.85, 1.0, 0.0, 1.0, 36000, "converged"),
     "run_naca0012_160k_m085_a1_rk4_lim1": (512, 311, 2403_13287, 2, 1, 0.85, 1.0, 1.0, 0.2, 2000, "run"),
 }
 
