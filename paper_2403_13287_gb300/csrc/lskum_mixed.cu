@@ -766,7 +766,10 @@ struct VariantTable {
         flux_v<128, 3, true, K>,
         // staged tiles (one 64-point tile per CTA, rows in shared memory)
         flux_v<64, 14, true, K, true>, flux_v<64, 16, true, K, true>, flux_v<64, 12, true, K, true>,
-        flux_v<64, 10, true, K, true>, flux_v<64, 8, true, K, true>};
+        flux_v<64, 10, true, K, true>, flux_v<64, 8, true, K, true>,
+        // the pipelined loop at 64 threads with the register budgets between
+        // shapes 7 (spills) and 14
+        flux_v<64, 12, true, K>, flux_v<64, 10, true, K>};
 };
 static const QgradFn *const kQgradVariants[2] = {VariantTable<false>::qgrad, VariantTable<true>::qgrad};
 static const FluxFn *const kFluxVariants[2] = {VariantTable<false>::flux, VariantTable<true>::flux};
@@ -774,16 +777,19 @@ static constexpr int kNumQgradVariants = sizeof VariantTable<false>::qgrad / siz
 static constexpr int kNumFluxVariants = sizeof VariantTable<false>::flux / sizeof(FluxFn);
 static const int kQgradShape[][2] = {{128, 8}, {64, 16}, {256, 4}, {128, 6}, {256, 3}, {96, 10}};
 // flux shapes 6-11 repeat 0-5 with the software-pipelined neighbour loop,
-// 12-16 give that loop more registers, 17-21 stage each tile's rows in
-// shared memory
+// 12-16 and 22-23 give that loop more registers, 17-21 stage each tile's
+// rows in shared memory
 static constexpr int kFirstStagedFlux = 17;
+static constexpr int kLastStagedFlux = 21;
 static const int kFluxShape[][2] = {{128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4},
                                     {128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4},
                                     {128, 5}, {128, 4}, {64, 8},  {96, 6},  {128, 3},
-                                    {64, 14}, {64, 16}, {64, 12}, {64, 10}, {64, 8}};
+                                    {64, 14}, {64, 16}, {64, 12}, {64, 10}, {64, 8},
+                                    {64, 12}, {64, 10}};
 static_assert(sizeof kFluxShape / sizeof kFluxShape[0] == kNumFluxVariants, "one shape per flux variant");
 
 int mixed_first_staged_variant() { return kFirstStagedFlux; }
+int mixed_last_staged_variant() { return kLastStagedFlux; }
 
 int mixed_variants(int kernel_class)
 {

@@ -97,7 +97,7 @@ def test_every_launch_shape_gives_the_same_solution(clouds):
     c = clouds[0]
     U0 = smooth_state(c, 0.85, 1.0, amp=0.05, seed=70)
     ref = None
-    for v in range(22):                                 # 22 flux shapes (17-21 staged), 6 q-derivative shapes
+    for v in range(24):                                 # 24 flux shapes (17-21 staged), 6 q-derivative shapes
         s = Solver(c, order=2, inner_iters=3, time_scheme=1, mach=0.85, aoa_deg=1.0, limiter_K=1.0, precision=1)
         s.set_tuning(v, v % 6)
         s.set_state(U0)
