@@ -15,7 +15,7 @@ run_naca0012_160k_*.json is the 160k-point transonic workload (second order,
 3 inner iterations, RK4, M 0.85, alpha 1, limiter K = 1, CFL 0.2) over its
 2000 iterations with the whole residue history. The FP64 path matches it to
 1e-8; the mixed form's gap over those 2000 (unconverged) iterations is
-bounded at 1e-3 relative in the residue history and in Cl and Cd.
+bounded at 2e-4 relative in the residue history and 1e-5 in Cl and Cd.
 """
 import glob
 import json
@@ -101,5 +101,6 @@ def test_mixed_160k_run_gap_is_bounded():
     print("mixed 160k over 2000 iterations: residue gap %.2e, Cl %.2e, Cd %.2e (relative), Cp %.2e" % (
         gap, abs(cl - g["cl"]) / abs(g["cl"]), abs(cd - g["cd"]) / abs(g["cd"]),
         np.max(np.abs(cp - np.array(g["cp"])))))
-    assert gap <= 1e-3
-    assert abs(cl - g["cl"]) <= 1e-3 * abs(g["cl"]) and abs(cd - g["cd"]) <= 1e-3 * abs(g["cd"])
+    # measured: residue gap 3.8e-5, Cl 5.9e-7, Cd 2.5e-7 relative
+    assert gap <= 2e-4
+    assert abs(cl - g["cl"]) <= 1e-5 * abs(g["cl"]) and abs(cd - g["cd"]) <= 1e-5 * abs(g["cd"])
