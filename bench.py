@@ -211,7 +211,7 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
 # profiles/launch_list_naca0012_2p5m_fp64.md).
 FP64_INSTR_PER_EDGE_FLUX = 180.33
 FP64_FLOPS_PER_EDGE_FLUX = 287.05
-FLUX_DRAM_BYTES_PER_POINT = 599.1
+FLUX_DRAM_BYTES_PER_POINT = 598.3
 # FP64 peak: ncu's DFMA unit count, 304 FP64 thread-instructions per cycle
 # (each DFMA 2 flops), at the 2070 MHz maximum SM clock
 FP64_PEAK_GINSTR = 304 * 2.070
@@ -476,7 +476,7 @@ def measure_e2e(solver, n, steps, dist):
 # DRAM bytes per point of one launch of the mixed kernels on the 2.5M-point
 # workload, from a full-size single-pass ncu capture of the current kernels
 # (profiles/mixed_kernels_naca0012_2p5m.md); None where not captured
-MIXED_TRAFFIC_PER_POINT = {"flux": 351.0, "qgrad": 192.7}
+MIXED_TRAFFIC_PER_POINT = {"flux": 351.6, "qgrad": 193.1}
 # warp instructions per stencil edge of the mixed flux kernel at its autotuned
 # shape (ncu smsp__inst_executed.sum, 640k-point capture,
 # profiles/k_flux_update_mixed_naca0012_640k.md): the kernel is bound by

@@ -134,7 +134,60 @@ def _gradient_pass(E, dx, dy, q, gx_old=None, gy_old=None):
     return gx, gy
 
 
-def _residual(cloud, mask, U, x, y, order, inner, gamma):
+def _first_per_point(src, key, order, n):
+    """For every point, the position (into the edge arrays) of its entry with
+    the smallest real key, the earliest in `order` among equal keys; -1 for a
+    point without entries."""
+    pick = np.full(n, -1, dtype=np.int64)
+    if len(src) == 0:
+        return pick
+    o = np.lexsort((order, key, src))
+    first = np.ones(len(o), dtype=bool)
+    first[1:] = src[o][1:] != src[o][:-1]
+    pick[src[o][first]] = o[first]
+    return pick
+
+
+def _limit(E, dx, dy, q, gx, gy, K):
+    """Venkatakrishnan's limiter exactly as the C oracle's limit_gradients
+    takes it, over complex numbers: every choice (the nearest neighbour, the
+    stencil maximum and minimum, the smallest f over all reconstruction
+    shifts) is made on real parts, with the C loops' first-wins tie order,
+    and the chosen complex values are carried through."""
+    n = E.n
+    ne = len(E.dst)
+    eidx = np.arange(ne)
+    dist = np.sqrt(dx * dx + dy * dy)
+    near = _first_per_point(E.src, dist.real, eidx, n)
+    h = dist[near]
+    eps2 = (K * h) * (K * h) * (K * h)
+    gx = gx.copy()
+    gy = gy.copy()
+    for k in range(4):
+        q0 = q[k]
+        qi = q[k][E.dst]
+        # stencil extremes over P_0 and its neighbours (P_0 wins ties, then CSR order)
+        amax = _first_per_point(E.src, -qi.real, eidx, n)
+        amin = _first_per_point(E.src, qi.real, eidx, n)
+        qmax = np.where(qi[amax].real > q0.real, qi[amax], q0)
+        qmin = np.where(qi[amin].real < q0.real, qi[amin], q0)
+        half = 0.5 * (dx * gx[k][E.src] + dy * gy[k][E.src])
+        # the shifts -half then +half of every member, in the C loop's order
+        d = np.concatenate([-half, half])
+        s2 = np.concatenate([E.src, E.src])
+        ordr = np.concatenate([2 * eidx, 2 * eidx + 1])
+        D = np.where(d.real > 0.0, (qmax - q0)[s2], (qmin - q0)[s2])
+        e2 = eps2[s2]
+        f = (D * D + e2 + 2.0 * D * d) / (D * D + 2.0 * d * d + D * d + e2)
+        f = np.where(d.real != 0.0, f, 1.0 + 0.0 * f)
+        best = _first_per_point(s2, f.real, ordr, n)
+        phi = np.where(f[best].real < 1.0, f[best], 1.0 + 0.0 * f[best])
+        gx[k] = gx[k] * phi
+        gy[k] = gy[k] * phi
+    return gx, gy
+
+
+def _residual(cloud, mask, U, x, y, order, inner, gamma, limiter=0.0):
     E = _Edges(cloud)
     n = E.n
     nx = np.asarray(cloud["nx"], dtype=np.float64)
@@ -148,6 +201,8 @@ def _residual(cloud, mask, U, x, y, order, inner, gamma):
         gx, gy = _gradient_pass(E, dx, dy, q)
         for _ in range(inner):
             gx, gy = _gradient_pass(E, dx, dy, q, gx, gy)
+        if limiter > 0.0:
+            gx, gy = _limit(E, dx, dy, q, gx, gy, limiter)
         qt_i = np.stack([q[k][E.dst] - 0.5 * (dx * gx[k][E.dst] + dy * gy[k][E.dst]) for k in range(4)])
         qt_0 = np.stack([q[k][E.src] - 0.5 * (dx * gx[k][E.src] + dy * gy[k][E.src]) for k in range(4)])
     else:
@@ -188,15 +243,18 @@ def _residual(cloud, mask, U, x, y, order, inner, gamma):
     return np.stack([Rl[0], Rl[1] * tx + Rl[2] * nx, Rl[1] * ty + Rl[2] * ny, Rl[3]])
 
 
-def residual(cloud, mask, U, order=2, inner=3, gamma=1.4):
-    """R(U) of the unlimited scheme in real arithmetic (equals the C oracle's)."""
+def residual(cloud, mask, U, order=2, inner=3, gamma=1.4, limiter=0.0):
+    """R(U) of the scheme in real arithmetic (equals the C oracle's); limiter
+    K > 0 applies Venkatakrishnan's limiter to the last iterate."""
     x = np.asarray(cloud["x"], dtype=np.float64)
     y = np.asarray(cloud["y"], dtype=np.float64)
-    return _residual(cloud, mask, np.asarray(U, dtype=np.float64), x, y, order, inner, gamma)
+    return _residual(cloud, mask, np.asarray(U, dtype=np.float64), x, y, order, inner, gamma, limiter)
 
 
-def jvp(cloud, mask, U, dU=None, dx=None, dy=None, order=2, inner=3, gamma=1.4, h=1e-30):
-    """J v = dR/dU dU + dR/dx dx + dR/dy dy at (U, x, y), by complex step."""
+def jvp(cloud, mask, U, dU=None, dx=None, dy=None, order=2, inner=3, gamma=1.4, h=1e-30, limiter=0.0):
+    """J v = dR/dU dU + dR/dx dx + dR/dy dy at (U, x, y), by complex step.
+    With the limiter the derivative is that of the branch the real parts
+    select (the limiter is piecewise smooth)."""
     U = np.asarray(U, dtype=np.float64).astype(np.complex128)
     x = np.asarray(cloud["x"], dtype=np.float64).astype(np.complex128)
     y = np.asarray(cloud["y"], dtype=np.float64).astype(np.complex128)
@@ -206,10 +264,10 @@ def jvp(cloud, mask, U, dU=None, dx=None, dy=None, order=2, inner=3, gamma=1.4, 
         x = x + 1j * h * np.asarray(dx, dtype=np.float64)
     if dy is not None:
         y = y + 1j * h * np.asarray(dy, dtype=np.float64)
-    return _residual(cloud, mask, U, x, y, order, inner, gamma).imag / h
+    return _residual(cloud, mask, U, x, y, order, inner, gamma, limiter).imag / h
 
 
-def vjp_entries(cloud, mask, U, R_bar, entries, order=2, inner=3, gamma=1.4):
+def vjp_entries(cloud, mask, U, R_bar, entries, order=2, inner=3, gamma=1.4, limiter=0.0):
     """Selected entries of the VJP J^T R_bar: entries is a list of
     ("U", component, point), ("x", point) or ("y", point); each is
     <R_bar, J e> for the unit direction e of that entry."""
@@ -219,11 +277,12 @@ def vjp_entries(cloud, mask, U, R_bar, entries, order=2, inner=3, gamma=1.4):
         if ent[0] == "U":
             d = np.zeros((4, n))
             d[ent[1], ent[2]] = 1.0
-            Jv = jvp(cloud, mask, U, dU=d, order=order, inner=inner, gamma=gamma)
+            Jv = jvp(cloud, mask, U, dU=d, order=order, inner=inner, gamma=gamma, limiter=limiter)
         else:
             d = np.zeros(n)
             d[ent[1]] = 1.0
-            Jv = jvp(cloud, mask, U, **{"d" + ent[0]: d}, order=order, inner=inner, gamma=gamma)
+            Jv = jvp(cloud, mask, U, **{"d" + ent[0]: d}, order=order, inner=inner, gamma=gamma,
+                     limiter=limiter)
         out[j] = float(np.sum(R_bar * Jv))
     return out
 

@@ -183,3 +183,60 @@ def test_unrolled_force_derivative_matches_central_differences_of_the_c_oracle()
     (_, _), (tcl, tcd) = lskum_jvp.unrolled_forces(c, mask, U0, 3, dx=np.ones(n), dy=np.ones(n), scheme=1,
                                                    mach=0.63, aoa_deg=2.0)
     assert tcl == 0.0 and tcd == 0.0
+
+
+# ---------------------------------------------------------------------------
+# the limiter (Venkatakrishnan, K > 0) in the derivative oracle
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def limited():
+    c = naca0012_cloud(64, 16, seed=3)
+    return c, oracle.split_stencils(c), smooth_state(c, 0.85, 1.0, amp=0.05, seed=2)
+
+
+@pytest.mark.parametrize("K", [1.0, 0.3])
+def test_limited_real_part_is_the_c_oracle_residual(limited, K):
+    c, mask, U = limited
+    R_c, S = oracle.residual(c, mask, U, order=2, inner=3, limiter=K, want_scale=True)
+    R_py = lskum_jvp.residual(c, mask, U, order=2, inner=3, limiter=K)
+    assert np.all(np.abs(R_py - R_c) <= 1e-13 * S + 1e-300)
+    # the limiter acts on this state
+    R_free = lskum_jvp.residual(c, mask, U, order=2, inner=3)
+    assert np.max(np.abs(R_free - R_c)) > 1e-2 * np.max(S)
+
+
+@pytest.mark.parametrize("what", ["U", "xy"])
+def test_limited_jvp_matches_central_differences_of_the_c_oracle(limited, what):
+    """The limiter is piecewise smooth: its choices (nearest neighbour,
+    stencil extremes, the smallest shift factor) switch at ties, where a
+    central difference straddles two branches. Far-field points all carry
+    the free stream, so their q are tied stencil extremes; the nose and tail
+    points of the mirror-symmetric contour have two nearest neighbours at
+    equal distances. The directions here leave the far-field states and the
+    wall points fixed, and the step (1e-5) stays inside one branch."""
+    c, mask, U = limited
+    n = c["n"]
+    rng = np.random.default_rng(23)
+    far = c["flags"] == 2
+    dU = np.zeros((4, n))
+    dx = np.zeros(n)
+    dy = np.zeros(n)
+    if what == "U":
+        dU = rng.standard_normal((4, n)) * np.abs(U) * 1e-2
+        dU[:, far] = 0.0
+    else:
+        dx = rng.standard_normal(n) * 1e-3
+        dy = rng.standard_normal(n) * 1e-3
+        wall = c["flags"] == 1
+        dx[wall] = 0.0
+        dy[wall] = 0.0
+    J = lskum_jvp.jvp(c, mask, U, dU, dx, dy, order=2, inner=3, limiter=1.0)
+
+    def R(s):
+        cc = dict(c)
+        cc["x"] = c["x"] + s * dx
+        cc["y"] = c["y"] + s * dy
+        return oracle.residual(cc, mask, U + s * dU, order=2, inner=3, limiter=1.0)
+    F = (R(1e-5) - R(-1e-5)) / 2e-5
+    assert np.max(np.abs(J)) > 0
+    assert np.max(np.abs(J - F)) <= 1e-7 * np.max(np.abs(J))
