@@ -218,10 +218,14 @@ lskum_status lskum_residual(lskum_ctx *ctx, const double *U, double *R);
  *   x_bar, y_bar  device float64[n] in input order (written, or added into with
  *                 LSKUM_VJP_ACCUMULATE_XY), or NULL
  *   flags  0, or LSKUM_VJP_ACCUMULATE_XY and/or LSKUM_VJP_FP32
- * Requires limiter_K = 0 (the limiter's min/max is not differentiated):
- * LSKUM_ERR_ARG otherwise. Its workspace (about 0.53 KB per point plus
- * 88 B per edge for K = 3: 0.8 GB at 640k points) is allocated on the first
- * call and kept.
+ * With limiter_K > 0 the limiter is differentiated too (FP64 product only;
+ * LSKUM_ERR_ARG with LSKUM_VJP_FP32): it is piecewise smooth, and the
+ * product is that of the branch the forward takes, with the forward's
+ * choices (the first stencil extremum, the first largest reconstruction
+ * shift, the first nearest neighbour in row order). Its workspace (about
+ * 0.53 KB per point plus 88 B per edge for K = 3: 0.8 GB at 640k points;
+ * 0.16 KB per point more with the limiter) is allocated on the first call
+ * and kept. The kinetic boundary mode is not differentiated (LSKUM_ERR_ARG).
  * Does not change the context's state.
  */
 #define LSKUM_VJP_ACCUMULATE_XY 1 /* flags: add into x_bar, y_bar instead of overwriting them */
@@ -245,8 +249,8 @@ lskum_status lskum_residual_vjp(lskum_ctx *ctx, const double *U, const double *R
  *   U_bar = (dU^{n+1}/dU^n)^T U_bar_next,  x_bar, y_bar likewise.
  * Differentiates the FP64 scheme whatever the context's precision; the stage
  * states are recomputed in FP64. Frame normals, connectivity and sub-stencil
- * membership are held fixed, as in lskum_residual_vjp; limiter_K = 0 is
- * required (LSKUM_ERR_ARG otherwise).
+ * membership are held fixed, as in lskum_residual_vjp, and the limiter is
+ * differentiated as there.
  *   U           device float64[4*n] in input order, or NULL for the context's state
  *   U_bar_next  device float64[4*n] in input order
  *   U_bar       device float64[4*n] in input order (written), or NULL

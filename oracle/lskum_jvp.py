@@ -333,7 +333,7 @@ def _freestream(mach, aoa_deg, gamma):
     return np.array([rho, rho * u1, rho * u2, p / (gamma - 1.0) + 0.5 * rho * (u1 * u1 + u2 * u2)])
 
 
-def _iterate(cloud, mask, U, x, y, scheme, cfl, mach, aoa_deg, order, inner, gamma):
+def _iterate(cloud, mask, U, x, y, scheme, cfl, mach, aoa_deg, order, inner, gamma, limiter=0.0):
     """One pseudo-time iteration: forward Euler (E16) or RK4 with dt frozen."""
     E = _Edges(cloud)
     flags = np.asarray(cloud["flags"])
@@ -343,7 +343,7 @@ def _iterate(cloud, mask, U, x, y, scheme, cfl, mach, aoa_deg, order, inner, gam
     dt = _timestep(E, U, x, y, cfl, gamma)
 
     def R(V):
-        return _residual(cloud, mask, V, x, y, order, inner, gamma)
+        return _residual(cloud, mask, V, x, y, order, inner, gamma, limiter)
 
     if scheme == 0:
         return _boundary(U - dt * R(U), flags, nx, ny, Uinf)
@@ -378,26 +378,27 @@ def _forces(cloud, U, x, y, mach, aoa_deg, gamma):
     return cy * math.cos(a) - cx * math.sin(a), cx * math.cos(a) + cy * math.sin(a)
 
 
-def _unrolled(cloud, mask, U0, x, y, iters, scheme, cfl, mach, aoa_deg, order, inner, gamma):
+def _unrolled(cloud, mask, U0, x, y, iters, scheme, cfl, mach, aoa_deg, order, inner, gamma, limiter=0.0):
     U = U0
     for _ in range(iters):
-        U = _iterate(cloud, mask, U, x, y, scheme, cfl, mach, aoa_deg, order, inner, gamma)
+        U = _iterate(cloud, mask, U, x, y, scheme, cfl, mach, aoa_deg, order, inner, gamma, limiter)
     return U
 
 
-def iterate(cloud, mask, U, scheme=1, cfl=0.2, mach=0.63, aoa_deg=2.0, order=2, inner=3, gamma=1.4):
+def iterate(cloud, mask, U, scheme=1, cfl=0.2, mach=0.63, aoa_deg=2.0, order=2, inner=3, gamma=1.4,
+            limiter=0.0):
     """One iteration in real arithmetic (equals the C oracle's)."""
     x = np.asarray(cloud["x"], dtype=np.float64)
     y = np.asarray(cloud["y"], dtype=np.float64)
     return _iterate(cloud, mask, np.asarray(U, dtype=np.float64), x, y, scheme, cfl, mach, aoa_deg, order,
-                    inner, gamma)
+                    inner, gamma, limiter)
 
 
 def iterate_jvp(cloud, mask, U, dU=None, dx=None, dy=None, scheme=1, cfl=0.2, mach=0.63, aoa_deg=2.0,
-                order=2, inner=3, gamma=1.4, h=1e-30):
+                order=2, inner=3, gamma=1.4, h=1e-30, limiter=0.0):
     """J v of one iteration U^n -> U^{n+1}, by complex step."""
     U, x, y = _lift(cloud, U, dU, dx, dy, h)
-    return _iterate(cloud, mask, U, x, y, scheme, cfl, mach, aoa_deg, order, inner, gamma).imag / h
+    return _iterate(cloud, mask, U, x, y, scheme, cfl, mach, aoa_deg, order, inner, gamma, limiter).imag / h
 
 
 def forces_jvp(cloud, U, dU=None, dx=None, dy=None, mach=0.63, aoa_deg=2.0, gamma=1.4, h=1e-30):
@@ -408,11 +409,11 @@ def forces_jvp(cloud, U, dU=None, dx=None, dy=None, mach=0.63, aoa_deg=2.0, gamm
 
 
 def unrolled_forces(cloud, mask, U0, iters, dx=None, dy=None, scheme=1, cfl=0.2, mach=0.63, aoa_deg=2.0,
-                    order=2, inner=3, gamma=1.4, h=1e-30):
+                    order=2, inner=3, gamma=1.4, h=1e-30, limiter=0.0):
     """(Cl, Cd) after `iters` iterations from U0, and their derivatives along
     a displacement (dx, dy) of the points (frame normals and connectivity fixed)."""
     U, x, y = _lift(cloud, U0, None, dx, dy, h)
-    U = _unrolled(cloud, mask, U, x, y, iters, scheme, cfl, mach, aoa_deg, order, inner, gamma)
+    U = _unrolled(cloud, mask, U, x, y, iters, scheme, cfl, mach, aoa_deg, order, inner, gamma, limiter)
     cl, cd = _forces(cloud, U, x, y, mach, aoa_deg, gamma)
     return (float(np.real(cl)), float(np.real(cd))), (float(np.imag(cl)) / h, float(np.imag(cd)) / h)
 

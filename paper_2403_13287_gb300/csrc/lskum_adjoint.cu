@@ -650,6 +650,158 @@ __global__ void __launch_bounds__(128) k_adj_grad(AdjParamsT<T> P, const T *__re
 }
 
 // ---------------------------------------------------------------------------
+// Venkatakrishnan's limiter in reverse. Forward (k_qgrad's limited pass, per
+// component): g = phi g_raw with phi = f(x_m, d_m) when x_m < 2 d_m, else 1;
+//   f(x, d) = N/M, N = x (x + 2d) + eps^2, M = x (x + d) + 2 d^2 + eps^2,
+//   x_m = min(D+, -D-), D+- the largest / smallest q_i - q_0 over the stencil
+//   and P_0 itself (0), d_m = max_e |h_e . g_raw| (h_e the half offset),
+//   eps^2 = (K dmin)^3, dmin the nearest neighbour's distance.
+// With G = gbar . g_raw (the cotangent of phi):
+//   g_raw_bar = phi gbar + G f_d s h*          (h* the edge of d_m, s the sign
+//                                               of h*.g_raw)
+//   x_m = q_i - q_0 (D+) or q_0 - q_j (-D-): q_0 and the extreme neighbour get
+//         -+ G f_x; the neighbour's share is handed over through lidx/lval
+//         and added by k_adj_limit_gather
+//   the offsets: d* = 2 h* gets G f_d s g_raw / 2, the nearest neighbour's
+//         offset gets 3 K^3 dmin^2 G f_eps d/|d| (through eps^2)
+// The choices are the forward's: the first largest (smallest) q_i - q_0 in
+// row order, P_0's own 0 winning ties; the first largest |h . g_raw|; the
+// first nearest neighbour by squared distance. Where phi = 1 the limiter is
+// inactive and gbar passes through.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_adj_limit(AdjParams P, const double *__restrict__ graw,
+                                                   const double *__restrict__ gbar_in, double *__restrict__ gbar_out,
+                                                   int32_t *__restrict__ lidx, double *__restrict__ lval,
+                                                   double limK)
+{
+    const DevGeom &g = P.g;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.n) return;
+    double q0[4], gr[8], gb[8], qb[4];
+    ld4(P.q, p, q0);
+    ld8(graw, p, gr);
+    ld8(gbar_in, p, gb);
+    ld4(P.qbar, p, qb);
+    const double2 P0 = g.xy[p];
+    double dmx[4] = {0.0, 0.0, 0.0, 0.0}, dmn[4] = {0.0, 0.0, 0.0, 0.0}, hm[4] = {-1.0, -1.0, -1.0, -1.0};
+    int emx[4] = {-1, -1, -1, -1}, emn[4] = {-1, -1, -1, -1}, eh[4] = {-1, -1, -1, -1};
+    double sh[4] = {0.0, 0.0, 0.0, 0.0};
+    double2 hh[4];
+    int enear = -1;
+    double d2near = 0.0;
+    for (int e = g.off[p]; e < g.off[p + 1]; ++e) {
+        const int i = g.idx[e];
+        double qi[4];
+        ld4(P.q, i, qi);
+        const double2 Pi = g.xy[i];
+        const double dx = Pi.x - P0.x, dy = Pi.y - P0.y;
+        const double2 h = g.hd ? g.hd[e] : make_double2(0.5 * dx, 0.5 * dy);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double dq = qi[k] - q0[k];
+            if (dq > dmx[k]) {
+                dmx[k] = dq;
+                emx[k] = e;
+            }
+            if (dq < dmn[k]) {
+                dmn[k] = dq;
+                emn[k] = e;
+            }
+            const double c = fma(h.x, gr[k], h.y * gr[4 + k]);
+            if (fabs(c) > hm[k]) {
+                hm[k] = fabs(c);
+                eh[k] = e;
+                sh[k] = c < 0.0 ? -1.0 : 1.0;
+                hh[k] = h;
+            }
+        }
+        const double d2 = dx * dx + dy * dy;
+        if (enear < 0 || d2 < d2near) {
+            enear = e;
+            d2near = d2;
+        }
+    }
+    const double dmin = g.dmin[p], hK = dmin * limK, eps2 = hK * hK * hK;
+    double go[8];
+    double dminb = 0.0;
+    int32_t li[4] = {-1, -1, -1, -1};
+    double lv[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        go[k] = gb[k];
+        go[4 + k] = gb[4 + k];
+        const bool plus = dmx[k] <= -dmn[k];
+        const double x = plus ? dmx[k] : -dmn[k], d = hm[k];
+        if (eh[k] < 0 || !(x < 2.0 * d)) continue;   // phi = 1
+        const double N = fma(x, x + 2.0 * d, eps2), M = fma(x, x + d, fma(2.0 * d, d, eps2));
+        const double phi = N / M, iM2 = 1.0 / (M * M);
+        const double fx = ((2.0 * x + 2.0 * d) * M - N * (2.0 * x + d)) * iM2;
+        const double fd = (2.0 * x * M - N * (x + 4.0 * d)) * iM2;
+        const double fe = (M - N) * iM2;
+        const double G = gb[k] * gr[k] + gb[4 + k] * gr[4 + k];
+        const double gd = G * fd * sh[k];
+        go[k] = phi * gb[k] + gd * hh[k].x;
+        go[4 + k] = phi * gb[4 + k] + gd * hh[k].y;
+        const double xb = G * fx;
+        if (plus && emx[k] >= 0) {
+            qb[k] -= xb;
+            li[k] = emx[k];
+            lv[k] = xb;
+        } else if (!plus && emn[k] >= 0) {
+            qb[k] += xb;
+            li[k] = emn[k];
+            lv[k] = -xb;
+        }
+        // d* = 2 h*: its offset cotangent is half that of h*
+        double2 db = P.dbar[eh[k]];
+        db.x += 0.5 * gd * gr[k];
+        db.y += 0.5 * gd * gr[4 + k];
+        P.dbar[eh[k]] = db;
+        dminb += G * fe * 3.0 * limK * limK * limK * dmin * dmin;
+    }
+    if (dminb != 0.0 && enear >= 0 && dmin > 0.0) {
+        const double2 Pi = g.xy[g.idx[enear]];
+        double2 db = P.dbar[enear];
+        db.x += dminb * (Pi.x - P0.x) / dmin;
+        db.y += dminb * (Pi.y - P0.y) / dmin;
+        P.dbar[enear] = db;
+    }
+    st4(P.qbar, p, qb);
+    st8(gbar_out, p, go);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        lidx[4 * p + k] = li[k];
+        lval[4 * p + k] = lv[k];
+    }
+}
+
+// the extreme neighbours' share of the limiter's q cotangent (k_adj_limit),
+// gathered over each point's incoming edges (no atomics)
+__global__ void __launch_bounds__(128) k_adj_limit_gather(AdjParams P, const int32_t *__restrict__ lidx,
+                                                          const double *__restrict__ lval)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.g.n) return;
+    const int t0 = P.toff[p], t1 = P.toff[p + 1];
+    if (t0 == t1) return;
+    double qb[4];
+    ld4(P.qbar, p, qb);
+    bool any = false;
+    for (int t = t0; t < t1; ++t) {
+        const int e = P.tedge[t];
+        const int64_t src = P.tsrc[t];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (lidx[4 * src + k] == e) {
+                qb[k] += lval[4 * src + k];
+                any = true;
+            }
+        }
+    }
+    if (any) st4(P.qbar, p, qb);
+}
+
+// ---------------------------------------------------------------------------
 // least-squares weights back to edge offsets (owner side)
 // ---------------------------------------------------------------------------
 struct Sym2 {
@@ -902,6 +1054,16 @@ template <class T>
 cudaError_t launch_adj_grad(const AdjParamsT<T> &P, const T *gprev, const T *gbar_in, T *gbar_out, cudaStream_t s)
 {
     k_adj_grad<T><<<blocks(P.g.n, 128), 128, 0, s>>>(P, gprev, gbar_in, gbar_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_limit(const AdjParams &P, const double *graw, const double *gbar_in, double *gbar_out,
+                             int32_t *lidx, double *lval, double limK, cudaStream_t s)
+{
+    k_adj_limit<<<blocks(P.g.n, 128), 128, 0, s>>>(P, graw, gbar_in, gbar_out, lidx, lval, limK);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    k_adj_limit_gather<<<blocks(P.g.n, 128), 128, 0, s>>>(P, lidx, lval);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,13 @@ cudaError_t launch_adj_flux(const AdjParamsT<T> &P, cudaStream_t s);
 // gbar_out receives that of its input iterate gprev (nullptr for the first-order pass)
 template <class T>
 cudaError_t launch_adj_grad(const AdjParamsT<T> &P, const T *gprev, const T *gbar_in, T *gbar_out, cudaStream_t s);
+// the limiter (limiter_K > 0) in reverse, between the flux adjoint and the
+// last pass's: gbar_in is the cotangent of the limited last iterate, graw the
+// unlimited one; gbar_out receives the unlimited iterate's cotangent; adds
+// into qbar (the point and, through lidx/lval ([n][4] scratch), its extreme
+// neighbours) and into dbar (the largest-shift and nearest-neighbour edges)
+cudaError_t launch_adj_limit(const AdjParams &P, const double *graw, const double *gbar_in, double *gbar_out,
+                             int32_t *lidx, double *lval, double limK, cudaStream_t s);
 // least-squares weight cotangents (abar, wbar) into the offset cotangents dbar
 cudaError_t launch_adj_weights(const AdjParams &P, cudaStream_t s);
 // offsets (dbar) plus per-point cotangents pxy (internal, or nullptr) to x_bar, y_bar in input

@@ -120,6 +120,10 @@ struct lskum_ctx {
     double *vebar = nullptr;
     double2 *vwbar = nullptr, *vabar = nullptr, *vdbar = nullptr;
     int32_t *toff = nullptr, *tedge = nullptr, *tsrc = nullptr;
+    double *vGlim = nullptr;      // [n][8] the limited last iterate (limiter_K > 0)
+    double *vext = nullptr;       // [n][4] the limiter's extremum measure (limiter_K > 0)
+    int32_t *vlidx = nullptr;     // [n][4] limiter reverse: the extreme neighbour's edge
+    double *vlval = nullptr;      // [n][4] limiter reverse: its q cotangent
     double *vUacc = nullptr;      // [n][4] U cotangent being accumulated (internal order)
     double2 *vpxy = nullptr;      // [n] point cotangents of x, y gathered directly (forces)
     // update-step VJP (allocated on the first lskum_step_vjp): stage states,
@@ -1281,6 +1285,16 @@ extern "C" lskum_status lskum_residual(lskum_ctx *c, const double *U, double *R)
     return check_nonphysical(c);
 }
 
+// second order with the limiter on
+static bool limited(const lskum_ctx *c) { return c->cfg.order == 2 && c->cfg.limiter_K > 0.0; }
+
+// the final q-derivative iterate of the FP64 forward recomputation (vjp_forward)
+static const double *vjp_final_gradient(const lskum_ctx *c)
+{
+    if (c->cfg.order != 2) return nullptr;
+    return limited(c) ? c->vGlim : c->vG + (int64_t)c->cfg.inner_iters * 8 * c->n;
+}
+
 static lskum_status vjp_workspace(lskum_ctx *c)
 {
     if (c->vjp_ready) return LSKUM_OK;
@@ -1304,6 +1318,12 @@ static lskum_status vjp_workspace(lskum_ctx *c)
     CK(c, dalloc(c, &c->vUacc, 4 * n));
     CK(c, dalloc(c, &c->vpxy, n));
     CK(c, dalloc(c, &c->fdsb, std::max<int64_t>(c->n_wall, 1)));
+    if (limited(c)) {
+        CK(c, dalloc(c, &c->vGlim, 8 * n));
+        CK(c, dalloc(c, &c->vext, 4 * n));
+        CK(c, dalloc(c, &c->vlidx, 4 * n));
+        CK(c, dalloc(c, &c->vlval, 4 * n));
+    }
     c->launches += 4;
     LAUNCH(c, build_transpose_csr(n, c->nnz, c->off, c->idx, c->toff, c->tedge, c->tsrc, c->stream));
     c->vjp_ready = true;
@@ -1317,7 +1337,7 @@ static AdjParams adj_params(lskum_ctx *c)
     AdjParams P{};
     P.g = c->geom();
     P.q = c->vq;
-    P.qg = c->cfg.order == 2 ? c->vG + (int64_t)K * 8 * n : nullptr;
+    P.qg = vjp_final_gradient(c);
     P.Rbar = c->vRb;
     P.qbar = c->vqb;
     P.gbar = c->vgb;
@@ -1335,17 +1355,28 @@ static AdjParams adj_params(lskum_ctx *c)
     return P;
 }
 
-// FP64 q and q-derivative iterates of an internal state (vq, vG)
+// FP64 q and q-derivative iterates of an internal state (vq, vG; with the
+// limiter also the limited last iterate vGlim, the forward's last pass run
+// again with the limiter)
 static lskum_status vjp_forward(lskum_ctx *c, const double *Ui)
 {
     const int64_t n = c->n;
+    const int K = c->cfg.inner_iters;
     const DevGeom g = c->geom();
     LAUNCH(c, launch_q_from_U(n, c->gas, Ui, c->vq, c->status, c->stream));
     if (c->cfg.order == 2) {
-        LAUNCH(c, launch_qgrad(g, c->vq, nullptr, nullptr, c->vG, nullptr, 0.0, c->stream));
-        for (int k = 1; k <= c->cfg.inner_iters; ++k)
+        const double limK = c->cfg.limiter_K;
+        double *ext = limited(c) && K > 0 ? c->vext : nullptr;
+        LAUNCH(c, launch_qgrad(g, c->vq, nullptr, nullptr, c->vG, ext, 0.0, c->stream));
+        for (int k = 1; k <= K; ++k)
             LAUNCH(c, launch_qgrad(g, c->vq, c->vG + (int64_t)(k - 1) * 8 * n, c->vG, c->vG + (int64_t)k * 8 * n,
                                    nullptr, 0.0, c->stream));
+        if (limited(c)) {
+            if (K == 0) LAUNCH(c, launch_qgrad(g, c->vq, nullptr, nullptr, c->vGlim, nullptr, limK, c->stream));
+            else
+                LAUNCH(c, launch_qgrad(g, c->vq, c->vG + (int64_t)(K - 1) * 8 * n, c->vG, c->vGlim, ext, limK,
+                                       c->stream));
+        }
     }
     return LSKUM_OK;
 }
@@ -1357,7 +1388,7 @@ static lskum_status residual_fp64(lskum_ctx *c, const double *Ui, double *Rout)
     if (st != LSKUM_OK) return st;
     FluxLaunch L{};
     L.q = c->vq;
-    L.qg = c->cfg.order == 2 ? c->vG + (int64_t)c->cfg.inner_iters * 8 * c->n : nullptr;
+    L.qg = vjp_final_gradient(c);
     L.R = Rout;
     L.norm_part = c->norm_part;
     L.status = c->status;
@@ -1459,6 +1490,13 @@ static lskum_status vjp_residual(lskum_ctx *c, const double *Ui, double *Ub_acc,
     if (second) {
         CK(c, cudaMemsetAsync(c->vabar, 0, std::max<int64_t>(c->nnz, 1) * sizeof(double2), c->stream));
         double *gin = c->vgb, *gout = c->vgb2;
+        if (limited(c)) {
+            // the limiter first: the flux saw the limited last iterate
+            c->launches++;
+            LAUNCH(c, launch_adj_limit(P, c->vG + (int64_t)K * 8 * n, gin, gout, c->vlidx, c->vlval,
+                                       c->cfg.limiter_K, c->stream));
+            std::swap(gin, gout);
+        }
         for (int k = K; k >= 1; --k) {
             LAUNCH(c, launch_adj_grad(P, c->vG + (int64_t)(k - 1) * 8 * n, gin, gout, c->stream));
             std::swap(gin, gout);
@@ -1472,8 +1510,6 @@ static lskum_status vjp_residual(lskum_ctx *c, const double *Ui, double *Ub_acc,
 
 static lskum_status vjp_begin(lskum_ctx *c)
 {
-    if (c->cfg.order == 2 && c->cfg.limiter_K != 0.0)
-        return fail(c, LSKUM_ERR_ARG, "derivatives need limiter_K = 0 (the limiter is not differentiated)");
     if (c->kinetic)
         return fail(c, LSKUM_ERR_ARG, "derivatives need boundary = 0 (the mirror images are not differentiated)");
     lskum_status st = vjp_workspace(c);
@@ -1514,6 +1550,8 @@ extern "C" lskum_status lskum_residual_vjp(lskum_ctx *c, const double *U, const 
     LAUNCH(c, launch_state_in(c->n, c->perm, R_bar, c->vRb, c->stream));
     if (flags & LSKUM_VJP_FP32) {
         if (!c->mixed) return fail(c, LSKUM_ERR_ARG, "the FP32 product needs a mixed-precision context");
+        if (limited(c))
+            return fail(c, LSKUM_ERR_ARG, "the FP32 product needs limiter_K = 0 (the FP64 product covers the limiter)");
         if ((st = vjp_residual_fp32(c, Ui, c->vUacc, x_bar || y_bar)) != LSKUM_OK) return st;
     } else if ((st = vjp_residual(c, Ui, c->vUacc, x_bar || y_bar, false)) != LSKUM_OK) {
         return st;

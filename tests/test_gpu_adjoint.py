@@ -104,14 +104,30 @@ def test_step_vjp_is_the_same_in_a_mixed_context(small):
         assert np.array_equal(x, y)
 
 
-def test_vjp_calls_need_the_unlimited_scheme(small):
-    from paper_2403_13287_gb300.lskum import LskumError, LSKUM_ERR_ARG
-    c, _ = small
-    s = _solver(c, order=2, limiter_K=1.0)
-    W = _dev(np.zeros((4, c["n"])))
-    with pytest.raises(LskumError) as e:
-        s.step_vjp(W)
-    assert e.value.status == LSKUM_ERR_ARG
+def test_limited_step_vjp_dot_products(small):
+    """One RK4 iteration with the limiter (K = 1, M 0.85) in reverse against
+    the oracle's complex step through the same iteration; the directions
+    leave the far-field states and the wall points fixed (tied choices of
+    the limiter and of the nearest-neighbour distance sit there)."""
+    c, mask = small
+    n = c["n"]
+    U = smooth_state(c, 0.85, 1.0, amp=0.05, seed=16)
+    W = np.random.default_rng(2).standard_normal((4, n))
+    s = _solver(c, order=2, time_scheme=1, reorder=1, limiter_K=1.0, mach=0.85, aoa_deg=1.0)
+    Ub, xb, yb = (t.cpu().numpy() for t in s.step_vjp(_dev(W), _dev(U)))
+    rng = np.random.default_rng(11)
+    far, wall = c["flags"] == 2, c["flags"] == 1
+    vU = rng.standard_normal((4, n)) * np.abs(U)
+    vU[:, far] = 0.0
+    vx = rng.standard_normal(n) * 1e-3
+    vy = rng.standard_normal(n) * 1e-3
+    vx[wall] = 0.0
+    vy[wall] = 0.0
+    kw = dict(scheme=1, order=2, inner=3, mach=0.85, aoa_deg=1.0, limiter=1.0)
+    for dU, dx, dy, gpu in ((vU, None, None, np.sum(Ub * vU)), (None, vx, vy, np.sum(xb * vx) + np.sum(yb * vy))):
+        Jv = lskum_jvp.iterate_jvp(c, mask, U, dU=dU, dx=dx, dy=dy, **kw)
+        ref = np.sum(W * Jv)
+        assert abs(gpu - ref) <= 1e-10 * np.sum(np.abs(W * Jv)), (gpu, ref)
 
 
 # ---------------------------------------------------------------------------
@@ -162,3 +178,31 @@ def test_unrolled_cl_gradient_wrt_hicks_henne_amplitudes():
         d[k] = d[K + k] = 1.0
         fd = (_cl_after(_deformed(base, B, a + h * d), U0) - _cl_after(_deformed(base, B, a - h * d), U0)) / (2 * h)
         assert abs(fd - (g[k] + g[K + k])) <= 1e-5 * np.abs(g).max(), (k, fd, g[k] + g[K + k])
+
+
+def test_unrolled_cd_gradient_with_the_limiter():
+    """dCd/d(amplitudes) through 9 RK4 iterations of the limited scheme
+    (K = 1) at M 1.2, alpha 0: the checkpointed reverse sweep against the
+    oracle's complex step through the same iterations. Both differentiate
+    the branch the forward takes, with the same first-wins choices; a
+    central difference would straddle the limiter's switches, so there is
+    none here."""
+    from paper_2403_13287_gb300.adjoint import unrolled_force_gradient
+    base = naca0012_cloud(64, 35, seed=4)
+    B = hicks_henne_basis(base)
+    a = np.random.default_rng(2025).uniform(-2e-3, 2e-3, B.shape[0])
+    c = _deformed(base, B, a)
+    mach, aoa = 1.2, 0.0
+    U0 = oracle.freestream_state(c["n"], mach, aoa)
+    s = _solver(c, order=2, inner_iters=3, time_scheme=1, reorder=1, limiter_K=1.0, mach=mach, aoa_deg=aoa)
+    (cl, cd), (U0b, xb, yb), info = unrolled_force_gradient(s, _dev(U0), ITERS, cl_bar=0.0, cd_bar=1.0)
+    g = B @ yb.cpu().numpy()
+    mask = oracle.split_stencils(c)
+    ref = np.empty_like(g)
+    for k in range(B.shape[0]):
+        (_, cdo), (_, dcd) = lskum_jvp.unrolled_forces(c, mask, U0, ITERS, dy=B[k], scheme=1, mach=mach,
+                                                       aoa_deg=aoa, limiter=1.0)
+        ref[k] = dcd
+    assert abs(cd - cdo) <= 1e-10 * abs(cdo)
+    assert np.abs(ref).max() > 0
+    assert np.all(np.abs(g - ref) <= 1e-8 * np.abs(ref).max()), (g, ref)

@@ -145,10 +145,15 @@ def test_vjp_is_deterministic_and_precision_independent(small):
 def test_vjp_arguments(small):
     from paper_2403_13287_gb300.lskum import LskumError, LSKUM_ERR_ARG
     c, _ = small
-    s = _solver(c, order=2, limiter_K=1.0)
     Rb = _dev(np.zeros((4, c["n"])))
+    # the limiter is differentiated by the FP64 product only
+    sm = _solver(c, order=2, limiter_K=1.0, precision=1)
     with pytest.raises(LskumError) as e:
-        s.residual_vjp(Rb)
+        sm.residual_vjp(Rb, fp32=True)
+    assert e.value.status == LSKUM_ERR_ARG
+    sk = _solver(c, order=2, boundary=1)
+    with pytest.raises(LskumError) as e:
+        sk.residual_vjp(Rb)
     assert e.value.status == LSKUM_ERR_ARG
     s1 = _solver(c, order=2)
     Ub, xb, yb = s1.residual_vjp(Rb, want_xy=False)
@@ -200,3 +205,61 @@ def test_fp32_vjp_agrees_with_fp64(small, order):
     with pytest.raises(LskumError) as e:
         s64.residual_vjp(_dev(Rb), _dev(U), fp32=True)
     assert e.value.status == LSKUM_ERR_ARG
+
+
+# ---------------------------------------------------------------------------
+# the limiter (Venkatakrishnan, limiter_K > 0)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("K,reorder", [(1.0, 0), (1.0, 1), (0.3, 1)])
+def test_limited_vjp_entries_match_the_oracle(small, K, reorder):
+    """The limiter is piecewise smooth; both sides differentiate the branch
+    the forward takes, with the same first-wins choices (stencil extremes,
+    the largest reconstruction shift, the nearest neighbour), so ties such
+    as the far-field points' equal states give the same one-sided
+    derivative on both sides."""
+    c, mask = small
+    n = c["n"]
+    U = smooth_state(c, 0.85, 1.0, amp=0.05, seed=13)
+    rng = np.random.default_rng(200 + reorder)
+    Rb = rng.standard_normal((4, n))
+    s = _solver(c, order=2, inner_iters=3, reorder=reorder, limiter_K=K, mach=0.85, aoa_deg=1.0)
+    Ub, xb, yb = (t.cpu().numpy() for t in s.residual_vjp(_dev(Rb), _dev(U)))
+    ent = _sample(n, rng)
+    want = lskum_jvp.vjp_entries(c, mask, U, Rb, ent, order=2, inner=3, limiter=K)
+    got = _pick(ent, Ub, xb, yb)
+    scale = np.max(np.abs(want))
+    assert scale > 0
+    assert np.all(np.abs(got - want) <= 1e-10 * scale), np.max(np.abs(got - want)) / scale
+    # the limiter's terms matter here: the unlimited product differs
+    s0 = _solver(c, order=2, inner_iters=3, reorder=reorder, mach=0.85, aoa_deg=1.0)
+    U0b = s0.residual_vjp(_dev(Rb), _dev(U))[0].cpu().numpy()
+    assert np.max(np.abs(U0b - Ub)) > 1e-3 * np.max(np.abs(Ub))
+
+
+def test_limited_dot_product_identity_at_160k():
+    """<R_bar, J v> (oracle, complex step, limiter K = 1) = <J^T R_bar, v>
+    (GPU) on the 160k-point cloud at M 1.2 with the limiter active; the
+    directions leave the far-field states and the wall points fixed (tied
+    choices there are kinks, where a directional derivative has two sides)."""
+    c = naca0012_cloud(512, 311)
+    mask = oracle.split_stencils(c)
+    n = c["n"]
+    U = smooth_state(c, 1.2, 0.0, amp=0.05, seed=15)
+    rng = np.random.default_rng(41)
+    Rb = rng.standard_normal((4, n))
+    s = _solver(c, order=2, inner_iters=3, reorder=1, limiter_K=1.0, mach=1.2, aoa_deg=0.0)
+    Ub, xb, yb = (t.cpu().numpy() for t in s.residual_vjp(_dev(Rb), _dev(U)))
+    far, wall = c["flags"] == 2, c["flags"] == 1
+    vU = rng.standard_normal((4, n)) * np.abs(U)
+    vU[:, far] = 0.0
+    h = 1e-3 * np.median(np.abs(np.diff(c["x"])))
+    vx = rng.standard_normal(n) * h
+    vy = rng.standard_normal(n) * h
+    vx[wall] = 0.0
+    vy[wall] = 0.0
+    for dU, dx, dy, lhs_gpu in ((vU, None, None, np.sum(Ub * vU)),
+                                (None, vx, vy, np.sum(xb * vx) + np.sum(yb * vy))):
+        Jv = lskum_jvp.jvp(c, mask, U, dU=dU, dx=dx, dy=dy, order=2, inner=3, limiter=1.0)
+        lhs = np.sum(Rb * Jv)
+        mag = np.sum(np.abs(Rb * Jv))
+        assert abs(lhs_gpu - lhs) <= 1e-10 * mag, (lhs_gpu, lhs, mag)
