@@ -946,6 +946,14 @@ def measure_adjoint(args, dist, sampler):
     ms_res_m = timed(lambda: sm.residual(U), 5)
     ms_res_vjp32 = timed(lambda: sm.residual_vjp(Rb, U, fp32=True), 3)
     sm.close()
+    # the limited scheme (K = 1) at the supersonic condition: the residual VJP
+    # through the limiter, on the same cloud
+    sl = lskum.Solver(cloud, order=2, inner_iters=args.inner, time_scheme=1, cfl=args.cfl, mach=1.2,
+                      aoa_deg=0.0, reorder=1, limiter_K=1.0, precision=0, stream=stream.cuda_stream)
+    Ul = torch.from_numpy(smooth_state(cloud, 1.2, 0.0, amp=0.05, seed=9)).cuda()
+    ms_res_l = timed(lambda: sl.residual(Ul), 5)
+    ms_res_vjp_l = timed(lambda: sl.residual_vjp(Rb, Ul), 3)
+    sl.close()
     ms_step = timed(lambda: s.step(1, history=False), 3)
     s.set_state(U)
     ms_step_vjp = timed(lambda: s.step_vjp(Rb, U), 3)
@@ -962,7 +970,11 @@ def measure_adjoint(args, dist, sampler):
             "dtype": "f64", "residual_ms": ms_res, "residual_vjp_ms": ms_res_vjp,
             "residual_vjp_over_residual": ms_res_vjp / ms_res,
             "mixed_residual_ms": ms_res_m, "residual_vjp_fp32_ms": ms_res_vjp32,
-            "fp32_vjp_speedup": ms_res_vjp / ms_res_vjp32, "iteration_ms": ms_step,
+            "fp32_vjp_speedup": ms_res_vjp / ms_res_vjp32,
+            "limited_m12": {"residual_ms": ms_res_l, "residual_vjp_ms": ms_res_vjp_l,
+                            "residual_vjp_over_residual": ms_res_vjp_l / ms_res_l,
+                            "note": "limiter K = 1, M 1.2, alpha 0: the VJP through the limiter"},
+            "iteration_ms": ms_step,
             "iteration_vjp_ms": ms_step_vjp, "iteration_vjp_over_iteration": ms_step_vjp / ms_step,
             "residual_vjp_workspace_bytes": free0 - free1, "iteration_vjp_workspace_bytes": free1 - free2,
             "unrolled": {"iterations": iters, "seconds": sweep_s, "cl": cl, "checkpoint_every": info["checkpoint_every"],
