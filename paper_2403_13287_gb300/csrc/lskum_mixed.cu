@@ -779,8 +779,6 @@ static const int kQgradShape[][2] = {{128, 8}, {64, 16}, {256, 4}, {128, 6}, {25
 // flux shapes 6-11 repeat 0-5 with the software-pipelined neighbour loop,
 // 12-16 and 22-23 give that loop more registers, 17-21 stage each tile's
 // rows in shared memory
-static constexpr int kFirstStagedFlux = 17;
-static constexpr int kLastStagedFlux = 21;
 static const int kFluxShape[][2] = {{128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4},
                                     {128, 7}, {64, 14}, {256, 3}, {128, 6}, {128, 8}, {256, 4},
                                     {128, 5}, {128, 4}, {64, 8},  {96, 6},  {128, 3},
@@ -788,8 +786,6 @@ static const int kFluxShape[][2] = {{128, 7}, {64, 14}, {256, 3}, {128, 6}, {128
                                     {64, 12}, {64, 10}};
 static_assert(sizeof kFluxShape / sizeof kFluxShape[0] == kNumFluxVariants, "one shape per flux variant");
 
-int mixed_first_staged_variant() { return kFirstStagedFlux; }
-int mixed_last_staged_variant() { return kLastStagedFlux; }
 
 int mixed_variants(int kernel_class)
 {

@@ -81,9 +81,6 @@ cudaError_t launch_mixed_prep(const DevGeom &g, uint8_t *flag, float2 *nrm_f, fl
 cudaError_t launch_sell_fill(int64_t n, const int32_t *off, const int32_t *slice_off, const int32_t *idx,
                              const uint8_t *mask, const float2 *dxy, const float2 *lsw, const float2 *fxw,
                              const double2 *fxw64, const MixedGeom &m, cudaStream_t s);
-// the staged flux variants, first and last (they read MixedGeom's tile arrays)
-int mixed_first_staged_variant();
-int mixed_last_staged_variant();
 // launch-shape variants (threads per block, minimum resident blocks per SM);
 // kernel_class 0 = flux, 1 = q-derivatives; variant 0 is the default
 int mixed_variants(int kernel_class);
