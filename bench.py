@@ -66,7 +66,7 @@ def parse():
                     help="instead of timing: the mixed form's converged error against FP64 at 160k and 2.5M points")
     ap.add_argument("--acc-iters-160k", type=int, default=60000)
     ap.add_argument("--acc-cfl-160k", type=float, default=1.0)
-    ap.add_argument("--acc-iters-2p5m", type=int, default=100000)
+    ap.add_argument("--acc-iters-2p5m", type=int, default=300000)
     ap.add_argument("--acc-cfl-2p5m", type=float, default=0.5, help="CFL 0.8 loses positivity on this cloud")
     ap.add_argument("--acc-iters-fp64-restart", type=int, default=10000,
                     help="2.5M: iterations both forms run on from the mixed form's state")
