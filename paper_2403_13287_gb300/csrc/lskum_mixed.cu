@@ -354,6 +354,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
 // of the stage residuals being formed in FP32. FP64 <-> FP32 conversions go
 // through the integer pipe.
 // --------------------------------------------------------------------------
+// PTX prefetch of the line holding a into L2 (a hint; a must be a valid
+// global address)
+__device__ __forceinline__ void prefetch_l2(const void *a)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 __device__ __forceinline__ void flag_nonphysical_m(int *status, int64_t p)
 {
     atomicOr(status, STATUS_NONPHYSICAL);
@@ -471,26 +478,44 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
         sq = s_q;
         sg = s_g;
     }
+    // the point's own loads are all issued before its flag is tested, so
+    // that they are in flight together (far-field points read them in vain)
     uint8_t fl = FLAG_FARFIELD;
-    if (live) fl = g.flag[p];
-    const uint8_t flag = fl & 3;
-    const bool fp64 = (fl & FLAG_FP64_CLOSURE) != 0;
-    float Rl[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // residual, global frame
-    double R64g[4] = {0.0, 0.0, 0.0, 0.0};   // FP64-closure points
-    // far-field points are held at the free stream, except in the kinetic boundary mode
-    if (live && (flag != FLAG_FARFIELD || KIN)) {
-        const int deg = g.off[p + 1] - g.off[p];
-        const int64_t base = g.slice_off[p >> 5] + (p & 31);
-        const float2 n0 = g.nrm[p];
-        const float tx = n0.y, ty = -n0.x;
-        float q0[4], g0[8];
-        const bool second = P.order == 2;
+    int deg = 0;
+    int64_t base = 0;
+    float2 n0 = make_float2(0.0f, 0.0f);
+    float q0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, g0[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    const bool second = P.order == 2;
+    if (live) {
+        fl = g.flag[p];
+        deg = g.off[p + 1] - g.off[p];
+        base = g.slice_off[p >> 5] + (p & 31);
+        n0 = g.nrm[p];
         if constexpr (STAGE) {
             row_f(sq, sg, threadIdx.x, second, q0, g0);
         } else {
             load4f(P.q, p, q0);
             if (second) load8f(P.qg, p, g0);
         }
+        if (P.mode != 0) {
+            // the state update's inputs are brought into L2 while the fluxes
+            // are evaluated (a hint: no register waits for it)
+            prefetch_l2(P.Un + 4 * p);
+            if (P.mode == 2 && P.stage > 0) {
+                prefetch_l2(P.dt + p);
+                prefetch_l2(reinterpret_cast<const float *>(P.acc) + 4 * p);
+            } else {
+                prefetch_l2(g.dmin + p);
+            }
+        }
+    }
+    const uint8_t flag = fl & 3;
+    const bool fp64 = (fl & FLAG_FP64_CLOSURE) != 0;
+    float Rl[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // residual, global frame
+    double R64g[4] = {0.0, 0.0, 0.0, 0.0};   // FP64-closure points
+    // far-field points are held at the free stream, except in the kinetic boundary mode
+    if (live && (flag != FLAG_FARFIELD || KIN)) {
+        const float tx = n0.y, ty = -n0.x;
         float R[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         double R64[4] = {0.0, 0.0, 0.0, 0.0};
         bool ok = true;
