@@ -442,8 +442,9 @@ __device__ __forceinline__ void edge_residual_f(const float2 qt[4], uint32_t m, 
     }
 }
 
-// PF: software-pipelined neighbour loop (the next slot's record, index and
-// neighbour values are loaded while the current slot's fluxes are evaluated).
+// PF: software-pipelined neighbour loop (the next slot's record and
+// neighbour values, and the index of the slot after it, are loaded while the
+// current slot's fluxes are evaluated).
 // STAGE: the CTA is one tile of kTile points. It first copies the q and
 // grad q of its own points and of up to kHaloCap neighbours outside the tile
 // (each once, the list made at create) into shared memory with independent
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
         double R64[4] = {0.0, 0.0, 0.0, 0.0};
         bool ok = true;
         float4 rec_n = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        int32_t im_n = 0;
+        int32_t im_n = 0, im_nn = 0;  // slot records one ahead, indices two ahead
         float q_n[4] = {0, 0, 0, 0}, g_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if constexpr (STAGE) {
             // only the slot records are prefetched; the rows are in shared memory
@@ -561,6 +562,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
                 load4f(P.q, i, q_n);
                 if (second) gather8f(P.qg, i, g_n);
             }
+            if (deg > 1) im_nn = g.sidx[base + 32];
         }
         if constexpr (!STAGE) for (int s = 0; s < deg; ++s) {
             const int64_t e = base + 32 * s;
@@ -576,11 +578,14 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
 #pragma unroll
                 for (int k = 0; k < 8; ++k) gi[k] = g_n[k];
                 if (s + 1 < deg) {
+                    // the gathers of slot s + 1 use an index read one
+                    // iteration ago, so they issue without waiting for it
                     rec_n = g.gf[e + 32];
-                    im_n = g.sidx[e + 32];
+                    im_n = im_nn;
                     const int in = im_n & kSlotIndexMask;
                     load4f(P.q, in, q_n);
                     if (second) gather8f(P.qg, in, g_n);
+                    if (s + 2 < deg) im_nn = g.sidx[e + 64];
                 }
                 w = make_float2(rec.z, rec.w);
                 if (w.x == 0.0f && w.y == 0.0f) continue;
