@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
                 sy[k] += a.y * dq;
             }
         };
-#pragma unroll 2
+#pragma unroll 4
         for (int s = 0; s < deg; ++s) {
             const int64_t e = base + 32 * s;
             float qi[4];
@@ -323,6 +323,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
     if constexpr (LIMIT) {
         if constexpr (INNER) load4f(ext, p, xm);
         float dmax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        // the weights are read again (from L1); unrolled so that several
+        // reads are in flight (a maximum does not depend on the order)
+#pragma unroll 4
         for (int s = 0; s < deg; ++s) {
             const float2 a = g.ga[base + 32 * s];
             const float2 d = make_float2(M.x * a.x + M.y * a.y, M.y * a.x + M.z * a.y);
