@@ -85,7 +85,7 @@ struct Gas {
 // with the velocity taken in the frame (t, n) of P_0.
 struct Prim {
     double us, un;  // u.t, u.n
-    double sqb;     // sqrt(beta)
+    double Ss, Sn;  // S = u.t sqrt(beta), u.n sqrt(beta): the split fluxes' arguments
     double hrho;    // rho/2
     double hp;      // p/2
     double h;       // (rho E + p)/rho
@@ -163,9 +163,15 @@ __device__ __forceinline__ bool prim_from_q(const double qt[4], const Gas &gas, 
     // (p/rho below 1e-307) is reported non-physical instead
     const bool ib_ok = (__double_as_longlong(ib) >> 52) > 2;
     const double hib = half_of(ib);
-    s.us = fma(qt[1], tx, qt[2] * ty) * hib;
-    s.un = fma(qt[1], n0.x, qt[2] * n0.y) * hib;
-    s.sqb = beta * rsb;
+    // u.t = m_t/(2 beta) and S_t = u.t sqrt(beta) = m_t/(2 sqrt(beta)), with
+    // m_t = q2 tx + q3 ty: 1/(2 sqrt(beta)) is rsb/2, an exponent decrement,
+    // so no sqrt(beta) is formed (u.n and S_n alike)
+    const double mt = fma(qt[1], tx, qt[2] * ty), mn = fma(qt[1], n0.x, qt[2] * n0.y);
+    const double hrsb = half_of(rsb);
+    s.us = mt * hib;
+    s.un = mn * hib;
+    s.Ss = mt * hrsb;
+    s.Sn = mn * hrsb;
     const double w2 = fma(s.us, s.us, s.un * s.un);   // |u|^2
     double hrho;
     if (gas.g14) {
@@ -246,11 +252,11 @@ static constexpr unsigned long long kSignBit = 0x8000000000000000ull;
 // evaluated as Q = rho A = rho/2 (1 + sgn erf S), W = sgn rho B:
 // G0 = un Q + W, G1 = p A + un G0, G2 = ut G0, and with h = (rhoE + p)/rho,
 // e2 = (rhoE + p/2)/rho = h - 1/(4 beta): G3 = h un Q + e2 W = h G0 - W/(4 beta).
-// sbit = 0 for G+, kSignBit for G-: the products by sgn are sign flips.
+// sbit = 0 for G+, kSignBit for G-: the products by sgn are sign flips. S
+// (= un sqrt(beta)) comes from prim_from_q.
 __device__ __forceinline__ void split_flux(unsigned long long sbit, const Prim &s, double un, double ut,
-                                           double G[4])
+                                           double S, double G[4])
 {
-    const double S = un * s.sqb;
     double erfS, eS;
     erf_exp(S, erfS, eS);
     const double fe = flip_sign(erfS, sbit);

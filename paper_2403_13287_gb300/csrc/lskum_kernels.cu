@@ -306,8 +306,8 @@ __device__ __forceinline__ void edge_residual(const double qti[4], const double 
     if ((__double_as_longlong(w.x) & ~(long long)kSignBit) != 0) {
         const unsigned long long sg = (m & M_XPOS) ? 0ull : kSignBit;
         double Gi[4], G0[4];
-        split_flux(sg, si, us_i, un_i, Gi);
-        split_flux(sg, s0, us_0, un_0, G0);
+        split_flux(sg, si, us_i, un_i, si.Ss, Gi);
+        split_flux(sg, s0, us_0, un_0, s0.Ss, G0);
         // dG = G(q~_i) - G(q~_0) from the two rounded fluxes: an unfused
         // subtraction, so equal states give exactly zero (a contracted
         // fma(rho_i, m_i, -rho_0 m_0) would leave a product's rounding)
@@ -317,8 +317,8 @@ __device__ __forceinline__ void edge_residual(const double qti[4], const double 
     if ((__double_as_longlong(w.y) & ~(long long)kSignBit) != 0) {
         const unsigned long long sg = (m & M_YPOS) ? 0ull : kSignBit;
         double Gi[4], G0[4];
-        split_flux(sg, si, un_i, us_i, Gi);
-        split_flux(sg, s0, un_0, us_0, G0);
+        split_flux(sg, si, un_i, us_i, si.Sn, Gi);
+        split_flux(sg, s0, un_0, us_0, s0.Sn, G0);
         // Gn components are [mass, n-momentum, s-momentum, energy]
         R[0] += w.y * __dsub_rn(Gi[0], G0[0]);
         R[1] += w.y * __dsub_rn(Gi[2], G0[2]);
