@@ -207,12 +207,12 @@ def algorithmic_bytes_per_point_mixed(kernel, dbar, order, scheme):
 # Per-unit figures of the FP64 fused flux kernel (ncu counters, 640k-point
 # capture, profiles/k_flux_update_fp64_naca0012_640k.md): executed FP64
 # instructions per stencil edge (every FP64 instruction, of which DFMA + DMUL +
-# DADD are 178.0) and the flops they carry (2 DFMA + DMUL + DADD); DRAM bytes
+# DADD are 176.0) and the flops they carry (2 DFMA + DMUL + DADD); DRAM bytes
 # per point of one full-size 2.5M launch (single-pass capture,
 # profiles/launch_list_naca0012_2p5m_fp64.md).
-FP64_INSTR_PER_EDGE_FLUX = 180.33
-FP64_FLOPS_PER_EDGE_FLUX = 287.05
-FLUX_DRAM_BYTES_PER_POINT = 598.3
+FP64_INSTR_PER_EDGE_FLUX = 178.34
+FP64_FLOPS_PER_EDGE_FLUX = 285.05
+FLUX_DRAM_BYTES_PER_POINT = 598.0
 # FP64 peak: ncu's DFMA unit count, 304 FP64 thread-instructions per cycle
 # (each DFMA 2 flops), at the 2070 MHz maximum SM clock
 FP64_PEAK_GINSTR = 304 * 2.070
