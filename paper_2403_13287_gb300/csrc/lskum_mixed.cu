@@ -365,6 +365,42 @@ __global__ void __launch_bounds__(THREADS, MINB) k_qgrad_mixed(MixedGeom g, cons
 // of the stage residuals being formed in FP32. FP64 <-> FP32 conversions go
 // through the integer pipe.
 // --------------------------------------------------------------------------
+// the point's own q and grad q from its thread's slot of shared memory
+// (three float4: q, grad q x, grad q y); volatile, so the compiler reads them
+// where they are used instead of keeping them in registers across the loop,
+// and ordered after the stores that filled the slot (memory clobber)
+__device__ __forceinline__ void own_row(const float4 *slot, bool second, float q[4], float gq[8])
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(slot);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(q[0]), "=f"(q[1]), "=f"(q[2]), "=f"(q[3])
+                 : "r"(a)
+                 : "memory");
+    if (second) {
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(gq[0]), "=f"(gq[1]), "=f"(gq[2]), "=f"(gq[3])
+                     : "r"(a + 16)
+                     : "memory");
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(gq[4]), "=f"(gq[5]), "=f"(gq[6]), "=f"(gq[7])
+                     : "r"(a + 32)
+                     : "memory");
+    }
+}
+
+// a 16-byte copy from global to this thread's shared memory that bypasses
+// the registers (cp.async; both addresses 16-byte aligned), grouped by
+// commit and awaited by wait (this thread's own copies; the data is then
+// visible to this thread)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // PTX prefetch of the line holding a into L2 (a hint; a must be a valid
 // global address)
 __device__ __forceinline__ void prefetch_l2(const void *a)
@@ -455,7 +491,11 @@ __device__ __forceinline__ void edge_residual_f(const float2 qt[4], uint32_t m, 
 
 // PF: software-pipelined neighbour loop (the next slot's record and
 // neighbour values, and the index of the slot after it, are loaded while the
-// current slot's fluxes are evaluated).
+// current slot's fluxes are evaluated). In the plain boundary mode the
+// neighbour values travel by cp.async into this thread's slot of shared
+// memory and the point's own q and grad q wait there too, so that neither
+// holds registers across the loop: 80 registers without spills, 24 resident
+// warps per SM at 64 x 12 instead of 20 at 96 registers.
 // STAGE: the CTA is one tile of kTile points. It first copies the q and
 // grad q of its own points and of up to kHaloCap neighbours outside the tile
 // (each once, the list made at create) into shared memory with independent
@@ -490,6 +530,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
         sq = s_q;
         sg = s_g;
     }
+    // pipelined plain-mode loop: the point's own row waits in shared memory
+    // (this thread's slot) during the neighbour loop instead of in registers
+    constexpr bool OWN_SMEM = PF && !STAGE && !KIN;
+    __shared__ float4 s_own[OWN_SMEM ? 3 * THREADS : 1];
+    // and the next slot's neighbour row is copied there too (cp.async, two
+    // buffers: the one being read and the one being filled)
+    __shared__ float4 s_nb[OWN_SMEM ? 2 * 3 * THREADS : 1];
     // the point's own loads are all issued before its flag is tested, so
     // that they are in flight together (far-field points read them in vain)
     uint8_t fl = FLAG_FARFIELD;
@@ -508,6 +555,11 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
         } else {
             load4f(P.q, p, q0);
             if (second) load8f(P.qg, p, g0);
+        }
+        if constexpr (OWN_SMEM) {
+            s_own[3 * threadIdx.x] = make_float4(q0[0], q0[1], q0[2], q0[3]);
+            s_own[3 * threadIdx.x + 1] = make_float4(g0[0], g0[1], g0[2], g0[3]);
+            s_own[3 * threadIdx.x + 2] = make_float4(g0[4], g0[5], g0[6], g0[7]);
         }
         if (P.mode != 0) {
             // the state update's inputs are brought into L2 while the fluxes
@@ -565,6 +617,20 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
                 recon_pair(qi, gi, q0, g0, make_float2(rec.x, rec.y), second, qt);
                 edge_residual_f(qt, m, w, fp64, g.fxw64, e, n0, tx, ty, P.inv_gm1, P.g14, R, R64, ok);
             }
+        } else if constexpr (OWN_SMEM) {
+            if (deg > 0) {
+                rec_n = g.gf[base];
+                im_n = g.sidx[base];
+                const int i = im_n & kSlotIndexMask;
+                float4 *b = s_nb + 3 * threadIdx.x;
+                cp_async16(b, reinterpret_cast<const float4 *>(P.q) + i);
+                if (second) {
+                    cp_async16(b + 1, reinterpret_cast<const float4 *>(P.qg) + 2 * i);
+                    cp_async16(b + 2, reinterpret_cast<const float4 *>(P.qg) + 2 * i + 1);
+                }
+                cp_async_commit();
+            }
+            if (deg > 1) im_nn = g.sidx[base + 32];
         } else if constexpr (PF) {
             if (deg > 0) {
                 rec_n = g.gf[base];
@@ -580,7 +646,35 @@ __global__ void __launch_bounds__(THREADS, MINB) k_flux_update_mixed(MixedFluxPa
             float2 qt[4];
             uint32_t m;
             float2 w, d;
-            if constexpr (PF) {
+            if constexpr (OWN_SMEM) {
+                const float4 rec = rec_n;
+                const int32_t im = im_n;
+                // slot s's row has landed in buffer s & 1; slot s + 1's is
+                // copied into the other buffer while slot s is evaluated
+                cp_async_wait_all();
+                float qi[4], gi[8];
+                own_row(s_nb + 3 * (THREADS * (s & 1) + threadIdx.x), second, qi, gi);
+                if (s + 1 < deg) {
+                    rec_n = g.gf[e + 32];
+                    im_n = im_nn;
+                    const int in = im_n & kSlotIndexMask;
+                    float4 *b = s_nb + 3 * (THREADS * ((s + 1) & 1) + threadIdx.x);
+                    cp_async16(b, reinterpret_cast<const float4 *>(P.q) + in);
+                    if (second) {
+                        cp_async16(b + 1, reinterpret_cast<const float4 *>(P.qg) + 2 * in);
+                        cp_async16(b + 2, reinterpret_cast<const float4 *>(P.qg) + 2 * in + 1);
+                    }
+                    cp_async_commit();
+                    if (s + 2 < deg) im_nn = g.sidx[e + 64];
+                }
+                w = make_float2(rec.z, rec.w);
+                if (w.x == 0.0f && w.y == 0.0f) continue;
+                m = (uint32_t)im >> 28;
+                d = make_float2(rec.x, rec.y);
+                float q0s[4], g0s[8];
+                own_row(s_own + 3 * threadIdx.x, second, q0s, g0s);
+                recon_pair(qi, gi, q0s, g0s, d, second, qt);
+            } else if constexpr (PF) {
                 const float4 rec = rec_n;
                 const int32_t im = im_n;
                 float qi[4], gi[8];
