@@ -390,6 +390,15 @@ lskum_status lskum_autotune(lskum_ctx *ctx, int reps, lskum_tuning *out);
 lskum_status lskum_set_tuning(lskum_ctx *ctx, int flux_variant, int qgrad_variant);
 
 /*
+ * Mixed contexts: *count receives the number of points whose least-squares
+ * closures run in FP64 because FP32 would lose bits there (a sub-stencil
+ * with sum |w_i||P_i - P_0| > 16; not in the paper, a property of the mixed
+ * form). 0 for an FP64 context. Does not synchronise. LSKUM_ERR_ARG on a null
+ * argument.
+ */
+lskum_status lskum_mixed_fp64_points(lskum_ctx *ctx, int64_t *count);
+
+/*
  * Lift and drag of case k (a batch) or of the only case: as lskum_forces,
  * with case k's free stream; cp receives its n_wall values in its contour order.
  */

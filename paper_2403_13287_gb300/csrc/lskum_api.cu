@@ -1719,6 +1719,14 @@ extern "C" lskum_status lskum_set_tuning(lskum_ctx *c, int flux_variant, int qgr
     return LSKUM_OK;
 }
 
+extern "C" lskum_status lskum_mixed_fp64_points(lskum_ctx *c, int64_t *count)
+{
+    if (!c || !count) return LSKUM_ERR_ARG;
+    c->err.clear();
+    *count = c->mixed ? (int64_t)c->n_fp64_closure : 0;
+    return LSKUM_OK;
+}
+
 // times `reps` launches of one variant on the context's stream (milliseconds per launch)
 template <class F>
 static lskum_status time_variant(lskum_ctx *c, int reps, cudaEvent_t e0, cudaEvent_t e1, F launch, double *ms)

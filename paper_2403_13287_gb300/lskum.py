@@ -101,6 +101,7 @@ def load(build_if_missing: bool = True):
     L.lskum_case_forces.argtypes = [_p, _int, _p, _p, _p]
     L.lskum_autotune.argtypes = [_p, _int, ctypes.POINTER(lskum_tuning)]
     L.lskum_set_tuning.argtypes = [_p, _int, _int]
+    L.lskum_mixed_fp64_points.argtypes = [_p, ctypes.POINTER(ctypes.c_int64)]
     L.lskum_residual_vjp.argtypes = [_p, _p, _p, _p, _p, _p, _int]
     L.lskum_step_vjp.argtypes = [_p, _p, _p, _p, _p, _p, _int]
     L.lskum_forces_vjp.argtypes = [_p, _int, ctypes.c_double, ctypes.c_double, _p, _p, _p, _int]
@@ -116,7 +117,7 @@ def load(build_if_missing: bool = True):
     L.lskum_profile.argtypes = [_p, _int]
     L.lskum_kernel_time.argtypes = [_p, _int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]
     for name in ("lskum_case_range", "lskum_case_forces", "lskum_autotune", "lskum_set_tuning",
-                 "lskum_step_vjp", "lskum_forces_vjp"):
+                 "lskum_step_vjp", "lskum_forces_vjp", "lskum_mixed_fp64_points"):
         getattr(L, name).restype = _int
     for name in ("lskum_step", "lskum_residual", "lskum_residual_vjp", "lskum_q_derivatives", "lskum_timestep",
                  "lskum_forces", "lskum_get_state", "lskum_set_state", "lskum_get_stencil_masks",
@@ -243,6 +244,12 @@ class Solver:
 
     def set_tuning(self, flux_variant, qgrad_variant):
         self._check(self._L.lskum_set_tuning(self._ctx, int(flux_variant), int(qgrad_variant)))
+
+    def mixed_fp64_points(self):
+        """Points whose least-squares closures run in FP64 (mixed contexts; 0 for FP64)."""
+        v = ctypes.c_int64(0)
+        self._check(self._L.lskum_mixed_fp64_points(self._ctx, ctypes.byref(v)))
+        return int(v.value)
 
     def _check(self, st):
         if st != LSKUM_OK:

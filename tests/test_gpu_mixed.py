@@ -94,6 +94,53 @@ def test_mixed_q_derivatives_match_oracle(small, inner, limiter):
     assert np.all(np.abs(qy - oy) <= 2e-5 * S)
 
 
+@pytest.fixture(scope="module")
+def closure_cloud():
+    """A small cloud with FP64-closure points (least-squares closures that
+    FP32 would get wrong): the most irregular of a few jittered clouds."""
+    best, best_n = None, 0
+    for W, L, seed, jitter in ((130, 24, 11, 0.1), (160, 40, 5, 0.25), (96, 56, 3, 0.35), (120, 40, 7, 0.45)):
+        from paper_2403_13287_gb300.lskum import LskumError
+        c = naca0012_cloud(W, L, seed=seed, jitter=jitter, shuffle=True)
+        try:
+            s = _solver(c, order=2)
+        except LskumError:                  # a singular stencil: not a usable cloud
+            continue
+        n64 = s.mixed_fp64_points()
+        s.close()
+        if n64 > best_n:
+            best, best_n = c, n64
+    assert best_n > 0, "no candidate cloud has FP64-closure points"
+    return best
+
+
+@pytest.mark.parametrize("variant", [7, 22, 23])
+@pytest.mark.parametrize("order,limiter", [(1, 0.0), (2, 1.0)])
+def test_pipelined_shapes_residual_matches_oracle(closure_cloud, variant, order, limiter):
+    """The software-pipelined flux loop (shapes 7, 22, 23). In the plain
+    boundary mode it takes the neighbour rows by cp.async into shared memory,
+    where the point's own row and its FP64-closure sums also wait; on a
+    shuffled cloud with FP64-closure points it meets the mixed form's bar."""
+    c = closure_cloud
+    U = _perturbed_state(c, 0.85, 1.0, seed=5)
+    s = _solver(c, order=order, inner_iters=3, reorder=1, limiter_K=limiter)
+    assert s.mixed_fp64_points() > 0
+    s.set_tuning(variant, 0)
+    R = s.residual(_dev(U)).cpu().numpy()
+    s.close()
+    Ro, S = oracle.residual(c, oracle.split_stencils(c), U, order=order, inner=3, want_scale=True,
+                            limiter=limiter)
+    err = np.abs(R - Ro) / np.maximum(S, 1e-300)
+    assert np.all(np.abs(R - Ro) <= 3e-5 * S), err.max()
+
+
+def test_fp64_context_has_no_fp64_closure_points(small):
+    from paper_2403_13287_gb300.lskum import Solver
+    s = Solver(small, precision=0)
+    assert s.mixed_fp64_points() == 0
+    s.close()
+
+
 def test_mixed_freestream_is_exactly_preserved():
     c = naca0012_cloud(320, 30)
     s = _solver(c, order=2, mach=1.2, aoa_deg=0.0, limiter_K=1.0)
