@@ -477,13 +477,13 @@ def measure_e2e(solver, n, steps, dist):
 # DRAM bytes per point of one launch of the mixed kernels on the 2.5M-point
 # workload, from a full-size single-pass ncu capture of the current kernels
 # (profiles/mixed_kernels_naca0012_2p5m.md); None where not captured
-MIXED_TRAFFIC_PER_POINT = {"flux": 345.7, "qgrad": 193.2}
+MIXED_TRAFFIC_PER_POINT = {"flux": 345.9, "qgrad": 193.2}
 # warp instructions per stencil edge of the mixed flux kernel at its autotuned
-# shape (64 x 10; ncu smsp__inst_executed.sum, 640k-point capture with
+# shape (64 x 12; ncu smsp__inst_executed.sum, 640k-point capture with
 # 5,167,022 edges, profiles/k_flux_update_mixed_naca0012_640k.md), for the
 # issue view: 4 warp instructions per cycle per SM at the 2.07 GHz maximum
 # SM clock
-MIXED_FLUX_WARP_INSTR_PER_EDGE = 53635515 / 5167022
+MIXED_FLUX_WARP_INSTR_PER_EDGE = 55941364 / 5167022
 ISSUE_PEAK_GINSTR = 152 * 4 * 2.070
 
 
