@@ -40,6 +40,7 @@ struct lskum_ctx {
     double *dmin = nullptr;
     int32_t *off = nullptr, *idx = nullptr, *off_in = nullptr;
     double2 *lsw = nullptr, *fxw = nullptr, *hd = nullptr;
+    float2 *hd_f = nullptr;  // FP64 contexts: hd in FP32, for the limiter's screening of d_m
     // kinetic boundary mode: mirror images of the neighbours of wall and
     // far-field points (CSR per internal point) and each case's free-stream q
     bool kinetic = false;
@@ -146,7 +147,7 @@ struct lskum_ctx {
     {
         DevGeom g{};
         g.n = n; g.xy = xy; g.nrm = nrm; g.flag = flag; g.dmin = dmin;
-        g.off = off; g.idx = idx; g.mask = mask; g.lsw = lsw; g.fxw = fxw; g.hd = hd;
+        g.off = off; g.idx = idx; g.mask = mask; g.lsw = lsw; g.fxw = fxw; g.hd = hd; g.hd_f = hd_f;
         if (kinetic) {
             g.ioff = ioff; g.iidx = iidx; g.imask = imask; g.ilsw = ilsw; g.ifxw = ifxw; g.ihd = ihd;
             g.qinf = qinf; g.pcase = pcase;
@@ -643,7 +644,8 @@ static lskum_status create_impl(lskum_ctx *c, const double *x, const double *y, 
     }
     if (!c->mixed) {
         CK(c, dalloc(c, &c->hd, std::max<int64_t>(nnz, 1)));
-        LAUNCH(c, launch_half_offsets(n, c->xy, c->off, c->idx, c->hd, s));
+        CK(c, dalloc(c, &c->hd_f, std::max<int64_t>(nnz, 1)));
+        LAUNCH(c, launch_half_offsets(n, c->xy, c->off, c->idx, c->hd, c->hd_f, s));
     }
     int bad_h[2];
     CK(c, cudaMemcpyAsync(bad_h, bad, sizeof bad_h, cudaMemcpyDeviceToHost, s));

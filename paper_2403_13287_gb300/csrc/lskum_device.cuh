@@ -47,6 +47,7 @@ struct DevGeom {
     const double2 *__restrict__ lsw;
     const double2 *__restrict__ fxw;
     const double2 *__restrict__ hd;  // FP64 contexts: per edge (P_i - P_0)/2, or nullptr
+    const float2 *__restrict__ hd_f; // FP64 contexts: hd rounded to FP32 (the limiter's screening of d_m), or nullptr
     // kinetic boundary mode (all nullptr otherwise): the mirror images of the
     // neighbours of each wall and far-field point, per point in CSR form
     // (rows are empty at interior points); an image of P_i has local offsets

@@ -71,6 +71,64 @@ __device__ __forceinline__ long long order_key(long long b) { return b ^ ((b >> 
 // pass that follows.
 enum { QG_LIMIT = 1, QG_INNER = 2, QG_EXTREMA = 4 };
 
+// d_m = max_e |h_e . (sx, sy)| of each component, bit for bit the value of
+// the plain FP64 loop over the edges, with FP64 products only on the edges
+// that can hold the maximum. An FP32 pass bounds every edge's value: with
+// a = hf_x sf and b = hf_y tf (h, sx, sy rounded to FP32), the FP32
+// v = |a + b| lies within 4.01 u (|h_x sx| + |h_y sy|) of the FP64 |r_e|
+// (u = 2^-24: the three roundings to FP32, the two products and the sum,
+// each within u relative; r_e within 2^-52 of the exact value), and the
+// margin c = 2^-20 (|a| + |b|) + 2^-120 exceeds that with room for the
+// roundings of c, v - c and v + c (the absolute term covers FP32 underflow).
+// So L = max_e fl(v - c) <= max_e |r_e|, and the edge holding the maximum
+// has fl(v + c) >= L. A second FP32 pass marks the edges with
+// !(fl(v + c) < L) (a NaN or an overflow marks the edge too); the marked
+// edges (one bit each: at most LSKUM_MAX_DEGREE = 25) are then evaluated in
+// FP64 exactly as the plain loop evaluates them.
+__device__ __forceinline__ void largest_shift_screened(const DevGeom &g, int e0, int e1, const double sx[4],
+                                                       const double sy[4], unsigned long long dm[4])
+{
+    constexpr float kMargin = 9.5367431640625e-07f;  // 2^-20 = 16 u
+    constexpr float kTiny = 7.52316384526264e-37f;   // 2^-120
+    float sf[4], tf[4], L[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        sf[k] = __double2float_rn(sx[k]);
+        tf[k] = __double2float_rn(sy[k]);
+        L[k] = 0.0f;
+    }
+    for (int e = e0; e < e1; ++e) {
+        const float2 h = g.hd_f[e];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float a = h.x * sf[k], b = h.y * tf[k];
+            const float c = fmaf(kMargin, fabsf(a) + fabsf(b), kTiny);
+            L[k] = fmaxf(L[k], fabsf(a + b) - c);
+        }
+    }
+    uint32_t cand[4] = {0u, 0u, 0u, 0u};
+    for (int e = e0; e < e1; ++e) {
+        const float2 h = g.hd_f[e];
+        const uint32_t bit = 1u << (e - e0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float a = h.x * sf[k], b = h.y * tf[k];
+            const float c = fmaf(kMargin, fabsf(a) + fabsf(b), kTiny);
+            if (!(fabsf(a + b) + c < L[k])) cand[k] |= bit;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t m = cand[k];
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            const double2 h = g.hd[e0 + j];
+            dm[k] = max(dm[k], abs_bits(fma(h.x, sx[k], h.y * sy[k])));
+        }
+    }
+}
+
 // One pass, by kind:
 //   first:  G1 = sum_e a_e (q_i - q_0), the first-order solve;
 //   inner:  G1 - sum_e a_e (h_e . grad q_i) + grad q_0 / 2, which is the sum
@@ -212,16 +270,20 @@ __global__ void __launch_bounds__(128) k_qgrad(DevGeom g, const double *__restri
     if constexpr (LIMIT) {
         if constexpr (INNER) load4(ext, p, xm);
         unsigned long long dm[4] = {0, 0, 0, 0};   // bits of d_m (non-negative doubles order as integers)
-        for (int e = e0; e < e1; ++e) {
-            double2 h;
-            if (g.hd) {
-                h = g.hd[e];
-            } else {
-                const double2 xyi = g.xy[g.idx[e]];
-                h = make_double2(0.5 * (xyi.x - xy0.x), 0.5 * (xyi.y - xy0.y));
-            }
+        if (g.hd_f && e1 - e0 <= 32) {
+            largest_shift_screened(g, e0, e1, sx, sy, dm);
+        } else {
+            for (int e = e0; e < e1; ++e) {
+                double2 h;
+                if (g.hd) {
+                    h = g.hd[e];
+                } else {
+                    const double2 xyi = g.xy[g.idx[e]];
+                    h = make_double2(0.5 * (xyi.x - xy0.x), 0.5 * (xyi.y - xy0.y));
+                }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) dm[k] = max(dm[k], abs_bits(fma(h.x, sx[k], h.y * sy[k])));
+                for (int k = 0; k < 4; ++k) dm[k] = max(dm[k], abs_bits(fma(h.x, sx[k], h.y * sy[k])));
+            }
         }
         if constexpr (KIN) {
             for (int e = g.ioff[p]; e < g.ioff[p + 1]; ++e) {

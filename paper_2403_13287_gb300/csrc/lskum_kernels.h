@@ -88,7 +88,7 @@ cudaError_t launch_mask_out(int64_t n, const int32_t *inv, const int32_t *off_in
 cudaError_t launch_fill_state(int64_t n, const double Uinf[4], double *U, cudaStream_t s);
 // hd[e] = (P_i - P_0)/2 for every edge e = (P_0 -> P_i)
 cudaError_t launch_half_offsets(int64_t n, const double2 *xy, const int32_t *off, const int32_t *idx, double2 *hd,
-                                cudaStream_t s);
+                                float2 *hd_f, cudaStream_t s);
 cudaError_t launch_fill_state_cases(int64_t n, const uint16_t *pcase, const double *case_uinf, double *U,
                                     cudaStream_t s);
 // stable sort of 64-bit keys into a permutation (perm[k] = input index of the k-th smallest key)

@@ -145,23 +145,26 @@ cudaError_t launch_geometry(int64_t n, const double2 *xy, const double2 *nrm, co
 }
 
 // per edge (P_i - P_0)/2 (FP64 contexts): the E14 reconstruction and correction
-// terms use it directly, two fused multiply-adds per component
+// terms use it directly, two fused multiply-adds per component; hd_f (if not
+// null) receives it rounded to FP32
 __global__ void k_half_offsets(int64_t n, const double2 *__restrict__ xy, const int32_t *__restrict__ off,
-                               const int32_t *__restrict__ idx, double2 *__restrict__ hd)
+                               const int32_t *__restrict__ idx, double2 *__restrict__ hd, float2 *__restrict__ hd_f)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const double2 P0 = xy[p];
     for (int e = off[p]; e < off[p + 1]; ++e) {
         const double2 Pi = xy[idx[e]];
-        hd[e] = make_double2(0.5 * (Pi.x - P0.x), 0.5 * (Pi.y - P0.y));
+        const double2 h = make_double2(0.5 * (Pi.x - P0.x), 0.5 * (Pi.y - P0.y));
+        hd[e] = h;
+        if (hd_f) hd_f[e] = make_float2(__double2float_rn(h.x), __double2float_rn(h.y));
     }
 }
 
 cudaError_t launch_half_offsets(int64_t n, const double2 *xy, const int32_t *off, const int32_t *idx, double2 *hd,
-                                cudaStream_t s)
+                                float2 *hd_f, cudaStream_t s)
 {
-    k_half_offsets<<<nblk(n, 128), 128, 0, s>>>(n, xy, off, idx, hd);
+    k_half_offsets<<<nblk(n, 128), 128, 0, s>>>(n, xy, off, idx, hd, hd_f);
     return cudaGetLastError();
 }
 
