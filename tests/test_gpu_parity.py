@@ -121,6 +121,33 @@ def test_q_derivatives_match_oracle(small, inner, limiter):
     assert np.all(np.abs(qy - oy) <= 1e-12 * S)
 
 
+@pytest.mark.parametrize("limiter", [1.0, 0.05])
+def test_limited_q_derivatives_on_a_jump_and_a_constant_region(small, limiter):
+    """A state with a jump (density x3, energy x5 upstream of x = 0.3) and
+    the exact free stream elsewhere. Near the jump the gradients are large
+    and the limiter acts; away from it every q_i - q_0 is exactly zero, so
+    the largest shift d_m is 0 and the FP32 screen of d_m keeps every edge
+    (its absolute margin). Both must match the oracle, the constant region
+    exactly."""
+    c = small
+    U = oracle.freestream_state(c["n"], 0.85, 1.0).copy()
+    jump = c["x"] < 0.3
+    U[:3, jump] *= 3.0
+    U[3, jump] *= 5.0
+    U = np.ascontiguousarray(U)
+    s = _solver(c, order=2, inner_iters=3, limiter_K=limiter)
+    qx, qy = s.q_derivatives(_dev(U))
+    qx, qy = qx.cpu().numpy(), qy.cpu().numpy()
+    q = oracle.q_variables(U)
+    ox, oy = oracle.q_derivatives(c, q, inner=3)
+    S = _grad_scale(c, q, ox, oy)
+    lx, ly = oracle.limit_gradients(c, q, ox, oy, limiter)
+    assert np.mean(np.abs(lx) < np.abs(ox)) > 0.001            # the limiter acts at the jump
+    assert np.any(np.all(S == 0.0, axis=0))                    # and some stencils see no variation
+    assert np.all(np.abs(qx - lx) <= 1e-12 * S)
+    assert np.all(np.abs(qy - ly) <= 1e-12 * S)
+
+
 @pytest.mark.parametrize("order,limiter", [(1, 0.0), (2, 0.0), (2, 1.0)])
 @pytest.mark.parametrize("reorder", [0, 1, 2])
 def test_residual_matches_oracle(small, order, limiter, reorder):
